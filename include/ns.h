@@ -1,0 +1,173 @@
+/*
+ * ns.h -- C ABI of the network-sensing traffic-matrix library (CUDA, sm_103a).
+ *
+ * The library turns a stream of anonymized (src, dst) 32-bit address pairs
+ * into the hypersparse 2^32 x 2^32 traffic matrix A, where A(i,j) is the
+ * number of packets from source i to destination j, and computes the
+ * network quantities the paper lists in Table 2 (section "Implementation",
+ * paragraph "Graph Analytics"; the reverse quantities follow by exchanging
+ * src and dst, Table 2 caption).  The paper's graph is one dataframe with the
+ * columns src, dst and n_packets (same paragraph); here the columns are two
+ * uint32 arrays in, and A's nonzero list (uint64 key = src << 32 | dst,
+ * uint64 count) out.  Windows of packets are summed: A = sum_t A_t.
+ *
+ * Conventions that hold for every call:
+ *  - Pointers named d_* are CUDA device pointers (device memory, or managed
+ *    or mapped memory the device can address); h_* are host pointers.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    enqueued on it; only calls documented as blocking synchronize it.
+ *  - The caller owns the input buffers and must keep them valid and
+ *    unmodified until the stream work completes.  The library owns matrices
+ *    and all scratch memory it allocates.
+ *  - n == 0 is legal everywhere and gives an empty matrix / zero statistics.
+ *    Null pointers with n > 0, unknown enum values and mismatched devices
+ *    return NS_ERR_INVALID.  No call aborts, traps or hangs: device-side
+ *    bounded waits and probes record an error word that the next blocking
+ *    call (ns_network_stats, ns_matrix_nnz, ns_matrix_export, ns_sync)
+ *    returns as NS_ERR_CAPACITY or NS_ERR_TIMEOUT.
+ *  - ns_last_error() returns a thread-local message for the last non-OK
+ *    status on the calling thread.
+ *  - A context and its matrices are not thread-safe; use one per host thread
+ *    (the serving calls ns_stream_* are the exception and are thread-safe).
+ */
+#ifndef NS_H
+#define NS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ns_stream_t; /* identical to cudaStream_t */
+typedef struct ns_ctx ns_ctx;
+typedef struct ns_matrix ns_matrix;
+
+typedef enum {
+    NS_OK = 0,
+    NS_ERR_INVALID = 1,  /* bad argument */
+    NS_ERR_OOM = 2,      /* device allocation failed (or admission budget) */
+    NS_ERR_CAPACITY = 3, /* a hash probe exceeded its bound */
+    NS_ERR_CUDA = 4,     /* a CUDA runtime call failed */
+    NS_ERR_TIMEOUT = 5,  /* a device-side wait gave up, or a host wait timed out */
+    NS_ERR_BUSY = 6,     /* serving queue full: retry later */
+    NS_ERR_STATE = 7     /* call not valid in the object's current state */
+} ns_status;
+
+/* The nine quantities of Table 2 (matrix notation), all exact uint64:
+ *   valid_packets       1^T A 1            (row 1)
+ *   unique_links        1^T |A|_0 1        (row 2)
+ *   unique_sources      1^T |A 1|_0        (row 5)
+ *   unique_destinations 1^T |1^T A|_0      (row 5 reversed)
+ *   max_src_packets     max(A 1)           (row 7)
+ *   max_src_fanout      max(|A|_0 1)       (row 9)
+ *   max_dst_packets     max(1^T A)         (row 7 reversed)
+ *   max_dst_fanin       max(1^T |A|_0)     (row 9 reversed)
+ *   max_link_packets    max(A)             (row 4)
+ * A maximum over an empty matrix is 0. */
+typedef struct {
+    uint64_t valid_packets;
+    uint64_t unique_links;
+    uint64_t unique_sources;
+    uint64_t unique_destinations;
+    uint64_t max_src_packets;
+    uint64_t max_src_fanout;
+    uint64_t max_dst_packets;
+    uint64_t max_dst_fanin;
+    uint64_t max_link_packets;
+} ns_stats;
+
+/* Aggregation path.  Both give bit-identical results. */
+enum {
+    NS_PATH_AUTO = 0, /* the tuner's choice (hash unless a cache says sort) */
+    NS_PATH_SORT = 1, /* LSD radix sort of packed keys + run-length encode */
+    NS_PATH_HASH = 2  /* open-addressing hash table with atomic counts */
+};
+
+typedef struct {
+    int path;                  /* NS_PATH_* used by ns_window_build */
+    uint64_t hbm_budget_bytes; /* serving admission budget; 0 = 64 GiB */
+    int max_slots;             /* serving: windows in flight at once; 0 = 8 */
+    const char* tuner_cache;   /* autotuner cache file (JSON); NULL = none */
+} ns_config;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device` (which becomes current on the
+ * calling thread).  cfg may be NULL for defaults.  *ctx is owned by the
+ * caller and released with ns_destroy. */
+ns_status ns_create(ns_ctx** ctx, const ns_config* cfg, int device);
+
+/* Waits for the context's own work, frees everything it owns (matrices
+ * created from it must be freed first). */
+void ns_destroy(ns_ctx* ctx);
+
+/* Blocks until all work the context enqueued on `stream` is done, then
+ * returns any device-side error recorded since the last blocking call. */
+ns_status ns_sync(ns_ctx* ctx, ns_stream_t stream);
+
+/* ---- matrices ---------------------------------------------------------- */
+
+/* Creates an empty matrix owned by the library (no device memory yet). */
+ns_status ns_matrix_create(ns_ctx* ctx, ns_matrix** out);
+
+/* Pre-sizes a matrix for at least `max_links` nonzeros (and as many sources
+ * and destinations) so later builds and accumulations never reallocate.
+ * Optional: tables also grow on demand.  Enqueued on `stream`. */
+ns_status ns_matrix_reserve(ns_matrix* m, uint64_t max_links, ns_stream_t stream);
+
+/* Makes the matrix empty (A = 0) keeping its memory.  Enqueued on stream. */
+ns_status ns_matrix_clear(ns_matrix* m, ns_stream_t stream);
+
+/* Frees the matrix after its pending work completes. */
+void ns_matrix_free(ns_matrix* m);
+
+/* Number of nonzeros of A (unique links).  Blocking. */
+ns_status ns_matrix_nnz(const ns_matrix* m, uint64_t* h_nnz, ns_stream_t stream);
+
+/* Writes A's nonzero list ascending by key = src << 32 | dst into
+ * d_keys[0..nnz) and d_counts[0..nnz) (device uint64 arrays of `cap`
+ * entries each) and its length to *h_nnz.  Returns NS_ERR_CAPACITY (and
+ * writes nothing) if cap < nnz.  Blocking (it must read nnz). */
+ns_status ns_matrix_export(const ns_matrix* m, uint64_t* d_keys, uint64_t* d_counts,
+                           uint64_t cap, uint64_t* h_nnz, ns_stream_t stream);
+
+/* ---- the hot path (paper, Table 2) -------------------------------------- */
+
+/* out := A_t, the traffic matrix of one window of n packets given as two
+ * uint32 columns d_src[0..n), d_dst[0..n) (Table 2 row 3: link packets from
+ * i to j).  Any previous content of `out` is discarded.  Uses the context's
+ * path (sort or hash).  Asynchronous. */
+ns_status ns_window_build(ns_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
+                          ns_matrix* out, ns_stream_t stream);
+
+/* acc := acc + add (A = sum_t A_t; equal keys add their counts).  `add` is
+ * unchanged and may be rebuilt as soon as the stream work completes.
+ * acc and add must be distinct.  Asynchronous. */
+ns_status ns_accumulate(ns_ctx* ctx, ns_matrix* acc, const ns_matrix* add, ns_stream_t stream);
+
+/* acc := acc + A_t(d_src, d_dst): ns_window_build followed by ns_accumulate
+ * fused into one pass, without materializing A_t.  Asynchronous. */
+ns_status ns_window_ingest(ns_ctx* ctx, ns_matrix* acc, const uint32_t* d_src,
+                           const uint32_t* d_dst, uint64_t n, ns_stream_t stream);
+
+/* The nine quantities of m into *h_out (host memory).  Blocking: waits for
+ * the stream, then reports any device-side error of the matrix. */
+ns_status ns_network_stats(ns_ctx* ctx, const ns_matrix* m, ns_stats* h_out, ns_stream_t stream);
+
+/* Same quantities written to d_out (device memory, or mapped pinned host
+ * memory) when the stream reaches this point; does not block.  Device-side
+ * errors surface on the next blocking call. */
+ns_status ns_network_stats_async(ns_ctx* ctx, const ns_matrix* m, ns_stats* d_out,
+                                 ns_stream_t stream);
+
+/* ---- errors ------------------------------------------------------------ */
+
+const char* ns_last_error(void);
+const char* ns_status_string(ns_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NS_H */

@@ -1,0 +1,163 @@
+"""B300-native traffic-matrix engine for the network-sensing graph challenge.
+
+Python binding of the C ABI in include/ns.h, with the same names.  Every step
+of the path runs in the CUDA library (libns.so, built for sm_103a); this
+module only marshals arguments: torch tensors supply device pointers and
+torch streams supply cudaStream_t handles.  If the library is missing or
+cannot be loaded, every call raises -- there is no CPU fallback.
+
+Quantities (the paper's Table 2, matrix notation) come back as a dict with
+the keys in ``FIELDS``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from ._native import FIELDS, NsConfig, NsError, NsStats, check, load
+
+__all__ = [
+    "FIELDS", "NsError", "Context", "Matrix", "window_build", "accumulate", "window_ingest",
+    "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
+    "matrix_clear", "sync", "PATHS",
+]
+
+PATHS = {"auto": 0, "sort": 1, "hash": 2}
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _column(t: torch.Tensor, name: str) -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.element_size() != 4 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous 32-bit tensor (uint32/int32)")
+    if t.numel() and not t.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device")
+    return ctypes.c_void_p(t.data_ptr() if t.numel() else 0)
+
+
+class Context:
+    """A library context on one CUDA device (ns_create / ns_destroy)."""
+
+    def __init__(self, device: int = 0, path: str = "hash", hbm_budget_bytes: int = 0,
+                 max_slots: int = 0, tuner_cache: str | None = None):
+        self._L = load()
+        cfg = NsConfig(PATHS[path], hbm_budget_bytes, max_slots,
+                       tuner_cache.encode() if tuner_cache else None)
+        h = ctypes.c_void_p()
+        check(self._L.ns_create(ctypes.byref(h), ctypes.byref(cfg), device), "ns_create")
+        self.handle = h
+        self.device = device
+        self.path = path
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._L.ns_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Matrix:
+    """A library-owned traffic matrix (ns_matrix_create / ns_matrix_free)."""
+
+    def __init__(self, ctx: Context):
+        self._L = ctx._L
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        check(self._L.ns_matrix_create(ctx.handle, ctypes.byref(h)), "ns_matrix_create")
+        self.handle = h
+
+    def free(self):
+        if getattr(self, "handle", None):
+            self._L.ns_matrix_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def window_build(ctx: Context, src: torch.Tensor, dst: torch.Tensor, out: Matrix, stream=None):
+    """out := A_t of one window (ns_window_build)."""
+    n = src.numel()
+    if dst.numel() != n:
+        raise ValueError("src and dst differ in length")
+    check(ctx._L.ns_window_build(ctx.handle, _column(src, "src"), _column(dst, "dst"), n, out.handle,
+                                 _stream(stream)), "ns_window_build")
+
+
+def accumulate(ctx: Context, acc: Matrix, add: Matrix, stream=None):
+    """acc := acc + add (ns_accumulate)."""
+    check(ctx._L.ns_accumulate(ctx.handle, acc.handle, add.handle, _stream(stream)), "ns_accumulate")
+
+
+def window_ingest(ctx: Context, acc: Matrix, src: torch.Tensor, dst: torch.Tensor, stream=None):
+    """acc := acc + A_t(src, dst), fused (ns_window_ingest)."""
+    n = src.numel()
+    if dst.numel() != n:
+        raise ValueError("src and dst differ in length")
+    check(ctx._L.ns_window_ingest(ctx.handle, acc.handle, _column(src, "src"), _column(dst, "dst"), n,
+                                  _stream(stream)), "ns_window_ingest")
+
+
+def network_stats(ctx: Context, m: Matrix, stream=None) -> dict:
+    """The nine Table 2 quantities (ns_network_stats; blocking)."""
+    out = NsStats()
+    check(ctx._L.ns_network_stats(ctx.handle, m.handle, ctypes.byref(out), _stream(stream)),
+          "ns_network_stats")
+    return {f: int(getattr(out, f)) for f in FIELDS}
+
+
+def network_stats_async(ctx: Context, m: Matrix, out: torch.Tensor, stream=None):
+    """Writes the nine quantities into `out` (a device tensor of >= 9 64-bit
+    elements) when the stream gets there (ns_network_stats_async)."""
+    if out.element_size() != 8 or out.numel() < 9 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous 64-bit tensor with >= 9 elements")
+    check(ctx._L.ns_network_stats_async(ctx.handle, m.handle, ctypes.c_void_p(out.data_ptr()),
+                                        _stream(stream)), "ns_network_stats_async")
+
+
+def matrix_nnz(m: Matrix, stream=None) -> int:
+    v = ctypes.c_uint64()
+    check(m._L.ns_matrix_nnz(m.handle, ctypes.byref(v), _stream(stream)), "ns_matrix_nnz")
+    return int(v.value)
+
+
+def matrix_export(m: Matrix, stream=None, device=None):
+    """A's nonzeros ascending by key = src << 32 | dst, as two int64 device
+    tensors holding uint64 bit patterns (ns_matrix_export)."""
+    nnz = matrix_nnz(m, stream)
+    dev = device if device is not None else torch.device("cuda", m.ctx.device)
+    keys = torch.empty(max(nnz, 1), dtype=torch.int64, device=dev)
+    counts = torch.empty(max(nnz, 1), dtype=torch.int64, device=dev)
+    got = ctypes.c_uint64()
+    check(m._L.ns_matrix_export(m.handle, ctypes.c_void_p(keys.data_ptr()), ctypes.c_void_p(counts.data_ptr()),
+                                max(nnz, 1), ctypes.byref(got), _stream(stream)), "ns_matrix_export")
+    return keys[: got.value], counts[: got.value]
+
+
+def matrix_reserve(m: Matrix, max_links: int, stream=None):
+    check(m._L.ns_matrix_reserve(m.handle, max_links, _stream(stream)), "ns_matrix_reserve")
+
+
+def matrix_clear(m: Matrix, stream=None):
+    check(m._L.ns_matrix_clear(m.handle, _stream(stream)), "ns_matrix_clear")
+
+
+def sync(ctx: Context, stream=None):
+    check(ctx._L.ns_sync(ctx.handle, _stream(stream)), "ns_sync")

@@ -1,0 +1,84 @@
+"""ctypes declarations of the C ABI in include/ns.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+_lib = None
+
+P = ctypes.c_void_p
+U64 = ctypes.c_uint64
+I32 = ctypes.c_int
+ST = ctypes.c_int  # ns_status
+
+
+class NsConfig(ctypes.Structure):
+    _fields_ = [("path", I32), ("hbm_budget_bytes", U64), ("max_slots", I32), ("tuner_cache", ctypes.c_char_p)]
+
+
+class NsStats(ctypes.Structure):
+    _fields_ = [(f, U64) for f in (
+        "valid_packets", "unique_links", "unique_sources", "unique_destinations",
+        "max_src_packets", "max_src_fanout", "max_dst_packets", "max_dst_fanin", "max_link_packets")]
+
+
+FIELDS = tuple(f for f, _ in NsStats._fields_)
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "ns_create": (ST, [ctypes.POINTER(P), ctypes.POINTER(NsConfig), I32]),
+    "ns_destroy": (None, [P]),
+    "ns_sync": (ST, [P, P]),
+    "ns_matrix_create": (ST, [P, ctypes.POINTER(P)]),
+    "ns_matrix_reserve": (ST, [P, U64, P]),
+    "ns_matrix_clear": (ST, [P, P]),
+    "ns_matrix_free": (None, [P]),
+    "ns_matrix_nnz": (ST, [P, ctypes.POINTER(U64), P]),
+    "ns_matrix_export": (ST, [P, P, P, U64, ctypes.POINTER(U64), P]),
+    "ns_window_build": (ST, [P, P, P, U64, P, P]),
+    "ns_accumulate": (ST, [P, P, P, P]),
+    "ns_window_ingest": (ST, [P, P, P, P, U64, P]),
+    "ns_network_stats": (ST, [P, P, ctypes.POINTER(NsStats), P]),
+    "ns_network_stats_async": (ST, [P, P, P, P]),
+    "ns_last_error": (ctypes.c_char_p, []),
+    "ns_status_string": (ctypes.c_char_p, [ST]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libns.so (building it first if it is missing or stale and nvcc is
+    available).  Raises if the library cannot be loaded: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and _build.stale():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libns.so is not built; run python -m paper_2509_03653_b300.build")
+    L = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+class NsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        L = load()
+        self.status = status
+        self.name = L.ns_status_string(status).decode()
+        self.message = L.ns_last_error().decode()
+        super().__init__(f"{where}: {self.name}: {self.message}")
+
+
+def check(status: int, where: str):
+    if status != 0:
+        raise NsError(status, where)

@@ -1,0 +1,501 @@
+// ns_api.cu -- the C ABI (include/ns.h): contexts, matrices, path selection,
+// capacity planning and error reporting around the kernels.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "ns.h"
+#include "ns_api_internal.h"
+#include "ns_kernels.h"
+
+using namespace ns;
+
+namespace {
+
+thread_local std::string g_err;
+
+ns_status fail(ns_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) return fail(NS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define TRY(call)                    \
+    do {                             \
+        ns_status st_ = (call);      \
+        if (st_ != NS_OK) return st_; \
+    } while (0)
+
+u64 next_pow2(u64 x) {
+    u64 p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+namespace ns {
+
+ns_status buf_reserve(Buf& b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return NS_OK;
+    if (b.p) {
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (bytes == 0) return NS_OK;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(NS_ERR_OOM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    b.bytes = bytes;
+    return NS_OK;
+}
+
+void buf_free(Buf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+ns_status set_fail(ns_status s, const char* msg) { return fail(s, "%s", msg); }
+
+ns_status check_launch() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(NS_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return NS_OK;
+}
+
+HashView hash_view(const ns_matrix* m) {
+    HashView v;
+    v.links = (LinkSlot*)m->links.p;
+    v.link_mask = m->link_cap - 1;
+    v.rows = (NodeSlot*)m->rows.p;
+    v.row_mask = m->node_cap - 1;
+    v.cols = (NodeSlot*)m->cols.p;
+    v.col_mask = m->node_cap - 1;
+    v.stats = (DevStats*)m->stats.p;
+    return v;
+}
+
+// Allocates hash tables for at least `links` nonzeros at load <= 1/2 (rows and
+// columns sized alike, since sources, destinations <= links).  Contents are
+// undefined until cleared.
+ns_status hash_alloc(ns_matrix* m, u64 links) {
+    const u64 cap = next_pow2(std::max<u64>(2 * links, 1024));
+    if (m->link_cap >= cap && m->links.p) return NS_OK;
+    TRY(buf_reserve(m->links, (cap + 1) * sizeof(LinkSlot)));
+    TRY(buf_reserve(m->rows, cap * sizeof(NodeSlot)));
+    TRY(buf_reserve(m->cols, cap * sizeof(NodeSlot)));
+    m->link_cap = cap;
+    m->node_cap = cap;
+    return NS_OK;
+}
+
+ns_status hash_clear(ns_matrix* m, cudaStream_t s) {
+    CK(cudaMemsetAsync(m->links.p, 0, (m->link_cap + 1) * sizeof(LinkSlot), s));
+    CK(cudaMemsetAsync(m->rows.p, 0, m->node_cap * sizeof(NodeSlot), s));
+    CK(cudaMemsetAsync(m->cols.p, 0, m->node_cap * sizeof(NodeSlot), s));
+    CK(cudaMemsetAsync(m->stats.p, 0, sizeof(DevStats), s));
+    return NS_OK;
+}
+
+// Reads the matrix's statistics record (blocking) into the context's pinned
+// buffer and returns the device error word as a status.
+ns_status read_stats(const ns_matrix* m, cudaStream_t s, DevStats* out) {
+    ns_ctx* c = m->ctx;
+    CK(cudaMemcpyAsync(c->host_stats, m->stats.p, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *out = *c->host_stats;
+    if (out->err & ERR_TIMEOUT) return fail(NS_ERR_TIMEOUT, "a device-side wait gave up (look-back)");
+    if (out->err & ERR_CAPACITY) return fail(NS_ERR_CAPACITY, "a hash probe sequence exceeded its bound");
+    return NS_OK;
+}
+
+// Makes room in a hash-format accumulator for `extra` more nonzeros.  Uses
+// the host-side bound first; only when that is exhausted does it read the
+// true count and, if needed, rehash into larger tables.
+ns_status hash_grow(ns_matrix* m, u64 extra, cudaStream_t s) {
+    const u64 limit = m->link_cap / 2;
+    if (m->bound + extra <= limit) return NS_OK;
+    DevStats ds;
+    TRY(read_stats(m, s, &ds));
+    const u64 actual = ds.v[S_LINKS];
+    m->bound = actual;
+    if (actual + extra <= limit) return NS_OK;
+    // rehash: rebuild rows/cols/statistics from the link entries
+    ns_matrix tmp;
+    tmp.ctx = m->ctx;
+    tmp.stats = m->stats;
+    TRY(hash_alloc(&tmp, actual + extra));
+    CK(cudaMemsetAsync(tmp.links.p, 0, (tmp.link_cap + 1) * sizeof(LinkSlot), s));
+    CK(cudaMemsetAsync(tmp.rows.p, 0, tmp.node_cap * sizeof(NodeSlot), s));
+    CK(cudaMemsetAsync(tmp.cols.p, 0, tmp.node_cap * sizeof(NodeSlot), s));
+    CK(cudaMemsetAsync(m->stats.p, 0, sizeof(DevStats), s));
+    launch_insert_slots((const LinkSlot*)m->links.p, m->link_cap, hash_view(&tmp), m->ctx->sms, s);
+    TRY(check_launch());
+    CK(cudaStreamSynchronize(s));
+    buf_free(m->links);
+    buf_free(m->rows);
+    buf_free(m->cols);
+    m->links = tmp.links;
+    m->rows = tmp.rows;
+    m->cols = tmp.cols;
+    m->link_cap = tmp.link_cap;
+    m->node_cap = tmp.node_cap;
+    tmp.links = tmp.rows = tmp.cols = Buf{};
+    tmp.stats = Buf{};
+    return NS_OK;
+}
+
+// Turns an accumulator into hash format (empty, or from its sorted list).
+ns_status to_hash(ns_matrix* m, u64 extra, cudaStream_t s) {
+    if (m->fmt == FMT_HASH) return hash_grow(m, extra, s);
+    ns_ctx* c = m->ctx;
+    const u64 have = (m->fmt == FMT_LIST) ? m->bound : 0;
+    TRY(hash_alloc(m, have + extra));
+    if (m->fmt == FMT_LIST && have > 0) {
+        // the list length lives in the statistics record, which is rebuilt:
+        // keep a copy for the insert kernel
+        TRY(buf_reserve(c->counters, 16 * sizeof(u64)));
+        u64* nnz_copy = (u64*)c->counters.p + 15;
+        CK(cudaMemcpyAsync(nnz_copy, &((DevStats*)m->stats.p)->v[S_LINKS], sizeof(u64),
+                           cudaMemcpyDeviceToDevice, s));
+        TRY(hash_clear(m, s));
+        launch_insert_list((const u64*)m->keys.p, (const u64*)m->counts.p, have, nnz_copy,
+                           hash_view(m), c->sms, s);
+        TRY(check_launch());
+    } else {
+        TRY(hash_clear(m, s));
+        m->bound = 0;
+    }
+    m->fmt = FMT_HASH;
+    return NS_OK;
+}
+
+ns_status sort_scratch(ns_ctx* c, u64 n) {
+    const u64 tiles = sort_tiles(std::max<u64>(n, 1));
+    const u64 words = tiles * (u64)sort_radix();
+    if (c->status.bytes < words * sizeof(u64)) {
+        TRY(buf_reserve(c->status, words * sizeof(u64)));
+        CK(cudaMemset(c->status.p, 0, words * sizeof(u64)));
+        c->sc.tag = 0;
+    }
+    c->sc.status = (u64*)c->status.p;
+    c->sc.status_words = c->status.bytes / sizeof(u64);
+    return NS_OK;
+}
+
+// Sort path: A_t's sorted nonzero list and its statistics.
+ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n, ns_matrix* out,
+                     cudaStream_t s) {
+    out->fmt = FMT_LIST;
+    out->bound = n;
+    CK(cudaMemsetAsync(out->stats.p, 0, sizeof(DevStats), s));
+    if (n == 0) return NS_OK;
+    TRY(buf_reserve(out->keys, n * sizeof(u64)));
+    TRY(buf_reserve(out->counts, n * sizeof(u64)));
+    TRY(sort_scratch(c, n));
+    TRY(buf_reserve(c->k64[0], n * sizeof(u64)));
+    TRY(buf_reserve(c->k64[1], n * sizeof(u64)));
+    TRY(buf_reserve(c->pos, (n + 1) * sizeof(u64)));
+    TRY(buf_reserve(c->psum, (n + 1) * sizeof(u64)));
+    TRY(buf_reserve(c->k32[0], n * sizeof(u32)));
+    TRY(buf_reserve(c->k32[1], n * sizeof(u32)));
+    TRY(buf_reserve(c->v64[0], n * sizeof(u64)));
+    TRY(buf_reserve(c->v64[1], n * sizeof(u64)));
+    TRY(buf_reserve(c->counters, 16 * sizeof(u64)));
+    DevStats* st = (DevStats*)out->stats.p;
+    u64* nnz = &st->v[S_LINKS];
+    u64* runs_out = (u64*)c->counters.p;
+
+    // links: sort packed keys, then runs of equal keys (Table 2 row 3)
+    u64* kb[2] = {(u64*)c->k64[0].p, (u64*)c->k64[1].p};
+    const int r = radix_sort_packets(src, dst, kb, n, c->sc, st, s);
+    launch_runs(RUN_U64, false, kb[r], nullptr, n, nullptr, (u64*)out->keys.p,
+                (u64*)c->pos.p, nullptr, nnz, c->sc, st, s);
+    launch_run_stats(RS_LINKS, (const u64*)c->pos.p, nullptr, nnz, n, (u64*)out->counts.p,
+                     st, c->sms, s);
+    // rows: runs of equal src over the source-major list (rows 5-9)
+    launch_runs(RUN_SRC_OF_U64, true, out->keys.p, (const u64*)out->counts.p, n, nnz, nullptr,
+                (u64*)c->pos.p, (u64*)c->psum.p, runs_out, c->sc, st, s);
+    launch_run_stats(RS_ROWS, (const u64*)c->pos.p, (const u64*)c->psum.p, runs_out, n,
+                     nullptr, st, c->sms, s);
+    // columns: (dst, count) sorted by dst, then runs (the reverse operations)
+    u32* ck[2] = {(u32*)c->k32[0].p, (u32*)c->k32[1].p};
+    u64* cv[2] = {(u64*)c->v64[0].p, (u64*)c->v64[1].p};
+    const int r2 = radix_sort_dst_pairs((const u64*)out->keys.p, (const u64*)out->counts.p,
+                                        nnz, ck, cv, n, c->sc, st, s);
+    launch_runs(RUN_U32, true, ck[r2], cv[r2], n, nnz, nullptr, (u64*)c->pos.p,
+                (u64*)c->psum.p, runs_out + 1, c->sc, st, s);
+    launch_run_stats(RS_COLS, (const u64*)c->pos.p, (const u64*)c->psum.p, runs_out + 1, n,
+                     nullptr, st, c->sms, s);
+    return check_launch();
+}
+
+ns_status build_hash(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n, ns_matrix* out,
+                     cudaStream_t s) {
+    TRY(hash_alloc(out, n));
+    TRY(hash_clear(out, s));
+    out->fmt = FMT_HASH;
+    out->bound = n;
+    if (n == 0) return NS_OK;
+    launch_insert_packets(src, dst, n, hash_view(out), c->sms, s);
+    return check_launch();
+}
+
+}  // namespace ns
+
+// ============================================================================
+// C ABI
+// ============================================================================
+
+extern "C" {
+
+const char* ns_last_error(void) { return g_err.c_str(); }
+
+const char* ns_status_string(ns_status s) {
+    switch (s) {
+        case NS_OK: return "NS_OK";
+        case NS_ERR_INVALID: return "NS_ERR_INVALID";
+        case NS_ERR_OOM: return "NS_ERR_OOM";
+        case NS_ERR_CAPACITY: return "NS_ERR_CAPACITY";
+        case NS_ERR_CUDA: return "NS_ERR_CUDA";
+        case NS_ERR_TIMEOUT: return "NS_ERR_TIMEOUT";
+        case NS_ERR_BUSY: return "NS_ERR_BUSY";
+        case NS_ERR_STATE: return "NS_ERR_STATE";
+    }
+    return "NS_ERR_?";
+}
+
+ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
+    if (!out) return fail(NS_ERR_INVALID, "ns_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(NS_ERR_INVALID, "ns_create: no CUDA device %d", device);
+    ns_config c{};
+    if (cfg) c = *cfg;
+    if (c.path < NS_PATH_AUTO || c.path > NS_PATH_HASH)
+        return fail(NS_ERR_INVALID, "ns_create: unknown path %d", c.path);
+    CK(cudaSetDevice(device));
+    ns_ctx* x = new ns_ctx();
+    x->device = device;
+    x->cfg = c;
+    if (x->cfg.hbm_budget_bytes == 0) x->cfg.hbm_budget_bytes = 64ull << 30;
+    if (x->cfg.max_slots <= 0) x->cfg.max_slots = 8;
+    x->tuner_cache = c.tuner_cache ? c.tuner_cache : "";
+    x->cfg.tuner_cache = nullptr;
+    cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, device);
+    x->sc.sms = x->sms;
+    ns_status st = buf_reserve(x->ghist, 8 * 256 * sizeof(u32));
+    if (st == NS_OK) st = buf_reserve(x->offs, 8 * 256 * sizeof(u64));
+    if (st == NS_OK) st = buf_reserve(x->tcount, 16 * sizeof(u32));
+    if (st == NS_OK) st = buf_reserve(x->counters, 16 * sizeof(u64));
+    if (st == NS_OK && cudaMallocHost((void**)&x->host_stats, sizeof(DevStats)) != cudaSuccess)
+        st = fail(NS_ERR_OOM, "cudaMallocHost failed");
+    if (st != NS_OK) {
+        ns_destroy(x);
+        return st;
+    }
+    x->sc.ghist = (u32*)x->ghist.p;
+    x->sc.offs = (u64*)x->offs.p;
+    x->sc.tile_counters = (u32*)x->tcount.p;
+    x->sc.tag = 0;
+    x->sc.status = nullptr;
+    x->sc.status_words = 0;
+    *out = x;
+    return NS_OK;
+}
+
+void ns_destroy(ns_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    Buf* all[] = {&c->ghist, &c->offs, &c->tcount, &c->counters, &c->status, &c->k64[0], &c->k64[1],
+                  &c->pos, &c->psum, &c->k32[0], &c->k32[1], &c->v64[0], &c->v64[1], &c->xk, &c->xv};
+    for (Buf* b : all) buf_free(*b);
+    if (c->host_stats) cudaFreeHost(c->host_stats);
+    delete c;
+}
+
+ns_status ns_sync(ns_ctx* c, ns_stream_t stream) {
+    if (!c) return fail(NS_ERR_INVALID, "ns_sync: NULL context");
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return check_launch();
+}
+
+ns_status ns_matrix_create(ns_ctx* c, ns_matrix** out) {
+    if (!c || !out) return fail(NS_ERR_INVALID, "ns_matrix_create: NULL argument");
+    ns_matrix* m = new ns_matrix();
+    m->ctx = c;
+    ns_status st = buf_reserve(m->stats, sizeof(DevStats));
+    if (st == NS_OK && cudaMemset(m->stats.p, 0, sizeof(DevStats)) != cudaSuccess)
+        st = fail(NS_ERR_CUDA, "cudaMemset failed");
+    if (st != NS_OK) {
+        ns_matrix_free(m);
+        return st;
+    }
+    *out = m;
+    return NS_OK;
+}
+
+ns_status ns_matrix_reserve(ns_matrix* m, uint64_t max_links, ns_stream_t stream) {
+    if (!m) return fail(NS_ERR_INVALID, "ns_matrix_reserve: NULL matrix");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m->fmt == FMT_EMPTY) {
+        TRY(hash_alloc(m, max_links));
+        TRY(hash_clear(m, s));
+        m->fmt = FMT_HASH;
+        m->bound = 0;
+        return NS_OK;
+    }
+    if (m->fmt == FMT_HASH) return hash_grow(m, max_links > m->bound ? max_links - m->bound : 0, s);
+    return NS_OK;
+}
+
+ns_status ns_matrix_clear(ns_matrix* m, ns_stream_t stream) {
+    if (!m) return fail(NS_ERR_INVALID, "ns_matrix_clear: NULL matrix");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m->fmt == FMT_HASH) {
+        TRY(hash_clear(m, s));
+    } else {
+        CK(cudaMemsetAsync(m->stats.p, 0, sizeof(DevStats), s));
+        if (m->fmt == FMT_LIST) m->fmt = FMT_EMPTY;
+    }
+    m->bound = 0;
+    return NS_OK;
+}
+
+void ns_matrix_free(ns_matrix* m) {
+    if (!m) return;
+    cudaDeviceSynchronize();
+    buf_free(m->links);
+    buf_free(m->rows);
+    buf_free(m->cols);
+    buf_free(m->keys);
+    buf_free(m->counts);
+    buf_free(m->stats);
+    delete m;
+}
+
+ns_status ns_matrix_nnz(const ns_matrix* m, uint64_t* h_nnz, ns_stream_t stream) {
+    if (!m || !h_nnz) return fail(NS_ERR_INVALID, "ns_matrix_nnz: NULL argument");
+    DevStats ds;
+    ns_status st = read_stats(m, (cudaStream_t)stream, &ds);
+    *h_nnz = ds.v[S_LINKS];
+    return st;
+}
+
+ns_status ns_matrix_export(const ns_matrix* m, uint64_t* d_keys, uint64_t* d_counts, uint64_t cap,
+                           uint64_t* h_nnz, ns_stream_t stream) {
+    if (!m || !h_nnz) return fail(NS_ERR_INVALID, "ns_matrix_export: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevStats ds;
+    TRY(read_stats(m, s, &ds));
+    const u64 nnz = ds.v[S_LINKS];
+    *h_nnz = nnz;
+    if (nnz == 0) return NS_OK;
+    if (!d_keys || !d_counts) return fail(NS_ERR_INVALID, "ns_matrix_export: NULL output with nnz > 0");
+    if (cap < nnz) return fail(NS_ERR_CAPACITY, "ns_matrix_export: cap %llu < nnz %llu",
+                               (unsigned long long)cap, (unsigned long long)nnz);
+    ns_ctx* c = m->ctx;
+    if (m->fmt == FMT_LIST) {
+        CK(cudaMemcpyAsync(d_keys, m->keys.p, nnz * sizeof(u64), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(d_counts, m->counts.p, nnz * sizeof(u64), cudaMemcpyDeviceToDevice, s));
+    } else {
+        TRY(sort_scratch(c, nnz));
+        TRY(buf_reserve(c->xk, nnz * sizeof(u64)));
+        TRY(buf_reserve(c->xv, nnz * sizeof(u64)));
+        TRY(buf_reserve(c->k64[0], nnz * sizeof(u64)));
+        TRY(buf_reserve(c->v64[0], nnz * sizeof(u64)));
+        TRY(buf_reserve(c->counters, 16 * sizeof(u64)));
+        u64* cnt = (u64*)c->counters.p + 2;
+        CK(cudaMemsetAsync(cnt, 0, sizeof(u64), s));
+        DevStats* st = (DevStats*)m->stats.p;
+        launch_compact_links((const LinkSlot*)m->links.p, m->link_cap, (u64*)c->xk.p,
+                             (u64*)c->xv.p, cnt, nnz, st, c->sms, s);
+        u64* kb[2] = {(u64*)c->k64[0].p, (u64*)d_keys};
+        u64* vb[2] = {(u64*)c->v64[0].p, (u64*)d_counts};
+        const int r = radix_sort_pairs64((const u64*)c->xk.p, (const u64*)c->xv.p, cnt, kb, vb,
+                                         nnz, c->sc, st, s);
+        if (r != 1) return fail(NS_ERR_STATE, "export: unexpected sort parity");
+        TRY(check_launch());
+    }
+    DevStats after;
+    return read_stats(m, s, &after);
+}
+
+ns_status ns_window_build(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
+                          ns_matrix* out, ns_stream_t stream) {
+    if (!c || !out) return fail(NS_ERR_INVALID, "ns_window_build: NULL context or matrix");
+    if (n > 0 && (!d_src || !d_dst)) return fail(NS_ERR_INVALID, "ns_window_build: NULL input with n > 0");
+    if (n >= (1ull << 40)) return fail(NS_ERR_INVALID, "ns_window_build: n too large");
+    if (out->ctx != c) return fail(NS_ERR_INVALID, "ns_window_build: matrix belongs to another context");
+    const int path = c->cfg.path == NS_PATH_SORT ? NS_PATH_SORT : NS_PATH_HASH;
+    if (path == NS_PATH_SORT) return build_sort(c, d_src, d_dst, n, out, (cudaStream_t)stream);
+    return build_hash(c, d_src, d_dst, n, out, (cudaStream_t)stream);
+}
+
+ns_status ns_accumulate(ns_ctx* c, ns_matrix* acc, const ns_matrix* add, ns_stream_t stream) {
+    if (!c || !acc || !add) return fail(NS_ERR_INVALID, "ns_accumulate: NULL argument");
+    if (acc == add) return fail(NS_ERR_INVALID, "ns_accumulate: acc and add must be distinct");
+    if (acc->ctx != c || add->ctx != c) return fail(NS_ERR_INVALID, "ns_accumulate: foreign matrix");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (add->fmt == FMT_EMPTY || add->bound == 0) {
+        if (acc->fmt == FMT_EMPTY) return NS_OK;
+    }
+    TRY(to_hash(acc, add->bound, s));
+    if (add->fmt == FMT_HASH) {
+        launch_insert_slots((const LinkSlot*)add->links.p, add->link_cap, hash_view(acc), c->sms, s);
+    } else if (add->fmt == FMT_LIST && add->bound > 0) {
+        launch_insert_list((const u64*)add->keys.p, (const u64*)add->counts.p, add->bound,
+                           &((const DevStats*)add->stats.p)->v[S_LINKS], hash_view(acc), c->sms, s);
+    }
+    acc->bound += add->bound;
+    return check_launch();
+}
+
+ns_status ns_window_ingest(ns_ctx* c, ns_matrix* acc, const uint32_t* d_src, const uint32_t* d_dst,
+                           uint64_t n, ns_stream_t stream) {
+    if (!c || !acc) return fail(NS_ERR_INVALID, "ns_window_ingest: NULL argument");
+    if (n > 0 && (!d_src || !d_dst)) return fail(NS_ERR_INVALID, "ns_window_ingest: NULL input with n > 0");
+    if (acc->ctx != c) return fail(NS_ERR_INVALID, "ns_window_ingest: foreign matrix");
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(to_hash(acc, n, s));
+    if (n == 0) return NS_OK;
+    launch_insert_packets(d_src, d_dst, n, hash_view(acc), c->sms, s);
+    acc->bound += n;
+    return check_launch();
+}
+
+ns_status ns_network_stats(ns_ctx* c, const ns_matrix* m, ns_stats* h_out, ns_stream_t stream) {
+    if (!c || !m || !h_out) return fail(NS_ERR_INVALID, "ns_network_stats: NULL argument");
+    DevStats ds;
+    ns_status st = read_stats(m, (cudaStream_t)stream, &ds);
+    static_assert(sizeof(ns_stats) == S_NFIELDS * sizeof(uint64_t), "ns_stats layout");
+    memcpy(h_out, ds.v, sizeof(ns_stats));
+    return st;
+}
+
+ns_status ns_network_stats_async(ns_ctx* c, const ns_matrix* m, ns_stats* d_out, ns_stream_t stream) {
+    if (!c || !m || !d_out) return fail(NS_ERR_INVALID, "ns_network_stats_async: NULL argument");
+    launch_stats_out((const DevStats*)m->stats.p, (u64*)d_out, (cudaStream_t)stream);
+    return check_launch();
+}
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+// ns_kernels.h -- host-side launchers of the library's kernels (internal).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ns_common.cuh"
+
+namespace ns {
+
+// key loading modes of the radix sort
+enum { LOAD_KEYS = 0, LOAD_PACK = 1, LOAD_DST_OF = 2 };
+// run-key modes
+enum { RUN_U64 = 0, RUN_SRC_OF_U64 = 1, RUN_U32 = 2 };
+// run-statistics modes
+enum { RS_LINKS = 0, RS_ROWS = 1, RS_COLS = 2 };
+
+// Input of a sort pass.  n_dev, when set, holds the true element count on the
+// device (the host passes an upper bound): kernels read it, so a stage can
+// consume a count produced by the previous stage without a host round trip.
+struct SortIn {
+    const void* keys;
+    const u64* vals;
+    const u32* src;
+    const u32* dst;
+    const u64* n_dev;
+};
+
+// Per-context scratch of the sort path.
+struct SortScratch {
+    u32* ghist;          // [8][256] digit histograms
+    u64* offs;           // [8][256] bucket starts
+    u64* status;         // look-back status words
+    u64 status_words;
+    u32* tile_counters;  // [16]
+    u32 tag;             // last look-back tag issued
+    int sms;
+};
+
+// Look-back tags are 16 bits; when they wrap, the status words are cleared
+// on the stream so no stale word can carry a live tag.
+inline u32 next_tag(SortScratch& sc, cudaStream_t s) {
+    if (sc.tag >= 0xFFFFu) {
+        cudaMemsetAsync(sc.status, 0, sc.status_words * sizeof(u64), s);
+        sc.tag = 0;
+    }
+    return ++sc.tag;
+}
+
+u64 sort_tiles(u64 n);
+int sort_radix();
+
+// hash path (ns_hash.cu)
+void launch_insert_packets(const u32* src, const u32* dst, u64 n, const HashView& M,
+                           int sms, cudaStream_t s);
+void launch_insert_slots(const LinkSlot* in, u64 in_cap, const HashView& M, int sms,
+                         cudaStream_t s);
+void launch_insert_list(const u64* keys, const u64* counts, u64 n_bound,
+                        const u64* n_dev, const HashView& M, int sms, cudaStream_t s);
+void launch_compact_links(const LinkSlot* in, u64 cap, u64* out_keys, u64* out_counts,
+                          u64* out_n, u64 out_cap, DevStats* st, int sms, cudaStream_t s);
+void launch_stats_out(const DevStats* st, u64* out, cudaStream_t s);
+
+// sort path (ns_sort.cu).  Each radix sort returns the index of kbuf/vbuf
+// holding the result.  n is an upper bound when n_dev is given.
+int radix_sort_packets(const u32* src, const u32* dst, u64* kbuf[2], u64 n,
+                       SortScratch& sc, DevStats* st, cudaStream_t s);
+int radix_sort_pairs64(const u64* keys, const u64* vals, const u64* n_dev,
+                       u64* kbuf[2], u64* vbuf[2], u64 n, SortScratch& sc,
+                       DevStats* st, cudaStream_t s);
+int radix_sort_dst_pairs(const u64* link_keys, const u64* counts, const u64* n_dev,
+                         u32* kbuf[2], u64* vbuf[2], u64 n, SortScratch& sc,
+                         DevStats* st, cudaStream_t s);
+void launch_runs(int keymode, bool has_v, const void* keys, const u64* vals, u64 n,
+                 const u64* n_dev, u64* head_keys, u64* pos, u64* psum,
+                 u64* R_out, SortScratch& sc, DevStats* st, cudaStream_t s);
+void launch_run_stats(int mode, const u64* pos, const u64* psum, const u64* R_ptr,
+                      u64 bound, u64* counts_out, DevStats* st, int sms, cudaStream_t s);
+
+}  // namespace ns

@@ -1,0 +1,588 @@
+// ns_sort.cu -- sort-path kernels.
+//
+//  * LSD radix sort, 8-bit digits, "onesweep" structure: one histogram pass
+//    computes every digit's global bucket offsets up front, then each digit
+//    pass is a single kernel in which a CTA takes the next tile from an atomic
+//    counter, ranks its keys stably in shared memory, obtains its global
+//    per-digit offsets by decoupled look-back over its predecessors' published
+//    counts, and scatters.  Tile ids are handed out in launch order, so every
+//    predecessor a tile waits on is already resident; each wait is bounded
+//    and records ERR_TIMEOUT instead of spinning forever.
+//  * Run kernels: over a sorted sequence, emit each run's first position, its
+//    key and the exclusive prefix sum of a value column at that position;
+//    run lengths and run sums are then differences of neighbours.  This one
+//    primitive yields A's nonzeros (runs of equal keys, Table 2 row 3), the
+//    row aggregates (runs of equal src: A1 and |A|_0 1, rows 6 and 8) and the
+//    column aggregates (runs of equal dst after a sort by dst).
+//
+// Status words for look-back: tag(16) | flag(2) | value(46).  The tag is a
+// per-launch number, so a status array never needs clearing between launches.
+#include <algorithm>
+
+#include "ns_common.cuh"
+#include "ns_kernels.h"
+
+namespace ns {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;  // 4096
+constexpr int kRadix = 256;
+
+constexpr u64 kFlagAgg = 1, kFlagPrefix = 2;
+constexpr u64 kValMask = (1ull << 46) - 1;
+
+__device__ __forceinline__ u64 pack_status(u32 tag, u64 flag, u64 v) {
+    return ((u64)tag << 48) | (flag << 46) | (v & kValMask);
+}
+
+// Exclusive prefix for `tile` of one counter whose per-tile status words are
+// status[k * stride] (k = tile index).  Returns 0 for tile 0.
+__device__ u64 lookback(u64* status, u64 stride, u64 tile, u32 tag, DevStats* st) {
+    u64 prefix = 0;
+    long long k = (long long)tile - 1;
+    u32 spins = 0;
+    while (k >= 0) {
+        const u64 s = ld_volatile(&status[(u64)k * stride]);
+        const u32 stag = (u32)(s >> 48);
+        const u64 flag = (s >> 46) & 3;
+        if (stag == tag && flag != 0) {
+            prefix += s & kValMask;
+            if (flag == kFlagPrefix) break;
+            --k;
+            spins = 0;
+        } else {
+            if (++spins > kMaxSpin) {
+                set_error(st, ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(20);
+        }
+    }
+    return prefix;
+}
+
+// exclusive scan of one u32 per thread over a 256-thread block
+__device__ __forceinline__ u32 block_excl_scan(u32 v, u32* wsum, u32* total) {
+    const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    u32 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        u32 y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (u32)o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u32 run = 0;
+        for (int i = 0; i < kWarps; ++i) {
+            u32 t = wsum[i];
+            wsum[i] = run;
+            run += t;
+        }
+        *total = run;
+    }
+    __syncthreads();
+    return wsum[w] + x - v;
+}
+
+__device__ __forceinline__ u64 block_excl_scan64(u64 v, u64* wsum, u64* total) {
+    const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    u64 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        u64 y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (u32)o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u64 run = 0;
+        for (int i = 0; i < kWarps; ++i) {
+            u64 t = wsum[i];
+            wsum[i] = run;
+            run += t;
+        }
+        *total = run;
+    }
+    __syncthreads();
+    return wsum[w] + x - v;
+}
+
+// ---- key loading ---------------------------------------------------------
+
+template <typename K, int LOAD>
+__device__ __forceinline__ K load_key(const SortIn& in, u64 i) {
+    if constexpr (LOAD == LOAD_PACK) {
+        return (K)(((u64)__ldg(in.src + i) << 32) | (u64)__ldg(in.dst + i));
+    } else if constexpr (LOAD == LOAD_DST_OF) {
+        return (K)(u32)(reinterpret_cast<const u64*>(in.keys)[i]);
+    } else {
+        return reinterpret_cast<const K*>(in.keys)[i];
+    }
+}
+
+// ---- histogram of every digit pass ------------------------------------------
+
+template <typename K, int LOAD>
+__global__ void __launch_bounds__(kThreads) k_sort_hist(SortIn in, u64 n_arg, int begin_bit, int passes,
+                                                         u32* __restrict__ ghist) {
+    __shared__ u32 h[8][kRadix];
+    const u64 n = in.n_dev ? *in.n_dev : n_arg;
+    for (int i = threadIdx.x; i < 8 * kRadix; i += kThreads) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const u64 stride = (u64)gridDim.x * kThreads;
+    for (u64 i = (u64)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
+        const K k = load_key<K, LOAD>(in, i);
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(u32)(k >> (begin_bit + 8 * p)) & 0xFF], 1u);
+    }
+    __syncthreads();
+    for (int p = 0; p < passes; ++p) {
+        const u32 c = h[p][threadIdx.x];
+        if (c) atomicAdd(&ghist[p * kRadix + threadIdx.x], c);
+    }
+}
+
+// bucket starts: offs[p][d] = sum of ghist[p][0..d)
+__global__ void __launch_bounds__(kThreads) k_sort_offsets(const u32* __restrict__ ghist, int passes,
+                                                            u64* __restrict__ offs) {
+    __shared__ u64 wsum[kWarps];
+    __shared__ u64 tot;
+    for (int p = 0; p < passes; ++p) {
+        const u64 v = ghist[p * kRadix + threadIdx.x];
+        const u64 e = block_excl_scan64(v, wsum, &tot);
+        offs[p * kRadix + threadIdx.x] = e;
+        __syncthreads();
+    }
+}
+
+// ---- one digit pass -----------------------------------------------------------
+
+template <typename K, bool HAS_V>
+struct ScatterSmem {
+    K keys[kTile];
+    u64 vals[HAS_V ? kTile : 1];
+    u32 whist[kWarps][kRadix];
+    u32 lstart[kRadix];
+    u64 gbase[kRadix];
+    u32 wsum[kWarps];
+    u32 total;
+    u32 tile;
+};
+
+template <typename K, bool HAS_V, int LOAD>
+__global__ void __launch_bounds__(kThreads) k_onesweep(SortIn in, K* __restrict__ kout,
+                                                        u64* __restrict__ vout, u64 n_arg, int shift,
+                                                        const u64* __restrict__ offs,
+                                                        u64* __restrict__ status, u32* tile_counter,
+                                                        u32 tag, DevStats* st) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ScatterSmem<K, HAS_V>& sm = *reinterpret_cast<ScatterSmem<K, HAS_V>*>(smem_raw);
+    const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const u32 FULL = 0xFFFFFFFFu;
+
+    const u64 n = in.n_dev ? *in.n_dev : n_arg;
+    if (threadIdx.x == 0) sm.tile = atomicAdd(tile_counter, 1u);
+    for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&sm.whist[0][0])[i] = 0;
+    __syncthreads();
+    const u64 tile = sm.tile;
+    const u64 base = tile * kTile;
+    if (base >= n) return;  // launched for an upper bound; nothing to publish
+
+    // warp-striped load: warp w owns items [base + w*kItems*32, +kItems*32)
+    K k[kItems];
+    u64 v[kItems];
+    u32 rank[kItems];
+    const u64 wbase = base + (u64)w * kItems * 32;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const u64 i = wbase + (u64)j * 32 + lane;
+        if (i < n) {
+            k[j] = load_key<K, LOAD>(in, i);
+            if constexpr (HAS_V) v[j] = in.vals[i];
+        } else {
+            k[j] = 0;
+            if constexpr (HAS_V) v[j] = 0;
+        }
+    }
+    // stable rank within the warp, item by item
+    const u32 lt = lanemask_lt();
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const u64 i = wbase + (u64)j * 32 + lane;
+        const bool valid = i < n;
+        const u32 d = valid ? ((u32)(k[j] >> shift) & 0xFF) : 0x100u;
+        const u32 peers = __match_any_sync(FULL, d);
+        u32 before = 0;
+        if (valid) before = sm.whist[w][d];
+        __syncwarp();
+        if (valid) {
+            rank[j] = before + __popc(peers & lt);
+            if ((peers & lt) == 0) sm.whist[w][d] = before + __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // per digit (thread = digit): exclusive over warps, tile count
+    const u32 d = threadIdx.x;
+    u32 run = 0;
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) {
+        const u32 c = sm.whist[ww][d];
+        sm.whist[ww][d] = run;
+        run += c;
+    }
+    // publish this tile's count early so successors can proceed
+    st_volatile(&status[tile * kRadix + d], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, run));
+    const u32 ls = block_excl_scan(run, sm.wsum, &sm.total);
+    sm.lstart[d] = ls;
+    u64 prefix = 0;
+    if (tile > 0) {
+        prefix = lookback(status + d, kRadix, tile, tag, st);
+        st_volatile(&status[tile * kRadix + d], pack_status(tag, kFlagPrefix, prefix + run));
+    }
+    sm.gbase[d] = offs[d] + prefix;
+    __syncthreads();
+
+    // place keys in tile-local sorted order
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const u64 i = wbase + (u64)j * 32 + lane;
+        if (i < n) {
+            const u32 dj = (u32)(k[j] >> shift) & 0xFF;
+            const u32 pos = sm.lstart[dj] + sm.whist[w][dj] + rank[j];
+            if (pos < (u32)kTile) {
+                sm.keys[pos] = k[j];
+                if constexpr (HAS_V) sm.vals[pos] = v[j];
+            }
+        }
+    }
+    __syncthreads();
+
+    // write out: consecutive smem positions of one digit go to consecutive
+    // global positions
+    const u64 tile_n = (n - base) < (u64)kTile ? (n - base) : (u64)kTile;
+    for (u32 i = threadIdx.x; i < tile_n; i += kThreads) {
+        const K key = sm.keys[i];
+        const u32 dk = (u32)(key >> shift) & 0xFF;
+        const u64 dst = sm.gbase[dk] + (i - sm.lstart[dk]);
+        if (dst < n) {  // always true unless a look-back gave up
+            kout[dst] = key;
+            if constexpr (HAS_V) vout[dst] = sm.vals[i];
+        }
+    }
+}
+
+// ---- runs of a sorted sequence ------------------------------------------------
+
+template <int KEYMODE>
+__device__ __forceinline__ u64 run_key(const void* keys, u64 i) {
+    if constexpr (KEYMODE == RUN_U64) return reinterpret_cast<const u64*>(keys)[i];
+    else if constexpr (KEYMODE == RUN_SRC_OF_U64) return reinterpret_cast<const u64*>(keys)[i] >> 32;
+    else return reinterpret_cast<const u32*>(keys)[i];
+}
+
+struct RunsSmem {
+    u64 key[kTile + 1];
+    u64 val[kTile];
+    u64 wsum64[kWarps];
+    u32 wsum[kWarps];
+    u64 tot64;
+    u32 tot;
+    u32 tile;
+    u64 cbase, sbase;
+};
+
+// For each run head i (i == 0 or key(i) != key(i-1)), in order r = 0, 1, ...:
+//   pos[r] = i, psum[r] = sum of val[0..i) (if HAS_V), head_keys[r] = key(i)
+// and finally pos[R] = n, psum[R] = total, *R_out = R.
+template <int KEYMODE, bool HAS_V>
+__global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys,
+                                                    const u64* __restrict__ vals, u64 n_arg,
+                                                    const u64* __restrict__ n_dev,
+                                                    u64* __restrict__ head_keys, u64* __restrict__ pos,
+                                                    u64* __restrict__ psum, u64* status_c,
+                                                    u64* status_s, u32* tile_counter, u32 tag,
+                                                    u64* R_out, DevStats* st) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RunsSmem& sm = *reinterpret_cast<RunsSmem*>(smem_raw);
+    const u64 n = n_dev ? *n_dev : n_arg;
+    if (threadIdx.x == 0) sm.tile = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const u64 tile = sm.tile;
+    const u64 base = tile * kTile;
+    if (base >= n) {
+        // an empty sequence still needs its terminal entry
+        if (n == 0 && tile == 0 && threadIdx.x == 0) {
+            pos[0] = 0;
+            if constexpr (HAS_V) psum[0] = 0;
+            *R_out = 0;
+        }
+        return;
+    }
+    const u64 tile_n = (n - base) < (u64)kTile ? (n - base) : (u64)kTile;
+
+    // coalesced load into shared memory; key[0] is the element before the tile
+    for (u32 i = threadIdx.x; i < tile_n; i += kThreads) {
+        sm.key[i + 1] = run_key<KEYMODE>(keys, base + i);
+        if constexpr (HAS_V) sm.val[i] = vals[base + i];
+    }
+    if (threadIdx.x == 0) sm.key[0] = base > 0 ? run_key<KEYMODE>(keys, base - 1) : 0;
+    __syncthreads();
+
+    // blocked: thread t owns tile items [t*kItems, (t+1)*kItems)
+    const u32 t0 = threadIdx.x * kItems;
+    u32 heads = 0;
+    u64 vsum = 0;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const u32 li = t0 + j;
+        if (li < tile_n) {
+            const bool h = (base + li == 0) || sm.key[li + 1] != sm.key[li];
+            heads += h;
+            if constexpr (HAS_V) vsum += sm.val[li];
+        }
+    }
+    u32 hx = block_excl_scan(heads, sm.wsum, &sm.tot);
+    u64 sx = 0;
+    if constexpr (HAS_V) sx = block_excl_scan64(vsum, sm.wsum64, &sm.tot64);
+    if (threadIdx.x == 0) {
+        st_volatile(&status_c[tile], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, sm.tot));
+        u64 c = 0;
+        if (tile > 0) {
+            c = lookback(status_c, 1, tile, tag, st);
+            st_volatile(&status_c[tile], pack_status(tag, kFlagPrefix, c + sm.tot));
+        }
+        sm.cbase = c;
+    }
+    if (HAS_V && threadIdx.x == 32) {
+        st_volatile(&status_s[tile], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, sm.tot64));
+        u64 s = 0;
+        if (tile > 0) {
+            s = lookback(status_s, 1, tile, tag, st);
+            st_volatile(&status_s[tile], pack_status(tag, kFlagPrefix, s + sm.tot64));
+        }
+        sm.sbase = s;
+    }
+    __syncthreads();
+    u64 r = sm.cbase + hx;
+    u64 s = HAS_V ? sm.sbase + sx : 0;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const u32 li = t0 + j;
+        if (li < tile_n) {
+            const u64 i = base + li;
+            const bool h = (i == 0) || sm.key[li + 1] != sm.key[li];
+            if (h) {
+                if (r < n) {  // R <= n unless a look-back gave up
+                    pos[r] = i;
+                    if constexpr (HAS_V) psum[r] = s;
+                    if (head_keys) head_keys[r] = sm.key[li + 1];
+                }
+                ++r;
+            }
+            if constexpr (HAS_V) s += sm.val[li];
+        }
+    }
+    if (base + tile_n == n && threadIdx.x == 0) {
+        const u64 R = min(sm.cbase + sm.tot, n);
+        pos[R] = n;
+        if constexpr (HAS_V) psum[R] = sm.sbase + sm.tot64;
+        *R_out = R;
+    }
+}
+
+// Statistics of runs r < R from neighbour differences.
+//   RS_LINKS: counts[r] = pos[r+1]-pos[r]; links = R, max link, valid = n
+//   RS_ROWS : sources = R, max src packets (psum diff), max fan-out (pos diff)
+//   RS_COLS : destinations = R, max dst packets, max fan-in
+template <int MODE>
+__global__ void __launch_bounds__(256) k_run_stats(const u64* __restrict__ pos,
+                                                    const u64* __restrict__ psum,
+                                                    const u64* __restrict__ R_ptr,
+                                                    u64* __restrict__ counts_out, DevStats* st) {
+    __shared__ u64 m1, m2;
+    if (threadIdx.x == 0) m1 = m2 = 0;
+    __syncthreads();
+    const u64 R = *R_ptr;
+    u64 a = 0, b = 0;
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += stride) {
+        const u64 len = pos[r + 1] - pos[r];
+        if constexpr (MODE == RS_LINKS) {
+            counts_out[r] = len;
+            a = len > a ? len : a;
+        } else {
+            const u64 sum = psum[r + 1] - psum[r];
+            a = sum > a ? sum : a;
+            b = len > b ? len : b;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = max(a, __shfl_xor_sync(0xFFFFFFFFu, a, o));
+        b = max(b, __shfl_xor_sync(0xFFFFFFFFu, b, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (a) atomicMax(&m1, a);
+        if (b) atomicMax(&m2, b);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if constexpr (MODE == RS_LINKS) {
+            if (m1) atomicMax(&st->v[S_MAX_LINK], m1);
+            if (blockIdx.x == 0) {
+                st->v[S_LINKS] = R;
+                st->v[S_VALID] = pos[R];
+            }
+        } else if constexpr (MODE == RS_ROWS) {
+            if (m1) atomicMax(&st->v[S_MAX_SRC_PK], m1);
+            if (m2) atomicMax(&st->v[S_MAX_SRC_FO], m2);
+            if (blockIdx.x == 0) st->v[S_SRCS] = R;
+        } else {
+            if (m1) atomicMax(&st->v[S_MAX_DST_PK], m1);
+            if (m2) atomicMax(&st->v[S_MAX_DST_FI], m2);
+            if (blockIdx.x == 0) st->v[S_DSTS] = R;
+        }
+    }
+}
+
+template <typename K, bool HAS_V, int LOAD>
+void launch_onesweep(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs,
+                     u64* status, u32* tile_counter, u32 tag, DevStats* st, cudaStream_t s) {
+    const size_t smem = sizeof(ScatterSmem<K, HAS_V>);
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_onesweep<K, HAS_V, LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        configured = true;
+    }
+    const u64 tiles = (n + kTile - 1) / kTile;
+    if (tiles == 0) return;
+    k_onesweep<K, HAS_V, LOAD><<<(unsigned)tiles, kThreads, smem, s>>>(in, kout, vout, n, shift, offs,
+                                                                     status, tile_counter, tag, st);
+}
+
+template <int KEYMODE, bool HAS_V>
+void launch_runs_t(const void* keys, const u64* vals, u64 n, const u64* n_dev, u64* head_keys, u64* pos, u64* psum,
+                   u64* status_c, u64* status_s, u32* tile_counter, u32 tag, u64* R_out, DevStats* st,
+                   cudaStream_t s) {
+    const size_t smem = sizeof(RunsSmem);
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_runs<KEYMODE, HAS_V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        configured = true;
+    }
+    u64 tiles = (n + kTile - 1) / kTile;
+    if (tiles == 0) tiles = 1;
+    k_runs<KEYMODE, HAS_V><<<(unsigned)tiles, kThreads, smem, s>>>(
+        keys, vals, n, n_dev, head_keys, pos, psum, status_c, status_s, tile_counter, tag, R_out, st);
+}
+
+}  // namespace
+
+u64 sort_tiles(u64 n) { return (n + kTile - 1) / kTile; }
+int sort_radix() { return kRadix; }
+
+// Sort n keys by bits [begin_bit, begin_bit + 8*passes).  Pass p reads
+// buffer (p == 0 ? the input : bufs[(p-1)&1]) and writes bufs[p&1].
+// Returns the index (0 or 1) of the buffer holding the result.
+template <typename K, bool HAS_V, int LOAD>
+int radix_sort_t(const SortIn& in, K* kbuf[2], u64* vbuf[2], u64 n, int begin_bit, int passes,
+                 SortScratch& sc, DevStats* st, cudaStream_t s) {
+    cudaMemsetAsync(sc.ghist, 0, sizeof(u32) * 8 * kRadix, s);
+    cudaMemsetAsync(sc.tile_counters, 0, sizeof(u32) * 8, s);
+    const int hist_grid = (int)std::min<u64>((n + kThreads * 8 - 1) / (kThreads * 8), (u64)sc.sms * 4);
+    k_sort_hist<K, LOAD><<<hist_grid < 1 ? 1 : hist_grid, kThreads, 0, s>>>(in, n, begin_bit, passes,
+                                                                           sc.ghist);
+    k_sort_offsets<<<1, kThreads, 0, s>>>(sc.ghist, passes, sc.offs);
+    for (int p = 0; p < passes; ++p) {
+        const u32 tag = next_tag(sc, s);
+        const int shift = begin_bit + 8 * p;
+        if (p == 0) {
+            launch_onesweep<K, HAS_V, LOAD>(in, kbuf[0], vbuf[0], n, shift, sc.offs, sc.status,
+                                            sc.tile_counters + p, tag, st, s);
+        } else {
+            SortIn mid{};
+            mid.keys = kbuf[(p - 1) & 1];
+            mid.vals = vbuf[(p - 1) & 1];
+            mid.n_dev = in.n_dev;
+            launch_onesweep<K, HAS_V, LOAD_KEYS>(mid, kbuf[p & 1], vbuf[p & 1], n, shift,
+                                                 sc.offs + p * kRadix, sc.status, sc.tile_counters + p,
+                                                 tag, st, s);
+        }
+    }
+    return (passes - 1) & 1;
+}
+
+int radix_sort_packets(const u32* src, const u32* dst, u64* kbuf[2], u64 n,
+                       SortScratch& sc, DevStats* st, cudaStream_t s) {
+    SortIn in{};
+    in.src = src;
+    in.dst = dst;
+    u64* vb[2] = {nullptr, nullptr};
+    return radix_sort_t<u64, false, LOAD_PACK>(in, (u64**)kbuf, vb, n, 0, 8, sc, st, s);
+}
+
+int radix_sort_pairs64(const u64* keys, const u64* vals, const u64* n_dev,
+                       u64* kbuf[2], u64* vbuf[2], u64 n, SortScratch& sc,
+                       DevStats* st, cudaStream_t s) {
+    SortIn in{};
+    in.keys = keys;
+    in.vals = (const u64*)vals;
+    in.n_dev = (const u64*)n_dev;
+    return radix_sort_t<u64, true, LOAD_KEYS>(in, (u64**)kbuf, (u64**)vbuf, n, 0, 8, sc, st, s);
+}
+
+int radix_sort_dst_pairs(const u64* link_keys, const u64* counts, const u64* n_dev,
+                         u32* kbuf[2], u64* vbuf[2], u64 n, SortScratch& sc,
+                         DevStats* st, cudaStream_t s) {
+    SortIn in{};
+    in.keys = link_keys;
+    in.vals = (const u64*)counts;
+    in.n_dev = (const u64*)n_dev;
+    return radix_sort_t<u32, true, LOAD_DST_OF>(in, (u32**)kbuf, (u64**)vbuf, n, 0, 4, sc, st, s);
+}
+
+void launch_runs(int keymode, bool has_v, const void* keys, const u64* vals, u64 n,
+                 const u64* n_dev, u64* head_keys, u64* pos, u64* psum,
+                 u64* R_out, SortScratch& sc, DevStats* st, cudaStream_t s) {
+    cudaMemsetAsync(sc.tile_counters + 8, 0, sizeof(u32), s);
+    const u32 tag = next_tag(sc, s);
+    const u64* nd = (const u64*)n_dev;
+    u64* sc_c = sc.status;
+    u64* sc_s = sc.status + sc.status_words / 2;
+    u32* tc = sc.tile_counters + 8;
+    if (keymode == RUN_U64 && !has_v)
+        launch_runs_t<RUN_U64, false>(keys, (const u64*)vals, n, nd, (u64*)head_keys, (u64*)pos,
+                                      (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, s);
+    else if (keymode == RUN_SRC_OF_U64 && has_v)
+        launch_runs_t<RUN_SRC_OF_U64, true>(keys, (const u64*)vals, n, nd, (u64*)head_keys, (u64*)pos,
+                                            (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, s);
+    else if (keymode == RUN_U32 && has_v)
+        launch_runs_t<RUN_U32, true>(keys, (const u64*)vals, n, nd, (u64*)head_keys, (u64*)pos,
+                                     (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, s);
+}
+
+void launch_run_stats(int mode, const u64* pos, const u64* psum, const u64* R_ptr,
+                      u64 bound, u64* counts_out, DevStats* st, int sms, cudaStream_t s) {
+    u64 want = (bound + 255) / 256;
+    u64 cap = (u64)sms * 8;
+    int grid = (int)(want < 1 ? 1 : (want < cap ? want : cap));
+    if (mode == RS_LINKS)
+        k_run_stats<RS_LINKS><<<grid, 256, 0, s>>>((const u64*)pos, (const u64*)psum,
+                                                  (const u64*)R_ptr, (u64*)counts_out, st);
+    else if (mode == RS_ROWS)
+        k_run_stats<RS_ROWS><<<grid, 256, 0, s>>>((const u64*)pos, (const u64*)psum,
+                                                 (const u64*)R_ptr, (u64*)counts_out, st);
+    else
+        k_run_stats<RS_COLS><<<grid, 256, 0, s>>>((const u64*)pos, (const u64*)psum,
+                                                 (const u64*)R_ptr, (u64*)counts_out, st);
+}
+
+}  // namespace ns

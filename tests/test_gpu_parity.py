@@ -1,0 +1,189 @@
+"""Parity of the CUDA path with the CPU oracle, element by element.
+
+Every quantity and A's sorted nonzero list must match bit-exactly (all values
+are uint64 counts).  Sizes span several 4096-element tiles with ragged tails;
+edge cases cover the empty window, one packet, a single repeated key, the
+extreme keys 0 and 2^64-1, a star, self-loops and an all-distinct window.
+Both aggregation paths (sort, hash) are checked, and the windowed forms
+(build + accumulate, fused ingest) are checked after every window.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import gen
+import gen.workloads as W
+import oracle
+import paper_2509_03653_b300 as ns
+from gpu_util import assert_matrix_equal, export_np, stats_row, to_dev
+
+pytestmark = pytest.mark.gpu
+
+PATHS = ["hash", "sort"]
+
+
+@pytest.fixture(scope="module")
+def ctxs():
+    c = {p: ns.Context(0, path=p) for p in PATHS}
+    yield c
+    for x in c.values():
+        x.close()
+
+
+def check_window(ctx, s, d):
+    m = ns.Matrix(ctx)
+    ns.window_build(ctx, to_dev(s), to_dev(d), m)
+    got = ns.network_stats(ctx, m)
+    wk, wc = oracle.build_matrix(s, d)
+    assert got == oracle.stats(wk, wc)
+    assert_matrix_equal(m, wk, wc)
+    m.free()
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 4095, 4096, 4097, 12289, 100003, 1 << 17])
+def test_window_zipf(ctxs, path, n):
+    s, d = W.single_window(n)
+    check_window(ctxs[path], s, d)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_window_rmat(ctxs, path):
+    s, d = W.rmat_stream(70001)
+    check_window(ctxs[path], s, d)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_edge_all_identical(ctxs, path):
+    n = 50000
+    check_window(ctxs[path], np.full(n, 7, np.uint32), np.full(n, 9, np.uint32))
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_edge_extreme_keys(ctxs, path):
+    # keys 0 (src = dst = 0) and 2^64 - 1 (src = dst = 0xFFFFFFFF) with others
+    s = np.array([0, 0xFFFFFFFF, 0, 5, 0xFFFFFFFF, 0, 0xFFFFFFFF, 1] * 1000, np.uint32)
+    d = np.array([0, 0xFFFFFFFF, 0, 5, 0xFFFFFFFF, 1, 0, 0xFFFFFFFF] * 1000, np.uint32)
+    check_window(ctxs[path], s, d)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_edge_star_and_self_loops(ctxs, path):
+    n = 30000
+    s = np.full(n, 0xABCDEF01, np.uint32)
+    d = np.arange(n, dtype=np.uint32)
+    s2 = np.arange(5000, dtype=np.uint32)
+    check_window(ctxs[path], np.concatenate([s, s2]), np.concatenate([d, s2]))
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_edge_all_distinct(ctxs, path):
+    n = 1 << 16
+    s = gen.feistel(np.arange(n, dtype=np.uint32), 11)
+    d = gen.feistel(np.arange(n, dtype=np.uint32), 12)
+    check_window(ctxs[path], s, d)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_edge_tiny_address_space(ctxs, path):
+    # heavy collisions: 8-bit addresses widened to 32 bits
+    s8, d8 = gen.uniform_pairs(90001, 8, 5)
+    w = lambda a: (a.astype(np.uint32) * np.uint32(0x01010101)).astype(np.uint32)
+    check_window(ctxs[path], w(s8), w(d8))
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("mode", ["build_accumulate", "ingest"])
+def test_windows_accumulate(ctxs, path, mode):
+    ctx = ctxs[path]
+    sizes = [4096, 1, 0, 12289, 7000, 4097, 30000, 3]
+    total = sum(sizes)
+    s, d = W.rmat_stream(total)
+    # make some links repeat across windows
+    s[total // 2:] = s[: total - total // 2]
+    acc = ns.Matrix(ctx)
+    tmp = ns.Matrix(ctx)
+    off = 0
+    want = (np.zeros(0, np.uint64), np.zeros(0, np.uint64))
+    for n in sizes:
+        ws, wd = s[off:off + n], d[off:off + n]
+        off += n
+        if mode == "ingest":
+            ns.window_ingest(ctx, acc, to_dev(ws), to_dev(wd))
+        else:
+            ns.window_build(ctx, to_dev(ws), to_dev(wd), tmp)
+            ns.accumulate(ctx, acc, tmp)
+        want = oracle.accumulate(want, oracle.build_matrix(ws, wd))
+        got = ns.network_stats(ctx, acc)
+        assert got == oracle.stats(*want)
+    assert_matrix_equal(acc, *want)
+
+
+def test_mixed_formats_accumulate(ctxs):
+    """Sorted-list windows (sort path) summed into a hash accumulator, and a
+    sorted accumulator converted on its first accumulate."""
+    s, d = W.single_window(20000)
+    a1 = ns.Matrix(ctxs["sort"])
+    ns.window_build(ctxs["sort"], to_dev(s[:9000]), to_dev(d[:9000]), a1)
+    a2 = ns.Matrix(ctxs["sort"])
+    ns.window_build(ctxs["sort"], to_dev(s[9000:]), to_dev(d[9000:]), a2)
+    ns.accumulate(ctxs["sort"], a1, a2)  # list accumulator -> hash
+    want = oracle.build_matrix(s, d)
+    assert ns.network_stats(ctxs["sort"], a1) == oracle.stats(*want)
+    assert_matrix_equal(a1, *want)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_async_stats_match_blocking(ctxs, path):
+    ctx = ctxs[path]
+    s, d = W.single_window(1 << 15)
+    m = ns.Matrix(ctx)
+    ns.window_build(ctx, to_dev(s), to_dev(d), m)
+    out = torch.zeros(16, dtype=torch.int64, device="cuda")
+    ns.network_stats_async(ctx, m, out)
+    torch.cuda.synchronize()
+    assert stats_row(out) == ns.network_stats(ctx, m)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_rebuild_reuses_matrix(ctxs, path):
+    """A matrix rebuilt from a different window forgets the old one."""
+    ctx = ctxs[path]
+    m = ns.Matrix(ctx)
+    s, d = W.single_window(50000)
+    ns.window_build(ctx, to_dev(s), to_dev(d), m)
+    s2, d2 = W.rmat_stream(3000)
+    ns.window_build(ctx, to_dev(s2), to_dev(d2), m)
+    want = oracle.build_matrix(s2, d2)
+    assert ns.network_stats(ctx, m) == oracle.stats(*want)
+    assert_matrix_equal(m, *want)
+
+
+def test_hash_accumulator_grows(ctxs):
+    """An accumulator sized for a small window grows (rehash) as windows add
+    new links, without changing any result."""
+    ctx = ctxs["hash"]
+    acc = ns.Matrix(ctx)
+    ns.matrix_reserve(acc, 1000)
+    s, d = W.rmat_stream(200000)
+    for i in range(4):
+        ns.window_ingest(ctx, acc, to_dev(s[i * 50000:(i + 1) * 50000]), to_dev(d[i * 50000:(i + 1) * 50000]))
+    want = oracle.build_matrix(s, d)
+    assert ns.network_stats(ctx, acc) == oracle.stats(*want)
+    assert_matrix_equal(acc, *want)
+
+
+def test_export_capacity_error(ctxs):
+    ctx = ctxs["hash"]
+    m = ns.Matrix(ctx)
+    s, d = W.single_window(5000)
+    ns.window_build(ctx, to_dev(s), to_dev(d), m)
+    keys = torch.empty(4, dtype=torch.int64, device="cuda")
+    import ctypes
+    got = ctypes.c_uint64()
+    st = ctx._L.ns_matrix_export(m.handle, ctypes.c_void_p(keys.data_ptr()), ctypes.c_void_p(keys.data_ptr()),
+                                 4, ctypes.byref(got), None)
+    assert st == 3  # NS_ERR_CAPACITY, nothing written
+    assert got.value == oracle.stats(*oracle.build_matrix(s, d))["unique_links"]
