@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark of the traffic-matrix hot path on one B300 (or N replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (default, "stream"): an accumulated packet stream of 2^26 packets in
+512 windows of 2^17 -- RMAT scale 32 with (a,b,c,d) = (0.57,0.19,0.19,0.05)
+plus 10% uniform background pairs, anonymized by a seeded 32-bit bijection --
+with the summed traffic matrix A and its nine Table 2 quantities produced
+after every window, one library call per window (plain per-window launches).
+
+One step = reset A, then for each window: fused build + accumulate
+(ns_window_ingest) and the statistics snapshot (ns_network_stats_async) into
+a device array; the per-window call sequence is captured once into a CUDA
+graph and replayed.  `value` times K steps with inputs resident in HBM; `e2e`
+adds, every step, the host-to-device copy of the step's packets from pinned
+memory and the device-to-host copy of the 512 statistics rows.
+
+Prints one JSON line.  Under torchrun (N > 1) every rank runs an independent
+replica of the stream on its own GPU (no data-path collective) and rank 0
+reports the whole-job throughput over the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "packets/s to traffic matrix+stats, %HBM roofline; batched vs plain; p99 latency"
+UNIT = "packets/s"
+WINDOWS = 512
+WINDOW = 1 << 17
+PROFILE = os.path.join(ROOT, "profiles", "k_insert_packets.stream_rmat_window_2p17.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2509_03653_b300", "csrc", f)
+                  for f in ("ns_hash.cu", "ns_common.cuh")]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0,
+                    help="seconds of oracle work for the cpu_baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(extra=None):
+    cfg = {
+        "workload": "accumulated RMAT stream: 2^26 packets as 512 windows of 2^17, "
+                    "stats of the summed A after every window (plain per-window launches)",
+        "packets": WINDOWS * WINDOW,
+        "windows": WINDOWS,
+        "window_packets": WINDOW,
+        "generator": "RMAT scale 32 (0.57,0.19,0.19,0.05) + 10% uniform, seeded bijection",
+        "l2": "inputs larger than L2 (512 MiB of packets, 10 GiB of tables per step)",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ----------------------------------------------------------------- CPU legs
+
+def oracle_stream_rate(src, dst, budget_s=None, windows=None):
+    """The CPU oracle as it stands, single thread: for each window build A_t,
+    A += A_t, and the nine quantities of A; stops after `windows` windows or
+    once `budget_s` seconds have passed.  Returns (packets/s, windows, s)."""
+    import oracle
+    acc = (np.zeros(0, np.uint64), np.zeros(0, np.uint64))
+    t0 = time.perf_counter()
+    w = 0
+    while w < WINDOWS:
+        sl = slice(w * WINDOW, (w + 1) * WINDOW)
+        acc = oracle.accumulate(acc, oracle.build_matrix(src[sl], dst[sl]))
+        oracle.stats(*acc)
+        w += 1
+        el = time.perf_counter() - t0
+        if windows is not None and w >= windows:
+            break
+        if budget_s is not None and el >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return w * WINDOW / el, w, el
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle on this arm's workload and metric, each
+    step a bounded sample (the first 16 windows)."""
+    if rank != 0:
+        return
+    import gen.workloads as W
+    sample_windows = 16
+    src, dst = W.rmat_stream(sample_windows * WINDOW)
+    for _ in range(args.warmup):
+        oracle_stream_rate(src, dst, windows=sample_windows)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_stream_rate(src, dst, windows=sample_windows)
+    el = time.perf_counter() - t0
+    value = args.steps * sample_windows * WINDOW / el
+    sample = f"first {sample_windows} windows (2^{int(np.log2(sample_windows * WINDOW))} packets) per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": workload_config({"sample": sample}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+
+    def summary(self, t0, t1):
+        rows = [r for t, r in self.rows if t0 <= t <= t1] or [r for _, r in self.rows[-3:]]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------- ours
+
+def kernel_traffic():
+    """ncu DRAM bytes per launch of the dominant kernel, if the committed
+    profile was taken on the current kernel source; else None."""
+    if not os.path.exists(PROFILE):
+        return None
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(p, "rb").read())
+    got_hash = traffic = None
+    for line in open(PROFILE):
+        if line.startswith("source_sha256:"):
+            got_hash = line.split(":", 1)[1].strip()
+        if line.startswith("traffic_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    return traffic if got_hash == h.hexdigest() else None
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import gen.workloads as W
+    import paper_2509_03653_b300 as ns
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    N = WINDOWS * WINDOW
+    # host input (pinned) and its resident device copy
+    h_src = torch.empty(N, dtype=torch.int32).pin_memory()
+    h_dst = torch.empty(N, dtype=torch.int32).pin_memory()
+    seed = W.seed_of(2) + 1000 * rank  # replicas draw independent streams
+    W.rmat_stream(N, src=h_src.numpy().view(np.uint32), dst=h_dst.numpy().view(np.uint32), seed=seed)
+    d_src = h_src.to(dev)
+    d_dst = h_dst.to(dev)
+
+    ctx = ns.Context(local, path="hash")
+    A = ns.Matrix(ctx)
+    ns.matrix_reserve(A, N)
+
+    # per-window distinct counts for the roofline bytes (bookkeeping only)
+    t_build = ns.Matrix(ctx)
+    alg_bytes = 0
+    for w in range(WINDOWS):
+        ns.window_build(ctx, d_src[w * WINDOW:(w + 1) * WINDOW], d_dst[w * WINDOW:(w + 1) * WINDOW], t_build)
+        st = ns.network_stats(ctx, t_build)
+        alg_bytes += 8 * WINDOW + 16 * st["unique_links"] + 16 * (st["unique_sources"] + st["unique_destinations"])
+    t_build.free()
+    alg_bytes_per_launch = alg_bytes / WINDOWS
+
+    stats_rows = torch.zeros(WINDOWS, 16, dtype=torch.int64, device=dev)
+    cap_stream = torch.cuda.Stream(dev)
+
+    def step(src, dst, ev=None):
+        ns.matrix_clear(A)
+        for w in range(WINDOWS):
+            sl = slice(w * WINDOW, (w + 1) * WINDOW)
+            if ev is not None:
+                ev[w][0].record()
+            ns.window_ingest(ctx, A, src[sl], dst[sl])
+            if ev is not None:
+                ev[w][1].record()
+            ns.network_stats_async(ctx, A, stats_rows[w])
+
+    # eager warm-up, then capture one graph per timed step (each with its own
+    # timing events around every ingest launch)
+    with torch.cuda.stream(cap_stream):
+        step(d_src, d_dst)
+    torch.cuda.synchronize()
+    graphs, events = [], []
+    for k in range(args.steps):
+        ev = [(torch.cuda.Event(enable_timing=True, external=True),
+               torch.cuda.Event(enable_timing=True, external=True)) for _ in range(WINDOWS)]
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap_stream):
+            step(d_src, d_dst, ev)
+        graphs.append(g)
+        events.append(ev)
+    g_plain = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_plain, stream=cap_stream):
+        step(d_src, d_dst)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    for _ in range(max(args.warmup, 3)):
+        g_plain.replay()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, inputs resident in HBM
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    cur = torch.cuda.current_stream()
+    tw0 = time.time()
+    e0.record(cur)
+    for g in graphs:
+        g.replay()
+    e1.record(cur)
+    torch.cuda.synchronize()
+    tw1 = time.time()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launch_ms = [a.elapsed_time(b) for ev in events for a, b in ev]
+    clock_summary = clocks.summary(tw0, tw1)
+
+    # correctness guard on the last step (cheap invariant, no oracle)
+    last = stats_rows[-1].cpu().numpy().view(np.uint64)
+    assert int(last[0]) == N, "valid packets != N"
+
+    # ---- end to end: H2D of the step's packets + graph + D2H of the stats
+    e2e = None
+    if not args.no_e2e:
+        h_stats = torch.empty(WINDOWS, 16, dtype=torch.int64).pin_memory()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        for _ in range(2):
+            d_src.copy_(h_src, non_blocking=True)
+            d_dst.copy_(h_dst, non_blocking=True)
+            g_plain.replay()
+            h_stats.copy_(stats_rows, non_blocking=True)
+        torch.cuda.synchronize()
+        barrier()
+        e2.record(cur)
+        for _ in range(args.steps):
+            d_src.copy_(h_src, non_blocking=True)
+            d_dst.copy_(h_dst, non_blocking=True)
+            g_plain.replay()
+            h_stats.copy_(stats_rows, non_blocking=True)
+        e3.record(cur)
+        torch.cuda.synchronize()
+        barrier()
+        e2e = {"ms": e2.elapsed_time(e3), "h2d": 2 * 4 * N, "d2h": WINDOWS * 9 * 8}
+    clocks.stop()
+
+    # ---- gather over ranks (max time)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, e2e["ms"] if e2e else 0.0], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t[0])
+        if e2e:
+            e2e["ms"] = float(t[1])
+    if rank != 0:
+        return
+
+    packets = world * args.steps * N
+    value = packets / (ms / 1e3)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    peak = peaks.get("hbm_gbs", 6400.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    avg_launch_ms = float(np.mean(launch_ms))
+    achieved = alg_bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": workload_config({"path": "hash (fused window ingest)", "graph": "per-window launches "
+                                   "captured in one CUDA graph per step",
+                                   "parallelism": "replicas" if world > 1 else "single GPU"}),
+        "roofline": {
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": kernel_traffic(), "kernel": "k_insert_packets",
+            "alg_bytes_per_launch": alg_bytes_per_launch, "launch_us_avg": avg_launch_ms * 1e3,
+            "launch_us_p50": float(np.percentile(launch_ms, 50)) * 1e3,
+            "peak_source": f"{peak_src} (hbm_gbs, copy read+write)",
+        },
+        "clocks": clock_summary,
+        "gpu_launches": args.steps * WINDOWS * 2,
+    }
+    if e2e:
+        line["e2e"] = {"value": world * args.steps * N / (e2e["ms"] / 1e3), "unit": UNIT,
+                       "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
+    if not args.no_cpu_baseline:
+        rate, wins, el = oracle_stream_rate(h_src.numpy().view(np.uint32), h_dst.numpy().view(np.uint32),
+                                            budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {wins} windows of the same stream ({wins * WINDOW} packets, "
+                                          f"{el:.1f} s), stats after each window"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()
