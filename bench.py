@@ -56,6 +56,8 @@ def parse():
                     help="seconds of oracle work for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--windows", type=int, default=WINDOWS,
+                    help="windows in the stream (512 = the full workload; fewer = a small case for profiling)")
     return ap.parse_args()
 
 
@@ -66,12 +68,12 @@ def dist_env():
     return rank, world, local
 
 
-def workload_config(extra=None):
+def workload_config(extra=None, windows=WINDOWS):
     cfg = {
         "workload": "accumulated RMAT stream: 2^26 packets as 512 windows of 2^17, "
                     "stats of the summed A after every window (plain per-window launches)",
-        "packets": WINDOWS * WINDOW,
-        "windows": WINDOWS,
+        "packets": windows * WINDOW,
+        "windows": windows,
         "window_packets": WINDOW,
         "generator": "RMAT scale 32 (0.57,0.19,0.19,0.05) + 10% uniform, seeded bijection",
         "l2": "inputs larger than L2 (512 MiB of packets, 10 GiB of tables per step)",
@@ -91,7 +93,7 @@ def oracle_stream_rate(src, dst, budget_s=None, windows=None):
     acc = (np.zeros(0, np.uint64), np.zeros(0, np.uint64))
     t0 = time.perf_counter()
     w = 0
-    while w < WINDOWS:
+    while w < len(src) // WINDOW:
         sl = slice(w * WINDOW, (w + 1) * WINDOW)
         acc = oracle.accumulate(acc, oracle.build_matrix(src[sl], dst[sl]))
         oracle.stats(*acc)
@@ -213,7 +215,8 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    N = WINDOWS * WINDOW
+    NW = args.windows
+    N = NW * WINDOW
     # host input (pinned) and its resident device copy
     h_src = torch.empty(N, dtype=torch.int32).pin_memory()
     h_dst = torch.empty(N, dtype=torch.int32).pin_memory()
@@ -229,19 +232,19 @@ def run_ours(args, rank, world, local):
     # per-window distinct counts for the roofline bytes (bookkeeping only)
     t_build = ns.Matrix(ctx)
     alg_bytes = 0
-    for w in range(WINDOWS):
+    for w in range(NW):
         ns.window_build(ctx, d_src[w * WINDOW:(w + 1) * WINDOW], d_dst[w * WINDOW:(w + 1) * WINDOW], t_build)
         st = ns.network_stats(ctx, t_build)
         alg_bytes += 8 * WINDOW + 16 * st["unique_links"] + 16 * (st["unique_sources"] + st["unique_destinations"])
     t_build.free()
-    alg_bytes_per_launch = alg_bytes / WINDOWS
+    alg_bytes_per_launch = alg_bytes / NW
 
-    stats_rows = torch.zeros(WINDOWS, 16, dtype=torch.int64, device=dev)
+    stats_rows = torch.zeros(NW, 16, dtype=torch.int64, device=dev)
     cap_stream = torch.cuda.Stream(dev)
 
     def step(src, dst, ev=None):
         ns.matrix_clear(A)
-        for w in range(WINDOWS):
+        for w in range(NW):
             sl = slice(w * WINDOW, (w + 1) * WINDOW)
             if ev is not None:
                 ev[w][0].record()
@@ -258,7 +261,7 @@ def run_ours(args, rank, world, local):
     graphs, events = [], []
     for k in range(args.steps):
         ev = [(torch.cuda.Event(enable_timing=True, external=True),
-               torch.cuda.Event(enable_timing=True, external=True)) for _ in range(WINDOWS)]
+               torch.cuda.Event(enable_timing=True, external=True)) for _ in range(NW)]
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=cap_stream):
             step(d_src, d_dst, ev)
@@ -306,7 +309,7 @@ def run_ours(args, rank, world, local):
     # ---- end to end: H2D of the step's packets + graph + D2H of the stats
     e2e = None
     if not args.no_e2e:
-        h_stats = torch.empty(WINDOWS, 16, dtype=torch.int64).pin_memory()
+        h_stats = torch.empty(NW, 16, dtype=torch.int64).pin_memory()
         e2 = torch.cuda.Event(enable_timing=True)
         e3 = torch.cuda.Event(enable_timing=True)
         for _ in range(2):
@@ -325,7 +328,7 @@ def run_ours(args, rank, world, local):
         e3.record(cur)
         torch.cuda.synchronize()
         barrier()
-        e2e = {"ms": e2.elapsed_time(e3), "h2d": 2 * 4 * N, "d2h": WINDOWS * 9 * 8}
+        e2e = {"ms": e2.elapsed_time(e3), "h2d": 2 * 4 * N, "d2h": NW * 9 * 8}
     clocks.stop()
 
     # ---- gather over ranks (max time)
@@ -354,7 +357,7 @@ def run_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": workload_config({"path": "hash (fused window ingest)", "graph": "per-window launches "
                                    "captured in one CUDA graph per step",
-                                   "parallelism": "replicas" if world > 1 else "single GPU"}),
+                                   "parallelism": "replicas" if world > 1 else "single GPU"}, windows=NW),
         "roofline": {
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": kernel_traffic(), "kernel": "k_insert_packets",
@@ -363,7 +366,7 @@ def run_ours(args, rank, world, local):
             "peak_source": f"{peak_src} (hbm_gbs, copy read+write)",
         },
         "clocks": clock_summary,
-        "gpu_launches": args.steps * WINDOWS * 2,
+        "gpu_launches": args.steps * NW * 2,
     }
     if e2e:
         line["e2e"] = {"value": world * args.steps * N / (e2e["ms"] / 1e3), "unit": UNIT,

@@ -161,6 +161,32 @@ ns_status ns_network_stats(ns_ctx* ctx, const ns_matrix* m, ns_stats* h_out, ns_
 ns_status ns_network_stats_async(ns_ctx* ctx, const ns_matrix* m, ns_stats* d_out,
                                  ns_stream_t stream);
 
+/* ---- statistics without device allocation ------------------------------ */
+
+/* The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory when they need a window's statistics -- for
+ * example a process whose GPU memory is already fully claimed by another
+ * framework's caching allocator, or a capture loop that must never block in
+ * cudaMalloc/cudaFree (both may synchronize the device).
+ *
+ * Writes the nine quantities of the window d_src[0..n), d_dst[0..n) (the
+ * same values ns_window_build + ns_network_stats give) to d_out, a device
+ * (or mapped pinned host) ns_stats, when the stream reaches this point.
+ * Needs no context and allocates nothing: its hash tables live in one fixed
+ * device array of about 5 MiB inside the library, which every GPU that loads
+ * the library keeps until the process exits.  n must not exceed
+ * NS_STATIC_MAX_PACKETS (larger n returns NS_ERR_INVALID and does nothing).
+ * Runs on the calling thread's current device.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it;
+ * make that first call before any stream capture on that device.  All calls
+ * on a device share the one array and each starts by clearing it, so calls
+ * whose GPU work overlaps (different streams, no ordering between them) race
+ * and give wrong results: order them on one stream.  Asynchronous; within
+ * the size limit no device-side error can occur. */
+#define NS_STATIC_MAX_PACKETS 32768
+ns_status ns_window_stats_static(const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
+                                 ns_stats* d_out, ns_stream_t stream);
+
 /* ---- errors ------------------------------------------------------------ */
 
 const char* ns_last_error(void);

@@ -20,8 +20,10 @@ from ._native import FIELDS, NsConfig, NsError, NsStats, check, load
 __all__ = [
     "FIELDS", "NsError", "Context", "Matrix", "window_build", "accumulate", "window_ingest",
     "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
-    "matrix_clear", "sync", "PATHS",
+    "matrix_clear", "sync", "PATHS", "window_stats_static", "STATIC_MAX_PACKETS",
 ]
+
+STATIC_MAX_PACKETS = 32768  # NS_STATIC_MAX_PACKETS in include/ns.h
 
 PATHS = {"auto": 0, "sort": 1, "hash": 2}
 
@@ -161,3 +163,19 @@ def matrix_clear(m: Matrix, stream=None):
 
 def sync(ctx: Context, stream=None):
     check(ctx._L.ns_sync(ctx.handle, _stream(stream)), "ns_sync")
+
+
+def window_stats_static(src: torch.Tensor, dst: torch.Tensor, out: torch.Tensor, stream=None):
+    """The nine quantities of one window of at most STATIC_MAX_PACKETS packets
+    written into `out` (a device tensor of >= 9 64-bit elements), without any
+    device allocation by the library (ns_window_stats_static).  For callers
+    that cannot allocate device memory at this point; calls share one fixed
+    device array, so order them on one stream."""
+    n = src.numel()
+    if dst.numel() != n:
+        raise ValueError("src and dst differ in length")
+    if out.element_size() != 8 or out.numel() < 9 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous 64-bit tensor with >= 9 elements")
+    L = load()
+    check(L.ns_window_stats_static(_column(src, "src"), _column(dst, "dst"), n, ctypes.c_void_p(out.data_ptr()),
+                                   _stream(stream)), "ns_window_stats_static")

@@ -42,6 +42,7 @@ SIGNATURES = {
     "ns_window_ingest": (ST, [P, P, P, P, U64, P]),
     "ns_network_stats": (ST, [P, P, ctypes.POINTER(NsStats), P]),
     "ns_network_stats_async": (ST, [P, P, P, P]),
+    "ns_window_stats_static": (ST, [P, P, U64, P, P]),
     "ns_last_error": (ctypes.c_char_p, []),
     "ns_status_string": (ctypes.c_char_p, [ST]),
 }
