@@ -151,6 +151,14 @@ ns_status ns_accumulate(ns_ctx* ctx, ns_matrix* acc, const ns_matrix* add, ns_st
 ns_status ns_window_ingest(ns_ctx* ctx, ns_matrix* acc, const uint32_t* d_src,
                            const uint32_t* d_dst, uint64_t n, ns_stream_t stream);
 
+/* ns_window_ingest followed by ns_network_stats_async(acc, d_out) in one
+ * kernel launch: the last CTA of the ingest writes the statistics of the
+ * updated acc.  This is the per-window call of a streaming pipeline that
+ * wants the running quantities after every window.  Asynchronous. */
+ns_status ns_window_ingest_stats(ns_ctx* ctx, ns_matrix* acc, const uint32_t* d_src,
+                                 const uint32_t* d_dst, uint64_t n, ns_stats* d_out,
+                                 ns_stream_t stream);
+
 /* The nine quantities of m into *h_out (host memory).  Blocking: waits for
  * the stream, then reports any device-side error of the matrix. */
 ns_status ns_network_stats(ns_ctx* ctx, const ns_matrix* m, ns_stats* h_out, ns_stream_t stream);
@@ -173,7 +181,7 @@ ns_status ns_network_stats_async(ns_ctx* ctx, const ns_matrix* m, ns_stats* d_ou
  * same values ns_window_build + ns_network_stats give) to d_out, a device
  * (or mapped pinned host) ns_stats, when the stream reaches this point.
  * Needs no context and allocates nothing: its hash tables live in one fixed
- * device array of about 5 MiB inside the library, which every GPU that loads
+ * device array of about 3 MiB inside the library, which every GPU that loads
  * the library keeps until the process exits.  n must not exceed
  * NS_STATIC_MAX_PACKETS (larger n returns NS_ERR_INVALID and does nothing).
  * Runs on the calling thread's current device.  The first call on a device

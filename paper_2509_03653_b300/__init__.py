@@ -19,7 +19,7 @@ from ._native import FIELDS, NsConfig, NsError, NsStats, check, load
 
 __all__ = [
     "FIELDS", "NsError", "Context", "Matrix", "window_build", "accumulate", "window_ingest",
-    "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
+    "window_ingest_stats", "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
     "matrix_clear", "sync", "PATHS", "window_stats_static", "STATIC_MAX_PACKETS",
 ]
 
@@ -115,6 +115,21 @@ def window_ingest(ctx: Context, acc: Matrix, src: torch.Tensor, dst: torch.Tenso
         raise ValueError("src and dst differ in length")
     check(ctx._L.ns_window_ingest(ctx.handle, acc.handle, _column(src, "src"), _column(dst, "dst"), n,
                                   _stream(stream)), "ns_window_ingest")
+
+
+def window_ingest_stats(ctx: Context, acc: Matrix, src: torch.Tensor, dst: torch.Tensor, out: torch.Tensor,
+                        stream=None):
+    """acc := acc + A_t(src, dst) and its nine quantities written into `out`
+    (a device tensor of >= 9 64-bit elements), in one launch
+    (ns_window_ingest_stats)."""
+    n = src.numel()
+    if dst.numel() != n:
+        raise ValueError("src and dst differ in length")
+    if out.element_size() != 8 or out.numel() < 9 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous 64-bit tensor with >= 9 elements")
+    check(ctx._L.ns_window_ingest_stats(ctx.handle, acc.handle, _column(src, "src"), _column(dst, "dst"), n,
+                                        ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+          "ns_window_ingest_stats")
 
 
 def network_stats(ctx: Context, m: Matrix, stream=None) -> dict:

@@ -40,6 +40,7 @@ SIGNATURES = {
     "ns_window_build": (ST, [P, P, P, U64, P, P]),
     "ns_accumulate": (ST, [P, P, P, P]),
     "ns_window_ingest": (ST, [P, P, P, P, U64, P]),
+    "ns_window_ingest_stats": (ST, [P, P, P, P, U64, P, P]),
     "ns_network_stats": (ST, [P, P, ctypes.POINTER(NsStats), P]),
     "ns_network_stats_async": (ST, [P, P, P, P]),
     "ns_window_stats_static": (ST, [P, P, U64, P, P]),

@@ -99,8 +99,8 @@ ns_status hash_alloc(ns_matrix* m, u64 links) {
     const u64 cap = next_pow2(std::max<u64>(2 * links, 1024));
     if (m->link_cap >= cap && m->links.p) return NS_OK;
     TRY(buf_reserve(m->links, (cap + 1) * sizeof(LinkSlot)));
-    TRY(buf_reserve(m->rows, cap * sizeof(NodeSlot)));
-    TRY(buf_reserve(m->cols, cap * sizeof(NodeSlot)));
+    TRY(buf_reserve(m->rows, (cap + 1) * sizeof(NodeSlot)));
+    TRY(buf_reserve(m->cols, (cap + 1) * sizeof(NodeSlot)));
     m->link_cap = cap;
     m->node_cap = cap;
     return NS_OK;
@@ -108,8 +108,8 @@ ns_status hash_alloc(ns_matrix* m, u64 links) {
 
 ns_status hash_clear(ns_matrix* m, cudaStream_t s) {
     CK(cudaMemsetAsync(m->links.p, 0, (m->link_cap + 1) * sizeof(LinkSlot), s));
-    CK(cudaMemsetAsync(m->rows.p, 0, m->node_cap * sizeof(NodeSlot), s));
-    CK(cudaMemsetAsync(m->cols.p, 0, m->node_cap * sizeof(NodeSlot), s));
+    CK(cudaMemsetAsync(m->rows.p, 0, (m->node_cap + 1) * sizeof(NodeSlot), s));
+    CK(cudaMemsetAsync(m->cols.p, 0, (m->node_cap + 1) * sizeof(NodeSlot), s));
     CK(cudaMemsetAsync(m->stats.p, 0, sizeof(DevStats), s));
     return NS_OK;
 }
@@ -143,8 +143,8 @@ ns_status hash_grow(ns_matrix* m, u64 extra, cudaStream_t s) {
     tmp.stats = m->stats;
     TRY(hash_alloc(&tmp, actual + extra));
     CK(cudaMemsetAsync(tmp.links.p, 0, (tmp.link_cap + 1) * sizeof(LinkSlot), s));
-    CK(cudaMemsetAsync(tmp.rows.p, 0, tmp.node_cap * sizeof(NodeSlot), s));
-    CK(cudaMemsetAsync(tmp.cols.p, 0, tmp.node_cap * sizeof(NodeSlot), s));
+    CK(cudaMemsetAsync(tmp.rows.p, 0, (tmp.node_cap + 1) * sizeof(NodeSlot), s));
+    CK(cudaMemsetAsync(tmp.cols.p, 0, (tmp.node_cap + 1) * sizeof(NodeSlot), s));
     CK(cudaMemsetAsync(m->stats.p, 0, sizeof(DevStats), s));
     launch_insert_slots((const LinkSlot*)m->links.p, m->link_cap, hash_view(&tmp), m->ctx->sms, s);
     TRY(check_launch());
@@ -479,6 +479,19 @@ ns_status ns_window_ingest(ns_ctx* c, ns_matrix* acc, const uint32_t* d_src, con
     TRY(to_hash(acc, n, s));
     if (n == 0) return NS_OK;
     launch_insert_packets(d_src, d_dst, n, hash_view(acc), c->sms, s);
+    acc->bound += n;
+    return check_launch();
+}
+
+ns_status ns_window_ingest_stats(ns_ctx* c, ns_matrix* acc, const uint32_t* d_src, const uint32_t* d_dst,
+                                 uint64_t n, ns_stats* d_out, ns_stream_t stream) {
+    if (!c || !acc || !d_out) return fail(NS_ERR_INVALID, "ns_window_ingest_stats: NULL argument");
+    if (n > 0 && (!d_src || !d_dst))
+        return fail(NS_ERR_INVALID, "ns_window_ingest_stats: NULL input with n > 0");
+    if (acc->ctx != c) return fail(NS_ERR_INVALID, "ns_window_ingest_stats: foreign matrix");
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(to_hash(acc, n, s));
+    launch_insert_packets_snapshot(d_src, d_dst, n, hash_view(acc), (u64*)d_out, c->sms, s);
     acc->bound += n;
     return check_launch();
 }

@@ -5,9 +5,13 @@
 //               key 0 marks an empty slot, so the one real key equal to 0
 //               (src = dst = 0) is kept in the extra slot links[cap].
 //               After a kernel completes, a slot is occupied iff count > 0.
-//   node tables NodeSlot[cap]: {id + 1, packets, degree, -}; 0 marks empty.
-//               Rows are keyed by src, columns by dst (Table 2 rows 5-9 and
-//               their reverses).
+//   node tables NodeSlot[cap + 1]: {id + 1 (u32), degree (u32), packets}; an
+//               id field of 0 marks an empty slot, so the id 0xFFFFFFFF (whose
+//               id + 1 wraps to 0) is kept in the extra slot [cap].  Rows are
+//               keyed by src, columns by dst (Table 2 rows 5-9 and their
+//               reverses).  A degree is at most the matrix's number of
+//               nonzeros; an increment that would pass 2^32 - 1 is reported as
+//               ERR_CAPACITY instead of wrapping.
 //   statistics  DevStats: the nine Table 2 quantities plus an error word.
 #pragma once
 
@@ -45,11 +49,10 @@ struct __align__(16) LinkSlot {
     u64 count;
 };
 
-struct __align__(32) NodeSlot {
-    u64 id1;  // id + 1, 0 = empty
-    u64 packets;
-    u64 degree;
-    u64 pad;
+struct __align__(16) NodeSlot {
+    u32 id1;     // id + 1, 0 = empty
+    u32 degree;  // number of distinct partners (|A|_0 1 or 1^T |A|_0)
+    u64 packets; // A 1 or 1^T A
 };
 
 // Bounds on device-side loops: a probe sequence or a spin that reaches its

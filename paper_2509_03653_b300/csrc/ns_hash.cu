@@ -26,37 +26,90 @@ struct BlockStats {
     u64 mx[5];   // max link, max src pk, max src fo, max dst pk, max dst fi
 };
 
-__device__ __forceinline__ LinkSlot* find_link(const HashView& M, u64 key) {
-    if (key == 0) return &M.links[M.link_mask + 1];
-    u64 i = mix64(key) & M.link_mask;
-    for (u32 p = 0; p < kMaxProbes; ++p) {
-        u64 old = atomicCAS(&M.links[i].key, 0ull, key);
-        if (old == 0ull || old == key) return &M.links[i];
-        i = (i + 1) & M.link_mask;
-    }
-    set_error(M.stats, ERR_CAPACITY);
-    return nullptr;
+constexpr u64 kNoSlot = ~0ull;
+
+// Home slot of a link key; key 0 lives in the extra slot [cap].
+__device__ __forceinline__ u64 link_home(const HashView& M, u64 key) {
+    return key == 0 ? M.link_mask + 1 : (mix64(key) & M.link_mask);
+}
+// Home slot of a node id; id 0xFFFFFFFF lives in the extra slot [cap].
+__device__ __forceinline__ u64 node_home(u64 mask, u32 id) {
+    return id == 0xFFFFFFFFu ? mask + 1 : (mix32(id) & mask);
 }
 
-__device__ __forceinline__ NodeSlot* find_node(NodeSlot* tbl, u64 mask, u32 id, DevStats* st) {
-    const u64 id1 = (u64)id + 1;
-    u64 i = mix32(id) & mask;
-    for (u32 p = 0; p < kMaxProbes; ++p) {
-        u64 old = atomicCAS(&tbl[i].id1, 0ull, id1);
-        if (old == 0ull || old == id1) return &tbl[i];
+// 128-bit compare-and-swap (PTX atom.cas.b128, sm_90 and later): one
+// atomic claims an empty 16-byte slot and writes both of its words.
+struct W128 {
+    u64 lo, hi;
+};
+__device__ __forceinline__ W128 cas128(void* p, u64 cmp_lo, u64 cmp_hi, u64 new_lo, u64 new_hi) {
+    W128 r;
+    asm volatile(
+        "{\n\t.reg .b128 d, c, v;\n\t"
+        "mov.b128 c, {%2, %3};\n\t"
+        "mov.b128 v, {%4, %5};\n\t"
+        "atom.cas.relaxed.gpu.b128 d, [%6], c, v;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t}"
+        : "=l"(r.lo), "=l"(r.hi)
+        : "l"(cmp_lo), "l"(cmp_hi), "l"(new_lo), "l"(new_hi), "l"(p)
+        : "memory");
+    return r;
+}
+
+// Result of adding c to the entry of a key: the slot and the entry's value
+// before the addition (0 = the entry was created by this call).
+struct Upsert {
+    u64 slot;
+    u64 prev;
+};
+
+// Link table: {key, count}.  An empty slot is {0, 0}; a claim writes {key, c}
+// in one 128-bit CAS, so a slot never holds a key with count 0.  Key 0 lives
+// in the extra slot [cap] and is only ever added to.
+__device__ __noinline__ Upsert link_probe(const HashView& M, u64 key, u64 c, u64 i) {
+    for (u32 p = 1; p < kMaxProbes; ++p) {
+        i = (i + 1) & M.link_mask;
+        const W128 o = cas128(&M.links[i], 0ull, 0ull, key, c);
+        if (o.lo == 0ull) return {i, 0ull};
+        if (o.lo == key) return {i, atomicAdd(&M.links[i].count, c)};
+    }
+    set_error(M.stats, ERR_CAPACITY);
+    return {kNoSlot, 1ull};
+}
+
+// Node table: {id + 1 (u32), degree (u32), packets}; claims write
+// {id + 1, degree 0, packets c}.  Id 0xFFFFFFFF lives in the extra slot [cap].
+__device__ __noinline__ Upsert node_probe(NodeSlot* tbl, u64 mask, u32 id1, u64 c, u64 i, DevStats* st) {
+    for (u32 p = 1; p < kMaxProbes; ++p) {
         i = (i + 1) & mask;
+        const W128 o = cas128(&tbl[i], 0ull, 0ull, (u64)id1, c);
+        if ((u32)o.lo == 0u) return {i, 0ull};
+        if ((u32)o.lo == id1) return {i, atomicAdd(&tbl[i].packets, c)};
     }
     set_error(st, ERR_CAPACITY);
-    return nullptr;
+    return {kNoSlot, 1ull};
 }
 
 __device__ __forceinline__ void smax(u64* p, u64 v) {
     if (v > *reinterpret_cast<volatile u64*>(p)) atomicMax(p, v);
 }
 
+// degree increment that refuses to wrap past 2^32 - 1
+__device__ __forceinline__ u64 degree_inc(NodeSlot* s, DevStats* st) {
+    const u32 old = atomicAdd(&s->degree, 1u);
+    if (old == 0xFFFFFFFFu) set_error(st, ERR_CAPACITY);
+    return (u64)old + 1;
+}
+
 // One item per lane; every lane of the warp must call this.  With `dedup`
 // set (raw packets, c == 1), lanes holding equal keys are merged first so a
 // hot link costs one atomic per warp instead of one per packet.
+//
+// Two dependent round trips to L2 per item: (1) the three 128-bit claims of
+// the link, row and column home slots, issued together -- a new entry is
+// complete after this, and whether the link is new is known; (2) the count
+// additions of entries that already existed and, for a new link, the degree
+// increments of its row and column, again issued together.
 __device__ __forceinline__ void insert_item(const HashView& M, bool valid, u64 key, u64 c, bool dedup,
                                             BlockStats& bs) {
     const u32 FULL = 0xFFFFFFFFu;
@@ -75,28 +128,40 @@ __device__ __forceinline__ void insert_item(const HashView& M, bool valid, u64 k
     bool newlink = false, newsrc = false, newdst = false;
     u64 cnt_new = 0, rpk = 0, rdeg = 0, cpk = 0, cdeg = 0;
     if (lead) {
-        LinkSlot* s = find_link(M, key);
-        if (s) {
-            u64 prev = atomicAdd(&s->count, cs);
-            newlink = (prev == 0);
-            cnt_new = prev + cs;
-        }
-        NodeSlot* r = find_node(M.rows, M.row_mask, (u32)(key >> 32), M.stats);
-        NodeSlot* q = find_node(M.cols, M.col_mask, (u32)key, M.stats);
-        if (r) {
-            u64 p = atomicAdd(&r->packets, cs);
-            newsrc = (p == 0);
-            rpk = p + cs;
-        }
-        if (q) {
-            u64 p = atomicAdd(&q->packets, cs);
-            newdst = (p == 0);
-            cpk = p + cs;
-        }
+        const u32 sid = (u32)(key >> 32), did = (u32)key;
+        const u64 li0 = link_home(M, key);
+        const u64 ri0 = node_home(M.row_mask, sid);
+        const u64 ci0 = node_home(M.col_mask, did);
+        const bool lside = (key == 0), rside = (sid == 0xFFFFFFFFu), cside = (did == 0xFFFFFFFFu);
+        // round trip 1
+        W128 lo = {0, 0}, ro = {0, 0}, co = {0, 0};
+        if (!lside) lo = cas128(&M.links[li0], 0ull, 0ull, key, cs);
+        if (!rside) ro = cas128(&M.rows[ri0], 0ull, 0ull, (u64)(sid + 1), cs);
+        if (!cside) co = cas128(&M.cols[ci0], 0ull, 0ull, (u64)(did + 1), cs);
+        // classify: 0 = created, 1 = existing entry found, 2 = probe on
+        const int lk = lside ? 1 : (lo.lo == 0ull ? 0 : (lo.lo == key ? 1 : 2));
+        const int rk = rside ? 1 : ((u32)ro.lo == 0u ? 0 : ((u32)ro.lo == sid + 1 ? 1 : 2));
+        const int ck = cside ? 1 : ((u32)co.lo == 0u ? 0 : ((u32)co.lo == did + 1 ? 1 : 2));
+        Upsert L = {li0, 0}, R = {ri0, 0}, C = {ci0, 0};
+        if (lk == 2) L = link_probe(M, key, cs, li0);
+        if (rk == 2) R = node_probe(M.rows, M.row_mask, sid + 1, cs, ri0, M.stats);
+        if (ck == 2) C = node_probe(M.cols, M.col_mask, did + 1, cs, ci0, M.stats);
+        // a found link cannot have count 0, so "new" is known now
+        newlink = (lk == 0) || (lk == 2 && L.slot != kNoSlot && L.prev == 0);
+        // round trip 2
+        if (lk == 1) L.prev = atomicAdd(&M.links[li0].count, cs);
+        if (rk == 1) R.prev = atomicAdd(&M.rows[ri0].packets, cs);
+        if (ck == 1) C.prev = atomicAdd(&M.cols[ci0].packets, cs);
+        if (lside) newlink = (L.prev == 0);  // the key-0 slot is only added to
         if (newlink) {
-            if (r) rdeg = atomicAdd(&r->degree, 1ull) + 1;
-            if (q) cdeg = atomicAdd(&q->degree, 1ull) + 1;
+            if (R.slot != kNoSlot) rdeg = degree_inc(&M.rows[R.slot], M.stats);
+            if (C.slot != kNoSlot) cdeg = degree_inc(&M.cols[C.slot], M.stats);
         }
+        newsrc = (R.slot != kNoSlot) && R.prev == 0;
+        newdst = (C.slot != kNoSlot) && C.prev == 0;
+        cnt_new = L.prev + cs;
+        rpk = R.prev + cs;
+        cpk = C.prev + cs;
     }
     // warp totals -> block accumulators
     const u32 nl = __popc(__ballot_sync(FULL, newlink));
@@ -143,10 +208,31 @@ __device__ __forceinline__ void block_stats_flush(BlockStats& bs, DevStats* st) 
     }
 }
 
+// After every CTA has flushed, the last one to finish copies the nine
+// quantities to `out` (the classic last-block pattern: each CTA's atomics are
+// fenced before it counts itself done).  The counter lives in the statistics
+// record and is reset by the last CTA for the next launch.
+__device__ __forceinline__ void last_block_snapshot(DevStats* st, u64* out) {
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const u64 done = atomicAdd(&st->pad[0], 1ull);
+        last = (done == (u64)gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x < S_NFIELDS) {
+        __threadfence();
+        out[threadIdx.x] = atomicAdd(&st->v[threadIdx.x], 0ull);
+    }
+    if (last && threadIdx.x == 0) st->pad[0] = 0;
+}
+
 // Raw packets: two uint32 columns (the paper's src and dst), count 1 each.
+// With `out` set, the statistics after this launch are written there.
 __global__ void __launch_bounds__(kInsertThreads) k_insert_packets(const u32* __restrict__ src,
                                                                    const u32* __restrict__ dst, u64 n,
-                                                                   HashView M) {
+                                                                   HashView M, u64* __restrict__ out) {
     __shared__ BlockStats bs;
     block_stats_init(bs);
     __syncthreads();
@@ -162,6 +248,7 @@ __global__ void __launch_bounds__(kInsertThreads) k_insert_packets(const u32* __
     }
     __syncthreads();
     block_stats_flush(bs, M.stats);
+    if (out) last_block_snapshot(M.stats, out);
 }
 
 // Entries of another hash matrix: its link table slots (count > 0 = occupied;
@@ -260,7 +347,17 @@ int grid_for(u64 n, int threads, int sms, int per_sm) {
 void launch_insert_packets(const u32* src, const u32* dst, u64 n, const HashView& M,
                            int sms, cudaStream_t s) {
     if (n == 0) return;
-    k_insert_packets<<<grid_for(n, kInsertThreads, sms, 8), kInsertThreads, 0, s>>>(src, dst, n, M);
+    k_insert_packets<<<grid_for(n, kInsertThreads, sms, 8), kInsertThreads, 0, s>>>(src, dst, n, M,
+                                                                                   nullptr);
+}
+
+void launch_insert_packets_snapshot(const u32* src, const u32* dst, u64 n, const HashView& M,
+                                    u64* out, int sms, cudaStream_t s) {
+    if (n == 0) {
+        launch_stats_out(M.stats, out, s);
+        return;
+    }
+    k_insert_packets<<<grid_for(n, kInsertThreads, sms, 8), kInsertThreads, 0, s>>>(src, dst, n, M, out);
 }
 
 void launch_insert_slots(const LinkSlot* in, u64 in_cap, const HashView& M, int sms,

@@ -53,6 +53,8 @@ int sort_radix();
 // hash path (ns_hash.cu)
 void launch_insert_packets(const u32* src, const u32* dst, u64 n, const HashView& M,
                            int sms, cudaStream_t s);
+void launch_insert_packets_snapshot(const u32* src, const u32* dst, u64 n, const HashView& M,
+                                    u64* out, int sms, cudaStream_t s);
 void launch_insert_slots(const LinkSlot* in, u64 in_cap, const HashView& M, int sms,
                          cudaStream_t s);
 void launch_insert_list(const u64* keys, const u64* counts, u64 n_bound,

@@ -9,7 +9,7 @@
 // whole device).  They still pass their own input columns and output record.
 //
 // The array below is a file-scope __device__ object: every GPU that loads
-// the library holds it (kScratchBytes, about 5 MiB) until the process exits.
+// the library holds it (kScratchBytes, about 3 MiB) until the process exits.
 // Host code must not pass its name to a kernel (on the host the name is only
 // a stand-in, not a device address); the first call on each device looks up
 // the real address with cudaGetSymbolAddress, with that device current, and
@@ -33,8 +33,8 @@ static_assert((kCap & (kCap - 1)) == 0, "capacity must be a power of two");
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kLinksOff = 0;
 constexpr size_t kRowsOff = align256(kLinksOff + (kCap + 1) * sizeof(LinkSlot));
-constexpr size_t kColsOff = align256(kRowsOff + kCap * sizeof(NodeSlot));
-constexpr size_t kStatsOff = align256(kColsOff + kCap * sizeof(NodeSlot));
+constexpr size_t kColsOff = align256(kRowsOff + (kCap + 1) * sizeof(NodeSlot));
+constexpr size_t kStatsOff = align256(kColsOff + (kCap + 1) * sizeof(NodeSlot));
 constexpr size_t kScratchBytes = align256(kStatsOff + sizeof(DevStats));
 
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];

@@ -187,3 +187,27 @@ def test_export_capacity_error(ctxs):
                                  4, ctypes.byref(got), None)
     assert st == 3  # NS_ERR_CAPACITY, nothing written
     assert got.value == oracle.stats(*oracle.build_matrix(s, d))["unique_links"]
+
+
+def test_ingest_stats_after_every_window(ctxs):
+    """ns_window_ingest_stats: the running quantities written by the last CTA
+    of each window's launch equal the oracle's quantities of the prefix."""
+    ctx = ctxs["hash"]
+    sizes = [4096, 0, 1, 70001, 12289, 3, 40000]
+    s, d = W.rmat_stream(sum(sizes))
+    s[60000:] = s[:sum(sizes) - 60000]  # repeated sources across windows
+    acc = ns.Matrix(ctx)
+    rows = torch.zeros(len(sizes), 16, dtype=torch.int64, device="cuda")
+    off = 0
+    want_rows = []
+    want = (np.zeros(0, np.uint64), np.zeros(0, np.uint64))
+    for w, n in enumerate(sizes):
+        ns.window_ingest_stats(ctx, acc, to_dev(s[off:off + n]), to_dev(d[off:off + n]), rows[w])
+        want = oracle.accumulate(want, oracle.build_matrix(s[off:off + n], d[off:off + n]))
+        want_rows.append(oracle.stats(*want))
+        off += n
+    torch.cuda.synchronize()
+    for w in range(len(sizes)):
+        assert stats_row(rows[w]) == want_rows[w], w
+    assert ns.network_stats(ctx, acc) == want_rows[-1]
+    assert_matrix_equal(acc, *want)
