@@ -195,6 +195,24 @@ ns_status ns_network_stats_async(ns_ctx* ctx, const ns_matrix* m, ns_stats* d_ou
 ns_status ns_window_stats_static(const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
                                  ns_stats* d_out, ns_stream_t stream);
 
+/* ---- tracing ----------------------------------------------------------- */
+
+/* Per-kernel timing.  While tracing is on, every kernel the context launches
+ * on a stream that is not being captured into a CUDA graph is bracketed by
+ * two CUDA events on that stream (a few microseconds of overhead per launch).
+ * ns_trace_read waits for the recorded events, writes one entry per kernel
+ * name (up to cap entries; *count receives the number of names) and forgets
+ * the records. */
+typedef struct {
+    char name[48];
+    uint64_t launches;
+    double total_ms;
+    double max_ms;
+} ns_trace_entry;
+
+ns_status ns_trace_enable(ns_ctx* ctx, int on);
+ns_status ns_trace_read(ns_ctx* ctx, ns_trace_entry* out, int cap, int* count);
+
 /* ---- errors ------------------------------------------------------------ */
 
 const char* ns_last_error(void);

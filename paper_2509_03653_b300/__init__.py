@@ -15,12 +15,13 @@ import ctypes
 
 import torch
 
-from ._native import FIELDS, NsConfig, NsError, NsStats, check, load
+from ._native import FIELDS, NsConfig, NsError, NsStats, NsTraceEntry, check, load
 
 __all__ = [
     "FIELDS", "NsError", "Context", "Matrix", "window_build", "accumulate", "window_ingest",
     "window_ingest_stats", "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
     "matrix_clear", "sync", "PATHS", "window_stats_static", "STATIC_MAX_PACKETS",
+    "trace_enable", "trace_read",
 ]
 
 STATIC_MAX_PACKETS = 32768  # NS_STATIC_MAX_PACKETS in include/ns.h
@@ -194,3 +195,19 @@ def window_stats_static(src: torch.Tensor, dst: torch.Tensor, out: torch.Tensor,
     L = load()
     check(L.ns_window_stats_static(_column(src, "src"), _column(dst, "dst"), n, ctypes.c_void_p(out.data_ptr()),
                                    _stream(stream)), "ns_window_stats_static")
+
+
+def trace_enable(ctx: Context, on: bool = True):
+    """Per-kernel timing of the context's launches (ns_trace_enable)."""
+    check(ctx._L.ns_trace_enable(ctx.handle, 1 if on else 0), "ns_trace_enable")
+
+
+def trace_read(ctx: Context) -> dict:
+    """{kernel name: (launches, total ms, max ms)} since the last read
+    (ns_trace_read; waits for the recorded events)."""
+    cap = 64
+    buf = (NsTraceEntry * cap)()
+    cnt = ctypes.c_int()
+    check(ctx._L.ns_trace_read(ctx.handle, buf, cap, ctypes.byref(cnt)), "ns_trace_read")
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms), float(buf[i].max_ms))
+            for i in range(min(cnt.value, cap))}

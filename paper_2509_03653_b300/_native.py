@@ -26,6 +26,11 @@ class NsStats(ctypes.Structure):
 
 FIELDS = tuple(f for f, _ in NsStats._fields_)
 
+
+class NsTraceEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", U64), ("total_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double)]
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "ns_create": (ST, [ctypes.POINTER(P), ctypes.POINTER(NsConfig), I32]),
@@ -44,6 +49,8 @@ SIGNATURES = {
     "ns_network_stats": (ST, [P, P, ctypes.POINTER(NsStats), P]),
     "ns_network_stats_async": (ST, [P, P, P, P]),
     "ns_window_stats_static": (ST, [P, P, U64, P, P]),
+    "ns_trace_enable": (ST, [P, I32]),
+    "ns_trace_read": (ST, [P, ctypes.POINTER(NsTraceEntry), I32, ctypes.POINTER(I32)]),
     "ns_last_error": (ctypes.c_char_p, []),
     "ns_status_string": (ctypes.c_char_p, [ST]),
 }

@@ -146,7 +146,10 @@ ns_status hash_grow(ns_matrix* m, u64 extra, cudaStream_t s) {
     CK(cudaMemsetAsync(tmp.rows.p, 0, (tmp.node_cap + 1) * sizeof(NodeSlot), s));
     CK(cudaMemsetAsync(tmp.cols.p, 0, (tmp.node_cap + 1) * sizeof(NodeSlot), s));
     CK(cudaMemsetAsync(m->stats.p, 0, sizeof(DevStats), s));
-    launch_insert_slots((const LinkSlot*)m->links.p, m->link_cap, hash_view(&tmp), m->ctx->sms, s);
+    {
+        TraceScope ts(&m->ctx->tracer, "k_insert_slots", s);
+        launch_insert_slots((const LinkSlot*)m->links.p, m->link_cap, hash_view(&tmp), m->ctx->sms, s);
+    }
     TRY(check_launch());
     CK(cudaStreamSynchronize(s));
     buf_free(m->links);
@@ -176,6 +179,7 @@ ns_status to_hash(ns_matrix* m, u64 extra, cudaStream_t s) {
         CK(cudaMemcpyAsync(nnz_copy, &((DevStats*)m->stats.p)->v[S_LINKS], sizeof(u64),
                            cudaMemcpyDeviceToDevice, s));
         TRY(hash_clear(m, s));
+        TraceScope ts(&c->tracer, "k_insert_list", s);
         launch_insert_list((const u64*)m->keys.p, (const u64*)m->counts.p, have, nnz_copy,
                            hash_view(m), c->sms, s);
         TRY(check_launch());
@@ -229,12 +233,12 @@ ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n,
     launch_runs(RUN_U64, false, kb[r], nullptr, n, nullptr, (u64*)out->keys.p,
                 (u64*)c->pos.p, nullptr, nnz, c->sc, st, s);
     launch_run_stats(RS_LINKS, (const u64*)c->pos.p, nullptr, nnz, n, (u64*)out->counts.p,
-                     st, c->sms, s);
+                     st, c->sms, &c->tracer, s);
     // rows: runs of equal src over the source-major list (rows 5-9)
     launch_runs(RUN_SRC_OF_U64, true, out->keys.p, (const u64*)out->counts.p, n, nnz, nullptr,
                 (u64*)c->pos.p, (u64*)c->psum.p, runs_out, c->sc, st, s);
     launch_run_stats(RS_ROWS, (const u64*)c->pos.p, (const u64*)c->psum.p, runs_out, n,
-                     nullptr, st, c->sms, s);
+                     nullptr, st, c->sms, &c->tracer, s);
     // columns: (dst, count) sorted by dst, then runs (the reverse operations)
     u32* ck[2] = {(u32*)c->k32[0].p, (u32*)c->k32[1].p};
     u64* cv[2] = {(u64*)c->v64[0].p, (u64*)c->v64[1].p};
@@ -243,7 +247,7 @@ ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n,
     launch_runs(RUN_U32, true, ck[r2], cv[r2], n, nnz, nullptr, (u64*)c->pos.p,
                 (u64*)c->psum.p, runs_out + 1, c->sc, st, s);
     launch_run_stats(RS_COLS, (const u64*)c->pos.p, (const u64*)c->psum.p, runs_out + 1, n,
-                     nullptr, st, c->sms, s);
+                     nullptr, st, c->sms, &c->tracer, s);
     return check_launch();
 }
 
@@ -254,6 +258,7 @@ ns_status build_hash(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n,
     out->fmt = FMT_HASH;
     out->bound = n;
     if (n == 0) return NS_OK;
+    TraceScope ts(&c->tracer, "k_insert_packets", s);
     launch_insert_packets(src, dst, n, hash_view(out), c->sms, s);
     return check_launch();
 }
@@ -318,6 +323,7 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
     x->sc.tag = 0;
     x->sc.status = nullptr;
     x->sc.status_words = 0;
+    x->sc.tr = &x->tracer;
     *out = x;
     return NS_OK;
 }
@@ -330,6 +336,7 @@ void ns_destroy(ns_ctx* c) {
                   &c->pos, &c->psum, &c->k32[0], &c->k32[1], &c->v64[0], &c->v64[1], &c->xk, &c->xv};
     for (Buf* b : all) buf_free(*b);
     if (c->host_stats) cudaFreeHost(c->host_stats);
+    tracer_destroy(&c->tracer);
     delete c;
 }
 
@@ -427,6 +434,7 @@ ns_status ns_matrix_export(const ns_matrix* m, uint64_t* d_keys, uint64_t* d_cou
         u64* cnt = (u64*)c->counters.p + 2;
         CK(cudaMemsetAsync(cnt, 0, sizeof(u64), s));
         DevStats* st = (DevStats*)m->stats.p;
+        TraceScope ts(&c->tracer, "k_compact_links", s);
         launch_compact_links((const LinkSlot*)m->links.p, m->link_cap, (u64*)c->xk.p,
                              (u64*)c->xv.p, cnt, nnz, st, c->sms, s);
         u64* kb[2] = {(u64*)c->k64[0].p, (u64*)d_keys};
@@ -461,8 +469,10 @@ ns_status ns_accumulate(ns_ctx* c, ns_matrix* acc, const ns_matrix* add, ns_stre
     }
     TRY(to_hash(acc, add->bound, s));
     if (add->fmt == FMT_HASH) {
+        TraceScope ts(&c->tracer, "k_insert_slots", s);
         launch_insert_slots((const LinkSlot*)add->links.p, add->link_cap, hash_view(acc), c->sms, s);
     } else if (add->fmt == FMT_LIST && add->bound > 0) {
+        TraceScope ts(&c->tracer, "k_insert_list", s);
         launch_insert_list((const u64*)add->keys.p, (const u64*)add->counts.p, add->bound,
                            &((const DevStats*)add->stats.p)->v[S_LINKS], hash_view(acc), c->sms, s);
     }
@@ -478,6 +488,7 @@ ns_status ns_window_ingest(ns_ctx* c, ns_matrix* acc, const uint32_t* d_src, con
     cudaStream_t s = (cudaStream_t)stream;
     TRY(to_hash(acc, n, s));
     if (n == 0) return NS_OK;
+    TraceScope ts(&c->tracer, "k_insert_packets", s);
     launch_insert_packets(d_src, d_dst, n, hash_view(acc), c->sms, s);
     acc->bound += n;
     return check_launch();
@@ -491,7 +502,10 @@ ns_status ns_window_ingest_stats(ns_ctx* c, ns_matrix* acc, const uint32_t* d_sr
     if (acc->ctx != c) return fail(NS_ERR_INVALID, "ns_window_ingest_stats: foreign matrix");
     cudaStream_t s = (cudaStream_t)stream;
     TRY(to_hash(acc, n, s));
-    launch_insert_packets_snapshot(d_src, d_dst, n, hash_view(acc), (u64*)d_out, c->sms, s);
+    {
+        TraceScope ts(&c->tracer, "k_insert_packets", s);
+        launch_insert_packets_snapshot(d_src, d_dst, n, hash_view(acc), (u64*)d_out, c->sms, s);
+    }
     acc->bound += n;
     return check_launch();
 }
@@ -507,6 +521,7 @@ ns_status ns_network_stats(ns_ctx* c, const ns_matrix* m, ns_stats* h_out, ns_st
 
 ns_status ns_network_stats_async(ns_ctx* c, const ns_matrix* m, ns_stats* d_out, ns_stream_t stream) {
     if (!c || !m || !d_out) return fail(NS_ERR_INVALID, "ns_network_stats_async: NULL argument");
+    TraceScope ts(&c->tracer, "k_stats_out", (cudaStream_t)stream);
     launch_stats_out((const DevStats*)m->stats.p, (u64*)d_out, (cudaStream_t)stream);
     return check_launch();
 }

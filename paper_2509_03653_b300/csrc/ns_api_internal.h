@@ -33,6 +33,7 @@ struct ns_ctx {
     ns::Buf ghist, offs, tcount, counters, status;
     ns::Buf k64[2], pos, psum, k32[2], v64[2], xk, xv;
     ns::DevStats* host_stats = nullptr;  // pinned
+    ns::Tracer tracer;
 };
 
 // A traffic matrix.  Hash format: link/row/column tables with incrementally

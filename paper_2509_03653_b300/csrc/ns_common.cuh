@@ -103,4 +103,56 @@ __device__ __forceinline__ u64 ld_volatile(const u64* p) {
 }
 __device__ __forceinline__ void st_volatile(u64* p, u64 v) { *reinterpret_cast<volatile u64*>(p) = v; }
 
+// ---- shared-memory staging with the bulk-copy (TMA) engine ----------------
+// A 1-D cp.async.bulk copy moves a contiguous global range into shared memory
+// and signals an mbarrier; both addresses must be 16-byte aligned and the
+// size a multiple of 16 bytes.
+
+__device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(u64* bar, u32 count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(u64* bar, u32 bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, u32 bytes, u64* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test_wait(u64* bar, u32 parity) {
+    u32 ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for an mbarrier phase.  If the bound is reached the error is
+// recorded and the wait continues, again bounded, so that no copy is still
+// landing in shared memory when the CTA retires.
+constexpr u32 kMaxBarrierPolls = 1u << 22;
+__device__ __forceinline__ void mbar_wait_bounded(u64* bar, u32 parity, DevStats* st) {
+    for (u32 i = 0; i < kMaxBarrierPolls; ++i) {
+        if (mbar_test_wait(bar, parity)) return;
+        if (i > 64) __nanosleep(32);
+    }
+    set_error(st, ERR_TIMEOUT);
+    for (u32 i = 0; i < kMaxBarrierPolls; ++i) {
+        if (mbar_test_wait(bar, parity)) return;
+        __nanosleep(64);
+    }
+}
+
 }  // namespace ns

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "ns_common.cuh"
@@ -24,7 +26,31 @@ struct SortIn {
     const u32* src;
     const u32* dst;
     const u64* n_dev;
+    bool bulk;  // every input address is 16-byte aligned: stage tiles with bulk copies
 };
+
+// Per-kernel timing (ns_trace.cu): a TraceScope around a launch records an
+// event pair on the launch stream when the context's tracer is on and the
+// stream is not capturing.
+struct Tracer {
+    struct Rec {
+        const char* name;
+        cudaEvent_t a, b;
+    };
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<Rec> recs;
+};
+struct TraceScope {
+    TraceScope(Tracer* t, const char* name, cudaStream_t s);
+    ~TraceScope();
+    Tracer* t;
+    const char* name;
+    cudaStream_t s;
+    cudaEvent_t a;
+};
+void tracer_destroy(Tracer* t);
 
 // Per-context scratch of the sort path.
 struct SortScratch {
@@ -35,6 +61,7 @@ struct SortScratch {
     u32* tile_counters;  // [16]
     u32 tag;             // last look-back tag issued
     int sms;
+    Tracer* tr;          // the context's tracer (may be off)
 };
 
 // Look-back tags are 16 bits; when they wrap, the status words are cleared
@@ -77,6 +104,6 @@ void launch_runs(int keymode, bool has_v, const void* keys, const u64* vals, u64
                  const u64* n_dev, u64* head_keys, u64* pos, u64* psum,
                  u64* R_out, SortScratch& sc, DevStats* st, cudaStream_t s);
 void launch_run_stats(int mode, const u64* pos, const u64* psum, const u64* R_ptr,
-                      u64 bound, u64* counts_out, DevStats* st, int sms, cudaStream_t s);
+                      u64 bound, u64* counts_out, DevStats* st, int sms, Tracer* tr, cudaStream_t s);
 
 }  // namespace ns

@@ -127,22 +127,28 @@ __device__ __forceinline__ K load_key(const SortIn& in, u64 i) {
 
 // ---- histogram of every digit pass ------------------------------------------
 
+// Each warp counts into its own copy of the histograms (fewer shared-memory
+// atomic collisions on skewed keys); the copies are summed before the one
+// global addition per bin and CTA.
 template <typename K, int LOAD>
 __global__ void __launch_bounds__(kThreads) k_sort_hist(SortIn in, u64 n_arg, int begin_bit, int passes,
                                                          u32* __restrict__ ghist) {
-    __shared__ u32 h[8][kRadix];
+    extern __shared__ __align__(16) u32 hs[];  // [kWarps][passes][kRadix]
     const u64 n = in.n_dev ? *in.n_dev : n_arg;
-    for (int i = threadIdx.x; i < 8 * kRadix; i += kThreads) (&h[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kWarps * passes * kRadix; i += kThreads) hs[i] = 0;
     __syncthreads();
+    u32* h = hs + (threadIdx.x >> 5) * passes * kRadix;
     const u64 stride = (u64)gridDim.x * kThreads;
     for (u64 i = (u64)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
         const K k = load_key<K, LOAD>(in, i);
-        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(u32)(k >> (begin_bit + 8 * p)) & 0xFF], 1u);
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p * kRadix + ((u32)(k >> (begin_bit + 8 * p)) & 0xFF)], 1u);
     }
     __syncthreads();
-    for (int p = 0; p < passes; ++p) {
-        const u32 c = h[p][threadIdx.x];
-        if (c) atomicAdd(&ghist[p * kRadix + threadIdx.x], c);
+    for (int i = threadIdx.x; i < passes * kRadix; i += kThreads) {
+        u32 c = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) c += hs[w * passes * kRadix + i];
+        if (c) atomicAdd(&ghist[i], c);
     }
 }
 
@@ -160,49 +166,113 @@ __global__ void __launch_bounds__(kThreads) k_sort_offsets(const u32* __restrict
 }
 
 // ---- one digit pass -----------------------------------------------------------
+//
+// One tile per CTA, tiles handed out in launch order by an atomic counter.
+// The tile is staged into shared memory by the bulk-copy engine (no register
+// is held while it streams in), ranked stably per warp, given its global
+// per-digit offsets by decoupled look-back, placed in digit order in the same
+// buffer and written out in digit runs.  (Reserving a second tile ahead of
+// time for double buffering was measured slower: successors then wait on a
+// tile whose count cannot be published until its CTA gets to it.)
 
 template <typename K, bool HAS_V>
 struct ScatterSmem {
-    K keys[kTile];
+    K keys[kTile];  // staged tile, then the tile in digit order
     u64 vals[HAS_V ? kTile : 1];
-    u32 whist[kWarps][kRadix];
+    unsigned short whist[kWarps][kRadix];  // per-warp digit counts (<= 512)
     u32 lstart[kRadix];
     u64 gbase[kRadix];
     u32 wsum[kWarps];
     u32 total;
     u32 tile;
+    u64 bar;
 };
 
+// Stages tile [base, base + tile_n) into shared memory.  With `bulk`, thread
+// 0 issues bulk copies of the 16-byte-aligned prefix and the threads load the
+// ragged tail (< 4 elements); otherwise all threads load.  Packed mode stages
+// the two uint32 columns side by side in the key buffer's bytes.
 template <typename K, bool HAS_V, int LOAD>
-__global__ void __launch_bounds__(kThreads) k_onesweep(SortIn in, K* __restrict__ kout,
-                                                        u64* __restrict__ vout, u64 n_arg, int shift,
-                                                        const u64* __restrict__ offs,
-                                                        u64* __restrict__ status, u32* tile_counter,
-                                                        u32 tag, DevStats* st) {
+__device__ __forceinline__ void stage_tile(const SortIn& in, ScatterSmem<K, HAS_V>& sm, u64 base, u32 tile_n,
+                                           bool bulk, DevStats* st) {
+    u32* s32 = reinterpret_cast<u32*>(sm.keys);
+    constexpr u32 kq = (LOAD == LOAD_PACK) ? 4u : (16u / (u32)sizeof(K));
+    const u32 nb = bulk ? (tile_n & ~(kq - 1)) : 0u;
+    const u32 nv = (bulk && HAS_V) ? (tile_n & ~1u) : 0u;
+    if (bulk && threadIdx.x == 0) {
+        u32 bytes;
+        if constexpr (LOAD == LOAD_PACK) bytes = 2u * nb * 4u;
+        else bytes = nb * (u32)sizeof(K) + nv * 8u;
+        mbar_arrive_expect_tx(&sm.bar, bytes);
+        if (nb) {
+            if constexpr (LOAD == LOAD_PACK) {
+                bulk_g2s(s32, in.src + base, nb * 4u, &sm.bar);
+                bulk_g2s(s32 + kTile, in.dst + base, nb * 4u, &sm.bar);
+            } else {
+                bulk_g2s(sm.keys, reinterpret_cast<const K*>(in.keys) + base, nb * (u32)sizeof(K), &sm.bar);
+            }
+        }
+        if constexpr (HAS_V && LOAD != LOAD_PACK) {
+            if (nv) bulk_g2s(sm.vals, in.vals + base, nv * 8u, &sm.bar);
+        }
+    }
+    for (u32 i = nb + threadIdx.x; i < tile_n; i += kThreads) {
+        if constexpr (LOAD == LOAD_PACK) {
+            s32[i] = in.src[base + i];
+            s32[kTile + i] = in.dst[base + i];
+        } else if constexpr (LOAD == LOAD_DST_OF) {
+            sm.keys[i] = (K)(u32)(reinterpret_cast<const u64*>(in.keys)[base + i]);
+        } else {
+            sm.keys[i] = reinterpret_cast<const K*>(in.keys)[base + i];
+        }
+    }
+    if constexpr (HAS_V && LOAD != LOAD_PACK) {
+        for (u32 i = nv + threadIdx.x; i < tile_n; i += kThreads) sm.vals[i] = in.vals[base + i];
+    }
+    if (bulk) mbar_wait_bounded(&sm.bar, 0, st);
+}
+
+template <typename K, bool HAS_V, int LOAD>
+__global__ void __launch_bounds__(kThreads, HAS_V ? 3 : 4) k_onesweep(SortIn in, K* __restrict__ kout,
+                                                                       u64* __restrict__ vout, u64 n_arg, int shift,
+                                                                       const u64* __restrict__ offs,
+                                                                       u64* __restrict__ status, u32* tile_counter,
+                                                                       u32 tag, DevStats* st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem<K, HAS_V>& sm = *reinterpret_cast<ScatterSmem<K, HAS_V>*>(smem_raw);
     const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const u32 FULL = 0xFFFFFFFFu;
-
     const u64 n = in.n_dev ? *in.n_dev : n_arg;
-    if (threadIdx.x == 0) sm.tile = atomicAdd(tile_counter, 1u);
+    // bulk copies only for aligned inputs, and never for the u64 -> u32 mode
+    const bool bulk = in.bulk && LOAD != LOAD_DST_OF;
+
+    if (threadIdx.x == 0) {
+        sm.tile = atomicAdd(tile_counter, 1u);
+        mbar_init(&sm.bar, 1);
+    }
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&sm.whist[0][0])[i] = 0;
     __syncthreads();
     const u64 tile = sm.tile;
     const u64 base = tile * kTile;
     if (base >= n) return;  // launched for an upper bound; nothing to publish
+    const u32 tile_n = (u32)((n - base) < (u64)kTile ? (n - base) : (u64)kTile);
 
-    // warp-striped load: warp w owns items [base + w*kItems*32, +kItems*32)
+    stage_tile<K, HAS_V, LOAD>(in, sm, base, tile_n, bulk, st);
+    __syncthreads();
+
+    // warp w owns tile items [w*kItems*32, +kItems*32), read consecutively
     K k[kItems];
     u64 v[kItems];
     u32 rank[kItems];
-    const u64 wbase = base + (u64)w * kItems * 32;
+    const u32 w0 = w * kItems * 32;
+    const u32* s32 = reinterpret_cast<const u32*>(sm.keys);
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
-        const u64 i = wbase + (u64)j * 32 + lane;
-        if (i < n) {
-            k[j] = load_key<K, LOAD>(in, i);
-            if constexpr (HAS_V) v[j] = in.vals[i];
+        const u32 li = w0 + j * 32 + lane;
+        if (li < tile_n) {
+            if constexpr (LOAD == LOAD_PACK) k[j] = (K)(((u64)s32[li] << 32) | (u64)s32[kTile + li]);
+            else k[j] = sm.keys[li];
+            if constexpr (HAS_V) v[j] = sm.vals[li];
         } else {
             k[j] = 0;
             if constexpr (HAS_V) v[j] = 0;
@@ -212,8 +282,8 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(SortIn in, K* __restrict_
     const u32 lt = lanemask_lt();
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
-        const u64 i = wbase + (u64)j * 32 + lane;
-        const bool valid = i < n;
+        const u32 li = w0 + j * 32 + lane;
+        const bool valid = li < tile_n;
         const u32 d = valid ? ((u32)(k[j] >> shift) & 0xFF) : 0x100u;
         const u32 peers = __match_any_sync(FULL, d);
         u32 before = 0;
@@ -221,7 +291,7 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(SortIn in, K* __restrict_
         __syncwarp();
         if (valid) {
             rank[j] = before + __popc(peers & lt);
-            if ((peers & lt) == 0) sm.whist[w][d] = before + __popc(peers);
+            if ((peers & lt) == 0) sm.whist[w][d] = (unsigned short)(before + __popc(peers));
         }
         __syncwarp();
     }
@@ -233,7 +303,7 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(SortIn in, K* __restrict_
 #pragma unroll
     for (int ww = 0; ww < kWarps; ++ww) {
         const u32 c = sm.whist[ww][d];
-        sm.whist[ww][d] = run;
+        sm.whist[ww][d] = (unsigned short)run;
         run += c;
     }
     // publish this tile's count early so successors can proceed
@@ -248,11 +318,11 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(SortIn in, K* __restrict_
     sm.gbase[d] = offs[d] + prefix;
     __syncthreads();
 
-    // place keys in tile-local sorted order
+    // place keys in tile-local digit order
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
-        const u64 i = wbase + (u64)j * 32 + lane;
-        if (i < n) {
+        const u32 li = w0 + j * 32 + lane;
+        if (li < tile_n) {
             const u32 dj = (u32)(k[j] >> shift) & 0xFF;
             const u32 pos = sm.lstart[dj] + sm.whist[w][dj] + rank[j];
             if (pos < (u32)kTile) {
@@ -265,7 +335,6 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(SortIn in, K* __restrict_
 
     // write out: consecutive smem positions of one digit go to consecutive
     // global positions
-    const u64 tile_n = (n - base) < (u64)kTile ? (n - base) : (u64)kTile;
     for (u32 i = threadIdx.x; i < tile_n; i += kThreads) {
         const K key = sm.keys[i];
         const u32 dk = (u32)(key >> shift) & 0xFF;
@@ -286,20 +355,26 @@ __device__ __forceinline__ u64 run_key(const void* keys, u64 i) {
     else return reinterpret_cast<const u32*>(keys)[i];
 }
 
+template <bool HAS_V>
 struct RunsSmem {
-    u64 key[kTile + 1];
-    u64 val[kTile];
-    u64 wsum64[kWarps];
-    u32 wsum[kWarps];
-    u64 tot64;
+    u64 key[kTile + 1];         // key[0] = the element before the tile
+    u64 val[HAS_V ? kTile : 1];
+    u32 wcnt[kWarps];           // heads per warp -> exclusive offsets
+    u64 wsum[kWarps];           // value sums per warp -> exclusive offsets
+    u64 cbase, sbase, tot64;
     u32 tot;
     u32 tile;
-    u64 cbase, sbase;
 };
 
 // For each run head i (i == 0 or key(i) != key(i-1)), in order r = 0, 1, ...:
 //   pos[r] = i, psum[r] = sum of val[0..i) (if HAS_V), head_keys[r] = key(i)
 // and finally pos[R] = n, psum[R] = total, *R_out = R.
+//
+// Warp w owns the tile's items [512 w, 512 w + 512), visited as 16 rounds
+// of 32 consecutive items, so every shared-memory access is consecutive
+// across the lanes; heads are counted with ballots, value prefixes with
+// shuffle scans.  Two sweeps over the tile: count, then (after the tile's
+// offsets are known by look-back) write.
 template <int KEYMODE, bool HAS_V>
 __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys,
                                                     const u64* __restrict__ vals, u64 n_arg,
@@ -309,7 +384,9 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
                                                     u64* status_s, u32* tile_counter, u32 tag,
                                                     u64* R_out, DevStats* st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    RunsSmem& sm = *reinterpret_cast<RunsSmem*>(smem_raw);
+    RunsSmem<HAS_V>& sm = *reinterpret_cast<RunsSmem<HAS_V>*>(smem_raw);
+    const u32 FULL = 0xFFFFFFFFu;
+    const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const u64 n = n_dev ? *n_dev : n_arg;
     if (threadIdx.x == 0) sm.tile = atomicAdd(tile_counter, 1u);
     __syncthreads();
@@ -326,30 +403,53 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
     }
     const u64 tile_n = (n - base) < (u64)kTile ? (n - base) : (u64)kTile;
 
-    // coalesced load into shared memory; key[0] is the element before the tile
     for (u32 i = threadIdx.x; i < tile_n; i += kThreads) {
         sm.key[i + 1] = run_key<KEYMODE>(keys, base + i);
         if constexpr (HAS_V) sm.val[i] = vals[base + i];
     }
-    if (threadIdx.x == 0) sm.key[0] = base > 0 ? run_key<KEYMODE>(keys, base - 1) : 0;
+    if (threadIdx.x == 0) sm.key[0] = base > 0 ? run_key<KEYMODE>(keys, base - 1) : ~0ull;
     __syncthreads();
 
-    // blocked: thread t owns tile items [t*kItems, (t+1)*kItems)
-    const u32 t0 = threadIdx.x * kItems;
-    u32 heads = 0;
-    u64 vsum = 0;
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-        const u32 li = t0 + j;
+    // sweep 1: heads and value sums per warp
+    const u32 w0 = w * (kItems * 32);
+    u32 cnt = 0;
+    u64 vs = 0;
+#pragma unroll 4
+    for (int r = 0; r < kItems; ++r) {
+        const u32 li = w0 + r * 32 + lane;
+        bool h = false;
         if (li < tile_n) {
-            const bool h = (base + li == 0) || sm.key[li + 1] != sm.key[li];
-            heads += h;
-            if constexpr (HAS_V) vsum += sm.val[li];
+            h = (base + li == 0) || sm.key[li + 1] != sm.key[li];
+            if constexpr (HAS_V) vs += sm.val[li];
         }
+        cnt += __popc(__ballot_sync(FULL, h));
     }
-    u32 hx = block_excl_scan(heads, sm.wsum, &sm.tot);
-    u64 sx = 0;
-    if constexpr (HAS_V) sx = block_excl_scan64(vsum, sm.wsum64, &sm.tot64);
+    if constexpr (HAS_V) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vs += __shfl_xor_sync(FULL, vs, o);
+    }
+    if (lane == 0) {
+        sm.wcnt[w] = cnt;
+        if constexpr (HAS_V) sm.wsum[w] = vs;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u32 c = 0;
+        u64 s = 0;
+        for (int i = 0; i < kWarps; ++i) {
+            const u32 tc = sm.wcnt[i];
+            sm.wcnt[i] = c;
+            c += tc;
+            if constexpr (HAS_V) {
+                const u64 ts = sm.wsum[i];
+                sm.wsum[i] = s;
+                s += ts;
+            }
+        }
+        sm.tot = c;
+        sm.tot64 = s;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         st_volatile(&status_c[tile], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, sm.tot));
         u64 c = 0;
@@ -369,24 +469,42 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
         sm.sbase = s;
     }
     __syncthreads();
-    u64 r = sm.cbase + hx;
-    u64 s = HAS_V ? sm.sbase + sx : 0;
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-        const u32 li = t0 + j;
+
+    // sweep 2: write heads in order
+    u64 r_run = sm.cbase + sm.wcnt[w];
+    u64 s_run = HAS_V ? sm.sbase + sm.wsum[w] : 0;
+    const u32 lt = lanemask_lt();
+#pragma unroll 4
+    for (int r = 0; r < kItems; ++r) {
+        const u32 li = w0 + r * 32 + lane;
+        bool h = false;
+        u64 v = 0;
         if (li < tile_n) {
-            const u64 i = base + li;
-            const bool h = (i == 0) || sm.key[li + 1] != sm.key[li];
-            if (h) {
-                if (r < n) {  // R <= n unless a look-back gave up
-                    pos[r] = i;
-                    if constexpr (HAS_V) psum[r] = s;
-                    if (head_keys) head_keys[r] = sm.key[li + 1];
-                }
-                ++r;
-            }
-            if constexpr (HAS_V) s += sm.val[li];
+            h = (base + li == 0) || sm.key[li + 1] != sm.key[li];
+            if constexpr (HAS_V) v = sm.val[li];
         }
+        const u32 bal = __ballot_sync(FULL, h);
+        u64 vex = 0, vtot = 0;
+        if constexpr (HAS_V) {
+            u64 x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const u64 y = __shfl_up_sync(FULL, x, o);
+                if (lane >= (u32)o) x += y;
+            }
+            vex = x - v;
+            vtot = __shfl_sync(FULL, x, 31);
+        }
+        if (h) {
+            const u64 rr = r_run + __popc(bal & lt);
+            if (rr < n) {  // R <= n unless a look-back gave up
+                pos[rr] = base + li;
+                if constexpr (HAS_V) psum[rr] = s_run + vex;
+                if (head_keys) head_keys[rr] = sm.key[li + 1];
+            }
+        }
+        r_run += __popc(bal);
+        s_run += vtot;
     }
     if (base + tile_n == n && threadIdx.x == 0) {
         const u64 R = min(sm.cbase + sm.tot, n);
@@ -451,27 +569,34 @@ __global__ void __launch_bounds__(256) k_run_stats(const u64* __restrict__ pos,
     }
 }
 
+template <typename K, bool HAS_V>
+constexpr const char* onesweep_name() {
+    if constexpr (sizeof(K) == 4) return "k_onesweep<u32 key, u64 value>";
+    else if constexpr (HAS_V) return "k_onesweep<u64 key, u64 value>";
+    else return "k_onesweep<u64 key>";
+}
+
 template <typename K, bool HAS_V, int LOAD>
-void launch_onesweep(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs,
-                     u64* status, u32* tile_counter, u32 tag, DevStats* st, cudaStream_t s) {
+void launch_onesweep(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
+                     u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s) {
     const size_t smem = sizeof(ScatterSmem<K, HAS_V>);
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_onesweep<K, HAS_V, LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        cudaFuncSetAttribute(k_onesweep<K, HAS_V, LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = true;
     }
     const u64 tiles = (n + kTile - 1) / kTile;
     if (tiles == 0) return;
-    k_onesweep<K, HAS_V, LOAD><<<(unsigned)tiles, kThreads, smem, s>>>(in, kout, vout, n, shift, offs,
-                                                                     status, tile_counter, tag, st);
+    TraceScope ts(tr, onesweep_name<K, HAS_V>(), s);
+    k_onesweep<K, HAS_V, LOAD><<<(unsigned)tiles, kThreads, smem, s>>>(in, kout, vout, n, shift, offs, status,
+                                                                       tile_counter, tag, st);
 }
 
 template <int KEYMODE, bool HAS_V>
 void launch_runs_t(const void* keys, const u64* vals, u64 n, const u64* n_dev, u64* head_keys, u64* pos, u64* psum,
                    u64* status_c, u64* status_s, u32* tile_counter, u32 tag, u64* R_out, DevStats* st,
-                   cudaStream_t s) {
-    const size_t smem = sizeof(RunsSmem);
+                   Tracer* tr, cudaStream_t s) {
+    const size_t smem = sizeof(RunsSmem<HAS_V>);
     static bool configured = false;
     if (!configured) {
         cudaFuncSetAttribute(k_runs<KEYMODE, HAS_V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -480,6 +605,8 @@ void launch_runs_t(const void* keys, const u64* vals, u64 n, const u64* n_dev, u
     }
     u64 tiles = (n + kTile - 1) / kTile;
     if (tiles == 0) tiles = 1;
+    TraceScope ts(tr, KEYMODE == RUN_U64 ? "k_runs<links>" : (KEYMODE == RUN_SRC_OF_U64 ? "k_runs<rows>" : "k_runs<cols>"),
+                  s);
     k_runs<KEYMODE, HAS_V><<<(unsigned)tiles, kThreads, smem, s>>>(
         keys, vals, n, n_dev, head_keys, pos, psum, status_c, status_s, tile_counter, tag, R_out, st);
 }
@@ -497,24 +624,39 @@ int radix_sort_t(const SortIn& in, K* kbuf[2], u64* vbuf[2], u64 n, int begin_bi
                  SortScratch& sc, DevStats* st, cudaStream_t s) {
     cudaMemsetAsync(sc.ghist, 0, sizeof(u32) * 8 * kRadix, s);
     cudaMemsetAsync(sc.tile_counters, 0, sizeof(u32) * 8, s);
-    const int hist_grid = (int)std::min<u64>((n + kThreads * 8 - 1) / (kThreads * 8), (u64)sc.sms * 4);
-    k_sort_hist<K, LOAD><<<hist_grid < 1 ? 1 : hist_grid, kThreads, 0, s>>>(in, n, begin_bit, passes,
-                                                                           sc.ghist);
-    k_sort_offsets<<<1, kThreads, 0, s>>>(sc.ghist, passes, sc.offs);
+    const int hist_grid = (int)std::min<u64>((n + kThreads * 8 - 1) / (kThreads * 8), (u64)sc.sms * 3);
+    {
+        const size_t hsmem = sizeof(u32) * kWarps * passes * kRadix;
+        static bool hconf = false;
+        if (!hconf) {
+            cudaFuncSetAttribute(k_sort_hist<K, LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(u32) * kWarps * 8 * kRadix));
+            hconf = true;
+        }
+        TraceScope ts(sc.tr, "k_sort_hist", s);
+        k_sort_hist<K, LOAD><<<hist_grid < 1 ? 1 : hist_grid, kThreads, hsmem, s>>>(in, n, begin_bit, passes,
+                                                                                   sc.ghist);
+    }
+    {
+        TraceScope ts(sc.tr, "k_sort_offsets", s);
+        k_sort_offsets<<<1, kThreads, 0, s>>>(sc.ghist, passes, sc.offs);
+    }
     for (int p = 0; p < passes; ++p) {
         const u32 tag = next_tag(sc, s);
         const int shift = begin_bit + 8 * p;
         if (p == 0) {
             launch_onesweep<K, HAS_V, LOAD>(in, kbuf[0], vbuf[0], n, shift, sc.offs, sc.status,
-                                            sc.tile_counters + p, tag, st, s);
+                                            sc.tile_counters + p, tag, st, sc.tr, s);
         } else {
             SortIn mid{};
             mid.keys = kbuf[(p - 1) & 1];
             mid.vals = vbuf[(p - 1) & 1];
             mid.n_dev = in.n_dev;
-            launch_onesweep<K, HAS_V, LOAD_KEYS>(mid, kbuf[p & 1], vbuf[p & 1], n, shift,
-                                                 sc.offs + p * kRadix, sc.status, sc.tile_counters + p,
-                                                 tag, st, s);
+            // a caller's output buffer can be one of the ping-pong buffers:
+            // stage with bulk copies only from 16-byte-aligned addresses
+            mid.bulk = (((uintptr_t)kbuf[(p - 1) & 1] | (uintptr_t)vbuf[(p - 1) & 1]) & 15) == 0;
+            launch_onesweep<K, HAS_V, LOAD_KEYS>(mid, kbuf[p & 1], vbuf[p & 1], n, shift, sc.offs + p * kRadix,
+                                                 sc.status, sc.tile_counters + p, tag, st, sc.tr, s);
         }
     }
     return (passes - 1) & 1;
@@ -525,6 +667,7 @@ int radix_sort_packets(const u32* src, const u32* dst, u64* kbuf[2], u64 n,
     SortIn in{};
     in.src = src;
     in.dst = dst;
+    in.bulk = (((uintptr_t)src | (uintptr_t)dst) & 15) == 0;
     u64* vb[2] = {nullptr, nullptr};
     return radix_sort_t<u64, false, LOAD_PACK>(in, (u64**)kbuf, vb, n, 0, 8, sc, st, s);
 }
@@ -536,6 +679,7 @@ int radix_sort_pairs64(const u64* keys, const u64* vals, const u64* n_dev,
     in.keys = keys;
     in.vals = (const u64*)vals;
     in.n_dev = (const u64*)n_dev;
+    in.bulk = (((uintptr_t)keys | (uintptr_t)vals) & 15) == 0;
     return radix_sort_t<u64, true, LOAD_KEYS>(in, (u64**)kbuf, (u64**)vbuf, n, 0, 8, sc, st, s);
 }
 
@@ -560,20 +704,22 @@ void launch_runs(int keymode, bool has_v, const void* keys, const u64* vals, u64
     u32* tc = sc.tile_counters + 8;
     if (keymode == RUN_U64 && !has_v)
         launch_runs_t<RUN_U64, false>(keys, (const u64*)vals, n, nd, (u64*)head_keys, (u64*)pos,
-                                      (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, s);
+                                      (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, sc.tr, s);
     else if (keymode == RUN_SRC_OF_U64 && has_v)
         launch_runs_t<RUN_SRC_OF_U64, true>(keys, (const u64*)vals, n, nd, (u64*)head_keys, (u64*)pos,
-                                            (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, s);
+                                            (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, sc.tr, s);
     else if (keymode == RUN_U32 && has_v)
         launch_runs_t<RUN_U32, true>(keys, (const u64*)vals, n, nd, (u64*)head_keys, (u64*)pos,
-                                     (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, s);
+                                     (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, sc.tr, s);
 }
 
 void launch_run_stats(int mode, const u64* pos, const u64* psum, const u64* R_ptr,
-                      u64 bound, u64* counts_out, DevStats* st, int sms, cudaStream_t s) {
+                      u64 bound, u64* counts_out, DevStats* st, int sms, Tracer* tr, cudaStream_t s) {
     u64 want = (bound + 255) / 256;
     u64 cap = (u64)sms * 8;
     int grid = (int)(want < 1 ? 1 : (want < cap ? want : cap));
+    TraceScope ts(tr, mode == RS_LINKS ? "k_run_stats<links>" : (mode == RS_ROWS ? "k_run_stats<rows>" : "k_run_stats<cols>"),
+                  s);
     if (mode == RS_LINKS)
         k_run_stats<RS_LINKS><<<grid, 256, 0, s>>>((const u64*)pos, (const u64*)psum,
                                                   (const u64*)R_ptr, (u64*)counts_out, st);

@@ -1,0 +1,107 @@
+// ns_trace.cu -- per-kernel timing (the library's tracing subsystem).
+//
+// When tracing is on, every kernel a context launches on a stream that is not
+// being captured into a graph is bracketed by two CUDA events on that stream;
+// ns_trace_read waits for the recorded events and returns, per kernel name,
+// the launch count and the total and largest elapsed time.
+#include <cstring>
+#include <map>
+#include <string>
+
+#include "ns.h"
+#include "ns_api_internal.h"
+#include "ns_kernels.h"
+
+namespace ns {
+
+cudaEvent_t tracer_event(Tracer* t) {
+    if (t->used == t->pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        t->pool.push_back(e);
+    }
+    return t->pool[t->used++];
+}
+
+TraceScope::TraceScope(Tracer* tr, const char* nm, cudaStream_t st) : t(tr), name(nm), s(st), a(nullptr) {
+    if (!t || !t->on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return;
+    }
+    a = tracer_event(t);
+    if (a && cudaEventRecord(a, s) != cudaSuccess) {
+        cudaGetLastError();
+        a = nullptr;
+    }
+}
+
+TraceScope::~TraceScope() {
+    if (!a) return;
+    cudaEvent_t b = tracer_event(t);
+    if (!b || cudaEventRecord(b, s) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    t->recs.push_back({name, a, b});
+}
+
+void tracer_destroy(Tracer* t) {
+    for (cudaEvent_t e : t->pool) cudaEventDestroy(e);
+    t->pool.clear();
+    t->recs.clear();
+    t->used = 0;
+}
+
+}  // namespace ns
+
+extern "C" {
+
+ns_status ns_trace_enable(ns_ctx* c, int on) {
+    if (!c) return ns::set_fail(NS_ERR_INVALID, "ns_trace_enable: NULL context");
+    c->tracer.on = on != 0;
+    return NS_OK;
+}
+
+ns_status ns_trace_read(ns_ctx* c, ns_trace_entry* out, int cap, int* count) {
+    if (!c || !count || (cap > 0 && !out)) return ns::set_fail(NS_ERR_INVALID, "ns_trace_read: NULL argument");
+    struct Agg {
+        uint64_t n = 0;
+        double total = 0, mx = 0;
+    };
+    std::map<std::string, Agg> agg;
+    ns_status st = NS_OK;
+    for (const auto& r : c->tracer.recs) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            st = ns::set_fail(NS_ERR_CUDA, "ns_trace_read: event query failed");
+            continue;
+        }
+        Agg& g = agg[r.name];
+        g.n += 1;
+        g.total += ms;
+        if (ms > g.mx) g.mx = ms;
+    }
+    c->tracer.recs.clear();
+    c->tracer.used = 0;
+    int i = 0;
+    for (const auto& kv : agg) {
+        if (i < cap) {
+            memset(&out[i], 0, sizeof(ns_trace_entry));
+            strncpy(out[i].name, kv.first.c_str(), sizeof(out[i].name) - 1);
+            out[i].launches = kv.second.n;
+            out[i].total_ms = kv.second.total;
+            out[i].max_ms = kv.second.mx;
+        }
+        ++i;
+    }
+    *count = i;
+    return st;
+}
+
+}  // extern "C"

@@ -211,3 +211,54 @@ def test_ingest_stats_after_every_window(ctxs):
         assert stats_row(rows[w]) == want_rows[w], w
     assert ns.network_stats(ctx, acc) == want_rows[-1]
     assert_matrix_equal(acc, *want)
+
+
+def test_trace_counts_kernels(ctxs):
+    ctx = ctxs["sort"]
+    ns.trace_enable(ctx, True)
+    m = ns.Matrix(ctx)
+    s, d = W.single_window(50000)
+    ns.window_build(ctx, to_dev(s), to_dev(d), m)
+    tr = ns.trace_read(ctx)
+    ns.trace_enable(ctx, False)
+    assert tr["k_onesweep<u64 key>"][0] == 8
+    assert tr["k_onesweep<u32 key, u64 value>"][0] == 4
+    assert tr["k_runs<links>"][0] == 1 and tr["k_run_stats<cols>"][0] == 1
+    assert all(v[1] >= 0 and v[2] >= 0 for v in tr.values())
+    assert ns.trace_read(ctx) == {}
+
+
+def test_export_into_unaligned_buffers(ctxs):
+    """ns_matrix_export into caller buffers that start 8 bytes past a 16-byte
+    boundary (the sort stages such buffers with plain loads)."""
+    import ctypes
+    for path in PATHS:
+        ctx = ctxs[path]
+        s, d = W.single_window(30000)
+        m = ns.Matrix(ctx)
+        ns.window_build(ctx, to_dev(s), to_dev(d), m)
+        want = oracle.build_matrix(s, d)
+        nnz = want[0].size
+        kb = torch.zeros(nnz + 2, dtype=torch.int64, device="cuda")
+        cb = torch.zeros(nnz + 2, dtype=torch.int64, device="cuda")
+        got = ctypes.c_uint64()
+        st = ctx._L.ns_matrix_export(m.handle, ctypes.c_void_p(kb.data_ptr() + 8), ctypes.c_void_p(cb.data_ptr() + 8),
+                                     nnz, ctypes.byref(got), None)
+        assert st == 0 and got.value == nnz
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(kb[1:nnz + 1].cpu().numpy().view(np.uint64), want[0])
+        np.testing.assert_array_equal(cb[1:nnz + 1].cpu().numpy().view(np.uint64), want[1])
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_window_from_unaligned_columns(ctxs, path):
+    """Packet columns that start 4 bytes past a 16-byte boundary."""
+    s, d = W.single_window(20001)
+    ds = to_dev(np.concatenate([[0], s]).astype(np.uint32))[1:]
+    dd = to_dev(np.concatenate([[0], d]).astype(np.uint32))[1:]
+    ctx = ctxs[path]
+    m = ns.Matrix(ctx)
+    ns.window_build(ctx, ds, dd, m)
+    want = oracle.build_matrix(s, d)
+    assert ns.network_stats(ctx, m) == oracle.stats(*want)
+    assert_matrix_equal(m, *want)
