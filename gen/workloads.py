@@ -82,9 +82,13 @@ def batched_plan(k: int = W4_WINDOWS, lo: float = 10.0, hi: float = 20.0):
 
 
 def batched_window(w: int, n: int, s: float, K: int = W4_K, src=None, dst=None):
-    """Window w of workload 4 (its own seed)."""
+    """Window w of workload 4: its own Zipf draws (own seed), one anonymizing
+    bijection shared by all windows."""
     seed = gen.splitmix64(seed_of(4) * 0x10001 + w)
-    return zipf_window(n, s, K, seed, src=src, dst=dst)
+    key = gen.bijection_key(seed_of(4))
+    src = gen.zipf_addresses(n, s, K, seed, 100, key, out=src)
+    dst = gen.zipf_addresses(n, s, K, seed, 101, key, out=dst)
+    return src, dst
 
 
 def serving_plan(k: int, rate: float):

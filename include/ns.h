@@ -116,6 +116,14 @@ ns_status ns_matrix_create(ns_ctx* ctx, ns_matrix** out);
  * Optional: tables also grow on demand.  Enqueued on `stream`. */
 ns_status ns_matrix_reserve(ns_matrix* m, uint64_t max_links, ns_stream_t stream);
 
+/* As ns_matrix_reserve, for an empty matrix, with a promise that A will
+ * never have more than max_nodes distinct sources nor more than max_nodes
+ * distinct destinations (e.g. the size of the address space in use), so the
+ * per-source and per-destination tables can be sized by it rather than by
+ * the number of links.  If the promise is broken, inserts that find no room
+ * are dropped and the next blocking call returns NS_ERR_CAPACITY. */
+ns_status ns_matrix_reserve_ex(ns_matrix* m, uint64_t max_links, uint64_t max_nodes, ns_stream_t stream);
+
 /* Makes the matrix empty (A = 0) keeping its memory.  Enqueued on stream. */
 ns_status ns_matrix_clear(ns_matrix* m, ns_stream_t stream);
 
@@ -168,6 +176,54 @@ ns_status ns_network_stats(ns_ctx* ctx, const ns_matrix* m, ns_stats* h_out, ns_
  * errors surface on the next blocking call. */
 ns_status ns_network_stats_async(ns_ctx* ctx, const ns_matrix* m, ns_stats* d_out,
                                  ns_stream_t stream);
+
+/* ---- batched windows ----------------------------------------------------- */
+
+/* Many independent windows at once: the windows are laid end to end in two
+ * uint32 columns, window w being packets [h_offsets[w], h_offsets[w+1]).
+ * Each window's nine quantities (Table 2, of that window alone) are written
+ * to d_window_stats[w], and, if acc is not NULL, acc := acc + sum_w A_w (the
+ * running aggregate).  Persistent segmented launches process all windows:
+ * CTAs take fixed-size tiles of packets in window order, each window's tables
+ * are carved from one arena, and windows are grouped into chunks that fit it.
+ * Results are bit-identical to ns_window_build + ns_network_stats per window
+ * and ns_accumulate into acc. */
+typedef struct ns_batch ns_batch;
+
+/* Launch parameters the autotuner chooses (ns_batch_tune). */
+typedef struct {
+    uint32_t tile_packets; /* packets per CTA work item (multiple of 32) */
+    uint32_t ctas_per_sm;  /* persistent CTAs per SM */
+    double max_load;       /* per-window table load bound, in [0.5, 0.9] */
+} ns_batch_params;
+
+/* A plan for batches of at most max_windows windows and max_packets packets:
+ * allocates the arena (capped by the context's hbm_budget_bytes), the
+ * per-window metadata and statistics.  Parameters come from the context's
+ * tuner cache when it has an entry for this GPU and batch shape. */
+ns_status ns_batch_create(ns_ctx* ctx, uint64_t max_windows, uint64_t max_packets, ns_batch** out);
+void ns_batch_free(ns_batch* batch);
+ns_status ns_batch_get_params(const ns_batch* batch, ns_batch_params* out);
+ns_status ns_batch_set_params(ns_batch* batch, const ns_batch_params* params);
+
+/* Runs one batch (see above).  h_offsets is host memory of windows + 1
+ * entries, starting at 0 and non-decreasing; d_window_stats is a device array
+ * of `windows` ns_stats.  acc must have room reserved for the batch's links
+ * if this call is captured into a CUDA graph (growing it needs a blocking
+ * read).  Asynchronous; allocates nothing. */
+ns_status ns_batch_run(ns_ctx* ctx, ns_batch* batch, const uint32_t* d_src, const uint32_t* d_dst,
+                       const uint64_t* h_offsets, uint64_t windows, ns_stats* d_window_stats,
+                       ns_matrix* acc, ns_stream_t stream);
+
+/* Autotuner: times ns_batch_run on this batch for every combination of tile
+ * size {1024..16384}, CTAs per SM {4, 8, 16} and load bound {0.5, 0.7},
+ * keeps the fastest in the plan, returns it in *chosen (may be NULL) and
+ * stores it in the context's tuner cache file keyed by GPU name and batch
+ * shape.  d_scratch_stats: `windows` device ns_stats for the trial runs.
+ * Blocking. */
+ns_status ns_batch_tune(ns_ctx* ctx, ns_batch* batch, const uint32_t* d_src, const uint32_t* d_dst,
+                        const uint64_t* h_offsets, uint64_t windows, ns_stats* d_scratch_stats,
+                        ns_stream_t stream, ns_batch_params* chosen);
 
 /* ---- statistics without device allocation ------------------------------ */
 

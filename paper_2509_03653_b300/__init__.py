@@ -15,13 +15,13 @@ import ctypes
 
 import torch
 
-from ._native import FIELDS, NsConfig, NsError, NsStats, NsTraceEntry, check, load
+from ._native import FIELDS, NsBatchParams, NsConfig, NsError, NsStats, NsTraceEntry, check, load
 
 __all__ = [
     "FIELDS", "NsError", "Context", "Matrix", "window_build", "accumulate", "window_ingest",
     "window_ingest_stats", "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
     "matrix_clear", "sync", "PATHS", "window_stats_static", "STATIC_MAX_PACKETS",
-    "trace_enable", "trace_read",
+    "trace_enable", "trace_read", "Batch", "batch_run", "batch_tune", "matrix_reserve_ex",
 ]
 
 STATIC_MAX_PACKETS = 32768  # NS_STATIC_MAX_PACKETS in include/ns.h
@@ -211,3 +211,75 @@ def trace_read(ctx: Context) -> dict:
     check(ctx._L.ns_trace_read(ctx.handle, buf, cap, ctypes.byref(cnt)), "ns_trace_read")
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms), float(buf[i].max_ms))
             for i in range(min(cnt.value, cap))}
+
+
+def matrix_reserve_ex(m: Matrix, max_links: int, max_nodes: int, stream=None):
+    """Reserve with a promise on the number of sources/destinations
+    (ns_matrix_reserve_ex)."""
+    check(m._L.ns_matrix_reserve_ex(m.handle, max_links, max_nodes, _stream(stream)), "ns_matrix_reserve_ex")
+
+
+class Batch:
+    """A plan for batched windows (ns_batch_create / ns_batch_free)."""
+
+    def __init__(self, ctx: Context, max_windows: int, max_packets: int):
+        self._L = ctx._L
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        check(self._L.ns_batch_create(ctx.handle, max_windows, max_packets, ctypes.byref(h)), "ns_batch_create")
+        self.handle = h
+
+    @property
+    def params(self) -> dict:
+        p = NsBatchParams()
+        check(self._L.ns_batch_get_params(self.handle, ctypes.byref(p)), "ns_batch_get_params")
+        return {"tile_packets": p.tile_packets, "ctas_per_sm": p.ctas_per_sm, "max_load": p.max_load}
+
+    def set_params(self, tile_packets: int, ctas_per_sm: int, max_load: float):
+        p = NsBatchParams(tile_packets, ctas_per_sm, max_load)
+        check(self._L.ns_batch_set_params(self.handle, ctypes.byref(p)), "ns_batch_set_params")
+
+    def free(self):
+        if getattr(self, "handle", None):
+            self._L.ns_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _offsets(offsets):
+    import numpy as _np
+    off = _np.ascontiguousarray(offsets, dtype=_np.uint64)
+    return off, off.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+
+
+def batch_run(ctx: Context, batch: Batch, src: torch.Tensor, dst: torch.Tensor, offsets, out: torch.Tensor,
+              acc: Matrix | None = None, stream=None):
+    """Per-window quantities of a batch into `out` (device, int64, windows x
+    >= 9, contiguous rows of 9) and optionally acc += the sum (ns_batch_run).
+    `offsets` (host, windows + 1) must stay alive until the stream reaches the
+    call's copy; keep a reference."""
+    off, ptr = _offsets(offsets)
+    W = off.size - 1
+    if out.element_size() != 8 or out.numel() < 9 * W or not out.is_contiguous():
+        raise ValueError("out must be a contiguous 64-bit tensor with >= 9 * windows elements")
+    check(ctx._L.ns_batch_run(ctx.handle, batch.handle, _column(src, "src"), _column(dst, "dst"), ptr, W,
+                              ctypes.c_void_p(out.data_ptr()), acc.handle if acc is not None else None,
+                              _stream(stream)), "ns_batch_run")
+    return off
+
+
+def batch_tune(ctx: Context, batch: Batch, src: torch.Tensor, dst: torch.Tensor, offsets, stream=None) -> dict:
+    """Autotune the batch's launch parameters on this batch (ns_batch_tune)."""
+    off, ptr = _offsets(offsets)
+    W = off.size - 1
+    scratch = torch.empty(max(9 * W, 9), dtype=torch.int64, device=src.device)
+    p = NsBatchParams()
+    check(ctx._L.ns_batch_tune(ctx.handle, batch.handle, _column(src, "src"), _column(dst, "dst"), ptr, W,
+                               ctypes.c_void_p(scratch.data_ptr()), _stream(stream), ctypes.byref(p)),
+          "ns_batch_tune")
+    return {"tile_packets": p.tile_packets, "ctas_per_sm": p.ctas_per_sm, "max_load": p.max_load}

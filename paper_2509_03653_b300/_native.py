@@ -27,6 +27,10 @@ class NsStats(ctypes.Structure):
 FIELDS = tuple(f for f, _ in NsStats._fields_)
 
 
+class NsBatchParams(ctypes.Structure):
+    _fields_ = [("tile_packets", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("max_load", ctypes.c_double)]
+
+
 class NsTraceEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", U64), ("total_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double)]
@@ -51,6 +55,13 @@ SIGNATURES = {
     "ns_window_stats_static": (ST, [P, P, U64, P, P]),
     "ns_trace_enable": (ST, [P, I32]),
     "ns_trace_read": (ST, [P, ctypes.POINTER(NsTraceEntry), I32, ctypes.POINTER(I32)]),
+    "ns_matrix_reserve_ex": (ST, [P, U64, U64, P]),
+    "ns_batch_create": (ST, [P, U64, U64, ctypes.POINTER(P)]),
+    "ns_batch_free": (None, [P]),
+    "ns_batch_get_params": (ST, [P, ctypes.POINTER(NsBatchParams)]),
+    "ns_batch_set_params": (ST, [P, ctypes.POINTER(NsBatchParams)]),
+    "ns_batch_run": (ST, [P, P, P, P, ctypes.POINTER(U64), U64, P, P, P]),
+    "ns_batch_tune": (ST, [P, P, P, P, ctypes.POINTER(U64), U64, P, P, ctypes.POINTER(NsBatchParams)]),
     "ns_last_error": (ctypes.c_char_p, []),
     "ns_status_string": (ctypes.c_char_p, [ST]),
 }

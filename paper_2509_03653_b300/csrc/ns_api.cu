@@ -74,6 +74,16 @@ void buf_free(Buf& b) {
 
 ns_status set_fail(ns_status s, const char* msg) { return fail(s, "%s", msg); }
 
+ns_status fail_fmt(ns_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
 ns_status check_launch() {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(NS_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
@@ -92,17 +102,21 @@ HashView hash_view(const ns_matrix* m) {
     return v;
 }
 
-// Allocates hash tables for at least `links` nonzeros at load <= 1/2 (rows and
-// columns sized alike, since sources, destinations <= links).  Contents are
-// undefined until cleared.
+// Sets the matrix's active table capacities for at least `links` nonzeros at
+// load <= 1/2, and for at least min(links, node_limit) sources and as many
+// destinations (sources, destinations <= links; node_limit is the caller's
+// optional promise, 0 = none).  Allocations only grow; a smaller active
+// capacity reuses them, so clearing and scanning cost what this window needs.
+// Contents are undefined until cleared.
 ns_status hash_alloc(ns_matrix* m, u64 links) {
     const u64 cap = next_pow2(std::max<u64>(2 * links, 1024));
-    if (m->link_cap >= cap && m->links.p) return NS_OK;
+    const u64 nodes = m->node_limit ? std::min<u64>(links, m->node_limit) : links;
+    const u64 ncap = next_pow2(std::max<u64>(2 * nodes, 1024));
     TRY(buf_reserve(m->links, (cap + 1) * sizeof(LinkSlot)));
-    TRY(buf_reserve(m->rows, (cap + 1) * sizeof(NodeSlot)));
-    TRY(buf_reserve(m->cols, (cap + 1) * sizeof(NodeSlot)));
+    TRY(buf_reserve(m->rows, (ncap + 1) * sizeof(NodeSlot)));
+    TRY(buf_reserve(m->cols, (ncap + 1) * sizeof(NodeSlot)));
     m->link_cap = cap;
-    m->node_cap = cap;
+    m->node_cap = ncap;
     return NS_OK;
 }
 
@@ -141,6 +155,7 @@ ns_status hash_grow(ns_matrix* m, u64 extra, cudaStream_t s) {
     ns_matrix tmp;
     tmp.ctx = m->ctx;
     tmp.stats = m->stats;
+    tmp.node_limit = m->node_limit;
     TRY(hash_alloc(&tmp, actual + extra));
     CK(cudaMemsetAsync(tmp.links.p, 0, (tmp.link_cap + 1) * sizeof(LinkSlot), s));
     CK(cudaMemsetAsync(tmp.rows.p, 0, (tmp.node_cap + 1) * sizeof(NodeSlot), s));
@@ -373,6 +388,13 @@ ns_status ns_matrix_reserve(ns_matrix* m, uint64_t max_links, ns_stream_t stream
     }
     if (m->fmt == FMT_HASH) return hash_grow(m, max_links > m->bound ? max_links - m->bound : 0, s);
     return NS_OK;
+}
+
+ns_status ns_matrix_reserve_ex(ns_matrix* m, uint64_t max_links, uint64_t max_nodes, ns_stream_t stream) {
+    if (!m) return fail(NS_ERR_INVALID, "ns_matrix_reserve_ex: NULL matrix");
+    if (m->fmt != FMT_EMPTY) return fail(NS_ERR_STATE, "ns_matrix_reserve_ex: matrix is not empty");
+    m->node_limit = max_nodes;
+    return ns_matrix_reserve(m, max_links, stream);
 }
 
 ns_status ns_matrix_clear(ns_matrix* m, ns_stream_t stream) {

@@ -18,6 +18,10 @@ struct Buf {
 enum { FMT_EMPTY = 0, FMT_HASH = 1, FMT_LIST = 2 };
 
 ns_status buf_reserve(Buf& b, size_t bytes);
+ns_status fail_fmt(ns_status s, const char* fmt, ...);
+ns_status to_hash(ns_matrix* m, u64 extra, cudaStream_t s);
+ns_status check_launch();
+HashView hash_view(const ns_matrix* m);
 void buf_free(Buf& b);
 ns_status check_launch();
 ns_status set_fail(ns_status s, const char* msg);
@@ -47,5 +51,6 @@ struct ns_matrix {
     uint64_t link_cap = 0, node_cap = 0;
     ns::Buf keys, counts;
     ns::Buf stats;       // ns::DevStats
-    uint64_t bound = 0;  // host-side upper bound on the number of nonzeros
+    uint64_t bound = 0;       // host-side upper bound on the number of nonzeros
+    uint64_t node_limit = 0;  // caller's bound on sources and destinations (0 = none)
 };

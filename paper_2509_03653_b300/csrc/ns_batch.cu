@@ -1,0 +1,349 @@
+// ns_batch.cu -- batched windows (persistent segmented launches) and the
+// autotuner that picks their launch parameters.
+//
+// A batch is a list of independent windows laid end to end in two uint32
+// columns, window w being packets [off[w], off[w+1]).  Each window gets its
+// own link/row/column tables, carved from one arena at per-window offsets;
+// per-window statistics come out of the same incremental inserts the hash
+// path uses.  Windows are grouped into chunks whose tables fit the arena; a
+// chunk costs one memset of its tables, one persistent insert launch and, if
+// the caller passed an accumulator, one launch adding the chunk's distinct
+// links into it.  Nothing here blocks or allocates after ns_batch_create, so
+// a run can be captured into a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "ns.h"
+#include "ns_api_internal.h"
+#include "ns_kernels.h"
+
+using namespace ns;
+
+struct ns_batch {
+    ns_ctx* ctx = nullptr;
+    uint64_t max_windows = 0, max_packets = 0;
+    ns_batch_params params{4096, 4, 0.5};
+    Buf meta;                  // win_off, tile_off, tab_off, tab_cap: 4 x (max_windows + 1) u64
+    u64* h_meta = nullptr;       // pinned staging of the same
+    Buf links, rows, cols;     // the arena
+    uint64_t arena_slots = 0;  // slots per table kind
+    Buf wstats;                // DevStats x max_windows
+    Buf counter;               // tile counters, one per chunk
+    uint64_t max_chunks = 0;
+};
+
+namespace {
+
+u64 pow2_at_least(u64 x) {
+    u64 p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// table capacity of one window: power of two, load <= max_load, >= 64 slots
+u64 window_cap(u64 n, double max_load) {
+    const double want = std::ceil((double)n / max_load);
+    return pow2_at_least(std::max<u64>((u64)want, 64));
+}
+
+struct Chunk {
+    u64 w0, w1;      // windows [w0, w1)
+    u64 slots;       // arena slots used (per table kind)
+    u64 tiles;
+    u64 packets;
+};
+
+// ---- tuner cache: one line per entry, "key": {"T": t, "per_sm": c, "load": l}
+
+std::string tuner_key(int device, u64 windows, u64 packets) {
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, device);
+    const int wb = windows ? (int)std::log2((double)windows) : 0;
+    const int mb = (windows && packets) ? (int)std::log2((double)packets / (double)windows) : 0;
+    char buf[384];
+    snprintf(buf, sizeof buf, "%.200s|batch|windows2^%d|mean2^%d", prop.name, wb, mb);
+    return buf;
+}
+
+std::map<std::string, ns_batch_params> tuner_read(const std::string& path) {
+    std::map<std::string, ns_batch_params> m;
+    if (path.empty()) return m;
+    FILE* f = fopen(path.c_str(), "r");
+    if (!f) return m;
+    char line[1024];
+    while (fgets(line, sizeof line, f)) {
+        char* q1 = strchr(line, '"');
+        if (!q1) continue;
+        char* q2 = strchr(q1 + 1, '"');
+        if (!q2) continue;
+        std::string key(q1 + 1, q2);
+        unsigned t = 0, c = 0;
+        double l = 0;
+        const char* pt = strstr(q2, "\"T\":");
+        const char* pc = strstr(q2, "\"per_sm\":");
+        const char* pl = strstr(q2, "\"load\":");
+        if (!pt || !pc || !pl) continue;
+        if (sscanf(pt + 4, "%u", &t) != 1 || sscanf(pc + 9, "%u", &c) != 1 || sscanf(pl + 7, "%lf", &l) != 1) continue;
+        m[key] = ns_batch_params{t, c, l};
+    }
+    fclose(f);
+    return m;
+}
+
+void tuner_write(const std::string& path, const std::map<std::string, ns_batch_params>& m) {
+    if (path.empty()) return;
+    const std::string tmp = path + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    fprintf(f, "{\n");
+    size_t i = 0;
+    for (const auto& kv : m) {
+        fprintf(f, "  \"%s\": {\"T\": %u, \"per_sm\": %u, \"load\": %.3f}%s\n", kv.first.c_str(), kv.second.tile_packets,
+                kv.second.ctas_per_sm, kv.second.max_load, ++i < m.size() ? "," : "");
+    }
+    fprintf(f, "}\n");
+    fclose(f);
+    rename(tmp.c_str(), path.c_str());
+}
+
+bool params_ok(const ns_batch_params& p) {
+    return p.tile_packets >= 256 && p.tile_packets <= (1u << 20) && (p.tile_packets % 32) == 0 &&
+           p.ctas_per_sm >= 1 && p.ctas_per_sm <= 32 && p.max_load > 0.05 && p.max_load <= 0.9;
+}
+
+ns_status plan(ns_batch* b, const uint64_t* h_off, u64 W, std::vector<Chunk>& chunks) {
+    chunks.clear();
+    u64* win_off = b->h_meta;
+    u64* tile_off = win_off + (b->max_windows + 1);
+    u64* tab_off = tile_off + (b->max_windows + 1);
+    u64* tab_cap = tab_off + (b->max_windows + 1);
+    const u64 T = b->params.tile_packets;
+    Chunk cur{0, 0, 0, 0, 0};
+    for (u64 w = 0; w < W; ++w) {
+        const u64 n = h_off[w + 1] - h_off[w];
+        const u64 cap = window_cap(n, b->params.max_load);
+        if (cap + 1 > b->arena_slots)
+            return fail_fmt(NS_ERR_CAPACITY, "ns_batch_run: window %llu (%llu packets) needs %llu table slots, "
+                            "the arena holds %llu", (unsigned long long)w, (unsigned long long)n,
+                            (unsigned long long)(cap + 1), (unsigned long long)b->arena_slots);
+        if (cur.slots + cap + 1 > b->arena_slots) {
+            chunks.push_back(cur);
+            cur = Chunk{w, w, 0, 0, 0};
+        }
+        win_off[w] = h_off[w];
+        tile_off[w] = cur.tiles;  // relative to the chunk's first window
+        tab_off[w] = cur.slots;
+        tab_cap[w] = cap;
+        cur.slots += cap + 1;
+        cur.tiles += (n + T - 1) / T;
+        cur.packets += n;
+        cur.w1 = w + 1;
+    }
+    win_off[W] = W ? h_off[W] : 0;
+    if (W) chunks.push_back(cur);
+    // tile offsets are relative to each chunk's first window; the kernel's
+    // binary search never reads the entry after a chunk's last window (the
+    // chunk's tile total is passed separately)
+    if (chunks.size() > b->max_chunks) return fail_fmt(NS_ERR_CAPACITY, "ns_batch_run: too many chunks");
+    return NS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ns_status ns_batch_create(ns_ctx* c, uint64_t max_windows, uint64_t max_packets, ns_batch** out) {
+    if (!c || !out) return set_fail(NS_ERR_INVALID, "ns_batch_create: NULL argument");
+    if (max_windows == 0) return set_fail(NS_ERR_INVALID, "ns_batch_create: max_windows == 0");
+    *out = nullptr;
+    ns_batch* b = new ns_batch();
+    b->ctx = c;
+    b->max_windows = max_windows;
+    b->max_packets = max_packets;
+    // tuned parameters for this shape, if the cache has them
+    auto cache = tuner_read(c->tuner_cache);
+    auto it = cache.find(tuner_key(c->device, max_windows, max_packets));
+    if (it != cache.end() && params_ok(it->second)) b->params = it->second;
+    // arena: enough for every window at the smallest load the tuner tries,
+    // capped by the context's HBM budget
+    const double min_load = 0.5;
+    const u64 need = (u64)std::ceil(2.0 * (double)max_packets / min_load) + 65 * max_windows;
+    const u64 budget_slots = c->cfg.hbm_budget_bytes / (sizeof(LinkSlot) + 2 * sizeof(NodeSlot));
+    b->arena_slots = std::max<u64>(std::min(need, budget_slots), 1024);
+    b->max_chunks = max_windows;
+    ns_status st = buf_reserve(b->meta, 4 * (max_windows + 1) * sizeof(u64));
+    if (st == NS_OK) st = buf_reserve(b->links, b->arena_slots * sizeof(LinkSlot));
+    if (st == NS_OK) st = buf_reserve(b->rows, b->arena_slots * sizeof(NodeSlot));
+    if (st == NS_OK) st = buf_reserve(b->cols, b->arena_slots * sizeof(NodeSlot));
+    if (st == NS_OK) st = buf_reserve(b->wstats, max_windows * sizeof(DevStats));
+    if (st == NS_OK) st = buf_reserve(b->counter, max_windows * sizeof(u32));
+    if (st == NS_OK && cudaMallocHost((void**)&b->h_meta, 4 * (max_windows + 1) * sizeof(u64)) != cudaSuccess) {
+        cudaGetLastError();
+        st = set_fail(NS_ERR_OOM, "ns_batch_create: pinned staging allocation failed");
+    }
+    if (st != NS_OK) {
+        ns_batch_free(b);
+        return st;
+    }
+    *out = b;
+    return NS_OK;
+}
+
+void ns_batch_free(ns_batch* b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    buf_free(b->meta);
+    buf_free(b->links);
+    buf_free(b->rows);
+    buf_free(b->cols);
+    buf_free(b->wstats);
+    buf_free(b->counter);
+    if (b->h_meta) cudaFreeHost(b->h_meta);
+    delete b;
+}
+
+ns_status ns_batch_get_params(const ns_batch* b, ns_batch_params* out) {
+    if (!b || !out) return set_fail(NS_ERR_INVALID, "ns_batch_get_params: NULL argument");
+    *out = b->params;
+    return NS_OK;
+}
+
+ns_status ns_batch_set_params(ns_batch* b, const ns_batch_params* p) {
+    if (!b || !p) return set_fail(NS_ERR_INVALID, "ns_batch_set_params: NULL argument");
+    if (!params_ok(*p)) return set_fail(NS_ERR_INVALID, "ns_batch_set_params: parameters out of range");
+    if (p->max_load < 0.5 - 1e-9) return set_fail(NS_ERR_INVALID, "ns_batch_set_params: max_load below 0.5");
+    b->params = *p;
+    return NS_OK;
+}
+
+ns_status ns_batch_run(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uint32_t* d_dst,
+                       const uint64_t* h_offsets, uint64_t windows, ns_stats* d_window_stats, ns_matrix* acc,
+                       ns_stream_t stream) {
+    if (!c || !b || !h_offsets || !d_window_stats) return set_fail(NS_ERR_INVALID, "ns_batch_run: NULL argument");
+    if (b->ctx != c || (acc && acc->ctx != c)) return set_fail(NS_ERR_INVALID, "ns_batch_run: foreign object");
+    if (windows > b->max_windows) return set_fail(NS_ERR_INVALID, "ns_batch_run: more windows than the batch plan");
+    if (windows == 0) return NS_OK;
+    if (h_offsets[0] != 0) return set_fail(NS_ERR_INVALID, "ns_batch_run: offsets must start at 0");
+    for (u64 w = 0; w < windows; ++w)
+        if (h_offsets[w + 1] < h_offsets[w]) return set_fail(NS_ERR_INVALID, "ns_batch_run: offsets decrease");
+    const u64 total = h_offsets[windows];
+    if (total > b->max_packets) return set_fail(NS_ERR_INVALID, "ns_batch_run: more packets than the batch plan");
+    if (total > 0 && (!d_src || !d_dst)) return set_fail(NS_ERR_INVALID, "ns_batch_run: NULL input");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<Chunk> chunks;
+    ns_status st = plan(b, h_offsets, windows, chunks);
+    if (st != NS_OK) return st;
+    if (acc) {
+        st = to_hash(acc, total, s);
+        if (st != NS_OK) return st;
+    }
+    const u64 M1 = b->max_windows + 1;
+    u64* dm = (u64*)b->meta.p;
+    if (cudaMemcpyAsync(dm, b->h_meta, 4 * M1 * sizeof(u64), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(b->wstats.p, 0, windows * sizeof(DevStats), s) != cudaSuccess ||
+        cudaMemsetAsync(b->counter.p, 0, chunks.size() * sizeof(u32), s) != cudaSuccess) {
+        cudaGetLastError();
+        return set_fail(NS_ERR_CUDA, "ns_batch_run: staging copy failed");
+    }
+    for (size_t ci = 0; ci < chunks.size(); ++ci) {
+        const Chunk& ch = chunks[ci];
+        if (cudaMemsetAsync(b->links.p, 0, ch.slots * sizeof(LinkSlot), s) != cudaSuccess ||
+            cudaMemsetAsync(b->rows.p, 0, ch.slots * sizeof(NodeSlot), s) != cudaSuccess ||
+            cudaMemsetAsync(b->cols.p, 0, ch.slots * sizeof(NodeSlot), s) != cudaSuccess) {
+            cudaGetLastError();
+            return set_fail(NS_ERR_CUDA, "ns_batch_run: clearing the arena failed");
+        }
+        BatchDev B;
+        B.src = d_src;
+        B.dst = d_dst;
+        B.win_off = dm + ch.w0;
+        B.tile_off = dm + M1 + ch.w0;
+        B.tab_off = dm + 2 * M1 + ch.w0;
+        B.tab_cap = dm + 3 * M1 + ch.w0;
+        B.links = (LinkSlot*)b->links.p;
+        B.rows = (NodeSlot*)b->rows.p;
+        B.cols = (NodeSlot*)b->cols.p;
+        B.wstats = (DevStats*)b->wstats.p + ch.w0;
+        B.W = ch.w1 - ch.w0;
+        B.T = b->params.tile_packets;
+        {
+            TraceScope ts(&c->tracer, "k_batch_insert", s);
+            launch_batch_insert(B, (u32*)b->counter.p + ci, ch.tiles, c->sms, (int)b->params.ctas_per_sm, s);
+        }
+        if (acc) {
+            // every window's link slots, side slots included (a side slot's
+            // key field is 0, which is the key it holds)
+            TraceScope ts(&c->tracer, "k_insert_slots", s);
+            launch_insert_slots((const LinkSlot*)b->links.p, ch.slots - 1, hash_view(acc), c->sms, s);
+        }
+    }
+    {
+        TraceScope ts(&c->tracer, "k_batch_stats_out", s);
+        launch_batch_stats_out((const DevStats*)b->wstats.p, windows, (u64*)d_window_stats, c->sms, s);
+    }
+    if (acc) acc->bound += total;
+    return check_launch();
+}
+
+ns_status ns_batch_tune(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uint32_t* d_dst,
+                        const uint64_t* h_offsets, uint64_t windows, ns_stats* d_scratch_stats, ns_stream_t stream,
+                        ns_batch_params* chosen) {
+    if (!c || !b || !d_scratch_stats) return set_fail(NS_ERR_INVALID, "ns_batch_tune: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned Ts[] = {1024, 2048, 4096, 8192, 16384};
+    const unsigned Cs[] = {4, 8, 16};
+    const double Ls[] = {0.5, 0.7};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return set_fail(NS_ERR_CUDA, "ns_batch_tune: event creation failed");
+    }
+    const ns_batch_params saved = b->params;
+    ns_batch_params best = saved;
+    float best_ms = 1e30f;
+    ns_status st = NS_OK;
+    for (unsigned T : Ts)
+        for (unsigned C : Cs)
+            for (double L : Ls) {
+                b->params = ns_batch_params{T, C, L};
+                float ms_min = 1e30f;
+                for (int rep = 0; rep < 3 && st == NS_OK; ++rep) {
+                    cudaEventRecord(e0, s);
+                    st = ns_batch_run(c, b, d_src, d_dst, h_offsets, windows, d_scratch_stats, nullptr, stream);
+                    cudaEventRecord(e1, s);
+                    if (st != NS_OK) break;
+                    if (cudaEventSynchronize(e1) != cudaSuccess) {
+                        cudaGetLastError();
+                        st = set_fail(NS_ERR_CUDA, "ns_batch_tune: timing failed");
+                        break;
+                    }
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) ms_min = std::min(ms_min, ms);  // first run warms up
+                }
+                if (st != NS_OK) break;
+                if (ms_min < best_ms) {
+                    best_ms = ms_min;
+                    best = b->params;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != NS_OK) {
+        b->params = saved;
+        return st;
+    }
+    b->params = best;
+    if (chosen) *chosen = best;
+    auto cache = tuner_read(c->tuner_cache);
+    cache[tuner_key(c->device, b->max_windows, b->max_packets)] = best;
+    tuner_write(c->tuner_cache, cache);
+    return NS_OK;
+}
+
+}  // extern "C"

@@ -12,6 +12,8 @@
 // increment; counts of sources / destinations / links grow by one exactly
 // when an add finds the old value 0.  Every quantity therefore stays exact
 // however the items are ordered or interleaved.
+#include <algorithm>
+
 #include "ns_common.cuh"
 #include "ns_kernels.h"
 
@@ -335,6 +337,71 @@ __global__ void k_stats_out(const DevStats* __restrict__ st, u64* __restrict__ o
     if (threadIdx.x < S_NFIELDS) out[threadIdx.x] = st->v[threadIdx.x];
 }
 
+// ---- batched windows ------------------------------------------------------
+//
+// Many independent windows in one persistent launch: CTAs take tiles of T
+// packets from an atomic counter in window-major order (so the tables in use
+// at any moment belong to a few windows and stay in L2), find the tile's
+// window by binary search over the tile prefix, and insert its packets into
+// that window's own tables, carved from one arena at per-window offsets.
+// Each tile flushes its block totals into its window's statistics record.
+__global__ void __launch_bounds__(kInsertThreads) k_batch_insert(BatchDev B, u32* tile_counter, u64 total_tiles) {
+    __shared__ BlockStats bs;
+    __shared__ u64 s_tile, s_w, s_p0, s_p1;
+    const u32 lane = lane_id();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const u64 tile = atomicAdd(tile_counter, 1u);
+            s_tile = tile;
+            if (tile < total_tiles) {
+                // largest w with tile_off[w] <= tile (windows without tiles are skipped)
+                u64 lo = 0, hi = B.W;  // invariant: tile_off[lo] <= tile < tile_off[hi]
+                while (hi - lo > 1) {
+                    const u64 mid = (lo + hi) >> 1;
+                    if (B.tile_off[mid] <= tile) lo = mid;
+                    else hi = mid;
+                }
+                const u64 p0 = B.win_off[lo] + (tile - B.tile_off[lo]) * (u64)B.T;
+                const u64 pe = B.win_off[lo + 1];
+                s_w = lo;
+                s_p0 = p0;
+                s_p1 = (p0 + B.T < pe) ? p0 + B.T : pe;
+            }
+        }
+        block_stats_init(bs);
+        __syncthreads();
+        if (s_tile >= total_tiles) break;
+        const u64 w = s_w, p0 = s_p0, p1 = s_p1;
+        const u64 off = B.tab_off[w], cap = B.tab_cap[w];
+        HashView M;
+        M.links = B.links + off;
+        M.link_mask = cap - 1;
+        M.rows = B.rows + off;
+        M.row_mask = cap - 1;
+        M.cols = B.cols + off;
+        M.col_mask = cap - 1;
+        M.stats = B.wstats + w;
+        for (u64 b = p0 + (threadIdx.x & ~31u); b < p1; b += kInsertThreads) {
+            const u64 i = b + lane;
+            const bool valid = i < p1;
+            u64 key = 0;
+            if (valid) key = ((u64)__ldg(B.src + i) << 32) | (u64)__ldg(B.dst + i);
+            insert_item(M, valid, key, 1, true, bs);
+        }
+        __syncthreads();
+        block_stats_flush(bs, M.stats);
+        __syncthreads();
+    }
+}
+
+__global__ void k_batch_stats_out(const DevStats* __restrict__ wstats, u64 W, u64* __restrict__ out) {
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < W * S_NFIELDS; i += stride) {
+        const u64 w = i / S_NFIELDS, f = i % S_NFIELDS;
+        out[i] = wstats[w].v[f];
+    }
+}
+
 int grid_for(u64 n, int threads, int sms, int per_sm) {
     u64 want = (n + threads - 1) / threads;
     u64 cap = (u64)sms * per_sm;
@@ -377,6 +444,18 @@ void launch_compact_links(const LinkSlot* in, u64 cap, u64* out_keys, u64* out_c
                           u64* out_n, u64 out_cap, DevStats* st, int sms, cudaStream_t s) {
     k_compact_links<<<grid_for(cap + 1, 256, sms, 8), 256, 0, s>>>(in, cap, out_keys, out_counts,
                                                                    (u64*)out_n, out_cap, st);
+}
+
+void launch_batch_insert(const BatchDev& B, u32* tile_counter, u64 total_tiles, int sms, int per_sm,
+                         cudaStream_t s) {
+    if (total_tiles == 0) return;
+    const u64 grid = std::min<u64>(total_tiles, (u64)sms * (u64)per_sm);
+    k_batch_insert<<<(unsigned)grid, kInsertThreads, 0, s>>>(B, tile_counter, total_tiles);
+}
+
+void launch_batch_stats_out(const DevStats* wstats, u64 W, u64* out, int sms, cudaStream_t s) {
+    if (W == 0) return;
+    k_batch_stats_out<<<grid_for(W * S_NFIELDS, 256, sms, 4), 256, 0, s>>>(wstats, W, out);
 }
 
 void launch_stats_out(const DevStats* st, u64* out, cudaStream_t s) {

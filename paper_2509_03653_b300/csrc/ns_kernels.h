@@ -77,6 +77,22 @@ inline u32 next_tag(SortScratch& sc, cudaStream_t s) {
 u64 sort_tiles(u64 n);
 int sort_radix();
 
+// Batched windows: per-window tables carved from one arena (ns_batch.cu).
+struct BatchDev {
+    const u32* src;
+    const u32* dst;
+    const u64* win_off;   // [W+1] packet offsets of the windows
+    const u64* tile_off;  // [W+1] tile offsets (tiles of T packets per window)
+    const u64* tab_off;   // [W] first slot of the window's tables in the arena
+    const u64* tab_cap;   // [W] power-of-two table capacity (plus one side slot)
+    LinkSlot* links;
+    NodeSlot* rows;
+    NodeSlot* cols;
+    DevStats* wstats;  // [W]
+    u64 W;
+    u32 T;
+};
+
 // hash path (ns_hash.cu)
 void launch_insert_packets(const u32* src, const u32* dst, u64 n, const HashView& M,
                            int sms, cudaStream_t s);
@@ -89,6 +105,9 @@ void launch_insert_list(const u64* keys, const u64* counts, u64 n_bound,
 void launch_compact_links(const LinkSlot* in, u64 cap, u64* out_keys, u64* out_counts,
                           u64* out_n, u64 out_cap, DevStats* st, int sms, cudaStream_t s);
 void launch_stats_out(const DevStats* st, u64* out, cudaStream_t s);
+void launch_batch_insert(const BatchDev& B, u32* tile_counter, u64 total_tiles, int sms, int per_sm,
+                         cudaStream_t s);
+void launch_batch_stats_out(const DevStats* wstats, u64 W, u64* out, int sms, cudaStream_t s);
 
 // sort path (ns_sort.cu).  Each radix sort returns the index of kbuf/vbuf
 // holding the result.  n is an upper bound when n_dev is given.
