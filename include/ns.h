@@ -84,11 +84,20 @@ enum {
     NS_PATH_HASH = 2  /* open-addressing hash table with atomic counts */
 };
 
+/* Per-CTA shared-memory staging of hot links, sources and destinations in
+ * the hash path (see ns_config.cta_cache). */
+enum {
+    NS_CACHE_AUTO = 0, /* on for inserts of >= 2^22 packets, off below */
+    NS_CACHE_ON = 1,
+    NS_CACHE_OFF = 2
+};
+
 typedef struct {
     int path;                  /* NS_PATH_* used by ns_window_build */
-    uint64_t hbm_budget_bytes; /* serving admission budget; 0 = 64 GiB */
+    uint64_t hbm_budget_bytes; /* serving admission and batch arena budget; 0 = 64 GiB */
     int max_slots;             /* serving: windows in flight at once; 0 = 8 */
     const char* tuner_cache;   /* autotuner cache file (JSON); NULL = none */
+    int cta_cache;             /* NS_CACHE_* for hash-path packet inserts */
 } ns_config;
 
 /* ---- context ----------------------------------------------------------- */
@@ -195,6 +204,7 @@ typedef struct {
     uint32_t tile_packets; /* packets per CTA work item (multiple of 32) */
     uint32_t ctas_per_sm;  /* persistent CTAs per SM */
     double max_load;       /* per-window table load bound, in [0.5, 0.9] */
+    uint32_t cta_cache;    /* 1 = stage hot keys in shared memory per tile */
 } ns_batch_params;
 
 /* A plan for batches of at most max_windows windows and max_packets packets:

@@ -51,10 +51,10 @@ class Context:
     """A library context on one CUDA device (ns_create / ns_destroy)."""
 
     def __init__(self, device: int = 0, path: str = "hash", hbm_budget_bytes: int = 0,
-                 max_slots: int = 0, tuner_cache: str | None = None):
+                 max_slots: int = 0, tuner_cache: str | None = None, cta_cache: str = "auto"):
         self._L = load()
         cfg = NsConfig(PATHS[path], hbm_budget_bytes, max_slots,
-                       tuner_cache.encode() if tuner_cache else None)
+                       tuner_cache.encode() if tuner_cache else None, {"auto": 0, "on": 1, "off": 2}[cta_cache])
         h = ctypes.c_void_p()
         check(self._L.ns_create(ctypes.byref(h), ctypes.byref(cfg), device), "ns_create")
         self.handle = h
@@ -233,10 +233,11 @@ class Batch:
     def params(self) -> dict:
         p = NsBatchParams()
         check(self._L.ns_batch_get_params(self.handle, ctypes.byref(p)), "ns_batch_get_params")
-        return {"tile_packets": p.tile_packets, "ctas_per_sm": p.ctas_per_sm, "max_load": p.max_load}
+        return {"tile_packets": p.tile_packets, "ctas_per_sm": p.ctas_per_sm, "max_load": p.max_load,
+                "cta_cache": p.cta_cache}
 
-    def set_params(self, tile_packets: int, ctas_per_sm: int, max_load: float):
-        p = NsBatchParams(tile_packets, ctas_per_sm, max_load)
+    def set_params(self, tile_packets: int, ctas_per_sm: int, max_load: float, cta_cache: int = 1):
+        p = NsBatchParams(tile_packets, ctas_per_sm, max_load, cta_cache)
         check(self._L.ns_batch_set_params(self.handle, ctypes.byref(p)), "ns_batch_set_params")
 
     def free(self):
@@ -282,4 +283,5 @@ def batch_tune(ctx: Context, batch: Batch, src: torch.Tensor, dst: torch.Tensor,
     check(ctx._L.ns_batch_tune(ctx.handle, batch.handle, _column(src, "src"), _column(dst, "dst"), ptr, W,
                                ctypes.c_void_p(scratch.data_ptr()), _stream(stream), ctypes.byref(p)),
           "ns_batch_tune")
-    return {"tile_packets": p.tile_packets, "ctas_per_sm": p.ctas_per_sm, "max_load": p.max_load}
+    return {"tile_packets": p.tile_packets, "ctas_per_sm": p.ctas_per_sm, "max_load": p.max_load,
+            "cta_cache": p.cta_cache}

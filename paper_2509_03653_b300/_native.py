@@ -15,7 +15,8 @@ ST = ctypes.c_int  # ns_status
 
 
 class NsConfig(ctypes.Structure):
-    _fields_ = [("path", I32), ("hbm_budget_bytes", U64), ("max_slots", I32), ("tuner_cache", ctypes.c_char_p)]
+    _fields_ = [("path", I32), ("hbm_budget_bytes", U64), ("max_slots", I32), ("tuner_cache", ctypes.c_char_p),
+                ("cta_cache", I32)]
 
 
 class NsStats(ctypes.Structure):
@@ -28,7 +29,8 @@ FIELDS = tuple(f for f, _ in NsStats._fields_)
 
 
 class NsBatchParams(ctypes.Structure):
-    _fields_ = [("tile_packets", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("max_load", ctypes.c_double)]
+    _fields_ = [("tile_packets", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("max_load", ctypes.c_double),
+                ("cta_cache", ctypes.c_uint32)]
 
 
 class NsTraceEntry(ctypes.Structure):

@@ -266,6 +266,14 @@ ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n,
     return check_launch();
 }
 
+// The per-CTA cache pays off when each CTA sees many packets (skewed keys
+// then repeat inside it); a single 2^17-packet window gives each CTA ~256.
+bool use_cta_cache(const ns_ctx* c, u64 n) {
+    if (c->cfg.cta_cache == NS_CACHE_ON) return true;
+    if (c->cfg.cta_cache == NS_CACHE_OFF) return false;
+    return n >= (1ull << 22);
+}
+
 ns_status build_hash(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n, ns_matrix* out,
                      cudaStream_t s) {
     TRY(hash_alloc(out, n));
@@ -274,7 +282,7 @@ ns_status build_hash(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n,
     out->bound = n;
     if (n == 0) return NS_OK;
     TraceScope ts(&c->tracer, "k_insert_packets", s);
-    launch_insert_packets(src, dst, n, hash_view(out), c->sms, s);
+    launch_insert_packets(src, dst, n, hash_view(out), c->sms, use_cta_cache(c, n), s);
     return check_launch();
 }
 
@@ -312,6 +320,8 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
     if (cfg) c = *cfg;
     if (c.path < NS_PATH_AUTO || c.path > NS_PATH_HASH)
         return fail(NS_ERR_INVALID, "ns_create: unknown path %d", c.path);
+    if (c.cta_cache < NS_CACHE_AUTO || c.cta_cache > NS_CACHE_OFF)
+        return fail(NS_ERR_INVALID, "ns_create: unknown cta_cache %d", c.cta_cache);
     CK(cudaSetDevice(device));
     ns_ctx* x = new ns_ctx();
     x->device = device;
@@ -511,7 +521,7 @@ ns_status ns_window_ingest(ns_ctx* c, ns_matrix* acc, const uint32_t* d_src, con
     TRY(to_hash(acc, n, s));
     if (n == 0) return NS_OK;
     TraceScope ts(&c->tracer, "k_insert_packets", s);
-    launch_insert_packets(d_src, d_dst, n, hash_view(acc), c->sms, s);
+    launch_insert_packets(d_src, d_dst, n, hash_view(acc), c->sms, use_cta_cache(c, n), s);
     acc->bound += n;
     return check_launch();
 }
@@ -526,7 +536,8 @@ ns_status ns_window_ingest_stats(ns_ctx* c, ns_matrix* acc, const uint32_t* d_sr
     TRY(to_hash(acc, n, s));
     {
         TraceScope ts(&c->tracer, "k_insert_packets", s);
-        launch_insert_packets_snapshot(d_src, d_dst, n, hash_view(acc), (u64*)d_out, c->sms, s);
+        launch_insert_packets_snapshot(d_src, d_dst, n, hash_view(acc), (u64*)d_out, c->sms,
+                                       use_cta_cache(c, n), s);
     }
     acc->bound += n;
     return check_launch();

@@ -27,7 +27,7 @@ using namespace ns;
 struct ns_batch {
     ns_ctx* ctx = nullptr;
     uint64_t max_windows = 0, max_packets = 0;
-    ns_batch_params params{4096, 4, 0.5};
+    ns_batch_params params{4096, 8, 0.5, 1};
     Buf meta;                  // win_off, tile_off, tab_off, tab_cap: 4 x (max_windows + 1) u64
     u64* h_meta = nullptr;       // pinned staging of the same
     Buf links, rows, cols;     // the arena
@@ -82,14 +82,16 @@ std::map<std::string, ns_batch_params> tuner_read(const std::string& path) {
         char* q2 = strchr(q1 + 1, '"');
         if (!q2) continue;
         std::string key(q1 + 1, q2);
-        unsigned t = 0, c = 0;
+        unsigned t = 0, c = 0, k = 1;
         double l = 0;
         const char* pt = strstr(q2, "\"T\":");
         const char* pc = strstr(q2, "\"per_sm\":");
         const char* pl = strstr(q2, "\"load\":");
         if (!pt || !pc || !pl) continue;
         if (sscanf(pt + 4, "%u", &t) != 1 || sscanf(pc + 9, "%u", &c) != 1 || sscanf(pl + 7, "%lf", &l) != 1) continue;
-        m[key] = ns_batch_params{t, c, l};
+        const char* pk = strstr(q2, "\"cache\":");
+        if (pk && sscanf(pk + 8, "%u", &k) != 1) k = 1;
+        m[key] = ns_batch_params{t, c, l, k};
     }
     fclose(f);
     return m;
@@ -103,8 +105,9 @@ void tuner_write(const std::string& path, const std::map<std::string, ns_batch_p
     fprintf(f, "{\n");
     size_t i = 0;
     for (const auto& kv : m) {
-        fprintf(f, "  \"%s\": {\"T\": %u, \"per_sm\": %u, \"load\": %.3f}%s\n", kv.first.c_str(), kv.second.tile_packets,
-                kv.second.ctas_per_sm, kv.second.max_load, ++i < m.size() ? "," : "");
+        fprintf(f, "  \"%s\": {\"T\": %u, \"per_sm\": %u, \"load\": %.3f, \"cache\": %u}%s\n", kv.first.c_str(),
+                kv.second.tile_packets, kv.second.ctas_per_sm, kv.second.max_load, kv.second.cta_cache,
+                ++i < m.size() ? "," : "");
     }
     fprintf(f, "}\n");
     fclose(f);
@@ -113,7 +116,7 @@ void tuner_write(const std::string& path, const std::map<std::string, ns_batch_p
 
 bool params_ok(const ns_batch_params& p) {
     return p.tile_packets >= 256 && p.tile_packets <= (1u << 20) && (p.tile_packets % 32) == 0 &&
-           p.ctas_per_sm >= 1 && p.ctas_per_sm <= 32 && p.max_load > 0.05 && p.max_load <= 0.9;
+           p.ctas_per_sm >= 1 && p.ctas_per_sm <= 32 && p.max_load > 0.05 && p.max_load <= 0.9 && p.cta_cache <= 1;
 }
 
 ns_status plan(ns_batch* b, const uint64_t* h_off, u64 W, std::vector<Chunk>& chunks) {
@@ -273,7 +276,8 @@ ns_status ns_batch_run(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uint
         B.T = b->params.tile_packets;
         {
             TraceScope ts(&c->tracer, "k_batch_insert", s);
-            launch_batch_insert(B, (u32*)b->counter.p + ci, ch.tiles, c->sms, (int)b->params.ctas_per_sm, s);
+            launch_batch_insert(B, (u32*)b->counter.p + ci, ch.tiles, c->sms, (int)b->params.ctas_per_sm,
+                                b->params.cta_cache != 0, s);
         }
         if (acc) {
             // every window's link slots, side slots included (a side slot's
@@ -295,9 +299,10 @@ ns_status ns_batch_tune(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uin
                         ns_batch_params* chosen) {
     if (!c || !b || !d_scratch_stats) return set_fail(NS_ERR_INVALID, "ns_batch_tune: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
-    const unsigned Ts[] = {1024, 2048, 4096, 8192, 16384};
+    const unsigned Ts[] = {2048, 4096, 16384};
     const unsigned Cs[] = {4, 8, 16};
     const double Ls[] = {0.5, 0.7};
+    const unsigned Ks[] = {0, 1};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
@@ -309,8 +314,9 @@ ns_status ns_batch_tune(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uin
     ns_status st = NS_OK;
     for (unsigned T : Ts)
         for (unsigned C : Cs)
-            for (double L : Ls) {
-                b->params = ns_batch_params{T, C, L};
+            for (double L : Ls)
+                for (unsigned K : Ks) {
+                b->params = ns_batch_params{T, C, L, K};
                 float ms_min = 1e30f;
                 for (int rep = 0; rep < 3 && st == NS_OK; ++rep) {
                     cudaEventRecord(e0, s);

@@ -103,17 +103,124 @@ __device__ __forceinline__ u64 degree_inc(NodeSlot* s, DevStats* st) {
     return (u64)old + 1;
 }
 
+// ---- CTA-level caches for skewed keys --------------------------------------
+//
+// With skewed traffic (Zipf, RMAT hubs) a few links, sources and destinations
+// take most of the updates, and thousands of atomics on one global address
+// serialize.  Each CTA keeps small shared-memory tables of links, rows and
+// columns (bounded probing; an item that finds no room goes to the global
+// tables directly).  Cached counts are added to the global tables once per CTA
+// at the flush.  Whether a cached link is new is only known at its flush, so
+// the degree increments of its row and column are applied there.
+constexpr int kCache = 512;
+constexpr int kCacheProbes = 4;
+
+struct CtaCache {
+    u64 lkey[kCache];
+    u64 lcnt[kCache];
+    u32 rid[kCache];   // id + 1, 0 = empty
+    u32 rdeg[kCache];
+    u64 rpk[kCache];
+    u32 cid[kCache];
+    u32 cdeg[kCache];
+    u64 cpk[kCache];
+};
+
+__device__ __forceinline__ void cache_clear(CtaCache& C) {
+    for (int i = threadIdx.x; i < kCache; i += blockDim.x) {
+        C.lkey[i] = 0;
+        C.lcnt[i] = 0;
+        C.rid[i] = 0;
+        C.rdeg[i] = 0;
+        C.rpk[i] = 0;
+        C.cid[i] = 0;
+        C.cdeg[i] = 0;
+        C.cpk[i] = 0;
+    }
+}
+
+// slot of `key` in the link cache (claimed if absent), or -1 if no room
+__device__ __forceinline__ int lcache_slot(CtaCache& C, u64 key) {
+    u32 h = (u32)(mix64(key) >> 40) & (kCache - 1);
+    for (int p = 0; p < kCacheProbes; ++p) {
+        const u64 old = atomicCAS(&C.lkey[h], 0ull, key);
+        if (old == 0ull || old == key) return (int)h;
+        h = (h + 1) & (kCache - 1);
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int ncache_slot(u32* ids, u32 id) {
+    if (id == 0xFFFFFFFFu) return -1;  // the side-slot id is never cached
+    u32 h = (u32)(mix32(id) >> 40) & (kCache - 1);
+    for (int p = 0; p < kCacheProbes; ++p) {
+        const u32 old = atomicCAS(&ids[h], 0u, id + 1);
+        if (old == 0u || old == id + 1) return (int)h;
+        h = (h + 1) & (kCache - 1);
+    }
+    return -1;
+}
+
+// Global node update with `pk` packets and `deg` new partners at once.
+// Returns the values before the update (prev packets, prev degree).
+struct NodePrev {
+    u64 pk;
+    u64 deg;
+    bool ok;
+};
+__device__ __noinline__ NodePrev node_add(NodeSlot* tbl, u64 mask, u32 id, u64 pk, u32 deg, DevStats* st) {
+    u64 i = node_home(mask, id);
+    if (id != 0xFFFFFFFFu) {
+        const u32 id1 = id + 1;
+        for (u32 p = 0;; ++p) {
+            if (p >= kMaxProbes) {
+                set_error(st, ERR_CAPACITY);
+                return {0, 0, false};
+            }
+            const W128 o = cas128(&tbl[i], 0ull, 0ull, (u64)id1 | ((u64)deg << 32), pk);
+            if ((u32)o.lo == 0u) return {0, 0, true};
+            if ((u32)o.lo == id1) break;
+            i = (i + 1) & mask;
+        }
+    }
+    NodePrev r{0, 0, true};
+    if (pk) r.pk = atomicAdd(&tbl[i].packets, pk);
+    else r.pk = 1;  // unchanged; not a new node
+    if (deg) {
+        const u32 old = atomicAdd(&tbl[i].degree, deg);
+        if ((u64)old + deg > 0xFFFFFFFFull) set_error(st, ERR_CAPACITY);
+        r.deg = old;
+    }
+    return r;
+}
+
+// Adds one new partner to a node: in the cache if the node is there (or fits),
+// else in the global table.  Returns the node's degree after the increment if
+// it was applied globally (0 if cached: the flush reports it).
+__device__ __forceinline__ u64 degree_add_cached(u32* cids, u32* cdeg, NodeSlot* tbl, u64 mask, u32 id,
+                                                 DevStats* st) {
+    const int s = ncache_slot(cids, id);
+    if (s >= 0) {
+        atomicAdd(&cdeg[s], 1u);
+        return 0;
+    }
+    const NodePrev r = node_add(tbl, mask, id, 0, 1, st);
+    return r.ok ? r.deg + 1 : 0;
+}
+
 // One item per lane; every lane of the warp must call this.  With `dedup`
 // set (raw packets, c == 1), lanes holding equal keys are merged first so a
 // hot link costs one atomic per warp instead of one per packet.
 //
-// Two dependent round trips to L2 per item: (1) the three 128-bit claims of
-// the link, row and column home slots, issued together -- a new entry is
-// complete after this, and whether the link is new is known; (2) the count
-// additions of entries that already existed and, for a new link, the degree
-// increments of its row and column, again issued together.
+// Without a cache, two dependent round trips to L2 per item: (1) the three
+// 128-bit claims of the link, row and column home slots, issued together --
+// a new entry is complete after this, and whether the link is new is known;
+// (2) the count additions of entries that already existed and, for a new
+// link, the degree increments of its row and column, again issued together.
+// With a cache, the parts that find room in it stay in shared memory.
+template <bool CACHE>
 __device__ __forceinline__ void insert_item(const HashView& M, bool valid, u64 key, u64 c, bool dedup,
-                                            BlockStats& bs) {
+                                            BlockStats& bs, CtaCache* C) {
     const u32 FULL = 0xFFFFFFFFu;
     const u32 lane = lane_id();
     const u32 vmask = __ballot_sync(FULL, valid);
@@ -131,39 +238,57 @@ __device__ __forceinline__ void insert_item(const HashView& M, bool valid, u64 k
     u64 cnt_new = 0, rpk = 0, rdeg = 0, cpk = 0, cdeg = 0;
     if (lead) {
         const u32 sid = (u32)(key >> 32), did = (u32)key;
+        const bool lside = (key == 0), rside = (sid == 0xFFFFFFFFu), cside = (did == 0xFFFFFFFFu);
+        int lc = -1, rc = -1, cc = -1;
+        if constexpr (CACHE) {
+            if (!lside) lc = lcache_slot(*C, key);
+            rc = ncache_slot(C->rid, sid);
+            cc = ncache_slot(C->cid, did);
+            if (lc >= 0) atomicAdd(&C->lcnt[lc], cs);
+            if (rc >= 0) atomicAdd(&C->rpk[rc], cs);
+            if (cc >= 0) atomicAdd(&C->cpk[cc], cs);
+        }
+        const bool ldir = lc < 0, rdir = rc < 0, cdir = cc < 0;
         const u64 li0 = link_home(M, key);
         const u64 ri0 = node_home(M.row_mask, sid);
         const u64 ci0 = node_home(M.col_mask, did);
-        const bool lside = (key == 0), rside = (sid == 0xFFFFFFFFu), cside = (did == 0xFFFFFFFFu);
         // round trip 1
         W128 lo = {0, 0}, ro = {0, 0}, co = {0, 0};
-        if (!lside) lo = cas128(&M.links[li0], 0ull, 0ull, key, cs);
-        if (!rside) ro = cas128(&M.rows[ri0], 0ull, 0ull, (u64)(sid + 1), cs);
-        if (!cside) co = cas128(&M.cols[ci0], 0ull, 0ull, (u64)(did + 1), cs);
+        if (ldir && !lside) lo = cas128(&M.links[li0], 0ull, 0ull, key, cs);
+        if (rdir && !rside) ro = cas128(&M.rows[ri0], 0ull, 0ull, (u64)(sid + 1), cs);
+        if (cdir && !cside) co = cas128(&M.cols[ci0], 0ull, 0ull, (u64)(did + 1), cs);
         // classify: 0 = created, 1 = existing entry found, 2 = probe on
         const int lk = lside ? 1 : (lo.lo == 0ull ? 0 : (lo.lo == key ? 1 : 2));
         const int rk = rside ? 1 : ((u32)ro.lo == 0u ? 0 : ((u32)ro.lo == sid + 1 ? 1 : 2));
         const int ck = cside ? 1 : ((u32)co.lo == 0u ? 0 : ((u32)co.lo == did + 1 ? 1 : 2));
-        Upsert L = {li0, 0}, R = {ri0, 0}, C = {ci0, 0};
-        if (lk == 2) L = link_probe(M, key, cs, li0);
-        if (rk == 2) R = node_probe(M.rows, M.row_mask, sid + 1, cs, ri0, M.stats);
-        if (ck == 2) C = node_probe(M.cols, M.col_mask, did + 1, cs, ci0, M.stats);
+        Upsert L = {li0, 0}, R = {ri0, 0}, Cl = {ci0, 0};
+        if (ldir && lk == 2) L = link_probe(M, key, cs, li0);
+        if (rdir && rk == 2) R = node_probe(M.rows, M.row_mask, sid + 1, cs, ri0, M.stats);
+        if (cdir && ck == 2) Cl = node_probe(M.cols, M.col_mask, did + 1, cs, ci0, M.stats);
         // a found link cannot have count 0, so "new" is known now
-        newlink = (lk == 0) || (lk == 2 && L.slot != kNoSlot && L.prev == 0);
+        newlink = ldir && ((lk == 0) || (lk == 2 && L.slot != kNoSlot && L.prev == 0));
         // round trip 2
-        if (lk == 1) L.prev = atomicAdd(&M.links[li0].count, cs);
-        if (rk == 1) R.prev = atomicAdd(&M.rows[ri0].packets, cs);
-        if (ck == 1) C.prev = atomicAdd(&M.cols[ci0].packets, cs);
-        if (lside) newlink = (L.prev == 0);  // the key-0 slot is only added to
+        if (ldir && lk == 1) L.prev = atomicAdd(&M.links[li0].count, cs);
+        if (rdir && rk == 1) R.prev = atomicAdd(&M.rows[ri0].packets, cs);
+        if (cdir && ck == 1) Cl.prev = atomicAdd(&M.cols[ci0].packets, cs);
+        if (ldir && lside) newlink = (L.prev == 0);  // the key-0 slot is only added to
         if (newlink) {
-            if (R.slot != kNoSlot) rdeg = degree_inc(&M.rows[R.slot], M.stats);
-            if (C.slot != kNoSlot) cdeg = degree_inc(&M.cols[C.slot], M.stats);
+            if (rdir) {
+                if (R.slot != kNoSlot) rdeg = degree_inc(&M.rows[R.slot], M.stats);
+            } else {
+                atomicAdd(&C->rdeg[rc], 1u);
+            }
+            if (cdir) {
+                if (Cl.slot != kNoSlot) cdeg = degree_inc(&M.cols[Cl.slot], M.stats);
+            } else {
+                atomicAdd(&C->cdeg[cc], 1u);
+            }
         }
-        newsrc = (R.slot != kNoSlot) && R.prev == 0;
-        newdst = (C.slot != kNoSlot) && C.prev == 0;
-        cnt_new = L.prev + cs;
-        rpk = R.prev + cs;
-        cpk = C.prev + cs;
+        newsrc = rdir && (R.slot != kNoSlot) && R.prev == 0;
+        newdst = cdir && (Cl.slot != kNoSlot) && Cl.prev == 0;
+        if (ldir) cnt_new = L.prev + cs;
+        if (rdir) rpk = R.prev + cs;
+        if (cdir) cpk = Cl.prev + cs;
     }
     // warp totals -> block accumulators
     const u32 nl = __popc(__ballot_sync(FULL, newlink));
@@ -189,6 +314,60 @@ __device__ __forceinline__ void insert_item(const HashView& M, bool valid, u64 k
         smax(&bs.mx[3], cpk);
         smax(&bs.mx[4], cdeg);
     }
+}
+
+// Moves a CTA's cached counts into the global tables; whole CTA, after a
+// barrier.  Links first: a link found new adds a partner to its row and
+// column, in the cache when they are there.  Then rows and columns.  Leaves
+// the cache empty.
+__device__ void cache_flush(const HashView& M, CtaCache& C, BlockStats& bs) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kCache; i += blockDim.x) {
+        const u64 key = C.lkey[i];
+        if (key == 0) continue;
+        const u64 cnt = C.lcnt[i];
+        const u64 h0 = link_home(M, key);
+        Upsert L;
+        const W128 o = cas128(&M.links[h0], 0ull, 0ull, key, cnt);
+        if (o.lo == 0ull) L = {h0, 0};
+        else if (o.lo == key) L = {h0, atomicAdd(&M.links[h0].count, cnt)};
+        else L = link_probe(M, key, cnt, h0);
+        if (L.slot == kNoSlot) continue;
+        smax(&bs.mx[0], L.prev + cnt);
+        if (L.prev == 0) {
+            atomicAdd(&bs.sum[1], 1ull);
+            const u64 rd = degree_add_cached(C.rid, C.rdeg, M.rows, M.row_mask, (u32)(key >> 32), M.stats);
+            const u64 cd = degree_add_cached(C.cid, C.cdeg, M.cols, M.col_mask, (u32)key, M.stats);
+            if (rd) smax(&bs.mx[2], rd);
+            if (cd) smax(&bs.mx[4], cd);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kCache; i += blockDim.x) {
+        if (C.rid[i]) {
+            const u64 pk = C.rpk[i];
+            const u32 dg = C.rdeg[i];
+            const NodePrev r = node_add(M.rows, M.row_mask, C.rid[i] - 1, pk, dg, M.stats);
+            if (r.ok) {
+                if (pk && r.pk == 0) atomicAdd(&bs.sum[2], 1ull);
+                if (pk) smax(&bs.mx[1], r.pk + pk);
+                if (dg) smax(&bs.mx[2], r.deg + dg);
+            }
+        }
+        if (C.cid[i]) {
+            const u64 pk = C.cpk[i];
+            const u32 dg = C.cdeg[i];
+            const NodePrev r = node_add(M.cols, M.col_mask, C.cid[i] - 1, pk, dg, M.stats);
+            if (r.ok) {
+                if (pk && r.pk == 0) atomicAdd(&bs.sum[3], 1ull);
+                if (pk) smax(&bs.mx[3], r.pk + pk);
+                if (dg) smax(&bs.mx[4], r.deg + dg);
+            }
+        }
+    }
+    __syncthreads();
+    cache_clear(C);
+    __syncthreads();
 }
 
 __device__ __forceinline__ void block_stats_init(BlockStats& bs) {
@@ -232,11 +411,15 @@ __device__ __forceinline__ void last_block_snapshot(DevStats* st, u64* out) {
 
 // Raw packets: two uint32 columns (the paper's src and dst), count 1 each.
 // With `out` set, the statistics after this launch are written there.
+template <bool CACHE>
 __global__ void __launch_bounds__(kInsertThreads) k_insert_packets(const u32* __restrict__ src,
                                                                    const u32* __restrict__ dst, u64 n,
                                                                    HashView M, u64* __restrict__ out) {
     __shared__ BlockStats bs;
+    extern __shared__ __align__(16) unsigned char cache_smem[];  // sized sizeof(CtaCache) when CACHE
+    CtaCache* C = CACHE ? reinterpret_cast<CtaCache*>(cache_smem) : nullptr;
     block_stats_init(bs);
+    if constexpr (CACHE) cache_clear(*C);
     __syncthreads();
     const u64 stride = (u64)gridDim.x * blockDim.x;
     // warp-uniform trip count so that every lane reaches the warp intrinsics
@@ -246,8 +429,9 @@ __global__ void __launch_bounds__(kInsertThreads) k_insert_packets(const u32* __
         const bool valid = i < n;
         u64 key = 0;
         if (valid) key = ((u64)__ldg(src + i) << 32) | (u64)__ldg(dst + i);
-        insert_item(M, valid, key, 1, true, bs);
+        insert_item<CACHE>(M, valid, key, 1, true, bs, C);
     }
+    if constexpr (CACHE) cache_flush(M, *C, bs);
     __syncthreads();
     block_stats_flush(bs, M.stats);
     if (out) last_block_snapshot(M.stats, out);
@@ -255,10 +439,14 @@ __global__ void __launch_bounds__(kInsertThreads) k_insert_packets(const u32* __
 
 // Entries of another hash matrix: its link table slots (count > 0 = occupied;
 // slot `cap` holds key 0).  Keys are unique, so no merging is needed.
+template <bool CACHE>
 __global__ void __launch_bounds__(kInsertThreads) k_insert_slots(const LinkSlot* __restrict__ in,
                                                                  u64 in_cap, HashView M) {
     __shared__ BlockStats bs;
+    extern __shared__ __align__(16) unsigned char cache_smem[];  // sized sizeof(CtaCache) when CACHE
+    CtaCache* C = CACHE ? reinterpret_cast<CtaCache*>(cache_smem) : nullptr;
     block_stats_init(bs);
+    if constexpr (CACHE) cache_clear(*C);
     __syncthreads();
     const u64 total = in_cap + 1;
     const u64 stride = (u64)gridDim.x * blockDim.x;
@@ -271,19 +459,24 @@ __global__ void __launch_bounds__(kInsertThreads) k_insert_slots(const LinkSlot*
             c = s.count;
             key = (i == in_cap) ? 0ull : s.key;
         }
-        insert_item(M, c > 0, key, c, false, bs);
+        insert_item<CACHE>(M, c > 0, key, c, false, bs, C);
     }
+    if constexpr (CACHE) cache_flush(M, *C, bs);
     __syncthreads();
     block_stats_flush(bs, M.stats);
 }
 
 // Entries of a sorted-list matrix (keys[i], counts[i]), i < n.
+template <bool CACHE>
 __global__ void __launch_bounds__(kInsertThreads) k_insert_list(const u64* __restrict__ keys,
                                                                 const u64* __restrict__ counts, u64 n_arg,
                                                                 const u64* __restrict__ n_dev,
                                                                 HashView M) {
     __shared__ BlockStats bs;
+    extern __shared__ __align__(16) unsigned char cache_smem[];  // sized sizeof(CtaCache) when CACHE
+    CtaCache* C = CACHE ? reinterpret_cast<CtaCache*>(cache_smem) : nullptr;
     block_stats_init(bs);
+    if constexpr (CACHE) cache_clear(*C);
     __syncthreads();
     const u64 n = n_dev ? *n_dev : n_arg;
     const u64 stride = (u64)gridDim.x * blockDim.x;
@@ -295,8 +488,9 @@ __global__ void __launch_bounds__(kInsertThreads) k_insert_list(const u64* __res
             key = keys[i];
             c = counts[i];
         }
-        insert_item(M, c > 0, key, c, false, bs);
+        insert_item<CACHE>(M, c > 0, key, c, false, bs, C);
     }
+    if constexpr (CACHE) cache_flush(M, *C, bs);
     __syncthreads();
     block_stats_flush(bs, M.stats);
 }
@@ -345,9 +539,13 @@ __global__ void k_stats_out(const DevStats* __restrict__ st, u64* __restrict__ o
 // window by binary search over the tile prefix, and insert its packets into
 // that window's own tables, carved from one arena at per-window offsets.
 // Each tile flushes its block totals into its window's statistics record.
+template <bool CACHE>
 __global__ void __launch_bounds__(kInsertThreads) k_batch_insert(BatchDev B, u32* tile_counter, u64 total_tiles) {
     __shared__ BlockStats bs;
     __shared__ u64 s_tile, s_w, s_p0, s_p1;
+    extern __shared__ __align__(16) unsigned char cache_smem[];  // sized sizeof(CtaCache) when CACHE
+    CtaCache* C = CACHE ? reinterpret_cast<CtaCache*>(cache_smem) : nullptr;
+    if constexpr (CACHE) cache_clear(*C);
     const u32 lane = lane_id();
     for (;;) {
         if (threadIdx.x == 0) {
@@ -386,8 +584,9 @@ __global__ void __launch_bounds__(kInsertThreads) k_batch_insert(BatchDev B, u32
             const bool valid = i < p1;
             u64 key = 0;
             if (valid) key = ((u64)__ldg(B.src + i) << 32) | (u64)__ldg(B.dst + i);
-            insert_item(M, valid, key, 1, true, bs);
+            insert_item<CACHE>(M, valid, key, 1, true, bs, C);
         }
+        if constexpr (CACHE) cache_flush(M, *C, bs);
         __syncthreads();
         block_stats_flush(bs, M.stats);
         __syncthreads();
@@ -412,31 +611,35 @@ int grid_for(u64 n, int threads, int sms, int per_sm) {
 }  // namespace
 
 void launch_insert_packets(const u32* src, const u32* dst, u64 n, const HashView& M,
-                           int sms, cudaStream_t s) {
+                           int sms, bool cache, cudaStream_t s) {
     if (n == 0) return;
-    k_insert_packets<<<grid_for(n, kInsertThreads, sms, 8), kInsertThreads, 0, s>>>(src, dst, n, M,
-                                                                                   nullptr);
+    if (cache)
+        k_insert_packets<true><<<grid_for(n, kInsertThreads, sms, 8), kInsertThreads, sizeof(CtaCache), s>>>(src, dst, n, M, nullptr);
+    else
+        k_insert_packets<false><<<grid_for(n, kInsertThreads, sms, 8), kInsertThreads, 0, s>>>(src, dst, n, M, nullptr);
 }
 
 void launch_insert_packets_snapshot(const u32* src, const u32* dst, u64 n, const HashView& M,
-                                    u64* out, int sms, cudaStream_t s) {
+                                    u64* out, int sms, bool cache, cudaStream_t s) {
     if (n == 0) {
         launch_stats_out(M.stats, out, s);
         return;
     }
-    k_insert_packets<<<grid_for(n, kInsertThreads, sms, 8), kInsertThreads, 0, s>>>(src, dst, n, M, out);
+    if (cache)
+        k_insert_packets<true><<<grid_for(n, kInsertThreads, sms, 8), kInsertThreads, sizeof(CtaCache), s>>>(src, dst, n, M, out);
+    else
+        k_insert_packets<false><<<grid_for(n, kInsertThreads, sms, 8), kInsertThreads, 0, s>>>(src, dst, n, M, out);
 }
 
 void launch_insert_slots(const LinkSlot* in, u64 in_cap, const HashView& M, int sms,
                          cudaStream_t s) {
-    k_insert_slots<<<grid_for(in_cap + 1, kInsertThreads, sms, 8), kInsertThreads, 0, s>>>(in, in_cap,
-                                                                                            M);
+    k_insert_slots<true><<<grid_for(in_cap + 1, kInsertThreads, sms, 8), kInsertThreads, sizeof(CtaCache), s>>>(in, in_cap, M);
 }
 
 void launch_insert_list(const u64* keys, const u64* counts, u64 n_bound,
                         const u64* n_dev, const HashView& M, int sms, cudaStream_t s) {
     if (n_bound == 0) return;
-    k_insert_list<<<grid_for(n_bound, kInsertThreads, sms, 8), kInsertThreads, 0, s>>>(
+    k_insert_list<true><<<grid_for(n_bound, kInsertThreads, sms, 8), kInsertThreads, sizeof(CtaCache), s>>>(
         (const u64*)keys, (const u64*)counts, n_bound, (const u64*)n_dev, M);
 }
 
@@ -447,10 +650,11 @@ void launch_compact_links(const LinkSlot* in, u64 cap, u64* out_keys, u64* out_c
 }
 
 void launch_batch_insert(const BatchDev& B, u32* tile_counter, u64 total_tiles, int sms, int per_sm,
-                         cudaStream_t s) {
+                         bool cache, cudaStream_t s) {
     if (total_tiles == 0) return;
     const u64 grid = std::min<u64>(total_tiles, (u64)sms * (u64)per_sm);
-    k_batch_insert<<<(unsigned)grid, kInsertThreads, 0, s>>>(B, tile_counter, total_tiles);
+    if (cache) k_batch_insert<true><<<(unsigned)grid, kInsertThreads, sizeof(CtaCache), s>>>(B, tile_counter, total_tiles);
+    else k_batch_insert<false><<<(unsigned)grid, kInsertThreads, 0, s>>>(B, tile_counter, total_tiles);
 }
 
 void launch_batch_stats_out(const DevStats* wstats, u64 W, u64* out, int sms, cudaStream_t s) {

@@ -94,10 +94,11 @@ struct BatchDev {
 };
 
 // hash path (ns_hash.cu)
+// `cache`: stage skewed keys in per-CTA shared-memory tables first
 void launch_insert_packets(const u32* src, const u32* dst, u64 n, const HashView& M,
-                           int sms, cudaStream_t s);
+                           int sms, bool cache, cudaStream_t s);
 void launch_insert_packets_snapshot(const u32* src, const u32* dst, u64 n, const HashView& M,
-                                    u64* out, int sms, cudaStream_t s);
+                                    u64* out, int sms, bool cache, cudaStream_t s);
 void launch_insert_slots(const LinkSlot* in, u64 in_cap, const HashView& M, int sms,
                          cudaStream_t s);
 void launch_insert_list(const u64* keys, const u64* counts, u64 n_bound,
@@ -106,7 +107,7 @@ void launch_compact_links(const LinkSlot* in, u64 cap, u64* out_keys, u64* out_c
                           u64* out_n, u64 out_cap, DevStats* st, int sms, cudaStream_t s);
 void launch_stats_out(const DevStats* st, u64* out, cudaStream_t s);
 void launch_batch_insert(const BatchDev& B, u32* tile_counter, u64 total_tiles, int sms, int per_sm,
-                         cudaStream_t s);
+                         bool cache, cudaStream_t s);
 void launch_batch_stats_out(const DevStats* wstats, u64 W, u64* out, int sms, cudaStream_t s);
 
 // sort path (ns_sort.cu).  Each radix sort returns the index of kbuf/vbuf

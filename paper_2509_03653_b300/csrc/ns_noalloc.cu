@@ -107,7 +107,7 @@ extern "C" ns_status ns_window_stats_static(const uint32_t* d_src, const uint32_
     v.cols = (NodeSlot*)(su.base + kColsOff);
     v.col_mask = kCap - 1;
     v.stats = (DevStats*)(su.base + kStatsOff);
-    launch_insert_packets(d_src, d_dst, n, v, su.sms, s);
+    launch_insert_packets(d_src, d_dst, n, v, su.sms, true, s);
     launch_stats_out(v.stats, (u64*)d_out, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) {

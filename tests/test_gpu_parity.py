@@ -262,3 +262,21 @@ def test_window_from_unaligned_columns(ctxs, path):
     want = oracle.build_matrix(s, d)
     assert ns.network_stats(ctx, m) == oracle.stats(*want)
     assert_matrix_equal(m, *want)
+
+
+@pytest.mark.parametrize("cache", ["on", "off"])
+@pytest.mark.parametrize("s_exp,K,n", [(1.5, 1 << 10, 1 << 20), (1.1, 1 << 14, 300007), (0.6, 1 << 20, 200003)])
+def test_skewed_windows_cache_modes(cache, s_exp, K, n):
+    """Very hot links/sources (Zipf 1.5 over 2^10: the top source carries a
+    third of the packets, across hundreds of CTAs), a cache-overflowing
+    mix, and near-uniform traffic -- with and without the per-CTA cache."""
+    ctx = ns.Context(0, path="hash", cta_cache=cache)
+    s, d = W.zipf_window(n, s_exp, K, 0x5EED + n)
+    check_window(ctx, s, d)
+    # and as two windows accumulated
+    acc = ns.Matrix(ctx)
+    ns.window_ingest(ctx, acc, to_dev(s[: n // 3]), to_dev(d[: n // 3]))
+    ns.window_ingest(ctx, acc, to_dev(s[n // 3:]), to_dev(d[n // 3:]))
+    want = oracle.build_matrix(s, d)
+    assert ns.network_stats(ctx, acc) == oracle.stats(*want)
+    assert_matrix_equal(acc, *want)
