@@ -235,6 +235,53 @@ ns_status ns_batch_tune(ns_ctx* ctx, ns_batch* batch, const uint32_t* d_src, con
                         const uint64_t* h_offsets, uint64_t windows, ns_stats* d_scratch_stats,
                         ns_stream_t stream, ns_batch_params* chosen);
 
+/* ---- streaming service (continuous batching) ---------------------------- */
+
+/* A service that takes windows from host threads while earlier ones are on
+ * the GPU.  Each submitted window is admitted, in submission order, as soon
+ * as a slot is free and its device memory fits the context's
+ * hbm_budget_bytes (counting the resident aggregate and the windows in
+ * flight); up to ns_config.max_slots windows build concurrently on their own
+ * streams.  Each window's A_t is then added to `acc` -- the device-resident
+ * running aggregate A -- on one accumulate stream in submission order, so a
+ * window's results are the same whether it ran alone or among others.  For
+ * each ticket the service returns A_t's quantities (per_window) and A's
+ * quantities right after A_t was added (running), with host timestamps.
+ * The server owns `ctx` and `acc` while it runs: do not use them from other
+ * threads until ns_server_destroy returns.  The ns_stream_* calls are
+ * thread-safe. */
+typedef struct ns_server ns_server;
+
+typedef struct {
+    double submit_us;   /* steady-clock time of ns_stream_submit */
+    double admit_us;    /* window admitted (slot and budget available) */
+    double complete_us; /* both statistics records on the host */
+    uint64_t window_id; /* as submitted */
+} ns_stream_timing;
+
+ns_status ns_server_create(ns_ctx* ctx, ns_matrix* acc, ns_server** out);
+
+/* Finishes every submitted window, then stops the service's threads and
+ * frees its slots (acc keeps the aggregate). */
+void ns_server_destroy(ns_server* server);
+
+/* Queues one window given as host uint32 columns h_src[0..n), h_dst[0..n);
+ * they must stay valid and unchanged until ns_stream_wait for this ticket
+ * returns (pinned memory makes the copy asynchronous).  Non-blocking;
+ * NS_ERR_BUSY when the queue is full (retry later). */
+ns_status ns_stream_submit(ns_server* server, const uint32_t* h_src, const uint32_t* h_dst, uint64_t n,
+                           uint64_t window_id, uint64_t* ticket);
+
+/* *done = 1 once the ticket's results are ready. */
+ns_status ns_stream_poll(ns_server* server, uint64_t ticket, int* done);
+
+/* Waits up to timeout_us (< 0: no limit) for a ticket and returns its
+ * results (any pointer may be NULL) and the window's status; NS_ERR_TIMEOUT
+ * if the time ran out (the ticket stays valid).  After a completed wait the
+ * ticket is forgotten. */
+ns_status ns_stream_wait(ns_server* server, uint64_t ticket, ns_stats* per_window, ns_stats* running,
+                         int64_t timeout_us, ns_stream_timing* timing);
+
 /* ---- statistics without device allocation ------------------------------ */
 
 /* The paper has no counterpart to this call; it exists for callers that

@@ -15,13 +15,15 @@ import ctypes
 
 import torch
 
-from ._native import FIELDS, NsBatchParams, NsConfig, NsError, NsStats, NsTraceEntry, check, load
+from ._native import (FIELDS, NsBatchParams, NsConfig, NsError, NsStats, NsStreamTiming, NsTraceEntry, check,
+                      load)
 
 __all__ = [
     "FIELDS", "NsError", "Context", "Matrix", "window_build", "accumulate", "window_ingest",
     "window_ingest_stats", "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
     "matrix_clear", "sync", "PATHS", "window_stats_static", "STATIC_MAX_PACKETS",
     "trace_enable", "trace_read", "Batch", "batch_run", "batch_tune", "matrix_reserve_ex",
+    "Server", "stream_submit", "stream_poll", "stream_wait",
 ]
 
 STATIC_MAX_PACKETS = 32768  # NS_STATIC_MAX_PACKETS in include/ns.h
@@ -285,3 +287,69 @@ def batch_tune(ctx: Context, batch: Batch, src: torch.Tensor, dst: torch.Tensor,
           "ns_batch_tune")
     return {"tile_packets": p.tile_packets, "ctas_per_sm": p.ctas_per_sm, "max_load": p.max_load,
             "cta_cache": p.cta_cache}
+
+
+class Server:
+    """Streaming service over `acc` (ns_server_create / ns_server_destroy).
+    The server owns ctx and acc until close()."""
+
+    def __init__(self, ctx: Context, acc: Matrix):
+        self._L = ctx._L
+        self.ctx, self.acc = ctx, acc
+        h = ctypes.c_void_p()
+        check(self._L.ns_server_create(ctx.handle, acc.handle, ctypes.byref(h)), "ns_server_create")
+        self.handle = h
+        self._keep = {}  # ticket -> host arrays that must outlive the window
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._L.ns_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_col(a):
+    import numpy as _np
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.element_size() != 4 or not a.is_contiguous():
+            raise ValueError("host columns must be contiguous 32-bit CPU tensors")
+        return a, ctypes.c_void_p(a.data_ptr() if a.numel() else 0)
+    a = _np.ascontiguousarray(a, dtype=_np.uint32)
+    return a, ctypes.c_void_p(a.ctypes.data if a.size else 0)
+
+
+def stream_submit(server: Server, src, dst, window_id: int = 0) -> int:
+    """Queue one window (host arrays; kept alive by the server until its
+    wait) and return its ticket; raises NsError(NS_ERR_BUSY) if full."""
+    s, ps = _host_col(src)
+    d, pd = _host_col(dst)
+    n = s.numel() if isinstance(s, torch.Tensor) else s.size
+    t = ctypes.c_uint64()
+    check(server._L.ns_stream_submit(server.handle, ps, pd, n, window_id, ctypes.byref(t)), "ns_stream_submit")
+    server._keep[t.value] = (s, d)
+    return int(t.value)
+
+
+def stream_poll(server: Server, ticket: int) -> bool:
+    d = ctypes.c_int()
+    check(server._L.ns_stream_poll(server.handle, ticket, ctypes.byref(d)), "ns_stream_poll")
+    return bool(d.value)
+
+
+def stream_wait(server: Server, ticket: int, timeout_us: int = -1):
+    """(per_window quantities, running quantities, timing dict)."""
+    pw, rn, tm = NsStats(), NsStats(), NsStreamTiming()
+    st = server._L.ns_stream_wait(server.handle, ticket, ctypes.byref(pw), ctypes.byref(rn), timeout_us,
+                                  ctypes.byref(tm))
+    if st != 5:  # a timeout keeps the ticket (and its arrays) alive
+        server._keep.pop(ticket, None)
+    check(st, "ns_stream_wait")
+    as_dict = lambda x: {f: int(getattr(x, f)) for f in FIELDS}
+    return as_dict(pw), as_dict(rn), {"submit_us": tm.submit_us, "admit_us": tm.admit_us,
+                                      "complete_us": tm.complete_us, "window_id": int(tm.window_id)}

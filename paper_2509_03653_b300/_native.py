@@ -33,6 +33,11 @@ class NsBatchParams(ctypes.Structure):
                 ("cta_cache", ctypes.c_uint32)]
 
 
+class NsStreamTiming(ctypes.Structure):
+    _fields_ = [("submit_us", ctypes.c_double), ("admit_us", ctypes.c_double), ("complete_us", ctypes.c_double),
+                ("window_id", U64)]
+
+
 class NsTraceEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", U64), ("total_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double)]
@@ -64,6 +69,12 @@ SIGNATURES = {
     "ns_batch_set_params": (ST, [P, ctypes.POINTER(NsBatchParams)]),
     "ns_batch_run": (ST, [P, P, P, P, ctypes.POINTER(U64), U64, P, P, P]),
     "ns_batch_tune": (ST, [P, P, P, P, ctypes.POINTER(U64), U64, P, P, ctypes.POINTER(NsBatchParams)]),
+    "ns_server_create": (ST, [P, P, ctypes.POINTER(P)]),
+    "ns_server_destroy": (None, [P]),
+    "ns_stream_submit": (ST, [P, P, P, U64, U64, ctypes.POINTER(U64)]),
+    "ns_stream_poll": (ST, [P, U64, ctypes.POINTER(I32)]),
+    "ns_stream_wait": (ST, [P, U64, ctypes.POINTER(NsStats), ctypes.POINTER(NsStats), ctypes.c_int64,
+                           ctypes.POINTER(NsStreamTiming)]),
     "ns_last_error": (ctypes.c_char_p, []),
     "ns_status_string": (ctypes.c_char_p, [ST]),
 }
