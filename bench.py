@@ -56,10 +56,12 @@ def parse():
                     help="seconds of oracle work for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="stream", choices=["stream", "oneshot", "batched"],
+    ap.add_argument("--workload", default="stream", choices=["stream", "oneshot", "batched", "serve"],
                     help="stream: 512 windows of 2^17 with stats after each (default); "
                          "oneshot: one 2^30-packet build, sort path vs hash path; "
-                         "batched: 8192 uneven windows, batched launch vs plain per-window launches")
+                         "batched: 8192 uneven windows, batched launch vs plain per-window launches; "
+                         "serve: Poisson arrivals at 80%% of capacity, p50/p99 window-to-stats latency")
+    ap.add_argument("--serve-windows", type=int, default=448, help="serve: windows per phase")
     ap.add_argument("--batch-windows", type=int, default=8192, help="batched: number of windows")
     ap.add_argument("--tuner-cache", default=None, help="batched: autotuner cache file (default: none, tune now)")
     ap.add_argument("--packets", type=int, default=1 << 30, help="oneshot: packets in the build")
@@ -590,6 +592,115 @@ def run_batched(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args, rank, world, local):
+    """Workload 5: windows of log-uniform size in [2^12, 2^22] packets (RMAT
+    scale 32 + 10% uniform) arrive from host memory.  Phase 1 measures the
+    service's capacity with every window submitted at once (closed loop);
+    phase 2 submits a fresh set as a Poisson process at 80% of that rate.
+    Latency is the library's submit -> both statistics records on the host."""
+    import threading as th
+    import torch
+    import gen.workloads as W
+    import paper_2509_03653_b300 as ns
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    Wn = args.serve_windows
+    sizes, _ = W.serving_plan(2 * Wn, 1.0)
+    wins = []
+    for w in range(2 * Wn):
+        s, d = W.serving_window(w, int(sizes[w]))
+        wins.append((torch.from_numpy(s.view(np.int32)).pin_memory(), torch.from_numpy(d.view(np.int32)).pin_memory()))
+    phase = [wins[:Wn], wins[Wn:]]
+    pk = [int(sizes[:Wn].sum()), int(sizes[Wn:].sum())]
+
+    def service(total):
+        ctx = ns.Context(local, path="hash", max_slots=8, hbm_budget_bytes=64 << 30)
+        acc = ns.Matrix(ctx)
+        ns.matrix_reserve(acc, total)
+        return ctx, acc, ns.Server(ctx, acc)
+
+    # warm-up (allocations of the slots)
+    ctx, acc, srv = service(pk[0])
+    for t in [ns.stream_submit(srv, s, d, i) for i, (s, d) in enumerate(phase[0][:16])]:
+        ns.stream_wait(srv, t)
+    srv.close()
+
+    # phase 1: closed loop -> capacity
+    ctx, acc, srv = service(pk[0])
+    t0 = time.perf_counter()
+    pending, i = [], 0
+    while i < Wn or pending:  # keep the queue full; wait in ticket order
+        while i < Wn:
+            try:
+                pending.append(ns.stream_submit(srv, phase[0][i][0], phase[0][i][1], i))
+                i += 1
+            except ns.NsError as e:
+                if e.name != "NS_ERR_BUSY":
+                    raise
+                break
+        if pending:
+            ns.stream_wait(srv, pending.pop(0))
+    cap_s = time.perf_counter() - t0
+    srv.close()
+    cap_wps = Wn / cap_s
+    cap_pps = pk[0] / cap_s
+
+    # phase 2: Poisson arrivals at 80% of capacity
+    rate = 0.8 * cap_wps
+    _, arrivals = W.serving_plan(Wn, rate)
+    ctx, acc, srv = service(pk[1])
+    tickets = [None] * Wn
+    busy = [0]
+
+    def submitter():
+        start = time.perf_counter()
+        for i, (s, d) in enumerate(phase[1]):
+            while True:
+                dt = start + float(arrivals[i]) - time.perf_counter()
+                if dt <= 0:
+                    break
+                time.sleep(min(dt, 0.0005))
+            while True:
+                try:
+                    tickets[i] = ns.stream_submit(srv, s, d, i)
+                    break
+                except ns.NsError as e:
+                    if e.name != "NS_ERR_BUSY":
+                        raise
+                    busy[0] += 1
+                    time.sleep(0.0001)
+
+    thr = th.Thread(target=submitter)
+    thr.start()
+    lat, first, last = [], None, None
+    for i in range(Wn):
+        while tickets[i] is None:
+            time.sleep(0.0001)
+        _, _, tm = ns.stream_wait(srv, tickets[i])
+        lat.append((tm["complete_us"] - tm["submit_us"]) / 1e3)
+        first = tm["submit_us"] if first is None else min(first, tm["submit_us"])
+        last = tm["complete_us"] if last is None else max(last, tm["complete_us"])
+    thr.join()
+    srv.close()
+    span_s = (last - first) / 1e6
+    lat = np.array(lat)
+    line = {
+        "metric": METRIC, "value": pk[1] / span_s, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": span_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"streaming serving: {Wn} windows per phase, sizes log-uniform in [2^12, 2^22], "
+                               "RMAT scale 32 + 10% uniform from pinned host memory, Poisson arrivals at 80% of "
+                               "measured capacity, 64 GiB HBM admission budget, 8 slots",
+                   "packets": pk[1]},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean": float(lat.mean()), "max": float(lat.max())},
+        "capacity": {"windows_per_s": cap_wps, "packets_per_s": cap_pps},
+        "offered_windows_per_s": rate, "busy_retries": busy[0],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -603,6 +714,10 @@ def main():
     if args.workload == "batched":
         if rank == 0:
             run_batched(args, rank, world, local)
+        return
+    if args.workload == "serve":
+        if rank == 0:
+            run_serve(args, rank, world, local)
         return
     run_ours(args, rank, world, local)
 
