@@ -31,6 +31,9 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kItems = 16;
 constexpr int kTile = kThreads * kItems;  // 4096
 constexpr int kRadix = 256;
+#ifndef NS_ONESWEEP_NT
+#define NS_ONESWEEP_NT 512
+#endif
 
 constexpr u64 kFlagAgg = 1, kFlagPrefix = 2;
 constexpr u64 kValMask = (1ull << 46) - 1;
@@ -63,30 +66,6 @@ __device__ u64 lookback(u64* status, u64 stride, u64 tile, u32 tag, DevStats* st
         }
     }
     return prefix;
-}
-
-// exclusive scan of one u32 per thread over a 256-thread block
-__device__ __forceinline__ u32 block_excl_scan(u32 v, u32* wsum, u32* total) {
-    const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    u32 x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        u32 y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-        if (lane >= (u32)o) x += y;
-    }
-    if (lane == 31) wsum[w] = x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        u32 run = 0;
-        for (int i = 0; i < kWarps; ++i) {
-            u32 t = wsum[i];
-            wsum[i] = run;
-            run += t;
-        }
-        *total = run;
-    }
-    __syncthreads();
-    return wsum[w] + x - v;
 }
 
 __device__ __forceinline__ u64 block_excl_scan64(u64 v, u64* wsum, u64* total) {
@@ -175,14 +154,15 @@ __global__ void __launch_bounds__(kThreads) k_sort_offsets(const u32* __restrict
 // time for double buffering was measured slower: successors then wait on a
 // tile whose count cannot be published until its CTA gets to it.)
 
-template <typename K, bool HAS_V>
+template <typename K, bool HAS_V, int NT>
 struct ScatterSmem {
-    K keys[kTile];  // staged tile, then the tile in digit order
-    u64 vals[HAS_V ? kTile : 1];
-    unsigned short whist[kWarps][kRadix];  // per-warp digit counts (<= 512)
+    static constexpr int NW = NT / 32, TILE = NT * kItems;
+    K keys[TILE];  // staged tile, then the tile in digit order
+    u64 vals[HAS_V ? TILE : 1];
+    unsigned short whist[NW][kRadix];  // per-warp digit counts (<= 512)
     u32 lstart[kRadix];
     u64 gbase[kRadix];
-    u32 wsum[kWarps];
+    u32 wsum[NW];
     u32 total;
     u32 tile;
     u64 bar;
@@ -192,9 +172,10 @@ struct ScatterSmem {
 // 0 issues bulk copies of the 16-byte-aligned prefix and the threads load the
 // ragged tail (< 4 elements); otherwise all threads load.  Packed mode stages
 // the two uint32 columns side by side in the key buffer's bytes.
-template <typename K, bool HAS_V, int LOAD>
-__device__ __forceinline__ void stage_tile(const SortIn& in, ScatterSmem<K, HAS_V>& sm, u64 base, u32 tile_n,
+template <typename K, bool HAS_V, int LOAD, int NT>
+__device__ __forceinline__ void stage_tile(const SortIn& in, ScatterSmem<K, HAS_V, NT>& sm, u64 base, u32 tile_n,
                                            bool bulk, DevStats* st) {
+    constexpr int kTile = NT * kItems;
     u32* s32 = reinterpret_cast<u32*>(sm.keys);
     constexpr u32 kq = (LOAD == LOAD_PACK) ? 4u : (16u / (u32)sizeof(K));
     const u32 nb = bulk ? (tile_n & ~(kq - 1)) : 0u;
@@ -216,7 +197,7 @@ __device__ __forceinline__ void stage_tile(const SortIn& in, ScatterSmem<K, HAS_
             if (nv) bulk_g2s(sm.vals, in.vals + base, nv * 8u, &sm.bar);
         }
     }
-    for (u32 i = nb + threadIdx.x; i < tile_n; i += kThreads) {
+    for (u32 i = nb + threadIdx.x; i < tile_n; i += NT) {
         if constexpr (LOAD == LOAD_PACK) {
             s32[i] = in.src[base + i];
             s32[kTile + i] = in.dst[base + i];
@@ -227,19 +208,44 @@ __device__ __forceinline__ void stage_tile(const SortIn& in, ScatterSmem<K, HAS_
         }
     }
     if constexpr (HAS_V && LOAD != LOAD_PACK) {
-        for (u32 i = nv + threadIdx.x; i < tile_n; i += kThreads) sm.vals[i] = in.vals[base + i];
+        for (u32 i = nv + threadIdx.x; i < tile_n; i += NT) sm.vals[i] = in.vals[base + i];
     }
     if (bulk) mbar_wait_bounded(&sm.bar, 0, st);
 }
 
-template <typename K, bool HAS_V, int LOAD>
-__global__ void __launch_bounds__(kThreads, HAS_V ? 3 : 4) k_onesweep(SortIn in, K* __restrict__ kout,
-                                                                       u64* __restrict__ vout, u64 n_arg, int shift,
-                                                                       const u64* __restrict__ offs,
-                                                                       u64* __restrict__ status, u32* tile_counter,
-                                                                       u32 tag, DevStats* st) {
+// exclusive scan of one u32 per thread over an NT-thread block
+template <int NT>
+__device__ __forceinline__ u32 block_excl_scan_nt(u32 v, u32* wsum, u32* total) {
+    constexpr int NW = NT / 32;
+    const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    u32 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        u32 y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (u32)o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u32 run = 0;
+        for (int i = 0; i < NW; ++i) {
+            u32 tt = wsum[i];
+            wsum[i] = run;
+            run += tt;
+        }
+        *total = run;
+    }
+    __syncthreads();
+    return wsum[w] + x - v;
+}
+
+template <typename K, bool HAS_V, int LOAD, int NT>
+__global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT == 512) ? 2 : (HAS_V ? 3 : 4))
+    k_onesweep(SortIn in, K* __restrict__ kout, u64* __restrict__ vout, u64 n_arg, int shift,
+               const u64* __restrict__ offs, u64* __restrict__ status, u32* tile_counter, u32 tag, DevStats* st) {
+    constexpr int kWarps = NT / 32, kTile = NT * kItems;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ScatterSmem<K, HAS_V>& sm = *reinterpret_cast<ScatterSmem<K, HAS_V>*>(smem_raw);
+    ScatterSmem<K, HAS_V, NT>& sm = *reinterpret_cast<ScatterSmem<K, HAS_V, NT>*>(smem_raw);
     const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const u32 FULL = 0xFFFFFFFFu;
     const u64 n = in.n_dev ? *in.n_dev : n_arg;
@@ -250,14 +256,14 @@ __global__ void __launch_bounds__(kThreads, HAS_V ? 3 : 4) k_onesweep(SortIn in,
         sm.tile = atomicAdd(tile_counter, 1u);
         mbar_init(&sm.bar, 1);
     }
-    for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&sm.whist[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kWarps * kRadix; i += NT) (&sm.whist[0][0])[i] = 0;
     __syncthreads();
     const u64 tile = sm.tile;
     const u64 base = tile * kTile;
     if (base >= n) return;  // launched for an upper bound; nothing to publish
     const u32 tile_n = (u32)((n - base) < (u64)kTile ? (n - base) : (u64)kTile);
 
-    stage_tile<K, HAS_V, LOAD>(in, sm, base, tile_n, bulk, st);
+    stage_tile<K, HAS_V, LOAD, NT>(in, sm, base, tile_n, bulk, st);
     __syncthreads();
 
     // warp w owns tile items [w*kItems*32, +kItems*32), read consecutively
@@ -300,22 +306,26 @@ __global__ void __launch_bounds__(kThreads, HAS_V ? 3 : 4) k_onesweep(SortIn in,
     // per digit (thread = digit): exclusive over warps, tile count
     const u32 d = threadIdx.x;
     u32 run = 0;
+    if (d < (u32)kRadix) {
 #pragma unroll
-    for (int ww = 0; ww < kWarps; ++ww) {
-        const u32 c = sm.whist[ww][d];
-        sm.whist[ww][d] = (unsigned short)run;
-        run += c;
+        for (int ww = 0; ww < kWarps; ++ww) {
+            const u32 c = sm.whist[ww][d];
+            sm.whist[ww][d] = (unsigned short)run;
+            run += c;
+        }
+        // publish this tile's count early so successors can proceed
+        st_volatile(&status[tile * kRadix + d], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, run));
     }
-    // publish this tile's count early so successors can proceed
-    st_volatile(&status[tile * kRadix + d], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, run));
-    const u32 ls = block_excl_scan(run, sm.wsum, &sm.total);
-    sm.lstart[d] = ls;
-    u64 prefix = 0;
-    if (tile > 0) {
-        prefix = lookback(status + d, kRadix, tile, tag, st);
-        st_volatile(&status[tile * kRadix + d], pack_status(tag, kFlagPrefix, prefix + run));
+    const u32 ls = block_excl_scan_nt<NT>(run, sm.wsum, &sm.total);
+    if (d < (u32)kRadix) {
+        sm.lstart[d] = ls;
+        u64 prefix = 0;
+        if (tile > 0) {
+            prefix = lookback(status + d, kRadix, tile, tag, st);
+            st_volatile(&status[tile * kRadix + d], pack_status(tag, kFlagPrefix, prefix + run));
+        }
+        sm.gbase[d] = offs[d] + prefix;
     }
-    sm.gbase[d] = offs[d] + prefix;
     __syncthreads();
 
     // place keys in tile-local digit order
@@ -335,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, HAS_V ? 3 : 4) k_onesweep(SortIn in,
 
     // write out: consecutive smem positions of one digit go to consecutive
     // global positions
-    for (u32 i = threadIdx.x; i < tile_n; i += kThreads) {
+    for (u32 i = threadIdx.x; i < tile_n; i += NT) {
         const K key = sm.keys[i];
         const u32 dk = (u32)(key >> shift) & 0xFF;
         const u64 dst = sm.gbase[dk] + (i - sm.lstart[dk]);
@@ -576,20 +586,35 @@ constexpr const char* onesweep_name() {
     else return "k_onesweep<u64 key>";
 }
 
+template <typename K, bool HAS_V, int LOAD, int NT>
+void launch_onesweep_nt(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
+                        u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s) {
+    const size_t smem = sizeof(ScatterSmem<K, HAS_V, NT>);
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_onesweep<K, HAS_V, LOAD, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        configured = true;
+    }
+    constexpr u64 tile = (u64)NT * kItems;
+    const u64 tiles = (n + tile - 1) / tile;
+    if (tiles == 0) return;
+    TraceScope ts(tr, onesweep_name<K, HAS_V>(), s);
+    k_onesweep<K, HAS_V, LOAD, NT><<<(unsigned)tiles, NT, smem, s>>>(in, kout, vout, n, shift, offs, status,
+                                                                     tile_counter, tag, st);
+}
+
+// 64-bit keys without values use 8192-key tiles (512 threads): half the
+// look-back hops and per-tile fixed work per key; pairs keep 4096-key tiles
+// (their shared memory would not fit twice).
 template <typename K, bool HAS_V, int LOAD>
 void launch_onesweep(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
                      u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s) {
-    const size_t smem = sizeof(ScatterSmem<K, HAS_V>);
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_onesweep<K, HAS_V, LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = true;
-    }
-    const u64 tiles = (n + kTile - 1) / kTile;
-    if (tiles == 0) return;
-    TraceScope ts(tr, onesweep_name<K, HAS_V>(), s);
-    k_onesweep<K, HAS_V, LOAD><<<(unsigned)tiles, kThreads, smem, s>>>(in, kout, vout, n, shift, offs, status,
-                                                                       tile_counter, tag, st);
+    if constexpr (sizeof(K) == 8 && !HAS_V)
+        launch_onesweep_nt<K, HAS_V, LOAD, NS_ONESWEEP_NT>(in, kout, vout, n, shift, offs, status, tile_counter, tag,
+                                                           st, tr, s);
+    else
+        launch_onesweep_nt<K, HAS_V, LOAD, 256>(in, kout, vout, n, shift, offs, status, tile_counter, tag, st, tr, s);
 }
 
 template <int KEYMODE, bool HAS_V>
