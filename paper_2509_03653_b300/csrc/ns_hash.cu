@@ -424,11 +424,27 @@ __global__ void __launch_bounds__(kInsertThreads) k_insert_packets(const u32* __
     const u64 stride = (u64)gridDim.x * blockDim.x;
     // warp-uniform trip count so that every lane reaches the warp intrinsics
     const u64 warp_base = ((u64)blockIdx.x * blockDim.x) + (threadIdx.x & ~31u);
-    for (u64 b = warp_base; b < n; b += stride) {
+    // When launched as a programmatic dependent of the previous window's
+    // launch, this grid may start before that one has finished: let the next
+    // launch start too, read this window's packets (which do not depend on
+    // the previous grid), and only then wait for the previous grid's writes to
+    // the tables and statistics.  Without such a launch the wait returns at once.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    u64 b = warp_base;
+    u64 key = 0;
+    bool valid = false;
+    if (b < n) {
         const u64 i = b + lane_id();
-        const bool valid = i < n;
-        u64 key = 0;
+        valid = i < n;
         if (valid) key = ((u64)__ldg(src + i) << 32) | (u64)__ldg(dst + i);
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    for (; b < n; b += stride) {
+        if (b != warp_base) {
+            const u64 i = b + lane_id();
+            valid = i < n;
+            key = valid ? (((u64)__ldg(src + i) << 32) | (u64)__ldg(dst + i)) : 0ull;
+        }
         insert_item<CACHE>(M, valid, key, 1, true, bs, C);
     }
     if constexpr (CACHE) cache_flush(M, *C, bs);
@@ -625,10 +641,20 @@ void launch_insert_packets_snapshot(const u32* src, const u32* dst, u64 n, const
         launch_stats_out(M.stats, out, s);
         return;
     }
-    if (cache)
-        k_insert_packets<true><<<grid_for(n, kInsertThreads, sms, 8), kInsertThreads, sizeof(CtaCache), s>>>(src, dst, n, M, out);
-    else
-        k_insert_packets<false><<<grid_for(n, kInsertThreads, sms, 8), kInsertThreads, 0, s>>>(src, dst, n, M, out);
+    // programmatic dependent launch: overlaps this launch's start and packet
+    // loads with the tail of the previous kernel on the stream
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid_for(n, kInsertThreads, sms, 8));
+    cfg.blockDim = dim3(kInsertThreads);
+    cfg.dynamicSmemBytes = cache ? sizeof(CtaCache) : 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cache) cudaLaunchKernelEx(&cfg, k_insert_packets<true>, src, dst, n, M, out);
+    else cudaLaunchKernelEx(&cfg, k_insert_packets<false>, src, dst, n, M, out);
 }
 
 void launch_insert_slots(const LinkSlot* in, u64 in_cap, const HashView& M, int sms,
