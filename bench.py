@@ -79,6 +79,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(values, world, device=None):
+    """Element-wise maximum of a list of floats over all ranks (the slowest
+    rank's times); identity when world == 1."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units per second of the whole job: every rank's units over the slowest
+    rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def workload_config(extra=None, windows=WINDOWS):
     cfg = {
         "workload": "accumulated RMAT stream: 2^26 packets as 512 windows of 2^17, "
@@ -374,18 +392,13 @@ def run_ours(args, rank, world, local):
     clocks.stop()
 
     # ---- gather over ranks (max time)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, e2e["ms"] if e2e else 0.0], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t[0])
-        if e2e:
-            e2e["ms"] = float(t[1])
+    ms, ms_instr, ms_e2e = max_over_ranks([ms, ms_instr, e2e["ms"] if e2e else 0.0], world, dev)
+    if e2e:
+        e2e["ms"] = ms_e2e
     if rank != 0:
         return
 
-    packets = world * args.steps * N
-    value = packets / (ms / 1e3)
+    value = whole_job_rate(args.steps * N, world, ms)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     peak = peaks.get("hbm_gbs", 6400.0)
@@ -412,7 +425,7 @@ def run_ours(args, rank, world, local):
         "ms_per_step_instrumented": ms_instr / args.steps,
     }
     if e2e:
-        line["e2e"] = {"value": world * args.steps * N / (e2e["ms"] / 1e3), "unit": UNIT,
+        line["e2e"] = {"value": whole_job_rate(args.steps * N, world, e2e["ms"]), "unit": UNIT,
                        "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]}
     if not args.no_cpu_baseline:
         rate, wins, el = oracle_stream_rate(h_src.numpy().view(np.uint32), h_dst.numpy().view(np.uint32),

@@ -326,6 +326,15 @@ typedef struct {
 ns_status ns_trace_enable(ns_ctx* ctx, int on);
 ns_status ns_trace_read(ns_ctx* ctx, ns_trace_entry* out, int cap, int* count);
 
+/* Diagnostic of the device-side wait bounds (no counterpart in the paper):
+ * runs one of the library's bounded waits against something nothing will
+ * signal -- which = 0: a decoupled look-back on a status word that is never
+ * published; which = 1: an mbarrier phase expecting bytes no copy delivers --
+ * and returns NS_ERR_TIMEOUT once the wait gives up (about one second for
+ * the look-back, two for the mbarrier, which waits a second time so that no
+ * copy can still be in flight).  Blocking; the context stays usable. */
+ns_status ns_diag_wait_timeout(int which, ns_stream_t stream);
+
 /* ---- errors ------------------------------------------------------------ */
 
 const char* ns_last_error(void);

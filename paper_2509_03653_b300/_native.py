@@ -75,6 +75,7 @@ SIGNATURES = {
     "ns_stream_poll": (ST, [P, U64, ctypes.POINTER(I32)]),
     "ns_stream_wait": (ST, [P, U64, ctypes.POINTER(NsStats), ctypes.POINTER(NsStats), ctypes.c_int64,
                            ctypes.POINTER(NsStreamTiming)]),
+    "ns_diag_wait_timeout": (ST, [I32, P]),
     "ns_last_error": (ctypes.c_char_p, []),
     "ns_status_string": (ctypes.c_char_p, [ST]),
 }

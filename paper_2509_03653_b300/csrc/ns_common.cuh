@@ -55,10 +55,18 @@ struct __align__(16) NodeSlot {
     u64 packets; // A 1 or 1^T A
 };
 
-// Bounds on device-side loops: a probe sequence or a spin that reaches its
-// bound records an error instead of continuing.
+// Bounds on device-side loops: a probe sequence or a wait that reaches its
+// bound records an error instead of continuing.  Waits are bounded in time
+// (about one second of the GPU's global timer) and, as a backstop, in polls.
 constexpr u32 kMaxProbes = 1u << 16;
 constexpr u32 kMaxSpin = 1u << 24;
+constexpr u64 kWaitLimitNs = 1000000000ull;
+
+__device__ __forceinline__ u64 globaltimer_ns() {
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // 64-bit finalizing mixer (two multiply-xorshift rounds with odd constants).
 __device__ __forceinline__ u64 mix64(u64 x) {
@@ -142,15 +150,23 @@ __device__ __forceinline__ bool mbar_test_wait(u64* bar, u32 parity) {
 // Bounded wait for an mbarrier phase.  If the bound is reached the error is
 // recorded and the wait continues, again bounded, so that no copy is still
 // landing in shared memory when the CTA retires.
-constexpr u32 kMaxBarrierPolls = 1u << 22;
+constexpr u32 kMaxBarrierPolls = 1u << 26;
 __device__ __forceinline__ void mbar_wait_bounded(u64* bar, u32 parity, DevStats* st) {
+    u64 t0 = 0;
     for (u32 i = 0; i < kMaxBarrierPolls; ++i) {
         if (mbar_test_wait(bar, parity)) return;
-        if (i > 64) __nanosleep(32);
+        if (i > 64) {
+            const u64 now = globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitLimitNs) break;
+            __nanosleep(32);
+        }
     }
     set_error(st, ERR_TIMEOUT);
+    t0 = globaltimer_ns();
     for (u32 i = 0; i < kMaxBarrierPolls; ++i) {
         if (mbar_test_wait(bar, parity)) return;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) return;
         __nanosleep(64);
     }
 }

@@ -75,6 +75,7 @@ inline u32 next_tag(SortScratch& sc, cudaStream_t s) {
 }
 
 u64 sort_tiles(u64 n);
+void launch_diag_wait(int which, u64* status_word, DevStats* st, cudaStream_t s);
 int sort_radix();
 
 // Batched windows: per-window tables carved from one arena (ns_batch.cu).

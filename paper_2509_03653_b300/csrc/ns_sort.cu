@@ -48,6 +48,7 @@ __device__ u64 lookback(u64* status, u64 stride, u64 tile, u32 tag, DevStats* st
     u64 prefix = 0;
     long long k = (long long)tile - 1;
     u32 spins = 0;
+    u64 t0 = 0;
     while (k >= 0) {
         const u64 s = ld_volatile(&status[(u64)k * stride]);
         const u32 stag = (u32)(s >> 48);
@@ -57,8 +58,11 @@ __device__ u64 lookback(u64* status, u64 stride, u64 tile, u32 tag, DevStats* st
             if (flag == kFlagPrefix) break;
             --k;
             spins = 0;
+            t0 = 0;
         } else {
-            if (++spins > kMaxSpin) {
+            const u64 now = globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            if (++spins > kMaxSpin || now - t0 > kWaitLimitNs) {
                 set_error(st, ERR_TIMEOUT);
                 break;
             }
@@ -636,6 +640,24 @@ void launch_runs_t(const void* keys, const u64* vals, u64 n, const u64* n_dev, u
         keys, vals, n, n_dev, head_keys, pos, psum, status_c, status_s, tile_counter, tag, R_out, st);
 }
 
+// Diagnostics: the library's bounded waits run against something nothing
+// will ever signal -- a look-back status word that is never published, an
+// mbarrier phase expecting bytes that no copy delivers -- so that they time
+// out and record ERR_TIMEOUT.  No fault, trap or unbounded wait is involved.
+__global__ void k_diag_lookback(u64* status, DevStats* st) {
+    if (threadIdx.x == 0) lookback(status, 1, 1, 0x7777u, st);
+}
+
+__global__ void k_diag_mbarrier(DevStats* st) {
+    __shared__ u64 bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_arrive_expect_tx(&bar, 64);  // no copy will deliver these bytes
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0, st);
+}
+
 }  // namespace
 
 u64 sort_tiles(u64 n) { return (n + kTile - 1) / kTile; }
@@ -756,4 +778,11 @@ void launch_run_stats(int mode, const u64* pos, const u64* psum, const u64* R_pt
                                                  (const u64*)R_ptr, (u64*)counts_out, st);
 }
 
+}  // namespace ns
+
+namespace ns {
+void launch_diag_wait(int which, u64* status_word, DevStats* st, cudaStream_t s) {
+    if (which == 0) k_diag_lookback<<<1, 32, 0, s>>>(status_word, st);
+    else k_diag_mbarrier<<<1, 32, 0, s>>>(st);
+}
 }  // namespace ns

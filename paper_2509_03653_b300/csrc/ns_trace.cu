@@ -104,4 +104,31 @@ ns_status ns_trace_read(ns_ctx* c, ns_trace_entry* out, int cap, int* count) {
     return st;
 }
 
+ns_status ns_diag_wait_timeout(int which, ns_stream_t stream) {
+    if (which != 0 && which != 1) return ns::set_fail(NS_ERR_INVALID, "ns_diag_wait_timeout: which must be 0 or 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    ns::Buf b;
+    ns_status st = ns::buf_reserve(b, sizeof(ns::DevStats) + 64);
+    if (st != NS_OK) return st;
+    ns::DevStats h{};
+    ns::DevStats* d = (ns::DevStats*)b.p;
+    ns::u64* status_word = (ns::u64*)((char*)b.p + sizeof(ns::DevStats));
+    if (cudaMemsetAsync(b.p, 0, sizeof(ns::DevStats) + 64, s) != cudaSuccess) {
+        cudaGetLastError();
+        ns::buf_free(b);
+        return ns::set_fail(NS_ERR_CUDA, "ns_diag_wait_timeout: memset failed");
+    }
+    ns::launch_diag_wait(which, status_word, d, s);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    ns::buf_free(b);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return ns::set_fail(NS_ERR_CUDA, "ns_diag_wait_timeout: launch failed");
+    }
+    if (h.err & ns::ERR_TIMEOUT) return ns::set_fail(NS_ERR_TIMEOUT, "bounded device wait gave up (as intended)");
+    return ns::set_fail(NS_ERR_STATE, "ns_diag_wait_timeout: the wait did not report a timeout");
+}
+
 }  // extern "C"

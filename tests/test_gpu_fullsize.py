@@ -1,0 +1,182 @@
+"""Parity at the full workload sizes, in the launch configurations bench.py
+times.  Where the oracle cannot run the whole workload in test time, outputs
+are checked by samples the oracle (or a direct count in the raw input)
+computes one by one, and by properties that hold at any size."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import gen.workloads as W
+import oracle
+import paper_2509_03653_b300 as ns
+from gpu_util import export_np, stats_row, to_dev
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def pinned_pair(n):
+    s = torch.empty(n, dtype=torch.int32).pin_memory()
+    d = torch.empty(n, dtype=torch.int32).pin_memory()
+    return s, d, s.numpy().view(np.uint32), d.numpy().view(np.uint32)
+
+
+def test_stream_512_windows_of_2p17():
+    """Workload 2 as bench.py runs it: one ns_window_ingest_stats launch per
+    window.  Exact A after all windows; exact running quantities after
+    sampled windows; invariants after every window."""
+    NW, WIN = W.W2_WINDOWS, W.W2_WINDOW
+    N = NW * WIN
+    hs, hd, s, d = pinned_pair(N)
+    W.rmat_stream(N, src=s, dst=d)
+    ds, dd = hs.cuda(), hd.cuda()
+    ctx = ns.Context(0, path="hash")
+    A = ns.Matrix(ctx)
+    ns.matrix_reserve(A, N)
+    rows = torch.zeros(NW, 16, dtype=torch.int64, device="cuda")
+    for w in range(NW):
+        sl = slice(w * WIN, (w + 1) * WIN)
+        ns.window_ingest_stats(ctx, A, ds[sl], dd[sl], rows[w])
+    torch.cuda.synchronize()
+    got = rows.cpu().numpy().view(np.uint64)[:, :9]
+    # invariants after every window
+    assert np.array_equal(got[:, 0], (np.arange(NW, dtype=np.uint64) + 1) * WIN)
+    assert np.all(np.diff(got.astype(np.int64), axis=0) >= 0)  # monotone running quantities
+    assert np.all(got[:, 1] <= got[:, 0]) and np.all(got[:, 5] <= got[:, 3]) and np.all(got[:, 7] <= got[:, 2])
+    # sampled windows against the oracle's prefix
+    for w in (0, 1, 2, 100, 255):
+        k, c = oracle.build_matrix(s[: (w + 1) * WIN], d[: (w + 1) * WIN])
+        assert stats_row(rows[w]) == oracle.stats(k, c), w
+    # the whole stream: A's nonzeros and the last window's quantities
+    k, c = oracle.build_matrix(s, d)
+    assert stats_row(rows[NW - 1]) == oracle.stats(k, c)
+    gk, gc = export_np(A)
+    np.testing.assert_array_equal(gk, k)
+    np.testing.assert_array_equal(gc, c)
+
+
+def test_oneshot_2p30_both_paths():
+    """Workload 3: 2^30 packets.  Both paths must agree on every quantity and
+    on A (order-independent digest); sampled links are counted directly in
+    the raw input; valid = N and the invariants hold."""
+    N = W.W3_N
+    hs, hd, s, d = pinned_pair(N)
+    W.large_build(N, src=s, dst=d)
+    ds, dd = hs.cuda(), hd.cuda()
+    res = {}
+    for path in ("sort", "hash"):
+        ctx = ns.Context(0, path=path)
+        m = ns.Matrix(ctx)
+        ns.window_build(ctx, ds, dd, m)
+        st = ns.network_stats(ctx, m)
+        k, c = export_np(m)
+        res[path] = (st, oracle.digest(k, c), k, c)
+        m.free()
+        ctx.close()
+        torch.cuda.empty_cache()
+    st, dg, k, c = res["sort"]
+    assert res["hash"][0] == st and res["hash"][1] == dg
+    assert st["valid_packets"] == N and int(c.sum()) == N and st["unique_links"] == k.size
+    assert np.all(np.diff(k.astype(np.uint64)) > 0)  # strictly ascending
+    assert st["max_link_packets"] == int(c.max())
+    assert st["max_src_fanout"] <= st["unique_destinations"] and st["max_dst_fanin"] <= st["unique_sources"]
+    # sampled links: count each in the raw input
+    rng = np.random.default_rng(7)
+    pick = np.unique(np.concatenate([rng.integers(0, k.size, 200), [int(np.argmax(c))]]))
+    sample = k[pick]
+    counts = np.zeros(sample.size, np.int64)
+    for a in range(0, N, 1 << 26):
+        keys = (s[a:a + (1 << 26)].astype(np.uint64) << np.uint64(32)) | d[a:a + (1 << 26)].astype(np.uint64)
+        pos = np.searchsorted(sample, keys)
+        pos[pos == sample.size] = 0
+        hit = sample[pos] == keys
+        counts += np.bincount(pos[hit], minlength=sample.size)
+    np.testing.assert_array_equal(counts.astype(np.uint64), c[pick])
+
+
+def test_batched_8192_windows():
+    """Workload 4: the batched launch equals plain per-window launches on
+    every window and on the aggregate; sampled windows equal the oracle."""
+    sizes, svals = W.batched_plan()
+    Wn = sizes.size
+    off = np.zeros(Wn + 1, np.uint64)
+    off[1:] = np.cumsum(sizes)
+    total = int(off[-1])
+    hs, hd, s, d = pinned_pair(total)
+    for w in range(Wn):
+        a, b = int(off[w]), int(off[w + 1])
+        W.batched_window(w, b - a, float(svals[w]), src=s[a:b], dst=d[a:b])
+    ds, dd = hs.cuda(), hd.cuda()
+    ctx = ns.Context(0, path="hash", hbm_budget_bytes=96 << 30)
+    acc = ns.Matrix(ctx)
+    ns.matrix_reserve_ex(acc, total, 1 << 21)
+    batch = ns.Batch(ctx, Wn, total)
+    out_b = torch.zeros(Wn * 9, dtype=torch.int64, device="cuda")
+    ns.batch_run(ctx, batch, ds, dd, off, out_b, acc)
+    torch.cuda.synchronize()
+    agg_b = ns.network_stats(ctx, acc)
+    batch.free()
+    # plain per-window launches
+    out_p = torch.zeros(Wn * 9, dtype=torch.int64, device="cuda")
+    ns.matrix_clear(acc)
+    At = ns.Matrix(ctx)
+    for w in range(Wn):
+        a, b = int(off[w]), int(off[w + 1])
+        ns.window_build(ctx, ds[a:b], dd[a:b], At)
+        ns.network_stats_async(ctx, At, out_p[w * 9:(w + 1) * 9])
+        ns.accumulate(ctx, acc, At)
+    torch.cuda.synchronize()
+    assert torch.equal(out_b, out_p)
+    assert ns.network_stats(ctx, acc) == agg_b
+    assert agg_b["valid_packets"] == total
+    rows = out_b.cpu().numpy().view(np.uint64).reshape(Wn, 9)
+    assert np.array_equal(rows[:, 0], sizes.astype(np.uint64))
+    rng = np.random.default_rng(3)
+    picks = set(rng.integers(0, Wn, 16).tolist()) | {int(np.argmin(sizes)), int(np.argmax(sizes))}
+    for w in sorted(picks):
+        a, b = int(off[w]), int(off[w + 1])
+        want = oracle.stats_of_packets(s[a:b], d[a:b])
+        assert {f: int(x) for f, x in zip(oracle.FIELDS, rows[w])} == want, w
+
+
+def test_serving_448_windows():
+    """Workload 5 windows through the service (8 slots): every window's
+    per-window quantities equal an independent build; the running
+    quantities of the last window equal a plain accumulation; sampled
+    windows equal the oracle."""
+    Wn = 448
+    sizes, _ = W.serving_plan(Wn, 1.0)
+    wins = []
+    for w in range(Wn):
+        s, d = W.serving_window(w, int(sizes[w]))
+        wins.append((torch.from_numpy(s.view(np.int32)).pin_memory(), torch.from_numpy(d.view(np.int32)).pin_memory()))
+    ctx = ns.Context(0, path="hash", max_slots=8, hbm_budget_bytes=64 << 30)
+    acc = ns.Matrix(ctx)
+    ns.matrix_reserve(acc, int(sizes.sum()))
+    srv = ns.Server(ctx, acc)
+    results = [None] * Wn
+    pending = []  # (window, ticket) in submission order
+    for w, (s, d) in enumerate(wins):
+        while True:
+            try:
+                pending.append((w, ns.stream_submit(srv, s, d, w)))
+                break
+            except ns.NsError as e:  # queue full: wait for the oldest window
+                assert e.name == "NS_ERR_BUSY"
+                pw, t = pending.pop(0)
+                results[pw] = ns.stream_wait(srv, t)
+    for pw, t in pending:
+        results[pw] = ns.stream_wait(srv, t)
+    srv.close()
+    ref = ns.Context(0, path="hash")
+    m, tot = ns.Matrix(ref), ns.Matrix(ref)
+    for w, (s, d) in enumerate(wins):
+        ds, dd = s.cuda(), d.cuda()
+        ns.window_build(ref, ds, dd, m)
+        assert results[w][0] == ns.network_stats(ref, m), w
+        ns.window_ingest(ref, tot, ds, dd)
+    assert results[-1][1] == ns.network_stats(ref, tot)
+    for w in (0, 7, 200, Wn - 1):
+        s, d = wins[w]
+        assert results[w][0] == oracle.stats_of_packets(s.numpy().view(np.uint32), d.numpy().view(np.uint32))

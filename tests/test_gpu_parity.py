@@ -280,3 +280,25 @@ def test_skewed_windows_cache_modes(cache, s_exp, K, n):
     want = oracle.build_matrix(s, d)
     assert ns.network_stats(ctx, acc) == oracle.stats(*want)
     assert_matrix_equal(acc, *want)
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_bounded_device_waits_time_out(which):
+    """A look-back on a status word nobody publishes, and an mbarrier phase
+    expecting bytes no copy delivers: the bounded waits give up with
+    NS_ERR_TIMEOUT within seconds and the device stays usable."""
+    import ctypes
+    import time
+    from paper_2509_03653_b300 import _native
+    L = _native.load()
+    t0 = time.time()
+    st = L.ns_diag_wait_timeout(which, None)
+    el = time.time() - t0
+    assert st == 5, L.ns_last_error()  # NS_ERR_TIMEOUT
+    assert el < 10.0
+    # the context still works afterwards
+    ctx = ns.Context(0, path="sort")
+    s, d = W.single_window(5000)
+    m = ns.Matrix(ctx)
+    ns.window_build(ctx, to_dev(s), to_dev(d), m)
+    assert ns.network_stats(ctx, m) == oracle.stats(*oracle.build_matrix(s, d))
