@@ -340,6 +340,11 @@ def run_ours(args, rank, world, local):
     ms_instr = e0.elapsed_time(e1)
     launch_ms = [a.elapsed_time(b) for ev in events for a, b in ev]
 
+    # the random-atomic ceiling of the same access pattern: one window's worth
+    # of threads, three random 8-byte atomics each, tables as large as A's
+    # link table (no hashing, probing or statistics)
+    rand_ceiling_us = ns.diag_random_atomics(1 << 28, WINDOW, 5)
+
     # correctness guard on the last step (cheap invariant, no oracle)
     last = stats_rows[-1].cpu().numpy().view(np.uint64)
     assert int(last[0]) == N, "valid packets != N"
@@ -419,6 +424,12 @@ def run_ours(args, rank, world, local):
             "alg_bytes_per_launch": alg_bytes_per_launch, "launch_us_avg": avg_launch_ms * 1e3,
             "launch_us_p50": float(np.percentile(launch_ms, 50)) * 1e3,
             "peak_source": f"{peak_src} (hbm_gbs, copy read+write)",
+        },
+        "roofline_random_access": {
+            "bound": "random 8-byte atomics", "kernel": "k_insert_packets",
+            "kernel_us": avg_launch_ms * 1e3, "ceiling_us": rand_ceiling_us,
+            "frac": rand_ceiling_us / (avg_launch_ms * 1e3),
+            "ceiling": "2^17 threads x 3 random atomics into three 2 GiB tables (measured live)",
         },
         "clocks": clock_summary,
         "gpu_launches": args.steps * NW,

@@ -335,6 +335,15 @@ ns_status ns_trace_read(ns_ctx* ctx, ns_trace_entry* out, int cap, int* count);
  * copy can still be in flight).  Blocking; the context stays usable. */
 ns_status ns_diag_wait_timeout(int which, ns_stream_t stream);
 
+/* Diagnostic of the hardware ceiling the hash ingest is bound by (no
+ * counterpart in the paper): `threads` threads each add 1 at one
+ * pseudo-random 8-byte word of each of three tables of table_words words
+ * (a power of two) -- the link, row and column updates of one packet, with
+ * no hashing or probing.  *best_us receives the fastest of `reps` timed
+ * launches (after one warm-up).  Allocates and frees its tables; blocking. */
+ns_status ns_diag_random_atomics(uint64_t table_words, uint64_t threads, int reps, double* best_us,
+                                 ns_stream_t stream);
+
 /* ---- errors ------------------------------------------------------------ */
 
 const char* ns_last_error(void);

@@ -23,7 +23,7 @@ __all__ = [
     "window_ingest_stats", "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
     "matrix_clear", "sync", "PATHS", "window_stats_static", "STATIC_MAX_PACKETS",
     "trace_enable", "trace_read", "Batch", "batch_run", "batch_tune", "matrix_reserve_ex",
-    "Server", "stream_submit", "stream_poll", "stream_wait",
+    "Server", "stream_submit", "stream_poll", "stream_wait", "diag_random_atomics",
 ]
 
 STATIC_MAX_PACKETS = 32768  # NS_STATIC_MAX_PACKETS in include/ns.h
@@ -353,3 +353,14 @@ def stream_wait(server: Server, ticket: int, timeout_us: int = -1):
     as_dict = lambda x: {f: int(getattr(x, f)) for f in FIELDS}
     return as_dict(pw), as_dict(rn), {"submit_us": tm.submit_us, "admit_us": tm.admit_us,
                                       "complete_us": tm.complete_us, "window_id": int(tm.window_id)}
+
+
+def diag_random_atomics(table_words: int, threads: int, reps: int = 5, stream=None) -> float:
+    """Microseconds for `threads` x 3 random 8-byte atomics into three tables
+    of `table_words` words (ns_diag_random_atomics): the ceiling the hash
+    ingest's access pattern is bound by."""
+    L = load()
+    us = ctypes.c_double()
+    check(L.ns_diag_random_atomics(table_words, threads, reps, ctypes.byref(us), _stream(stream)),
+          "ns_diag_random_atomics")
+    return float(us.value)

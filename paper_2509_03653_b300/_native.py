@@ -76,6 +76,7 @@ SIGNATURES = {
     "ns_stream_wait": (ST, [P, U64, ctypes.POINTER(NsStats), ctypes.POINTER(NsStats), ctypes.c_int64,
                            ctypes.POINTER(NsStreamTiming)]),
     "ns_diag_wait_timeout": (ST, [I32, P]),
+    "ns_diag_random_atomics": (ST, [U64, U64, I32, ctypes.POINTER(ctypes.c_double), P]),
     "ns_last_error": (ctypes.c_char_p, []),
     "ns_status_string": (ctypes.c_char_p, [ST]),
 }

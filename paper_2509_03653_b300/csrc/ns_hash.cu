@@ -617,6 +617,19 @@ __global__ void k_batch_stats_out(const DevStats* __restrict__ wstats, u64 W, u6
     }
 }
 
+// Diagnostic: the random-atomic ceiling for the ingest's access pattern --
+// each of `threads` threads adds 1 at one pseudo-random 8-byte word of each of
+// three tables (a link, a row and a column update), all three issued
+// together.  No hashing, probing or statistics: only the memory traffic.
+__global__ void k_diag_rand3(u64* a, u64* b, u64* c, u64 mask, u64 threads, u64 seed) {
+    const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= threads) return;
+    const u64 h = mix64(seed ^ (i * 0x9E3779B97F4A7C15ull));
+    atomicAdd(&a[h & mask], 1ull);
+    atomicAdd(&b[mix64(h + 1) & mask], 1ull);
+    atomicAdd(&c[mix64(h + 2) & mask], 1ull);
+}
+
 int grid_for(u64 n, int threads, int sms, int per_sm) {
     u64 want = (n + threads - 1) / threads;
     u64 cap = (u64)sms * per_sm;
@@ -686,6 +699,10 @@ void launch_batch_insert(const BatchDev& B, u32* tile_counter, u64 total_tiles, 
 void launch_batch_stats_out(const DevStats* wstats, u64 W, u64* out, int sms, cudaStream_t s) {
     if (W == 0) return;
     k_batch_stats_out<<<grid_for(W * S_NFIELDS, 256, sms, 4), 256, 0, s>>>(wstats, W, out);
+}
+
+void launch_diag_rand3(u64* a, u64* b, u64* c, u64 mask, u64 threads, u64 seed, cudaStream_t s) {
+    k_diag_rand3<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a, b, c, mask, threads, seed);
 }
 
 void launch_stats_out(const DevStats* st, u64* out, cudaStream_t s) {

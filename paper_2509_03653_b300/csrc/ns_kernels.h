@@ -76,6 +76,7 @@ inline u32 next_tag(SortScratch& sc, cudaStream_t s) {
 
 u64 sort_tiles(u64 n);
 void launch_diag_wait(int which, u64* status_word, DevStats* st, cudaStream_t s);
+void launch_diag_rand3(u64* a, u64* b, u64* c, u64 mask, u64 threads, u64 seed, cudaStream_t s);
 int sort_radix();
 
 // Batched windows: per-window tables carved from one arena (ns_batch.cu).

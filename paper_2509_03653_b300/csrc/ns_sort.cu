@@ -34,6 +34,9 @@ constexpr int kRadix = 256;
 #ifndef NS_ONESWEEP_NT
 #define NS_ONESWEEP_NT 512
 #endif
+#ifndef NS_ONESWEEP_ITEMS
+#define NS_ONESWEEP_ITEMS 16
+#endif
 
 constexpr u64 kFlagAgg = 1, kFlagPrefix = 2;
 constexpr u64 kValMask = (1ull << 46) - 1;
@@ -158,9 +161,9 @@ __global__ void __launch_bounds__(kThreads) k_sort_offsets(const u32* __restrict
 // time for double buffering was measured slower: successors then wait on a
 // tile whose count cannot be published until its CTA gets to it.)
 
-template <typename K, bool HAS_V, int NT>
+template <typename K, bool HAS_V, int NT, int IT>
 struct ScatterSmem {
-    static constexpr int NW = NT / 32, TILE = NT * kItems;
+    static constexpr int NW = NT / 32, TILE = NT * IT;
     K keys[TILE];  // staged tile, then the tile in digit order
     u64 vals[HAS_V ? TILE : 1];
     unsigned short whist[NW][kRadix];  // per-warp digit counts (<= 512)
@@ -176,10 +179,10 @@ struct ScatterSmem {
 // 0 issues bulk copies of the 16-byte-aligned prefix and the threads load the
 // ragged tail (< 4 elements); otherwise all threads load.  Packed mode stages
 // the two uint32 columns side by side in the key buffer's bytes.
-template <typename K, bool HAS_V, int LOAD, int NT>
-__device__ __forceinline__ void stage_tile(const SortIn& in, ScatterSmem<K, HAS_V, NT>& sm, u64 base, u32 tile_n,
+template <typename K, bool HAS_V, int LOAD, int NT, int IT>
+__device__ __forceinline__ void stage_tile(const SortIn& in, ScatterSmem<K, HAS_V, NT, IT>& sm, u64 base, u32 tile_n,
                                            bool bulk, DevStats* st) {
-    constexpr int kTile = NT * kItems;
+    constexpr int kTile = NT * IT;
     u32* s32 = reinterpret_cast<u32*>(sm.keys);
     constexpr u32 kq = (LOAD == LOAD_PACK) ? 4u : (16u / (u32)sizeof(K));
     const u32 nb = bulk ? (tile_n & ~(kq - 1)) : 0u;
@@ -243,13 +246,13 @@ __device__ __forceinline__ u32 block_excl_scan_nt(u32 v, u32* wsum, u32* total) 
     return wsum[w] + x - v;
 }
 
-template <typename K, bool HAS_V, int LOAD, int NT>
-__global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT == 512) ? 2 : (HAS_V ? 3 : 4))
+template <typename K, bool HAS_V, int LOAD, int NT, int IT>
+__global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >= 384) ? 2 : (HAS_V ? 3 : 4))
     k_onesweep(SortIn in, K* __restrict__ kout, u64* __restrict__ vout, u64 n_arg, int shift,
                const u64* __restrict__ offs, u64* __restrict__ status, u32* tile_counter, u32 tag, DevStats* st) {
-    constexpr int kWarps = NT / 32, kTile = NT * kItems;
+    constexpr int kWarps = NT / 32, kTile = NT * IT, kItems = IT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ScatterSmem<K, HAS_V, NT>& sm = *reinterpret_cast<ScatterSmem<K, HAS_V, NT>*>(smem_raw);
+    ScatterSmem<K, HAS_V, NT, IT>& sm = *reinterpret_cast<ScatterSmem<K, HAS_V, NT, IT>*>(smem_raw);
     const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const u32 FULL = 0xFFFFFFFFu;
     const u64 n = in.n_dev ? *in.n_dev : n_arg;
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT == 512) ? 2 : (HAS_
     if (base >= n) return;  // launched for an upper bound; nothing to publish
     const u32 tile_n = (u32)((n - base) < (u64)kTile ? (n - base) : (u64)kTile);
 
-    stage_tile<K, HAS_V, LOAD, NT>(in, sm, base, tile_n, bulk, st);
+    stage_tile<K, HAS_V, LOAD, NT, IT>(in, sm, base, tile_n, bulk, st);
     __syncthreads();
 
     // warp w owns tile items [w*kItems*32, +kItems*32), read consecutively
@@ -590,21 +593,21 @@ constexpr const char* onesweep_name() {
     else return "k_onesweep<u64 key>";
 }
 
-template <typename K, bool HAS_V, int LOAD, int NT>
+template <typename K, bool HAS_V, int LOAD, int NT, int IT>
 void launch_onesweep_nt(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
                         u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s) {
-    const size_t smem = sizeof(ScatterSmem<K, HAS_V, NT>);
+    const size_t smem = sizeof(ScatterSmem<K, HAS_V, NT, IT>);
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_onesweep<K, HAS_V, LOAD, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_onesweep<K, HAS_V, LOAD, NT, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
         configured = true;
     }
-    constexpr u64 tile = (u64)NT * kItems;
+    constexpr u64 tile = (u64)NT * IT;
     const u64 tiles = (n + tile - 1) / tile;
     if (tiles == 0) return;
     TraceScope ts(tr, onesweep_name<K, HAS_V>(), s);
-    k_onesweep<K, HAS_V, LOAD, NT><<<(unsigned)tiles, NT, smem, s>>>(in, kout, vout, n, shift, offs, status,
+    k_onesweep<K, HAS_V, LOAD, NT, IT><<<(unsigned)tiles, NT, smem, s>>>(in, kout, vout, n, shift, offs, status,
                                                                      tile_counter, tag, st);
 }
 
@@ -615,10 +618,11 @@ template <typename K, bool HAS_V, int LOAD>
 void launch_onesweep(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
                      u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s) {
     if constexpr (sizeof(K) == 8 && !HAS_V)
-        launch_onesweep_nt<K, HAS_V, LOAD, NS_ONESWEEP_NT>(in, kout, vout, n, shift, offs, status, tile_counter, tag,
-                                                           st, tr, s);
+        launch_onesweep_nt<K, HAS_V, LOAD, NS_ONESWEEP_NT, NS_ONESWEEP_ITEMS>(in, kout, vout, n, shift, offs, status,
+                                                                              tile_counter, tag, st, tr, s);
     else
-        launch_onesweep_nt<K, HAS_V, LOAD, 256>(in, kout, vout, n, shift, offs, status, tile_counter, tag, st, tr, s);
+        launch_onesweep_nt<K, HAS_V, LOAD, 256, kItems>(in, kout, vout, n, shift, offs, status, tile_counter, tag, st,
+                                                        tr, s);
 }
 
 template <int KEYMODE, bool HAS_V>

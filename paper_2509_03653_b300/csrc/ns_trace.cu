@@ -131,4 +131,47 @@ ns_status ns_diag_wait_timeout(int which, ns_stream_t stream) {
     return ns::set_fail(NS_ERR_STATE, "ns_diag_wait_timeout: the wait did not report a timeout");
 }
 
+ns_status ns_diag_random_atomics(uint64_t table_words, uint64_t threads, int reps, double* best_us,
+                                 ns_stream_t stream) {
+    if (!best_us || reps < 1 || table_words < 1024 || (table_words & (table_words - 1)) || threads == 0)
+        return ns::set_fail(NS_ERR_INVALID, "ns_diag_random_atomics: bad argument (table_words a power of two >= 1024)");
+    cudaStream_t s = (cudaStream_t)stream;
+    ns::Buf a, b, c;
+    ns_status st = ns::buf_reserve(a, table_words * 8);
+    if (st == NS_OK) st = ns::buf_reserve(b, table_words * 8);
+    if (st == NS_OK) st = ns::buf_reserve(c, table_words * 8);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == NS_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+        cudaGetLastError();
+        st = ns::set_fail(NS_ERR_CUDA, "ns_diag_random_atomics: event creation failed");
+    }
+    float best = 1e30f;
+    if (st == NS_OK) {
+        cudaMemsetAsync(a.p, 0, table_words * 8, s);
+        cudaMemsetAsync(b.p, 0, table_words * 8, s);
+        cudaMemsetAsync(c.p, 0, table_words * 8, s);
+        for (int r = 0; r <= reps && st == NS_OK; ++r) {  // the first run warms up
+            cudaEventRecord(e0, s);
+            ns::launch_diag_rand3((ns::u64*)a.p, (ns::u64*)b.p, (ns::u64*)c.p, table_words - 1, threads,
+                                  0x5EEDull + (ns::u64)r * 7919, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaGetLastError();
+                st = ns::set_fail(NS_ERR_CUDA, "ns_diag_random_atomics: launch failed");
+                break;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0 && ms < best) best = ms;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    ns::buf_free(a);
+    ns::buf_free(b);
+    ns::buf_free(c);
+    if (st == NS_OK) *best_us = best * 1e3;
+    return st;
+}
+
 }  // extern "C"

@@ -302,3 +302,10 @@ def test_bounded_device_waits_time_out(which):
     m = ns.Matrix(ctx)
     ns.window_build(ctx, to_dev(s), to_dev(d), m)
     assert ns.network_stats(ctx, m) == oracle.stats(*oracle.build_matrix(s, d))
+
+
+def test_random_atomic_ceiling_diagnostic():
+    us = ns.diag_random_atomics(1 << 20, 1 << 14, 2)
+    assert 0.0 < us < 1e6
+    with pytest.raises(ns.NsError):
+        ns.diag_random_atomics(1000, 10, 1)  # not a power of two
