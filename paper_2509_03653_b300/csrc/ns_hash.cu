@@ -267,19 +267,39 @@ __device__ __forceinline__ void insert_item(const HashView& M, bool valid, u64 k
         if (cdir && ck == 2) Cl = node_probe(M.cols, M.col_mask, did + 1, cs, ci0, M.stats);
         // a found link cannot have count 0, so "new" is known now
         newlink = ldir && ((lk == 0) || (lk == 2 && L.slot != kNoSlot && L.prev == 0));
-        // round trip 2
+        // round trip 2.  A node found at its home slot by the claim returned
+        // its contents: when the link is new, one 128-bit CAS from that
+        // snapshot adds the packets and the partner together (falling back
+        // to two additions if another update got there first).
         if (ldir && lk == 1) L.prev = atomicAdd(&M.links[li0].count, cs);
-        if (rdir && rk == 1) R.prev = atomicAdd(&M.rows[ri0].packets, cs);
-        if (cdir && ck == 1) Cl.prev = atomicAdd(&M.cols[ci0].packets, cs);
         if (ldir && lside) newlink = (L.prev == 0);  // the key-0 slot is only added to
+        bool rdone = false, cdone = false;
+        if (newlink && rdir && rk == 1 && !rside && (u32)(ro.lo >> 32) != 0xFFFFFFFFu) {
+            const W128 w = cas128(&M.rows[ri0], ro.lo, ro.hi, ro.lo + (1ull << 32), ro.hi + cs);
+            if (w.lo == ro.lo && w.hi == ro.hi) {
+                R.prev = ro.hi;
+                rdeg = (ro.lo >> 32) + 1;
+                rdone = true;
+            }
+        }
+        if (newlink && cdir && ck == 1 && !cside && (u32)(co.lo >> 32) != 0xFFFFFFFFu) {
+            const W128 w = cas128(&M.cols[ci0], co.lo, co.hi, co.lo + (1ull << 32), co.hi + cs);
+            if (w.lo == co.lo && w.hi == co.hi) {
+                Cl.prev = co.hi;
+                cdeg = (co.lo >> 32) + 1;
+                cdone = true;
+            }
+        }
+        if (rdir && rk == 1 && !rdone) R.prev = atomicAdd(&M.rows[ri0].packets, cs);
+        if (cdir && ck == 1 && !cdone) Cl.prev = atomicAdd(&M.cols[ci0].packets, cs);
         if (newlink) {
             if (rdir) {
-                if (R.slot != kNoSlot) rdeg = degree_inc(&M.rows[R.slot], M.stats);
+                if (R.slot != kNoSlot && !rdone) rdeg = degree_inc(&M.rows[R.slot], M.stats);
             } else {
                 atomicAdd(&C->rdeg[rc], 1u);
             }
             if (cdir) {
-                if (Cl.slot != kNoSlot) cdeg = degree_inc(&M.cols[Cl.slot], M.stats);
+                if (Cl.slot != kNoSlot && !cdone) cdeg = degree_inc(&M.cols[Cl.slot], M.stats);
             } else {
                 atomicAdd(&C->cdeg[cc], 1u);
             }
