@@ -79,7 +79,7 @@ typedef struct {
 
 /* Aggregation path.  Both give bit-identical results. */
 enum {
-    NS_PATH_AUTO = 0, /* the tuner's choice (hash unless a cache says sort) */
+    NS_PATH_AUTO = 0, /* per window size: ns_path_tune's choice, else sort from 2^24 packets */
     NS_PATH_SORT = 1, /* LSD radix sort of packed keys + run-length encode */
     NS_PATH_HASH = 2  /* open-addressing hash table with atomic counts */
 };
@@ -87,7 +87,7 @@ enum {
 /* Per-CTA shared-memory staging of hot links, sources and destinations in
  * the hash path (see ns_config.cta_cache). */
 enum {
-    NS_CACHE_AUTO = 0, /* on for inserts of >= 2^22 packets, off below */
+    NS_CACHE_AUTO = 0, /* ns_path_tune's choice for the size, else on from 2^22 packets */
     NS_CACHE_ON = 1,
     NS_CACHE_OFF = 2
 };
@@ -157,6 +157,24 @@ ns_status ns_matrix_export(const ns_matrix* m, uint64_t* d_keys, uint64_t* d_cou
  * path (sort or hash).  Asynchronous. */
 ns_status ns_window_build(ns_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
                           ns_matrix* out, ns_stream_t stream);
+
+/* Path tuner: builds A from d_src/d_dst (n > 0 packets, device memory)
+ * with the sort path, the hash path without per-CTA caches and the hash path
+ * with them (only the one the context's cta_cache forces, if it forces one),
+ * three times each, and keeps the fastest of the last two timings of each.
+ * The winner becomes the context's NS_PATH_AUTO / NS_CACHE_AUTO choice for
+ * every n' with floor(log2 n') = floor(log2 n), and is stored in the tuner
+ * cache file (if the context has one) keyed by GPU name and that power of
+ * two, where later contexts on the same GPU find it.  *chosen (NS_PATH_SORT
+ * or NS_PATH_HASH), *sort_ms and *hash_ms (the faster hash variant) may each
+ * be NULL.  Allocates a temporary matrix; blocking.  The paper has no
+ * counterpart: its two aggregation paths are this library's own. */
+ns_status ns_path_tune(ns_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
+                       ns_stream_t stream, int* chosen, float* sort_ms, float* hash_ms);
+
+/* The path ns_window_build would take for a window of n packets
+ * (NS_PATH_SORT or NS_PATH_HASH). */
+ns_status ns_path_resolve(const ns_ctx* ctx, uint64_t n, int* path);
 
 /* acc := acc + add (A = sum_t A_t; equal keys add their counts).  `add` is
  * unchanged and may be rebuilt as soon as the stream work completes.

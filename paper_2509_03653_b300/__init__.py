@@ -21,7 +21,7 @@ from ._native import (FIELDS, NsBatchParams, NsConfig, NsError, NsStats, NsStrea
 __all__ = [
     "FIELDS", "NsError", "Context", "Matrix", "window_build", "accumulate", "window_ingest",
     "window_ingest_stats", "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
-    "matrix_clear", "sync", "PATHS", "window_stats_static", "STATIC_MAX_PACKETS",
+    "matrix_clear", "sync", "PATHS", "path_tune", "path_resolve", "window_stats_static", "STATIC_MAX_PACKETS",
     "trace_enable", "trace_read", "Batch", "batch_run", "batch_tune", "matrix_reserve_ex",
     "Server", "stream_submit", "stream_poll", "stream_wait", "diag_random_atomics",
 ]
@@ -52,7 +52,7 @@ def _column(t: torch.Tensor, name: str) -> ctypes.c_void_p:
 class Context:
     """A library context on one CUDA device (ns_create / ns_destroy)."""
 
-    def __init__(self, device: int = 0, path: str = "hash", hbm_budget_bytes: int = 0,
+    def __init__(self, device: int = 0, path: str = "auto", hbm_budget_bytes: int = 0,
                  max_slots: int = 0, tuner_cache: str | None = None, cta_cache: str = "auto"):
         self._L = load()
         cfg = NsConfig(PATHS[path], hbm_budget_bytes, max_slots,
@@ -104,6 +104,29 @@ def window_build(ctx: Context, src: torch.Tensor, dst: torch.Tensor, out: Matrix
         raise ValueError("src and dst differ in length")
     check(ctx._L.ns_window_build(ctx.handle, _column(src, "src"), _column(dst, "dst"), n, out.handle,
                                  _stream(stream)), "ns_window_build")
+
+
+_PATH_NAMES = {v: k for k, v in PATHS.items()}
+
+
+def path_tune(ctx: Context, src: torch.Tensor, dst: torch.Tensor, stream=None) -> dict:
+    """Times both paths on this window and makes the faster one the
+    context's "auto" choice for its size (ns_path_tune)."""
+    n = src.numel()
+    if dst.numel() != n:
+        raise ValueError("src and dst differ in length")
+    chosen = ctypes.c_int(0)
+    ms_sort, ms_hash = ctypes.c_float(0), ctypes.c_float(0)
+    check(ctx._L.ns_path_tune(ctx.handle, _column(src, "src"), _column(dst, "dst"), n, _stream(stream),
+                              ctypes.byref(chosen), ctypes.byref(ms_sort), ctypes.byref(ms_hash)), "ns_path_tune")
+    return {"path": _PATH_NAMES[chosen.value], "sort_ms": ms_sort.value, "hash_ms": ms_hash.value}
+
+
+def path_resolve(ctx: Context, n: int) -> str:
+    """The path window_build takes for n packets (ns_path_resolve)."""
+    p = ctypes.c_int(0)
+    check(ctx._L.ns_path_resolve(ctx.handle, n, ctypes.byref(p)), "ns_path_resolve")
+    return _PATH_NAMES[p.value]
 
 
 def accumulate(ctx: Context, acc: Matrix, add: Matrix, stream=None):

@@ -3,8 +3,10 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "ns.h"
 #include "ns_api_internal.h"
@@ -268,21 +270,60 @@ ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n,
 
 // The per-CTA cache pays off when each CTA sees many packets (skewed keys
 // then repeat inside it); a single 2^17-packet window gives each CTA ~256.
+int floor_log2(u64 n) { return n ? 63 - __builtin_clzll(n) : 0; }
+
 bool use_cta_cache(const ns_ctx* c, u64 n) {
     if (c->cfg.cta_cache == NS_CACHE_ON) return true;
     if (c->cfg.cta_cache == NS_CACHE_OFF) return false;
+    const auto it = c->path_choice.find(floor_log2(n));
+    if (it != c->path_choice.end() && it->second.path == NS_PATH_HASH) return it->second.cta_cache;
     return n >= (1ull << 22);
 }
 
+// Sizes from which NS_PATH_AUTO takes the sort path when the context has no
+// tuned choice for that size: floor(log2 n) >= kAutoSortLog2.  Measured on a
+// B300 over Zipf(1.2) and RMAT windows of 2^14..2^30 packets: the hash path is
+// faster up to 2^22, the sort path from 2^24 on (1.3x at 2^26, 1.8-2.4x at 2^30).
+constexpr int kAutoSortLog2 = 24;
+
+std::string path_key(int device, int lg) {
+    char buf[32];
+    snprintf(buf, sizeof buf, "|path|n2^%d", lg);
+    return gpu_name(device) + buf;
+}
+
+// Tuned choices for this GPU from the context's cache file.
+void load_path_choices(ns_ctx* c) {
+    const std::string prefix = gpu_name(c->device) + "|path|n2^";
+    for (const auto& kv : tuner_load(c->tuner_cache)) {
+        if (kv.first.compare(0, prefix.size(), prefix) != 0) continue;
+        const int lg = atoi(kv.first.c_str() + prefix.size());
+        std::string p;
+        double cache = 0;
+        if (lg < 0 || lg > 40 || !json_string(kv.second, "path", &p)) continue;
+        json_number(kv.second, "cta_cache", &cache);
+        if (p == "sort") c->path_choice[lg] = {NS_PATH_SORT, false};
+        if (p == "hash") c->path_choice[lg] = {NS_PATH_HASH, cache != 0};
+    }
+}
+
+int resolve_path(const ns_ctx* c, u64 n) {
+    if (c->cfg.path != NS_PATH_AUTO) return c->cfg.path;
+    const int lg = floor_log2(n);
+    const auto it = c->path_choice.find(lg);
+    if (it != c->path_choice.end()) return it->second.path;
+    return lg >= kAutoSortLog2 ? NS_PATH_SORT : NS_PATH_HASH;
+}
+
 ns_status build_hash(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n, ns_matrix* out,
-                     cudaStream_t s) {
+                     cudaStream_t s, int cache) {
     TRY(hash_alloc(out, n));
     TRY(hash_clear(out, s));
     out->fmt = FMT_HASH;
     out->bound = n;
     if (n == 0) return NS_OK;
     TraceScope ts(&c->tracer, "k_insert_packets", s);
-    launch_insert_packets(src, dst, n, hash_view(out), c->sms, use_cta_cache(c, n), s);
+    launch_insert_packets(src, dst, n, hash_view(out), c->sms, cache < 0 ? use_cta_cache(c, n) : cache != 0, s);
     return check_launch();
 }
 
@@ -330,6 +371,7 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
     if (x->cfg.max_slots <= 0) x->cfg.max_slots = 8;
     x->tuner_cache = c.tuner_cache ? c.tuner_cache : "";
     x->cfg.tuner_cache = nullptr;
+    load_path_choices(x);
     cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, device);
     x->sc.sms = x->sms;
     ns_status st = buf_reserve(x->ghist, 8 * 256 * sizeof(u32));
@@ -486,9 +528,80 @@ ns_status ns_window_build(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_ds
     if (n > 0 && (!d_src || !d_dst)) return fail(NS_ERR_INVALID, "ns_window_build: NULL input with n > 0");
     if (n >= (1ull << 40)) return fail(NS_ERR_INVALID, "ns_window_build: n too large");
     if (out->ctx != c) return fail(NS_ERR_INVALID, "ns_window_build: matrix belongs to another context");
-    const int path = c->cfg.path == NS_PATH_SORT ? NS_PATH_SORT : NS_PATH_HASH;
-    if (path == NS_PATH_SORT) return build_sort(c, d_src, d_dst, n, out, (cudaStream_t)stream);
+    if (resolve_path(c, n) == NS_PATH_SORT) return build_sort(c, d_src, d_dst, n, out, (cudaStream_t)stream);
     return build_hash(c, d_src, d_dst, n, out, (cudaStream_t)stream);
+}
+
+ns_status ns_path_tune(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n, ns_stream_t stream,
+                       int* chosen, float* sort_ms, float* hash_ms) {
+    if (!c) return fail(NS_ERR_INVALID, "ns_path_tune: NULL context");
+    if (n == 0) return fail(NS_ERR_INVALID, "ns_path_tune: n == 0");
+    if (!d_src || !d_dst) return fail(NS_ERR_INVALID, "ns_path_tune: NULL input");
+    if (n >= (1ull << 40)) return fail(NS_ERR_INVALID, "ns_path_tune: n too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    // candidates: the sort path, then the hash path without and with per-CTA
+    // caches (only the forced one if the context fixes cta_cache)
+    struct Cand {
+        int path, cache;
+        float ms;
+    };
+    std::vector<Cand> cand = {{NS_PATH_SORT, 0, 1e30f}};
+    if (c->cfg.cta_cache != NS_CACHE_ON) cand.push_back({NS_PATH_HASH, 0, 1e30f});
+    if (c->cfg.cta_cache != NS_CACHE_OFF) cand.push_back({NS_PATH_HASH, 1, 1e30f});
+    ns_matrix* m = nullptr;
+    TRY(ns_matrix_create(c, &m));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    ns_status st = NS_OK;
+    for (Cand& k : cand) {
+        // the first build of each candidate sizes its scratch and tables;
+        // the next two are timed
+        for (int rep = 0; rep < 3 && st == NS_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            st = k.path == NS_PATH_SORT ? build_sort(c, d_src, d_dst, n, m, s)
+                                        : build_hash(c, d_src, d_dst, n, m, s, k.cache);
+            cudaEventRecord(e1, s);
+            if (st != NS_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = check_launch();
+                if (st == NS_OK) st = fail(NS_ERR_CUDA, "ns_path_tune: event wait failed");
+                break;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) k.ms = std::min(k.ms, ms);
+        }
+        if (st != NS_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ns_matrix_free(m);
+    TRY(st);
+    const Cand* best = &cand[0];
+    float best_hash = 1e30f;
+    for (const Cand& k : cand) {
+        if (k.ms < best->ms) best = &k;
+        if (k.path == NS_PATH_HASH) best_hash = std::min(best_hash, k.ms);
+    }
+    const int lg = floor_log2(n);
+    c->path_choice[lg] = {best->path, best->cache != 0};
+    if (chosen) *chosen = best->path;
+    if (sort_ms) *sort_ms = cand[0].ms;
+    if (hash_ms) *hash_ms = best_hash;
+    auto cache = tuner_load(c->tuner_cache);
+    char val[160];
+    snprintf(val, sizeof val, "{\"path\": \"%s\", \"cta_cache\": %d, \"sort_ms\": %.4f, \"hash_ms\": %.4f}",
+             best->path == NS_PATH_SORT ? "sort" : "hash", best->cache, cand[0].ms, best_hash);
+    cache[path_key(c->device, lg)] = val;
+    tuner_store(c->tuner_cache, cache);
+    return NS_OK;
+}
+
+ns_status ns_path_resolve(const ns_ctx* c, uint64_t n, int* path) {
+    if (!c || !path) return fail(NS_ERR_INVALID, "ns_path_resolve: NULL argument");
+    *path = resolve_path(c, n);
+    return NS_OK;
 }
 
 ns_status ns_accumulate(ns_ctx* c, ns_matrix* acc, const ns_matrix* add, ns_stream_t stream) {

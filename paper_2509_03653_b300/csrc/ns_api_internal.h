@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <map>
 #include <string>
 
 #include "ns.h"
@@ -25,6 +26,17 @@ HashView hash_view(const ns_matrix* m);
 void buf_free(Buf& b);
 ns_status check_launch();
 ns_status set_fail(ns_status s, const char* msg);
+// Hash path: out := A_t.  cache: -1 = the context's rule, 0 = off, 1 = on.
+ns_status build_hash(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n, ns_matrix* out,
+                     cudaStream_t s, int cache = -1);
+
+// Autotuner cache file (ns_tuner.cu): entries keyed "<gpu>|<kind>|<shape>",
+// each a one-line JSON object kept as text.
+std::string gpu_name(int device);
+std::map<std::string, std::string> tuner_load(const std::string& path);
+void tuner_store(const std::string& path, const std::map<std::string, std::string>& m);
+bool json_number(const std::string& obj, const char* name, double* v);
+bool json_string(const std::string& obj, const char* name, std::string* v);
 
 }  // namespace ns
 
@@ -33,6 +45,13 @@ struct ns_ctx {
     int sms = 148;
     ns_config cfg{};
     std::string tuner_cache;
+    // ns_path_tune's choices by floor(log2 n): path (NS_PATH_SORT / NS_PATH_HASH)
+    // and, for the hash path, whether inserts stage hot keys in shared memory
+    struct PathChoice {
+        int path;
+        bool cta_cache;
+    };
+    std::map<int, PathChoice> path_choice;
     ns::SortScratch sc{};
     ns::Buf ghist, offs, tcount, counters, status;
     ns::Buf k64[2], pos, psum, k32[2], v64[2], xk, xv;

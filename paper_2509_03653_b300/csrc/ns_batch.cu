@@ -58,60 +58,29 @@ struct Chunk {
     u64 packets;
 };
 
-// ---- tuner cache: one line per entry, "key": {"T": t, "per_sm": c, "load": l}
+// ---- tuner cache entries of kind "batch": {"T": t, "per_sm": c, "load": l, "cache": k}
 
 std::string tuner_key(int device, u64 windows, u64 packets) {
-    cudaDeviceProp prop;
-    cudaGetDeviceProperties(&prop, device);
     const int wb = windows ? (int)std::log2((double)windows) : 0;
     const int mb = (windows && packets) ? (int)std::log2((double)packets / (double)windows) : 0;
-    char buf[384];
-    snprintf(buf, sizeof buf, "%.200s|batch|windows2^%d|mean2^%d", prop.name, wb, mb);
+    char buf[64];
+    snprintf(buf, sizeof buf, "|batch|windows2^%d|mean2^%d", wb, mb);
+    return gpu_name(device) + buf;
+}
+
+bool params_parse(const std::string& obj, ns_batch_params* p) {
+    double t, c, l, k = 1;
+    if (!json_number(obj, "T", &t) || !json_number(obj, "per_sm", &c) || !json_number(obj, "load", &l)) return false;
+    json_number(obj, "cache", &k);
+    *p = ns_batch_params{(uint32_t)t, (uint32_t)c, l, (uint32_t)k};
+    return true;
+}
+
+std::string params_format(const ns_batch_params& p) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "{\"T\": %u, \"per_sm\": %u, \"load\": %.3f, \"cache\": %u}", p.tile_packets,
+             p.ctas_per_sm, p.max_load, p.cta_cache);
     return buf;
-}
-
-std::map<std::string, ns_batch_params> tuner_read(const std::string& path) {
-    std::map<std::string, ns_batch_params> m;
-    if (path.empty()) return m;
-    FILE* f = fopen(path.c_str(), "r");
-    if (!f) return m;
-    char line[1024];
-    while (fgets(line, sizeof line, f)) {
-        char* q1 = strchr(line, '"');
-        if (!q1) continue;
-        char* q2 = strchr(q1 + 1, '"');
-        if (!q2) continue;
-        std::string key(q1 + 1, q2);
-        unsigned t = 0, c = 0, k = 1;
-        double l = 0;
-        const char* pt = strstr(q2, "\"T\":");
-        const char* pc = strstr(q2, "\"per_sm\":");
-        const char* pl = strstr(q2, "\"load\":");
-        if (!pt || !pc || !pl) continue;
-        if (sscanf(pt + 4, "%u", &t) != 1 || sscanf(pc + 9, "%u", &c) != 1 || sscanf(pl + 7, "%lf", &l) != 1) continue;
-        const char* pk = strstr(q2, "\"cache\":");
-        if (pk && sscanf(pk + 8, "%u", &k) != 1) k = 1;
-        m[key] = ns_batch_params{t, c, l, k};
-    }
-    fclose(f);
-    return m;
-}
-
-void tuner_write(const std::string& path, const std::map<std::string, ns_batch_params>& m) {
-    if (path.empty()) return;
-    const std::string tmp = path + ".tmp";
-    FILE* f = fopen(tmp.c_str(), "w");
-    if (!f) return;
-    fprintf(f, "{\n");
-    size_t i = 0;
-    for (const auto& kv : m) {
-        fprintf(f, "  \"%s\": {\"T\": %u, \"per_sm\": %u, \"load\": %.3f, \"cache\": %u}%s\n", kv.first.c_str(),
-                kv.second.tile_packets, kv.second.ctas_per_sm, kv.second.max_load, kv.second.cta_cache,
-                ++i < m.size() ? "," : "");
-    }
-    fprintf(f, "}\n");
-    fclose(f);
-    rename(tmp.c_str(), path.c_str());
 }
 
 bool params_ok(const ns_batch_params& p) {
@@ -169,9 +138,10 @@ ns_status ns_batch_create(ns_ctx* c, uint64_t max_windows, uint64_t max_packets,
     b->max_windows = max_windows;
     b->max_packets = max_packets;
     // tuned parameters for this shape, if the cache has them
-    auto cache = tuner_read(c->tuner_cache);
-    auto it = cache.find(tuner_key(c->device, max_windows, max_packets));
-    if (it != cache.end() && params_ok(it->second)) b->params = it->second;
+    const auto cache = tuner_load(c->tuner_cache);
+    const auto it = cache.find(tuner_key(c->device, max_windows, max_packets));
+    ns_batch_params cached;
+    if (it != cache.end() && params_parse(it->second, &cached) && params_ok(cached)) b->params = cached;
     // arena: enough for every window at the smallest load the tuner tries,
     // capped by the context's HBM budget
     const double min_load = 0.5;
@@ -346,9 +316,9 @@ ns_status ns_batch_tune(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uin
     }
     b->params = best;
     if (chosen) *chosen = best;
-    auto cache = tuner_read(c->tuner_cache);
-    cache[tuner_key(c->device, b->max_windows, b->max_packets)] = best;
-    tuner_write(c->tuner_cache, cache);
+    auto cache = tuner_load(c->tuner_cache);
+    cache[tuner_key(c->device, b->max_windows, b->max_packets)] = params_format(best);
+    tuner_store(c->tuner_cache, cache);
     return NS_OK;
 }
 

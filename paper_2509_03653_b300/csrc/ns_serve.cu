@@ -26,10 +26,6 @@
 
 using namespace ns;
 
-namespace ns {
-ns_status build_hash(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n, ns_matrix* out, cudaStream_t s);
-}
-
 namespace {
 
 using Clock = std::chrono::steady_clock;
