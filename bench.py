@@ -26,6 +26,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -67,6 +68,8 @@ def parse():
     ap.add_argument("--tuner-cache", default=None, help="batched: autotuner cache file (default: none, tune now)")
     ap.add_argument("--packets", type=int, default=1 << 30, help="oneshot: packets in the build")
     ap.add_argument("--paths", default="sort,hash", help="oneshot: aggregation paths to run")
+    ap.add_argument("--hash-load", type=float, default=0.25,
+                    help="stream: load bound of the accumulated matrix's hash tables (sizes them for 2^26 links)")
     ap.add_argument("--windows", type=int, default=WINDOWS,
                     help="windows in the stream (512 = the full workload; fewer = a small case for profiling)")
     return ap.parse_args()
@@ -105,7 +108,7 @@ def workload_config(extra=None, windows=WINDOWS):
         "windows": windows,
         "window_packets": WINDOW,
         "generator": "RMAT scale 32 (0.57,0.19,0.19,0.05) + 10% uniform, seeded bijection",
-        "l2": "inputs larger than L2 (512 MiB of packets, 10 GiB of tables per step)",
+        "l2": "inputs larger than L2 (512 MiB of packets; the accumulated matrix's tables are GiB-sized)",
     }
     if extra:
         cfg.update(extra)
@@ -254,7 +257,7 @@ def run_ours(args, rank, world, local):
     d_src = h_src.to(dev)
     d_dst = h_dst.to(dev)
 
-    ctx = ns.Context(local, path="hash")
+    ctx = ns.Context(local, path="hash", hash_load=args.hash_load)
     A = ns.Matrix(ctx)
     ns.matrix_reserve(A, N)
 
@@ -416,7 +419,8 @@ def run_ours(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": workload_config({"path": "hash (fused window ingest + statistics, one launch per window)", "graph": "per-window launches "
-                                   "captured in one CUDA graph per step",
+                                   "captured in one CUDA graph per step", "hash_load": args.hash_load,
+                                   "table_gib": round(3 * 16 * (1 << math.ceil(math.log2(N / args.hash_load))) / 2**30, 1),
                                    "parallelism": "replicas" if world > 1 else "single GPU"}, windows=NW),
         "roofline": {
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -501,10 +505,13 @@ def run_oneshot(args, rank, world, local):
         if path == "sort":
             kname = "k_onesweep<u64 key>"
             kbytes = 16 * N  # one digit pass reads and writes every 8-byte key
-            # minimal sort-path passes: histogram read, 8 digit passes, run
-            # read, A written, rows read, column sort (4 passes of 12-byte
-            # pairs, read+write), column runs read
-            path_bytes = 8 * N + 8 * 16 * N + 8 * N + 16 * U + 16 * U + 4 * 24 * U + 12 * U
+            # minimal bytes of each sort-path kernel (N < 2^32: the column
+            # side sorts one word per link): histogram 8N; 8 digit passes
+            # 16N each; link runs 8N + 16U (pos, keys); link counts 16U; row
+            # runs 24U + 16S (reads keys and counts, writes the dst words,
+            # pos, psum); row stats 16S; column histogram 8U; 4 digit passes
+            # 16U each; column runs 8U + 16D; column stats 16D
+            path_bytes = 144 * N + 136 * U + 32 * (S + D)
         else:
             kname = "k_insert_packets"
             kbytes = 8 * N + 16 * U + 16 * (S + D)

@@ -92,12 +92,24 @@ enum {
     NS_CACHE_OFF = 2
 };
 
+/* How the sort path orders A's nonzeros by destination (both exact). */
+enum {
+    NS_COLSORT_AUTO = 0,  /* below 2^32 packets (every count < 2^32): one u64 word
+                             (dst << 32 | count) per nonzero, sorted by its upper
+                             half; from 2^32 packets: (dst, count) pairs */
+    NS_COLSORT_PAIRS = 1  /* always (u32 dst, u64 count) pairs */
+};
+
 typedef struct {
     int path;                  /* NS_PATH_* used by ns_window_build */
     uint64_t hbm_budget_bytes; /* serving admission and batch arena budget; 0 = 64 GiB */
     int max_slots;             /* serving: windows in flight at once; 0 = 8 */
     const char* tuner_cache;   /* autotuner cache file (JSON); NULL = none */
     int cta_cache;             /* NS_CACHE_* for hash-path packet inserts */
+    int column_sort;           /* NS_COLSORT_* for the sort path's per-destination side */
+    double hash_load;          /* load bound of the link, source and destination tables the
+                                  library sizes (builds, reserves, growth), in [0.05, 0.9];
+                                  0 = 0.5.  Lower costs memory and shortens probe chains. */
 } ns_config;
 
 /* ---- context ----------------------------------------------------------- */

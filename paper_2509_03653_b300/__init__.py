@@ -53,10 +53,12 @@ class Context:
     """A library context on one CUDA device (ns_create / ns_destroy)."""
 
     def __init__(self, device: int = 0, path: str = "auto", hbm_budget_bytes: int = 0,
-                 max_slots: int = 0, tuner_cache: str | None = None, cta_cache: str = "auto"):
+                 max_slots: int = 0, tuner_cache: str | None = None, cta_cache: str = "auto",
+                 column_sort: str = "auto", hash_load: float = 0.0):
         self._L = load()
         cfg = NsConfig(PATHS[path], hbm_budget_bytes, max_slots,
-                       tuner_cache.encode() if tuner_cache else None, {"auto": 0, "on": 1, "off": 2}[cta_cache])
+                       tuner_cache.encode() if tuner_cache else None, {"auto": 0, "on": 1, "off": 2}[cta_cache],
+                       {"auto": 0, "pairs": 1}[column_sort], hash_load)
         h = ctypes.c_void_p()
         check(self._L.ns_create(ctypes.byref(h), ctypes.byref(cfg), device), "ns_create")
         self.handle = h

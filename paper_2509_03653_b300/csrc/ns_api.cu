@@ -1,6 +1,7 @@
 // ns_api.cu -- the C ABI (include/ns.h): contexts, matrices, path selection,
 // capacity planning and error reporting around the kernels.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -104,16 +105,22 @@ HashView hash_view(const ns_matrix* m) {
     return v;
 }
 
+// Smallest power-of-two capacity (>= 1024) holding `items` at load <= load.
+u64 table_cap(u64 items, double load) {
+    return next_pow2(std::max<u64>((u64)std::ceil((double)items / load), 1024));
+}
+
 // Sets the matrix's active table capacities for at least `links` nonzeros at
-// load <= 1/2, and for at least min(links, node_limit) sources and as many
+// the context's load bound, and for at least min(links, node_limit) sources and as many
 // destinations (sources, destinations <= links; node_limit is the caller's
 // optional promise, 0 = none).  Allocations only grow; a smaller active
 // capacity reuses them, so clearing and scanning cost what this window needs.
 // Contents are undefined until cleared.
 ns_status hash_alloc(ns_matrix* m, u64 links) {
-    const u64 cap = next_pow2(std::max<u64>(2 * links, 1024));
+    const double load = m->ctx->cfg.hash_load;
+    const u64 cap = table_cap(links, load);
     const u64 nodes = m->node_limit ? std::min<u64>(links, m->node_limit) : links;
-    const u64 ncap = next_pow2(std::max<u64>(2 * nodes, 1024));
+    const u64 ncap = table_cap(nodes, load);
     TRY(buf_reserve(m->links, (cap + 1) * sizeof(LinkSlot)));
     TRY(buf_reserve(m->rows, (ncap + 1) * sizeof(NodeSlot)));
     TRY(buf_reserve(m->cols, (ncap + 1) * sizeof(NodeSlot)));
@@ -146,7 +153,7 @@ ns_status read_stats(const ns_matrix* m, cudaStream_t s, DevStats* out) {
 // the host-side bound first; only when that is exhausted does it read the
 // true count and, if needed, rehash into larger tables.
 ns_status hash_grow(ns_matrix* m, u64 extra, cudaStream_t s) {
-    const u64 limit = m->link_cap / 2;
+    const u64 limit = (u64)((double)m->link_cap * m->ctx->cfg.hash_load);
     if (m->bound + extra <= limit) return NS_OK;
     DevStats ds;
     TRY(read_stats(m, s, &ds));
@@ -235,10 +242,16 @@ ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n,
     TRY(buf_reserve(c->k64[1], n * sizeof(u64)));
     TRY(buf_reserve(c->pos, (n + 1) * sizeof(u64)));
     TRY(buf_reserve(c->psum, (n + 1) * sizeof(u64)));
-    TRY(buf_reserve(c->k32[0], n * sizeof(u32)));
-    TRY(buf_reserve(c->k32[1], n * sizeof(u32)));
+    // Below 2^32 packets every count fits 32 bits, and the column side sorts
+    // single words (dst << 32 | count) by their upper half; otherwise it
+    // sorts (dst, count) pairs.
+    const bool packed_cols = n < (1ull << 32) && c->cfg.column_sort != NS_COLSORT_PAIRS;
     TRY(buf_reserve(c->v64[0], n * sizeof(u64)));
-    TRY(buf_reserve(c->v64[1], n * sizeof(u64)));
+    if (!packed_cols) {
+        TRY(buf_reserve(c->k32[0], n * sizeof(u32)));
+        TRY(buf_reserve(c->k32[1], n * sizeof(u32)));
+        TRY(buf_reserve(c->v64[1], n * sizeof(u64)));
+    }
     TRY(buf_reserve(c->counters, 16 * sizeof(u64)));
     DevStats* st = (DevStats*)out->stats.p;
     u64* nnz = &st->v[S_LINKS];
@@ -252,10 +265,21 @@ ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n,
     launch_run_stats(RS_LINKS, (const u64*)c->pos.p, nullptr, nnz, n, (u64*)out->counts.p,
                      st, c->sms, &c->tracer, s);
     // rows: runs of equal src over the source-major list (rows 5-9)
+    u64* packed = packed_cols ? (u64*)c->v64[0].p : nullptr;
     launch_runs(RUN_SRC_OF_U64, true, out->keys.p, (const u64*)out->counts.p, n, nnz, nullptr,
-                (u64*)c->pos.p, (u64*)c->psum.p, runs_out, c->sc, st, s);
+                (u64*)c->pos.p, (u64*)c->psum.p, runs_out, c->sc, st, s, packed);
     launch_run_stats(RS_ROWS, (const u64*)c->pos.p, (const u64*)c->psum.p, runs_out, n,
                      nullptr, st, c->sms, &c->tracer, s);
+    if (packed_cols) {
+        // columns: the words (dst << 32 | count) sorted by dst, then runs of
+        // equal dst (the reverse operations)
+        const int r2 = radix_sort_hi32(packed, nnz, kb, n, c->sc, st, s);
+        launch_runs(RUN_HI_OF_PACKED, true, kb[r2], nullptr, n, nnz, nullptr, (u64*)c->pos.p,
+                    (u64*)c->psum.p, runs_out + 1, c->sc, st, s);
+        launch_run_stats(RS_COLS, (const u64*)c->pos.p, (const u64*)c->psum.p, runs_out + 1, n,
+                         nullptr, st, c->sms, &c->tracer, s);
+        return check_launch();
+    }
     // columns: (dst, count) sorted by dst, then runs (the reverse operations)
     u32* ck[2] = {(u32*)c->k32[0].p, (u32*)c->k32[1].p};
     u64* cv[2] = {(u64*)c->v64[0].p, (u64*)c->v64[1].p};
@@ -363,6 +387,11 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
         return fail(NS_ERR_INVALID, "ns_create: unknown path %d", c.path);
     if (c.cta_cache < NS_CACHE_AUTO || c.cta_cache > NS_CACHE_OFF)
         return fail(NS_ERR_INVALID, "ns_create: unknown cta_cache %d", c.cta_cache);
+    if (c.column_sort < NS_COLSORT_AUTO || c.column_sort > NS_COLSORT_PAIRS)
+        return fail(NS_ERR_INVALID, "ns_create: unknown column_sort %d", c.column_sort);
+    if (c.hash_load == 0.0) c.hash_load = 0.5;
+    if (!(c.hash_load >= 0.05 && c.hash_load <= 0.9))
+        return fail(NS_ERR_INVALID, "ns_create: hash_load %g outside [0.05, 0.9]", c.hash_load);
     CK(cudaSetDevice(device));
     ns_ctx* x = new ns_ctx();
     x->device = device;

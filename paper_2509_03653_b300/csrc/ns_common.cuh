@@ -135,6 +135,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, u32 bytes, 
                  : "memory");
 }
 
+// A hint to pull [src, src + bytes) from HBM into L2; src 16-byte aligned,
+// bytes a multiple of 16.  Nothing waits for it.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, u32 bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_test_wait(u64* bar, u32 parity) {
     u32 ok;
     asm volatile(
@@ -151,10 +157,12 @@ __device__ __forceinline__ bool mbar_test_wait(u64* bar, u32 parity) {
 // recorded and the wait continues, again bounded, so that no copy is still
 // landing in shared memory when the CTA retires.
 constexpr u32 kMaxBarrierPolls = 1u << 26;
-__device__ __forceinline__ void mbar_wait_bounded(u64* bar, u32 parity, DevStats* st) {
+// Returns true once the phase completed; false (with ERR_TIMEOUT recorded)
+// if it did not within the bounds.
+__device__ __forceinline__ bool mbar_wait_bounded(u64* bar, u32 parity, DevStats* st) {
     u64 t0 = 0;
     for (u32 i = 0; i < kMaxBarrierPolls; ++i) {
-        if (mbar_test_wait(bar, parity)) return;
+        if (mbar_test_wait(bar, parity)) return true;
         if (i > 64) {
             const u64 now = globaltimer_ns();
             if (t0 == 0) t0 = now;
@@ -165,10 +173,11 @@ __device__ __forceinline__ void mbar_wait_bounded(u64* bar, u32 parity, DevStats
     set_error(st, ERR_TIMEOUT);
     t0 = globaltimer_ns();
     for (u32 i = 0; i < kMaxBarrierPolls; ++i) {
-        if (mbar_test_wait(bar, parity)) return;
-        if (globaltimer_ns() - t0 > kWaitLimitNs) return;
+        if (mbar_test_wait(bar, parity)) return false;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
         __nanosleep(64);
     }
+    return false;
 }
 
 }  // namespace ns

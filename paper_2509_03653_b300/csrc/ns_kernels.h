@@ -13,7 +13,9 @@ namespace ns {
 // key loading modes of the radix sort
 enum { LOAD_KEYS = 0, LOAD_PACK = 1, LOAD_DST_OF = 2 };
 // run-key modes
-enum { RUN_U64 = 0, RUN_SRC_OF_U64 = 1, RUN_U32 = 2 };
+// RUN_HI_OF_PACKED: u64 words (key << 32 | value), runs of equal key with
+// the low halves as values
+enum { RUN_U64 = 0, RUN_SRC_OF_U64 = 1, RUN_U32 = 2, RUN_HI_OF_PACKED = 3 };
 // run-statistics modes
 enum { RS_LINKS = 0, RS_ROWS = 1, RS_COLS = 2 };
 
@@ -27,6 +29,7 @@ struct SortIn {
     const u32* dst;
     const u64* n_dev;
     bool bulk;  // every input address is 16-byte aligned: stage tiles with bulk copies
+    const char* trace_name;  // tracer label of the digit passes (NULL: by key type)
 };
 
 // Per-kernel timing (ns_trace.cu): a TraceScope around a launch records an
@@ -119,12 +122,18 @@ int radix_sort_packets(const u32* src, const u32* dst, u64* kbuf[2], u64 n,
 int radix_sort_pairs64(const u64* keys, const u64* vals, const u64* n_dev,
                        u64* kbuf[2], u64* vbuf[2], u64 n, SortScratch& sc,
                        DevStats* st, cudaStream_t s);
+// Sorts n_dev (<= n) u64 words by their upper 32 bits (four 8-bit digit
+// passes, stable); returns the index of the buffer holding the result.
+int radix_sort_hi32(const u64* packed, const u64* n_dev, u64* kbuf[2], u64 n, SortScratch& sc, DevStats* st,
+                    cudaStream_t s);
 int radix_sort_dst_pairs(const u64* link_keys, const u64* counts, const u64* n_dev,
                          u32* kbuf[2], u64* vbuf[2], u64 n, SortScratch& sc,
                          DevStats* st, cudaStream_t s);
+// pack_out (RUN_SRC_OF_U64 only, may be NULL): also writes, for every input
+// element i, (low half of key i) << 32 | low half of value i.
 void launch_runs(int keymode, bool has_v, const void* keys, const u64* vals, u64 n,
                  const u64* n_dev, u64* head_keys, u64* pos, u64* psum,
-                 u64* R_out, SortScratch& sc, DevStats* st, cudaStream_t s);
+                 u64* R_out, SortScratch& sc, DevStats* st, cudaStream_t s, u64* pack_out = nullptr);
 void launch_run_stats(int mode, const u64* pos, const u64* psum, const u64* R_ptr,
                       u64 bound, u64* counts_out, DevStats* st, int sms, Tracer* tr, cudaStream_t s);
 

@@ -11,6 +11,7 @@
 // accumulate step is serialized, and it runs in ticket order, so a window's
 // results do not depend on what else is in flight.
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -71,10 +72,11 @@ struct InFlight {
 };
 
 // Device bytes a window of n packets needs while in flight: its two columns,
-// A_t's tables at load <= 1/2 and its statistics.
-u64 window_bytes(u64 n) {
+// A_t's tables at the context's load bound and its statistics.
+u64 window_bytes(u64 n, double load) {
+    const u64 want = (u64)std::ceil((double)n / load);
     u64 cap = 1024;
-    while (cap < 2 * n) cap <<= 1;
+    while (cap < want) cap <<= 1;
     return 8 * n + (cap + 1) * (sizeof(LinkSlot) + 2 * sizeof(NodeSlot)) + 2 * sizeof(ns_stats) + sizeof(DevStats);
 }
 
@@ -168,7 +170,7 @@ void scheduler_loop(ns_server* S) {
             for (auto& sl : S->slots) free_slot |= !sl.busy;
             // the resident aggregate counts against the budget too
             const u64 resident = S->acc->links.bytes + S->acc->rows.bytes + S->acc->cols.bytes;
-            return free_slot && (S->in_use == 0 || resident + S->in_use + window_bytes(r.n) <= S->budget);
+            return free_slot && (S->in_use == 0 || resident + S->in_use + window_bytes(r.n, S->ctx->cfg.hash_load) <= S->budget);
         });
         if (S->queue.empty()) return;  // stopping
         Request r = S->queue.front();
@@ -177,7 +179,7 @@ void scheduler_loop(ns_server* S) {
         while (S->slots[si].busy) ++si;
         Slot& sl = S->slots[si];
         sl.busy = true;
-        sl.reserved = window_bytes(r.n);
+        sl.reserved = window_bytes(r.n, S->ctx->cfg.hash_load);
         S->in_use += sl.reserved;
         const double t_admit = now_us();
         lk.unlock();

@@ -37,8 +37,17 @@ constexpr int kRadix = 256;
 #ifndef NS_ONESWEEP_ITEMS
 #define NS_ONESWEEP_ITEMS 16
 #endif
+// L2 prefetch distance of a digit pass, in multiples of the CTAs resident on
+// the whole GPU (0 = none)
+#ifndef NS_ONESWEEP_PF
+#define NS_ONESWEEP_PF 1
+#endif
 
 constexpr u64 kFlagAgg = 1, kFlagPrefix = 2;
+#ifndef NS_LOOK_DIGITS
+#define NS_LOOK_DIGITS 1
+#endif
+constexpr int kLookDigits = NS_LOOK_DIGITS;  // look-back window of the digit passes
 constexpr u64 kValMask = (1ull << 46) - 1;
 
 __device__ __forceinline__ u64 pack_status(u32 tag, u64 flag, u64 v) {
@@ -47,30 +56,75 @@ __device__ __forceinline__ u64 pack_status(u32 tag, u64 flag, u64 v) {
 
 // Exclusive prefix for `tile` of one counter whose per-tile status words are
 // status[k * stride] (k = tile index).  Returns 0 for tile 0.
+//
+// With hundreds of tiles in flight, the nearest predecessor holding an
+// inclusive prefix is typically a few dozen tiles back (measured: ~28 on
+// 2^30 keys), so the walk reads WIN predecessors per round trip (independent
+// loads) and sums aggregates until it meets a prefix.  A predecessor that has
+// published nothing yet is waited for (bounded), then the walk resumes from
+// it.  The digit passes walk one word at a time (their digit threads hold
+// the tile's keys in registers, which a wider window would spill; measured
+// no faster in any arrangement tried); the run kernels' single look-back
+// thread reads 8 at a time.
+template <int WIN>
 __device__ u64 lookback(u64* status, u64 stride, u64 tile, u32 tag, DevStats* st) {
+    constexpr int kLookWindow = WIN;
     u64 prefix = 0;
-    long long k = (long long)tile - 1;
+    long long k = (long long)tile - 1;  // nearest predecessor not yet accounted for
     u32 spins = 0;
     u64 t0 = 0;
     while (k >= 0) {
-        const u64 s = ld_volatile(&status[(u64)k * stride]);
-        const u32 stag = (u32)(s >> 48);
-        const u64 flag = (s >> 46) & 3;
-        if (stag == tag && flag != 0) {
-            prefix += s & kValMask;
-            if (flag == kFlagPrefix) break;
-            --k;
-            spins = 0;
-            t0 = 0;
-        } else {
-            const u64 now = globaltimer_ns();
-            if (t0 == 0) t0 = now;
-            if (++spins > kMaxSpin || now - t0 > kWaitLimitNs) {
-                set_error(st, ERR_TIMEOUT);
-                break;
+        u64 sv[kLookWindow];
+#pragma unroll
+        for (int q = 0; q < kLookWindow; ++q) sv[q] = (k - q >= 0) ? ld_volatile(&status[(u64)(k - q) * stride]) : 0ull;
+        int used = 0;
+        bool go = true, done = false;
+#pragma unroll
+        for (int q = 0; q < kLookWindow; ++q) {
+            if (go) {
+                if (k - q < 0) {
+                    done = true;
+                    go = false;
+                } else {
+                    const u64 s = sv[q];
+                    const u32 stag = (u32)(s >> 48);
+                    const u64 flag = (s >> 46) & 3;
+                    if (stag == tag && flag != 0) {
+                        prefix += s & kValMask;
+                        used = q + 1;
+                        if (flag == kFlagPrefix) {
+                            done = true;
+                            go = false;
+                        }
+                    } else {
+                        go = false;  // not published yet
+                    }
+                }
             }
-            __nanosleep(20);
         }
+        if (done) break;
+        k -= used;
+        if (used > 0) continue;
+        // the nearest predecessor has published nothing yet: poll that one
+        // word alone (bounded) before reading a window again
+        bool ready = false, gave_up = false;
+        while (!ready && !gave_up) {
+            const u64 s = ld_volatile(&status[(u64)k * stride]);
+            if ((u32)(s >> 48) == tag && ((s >> 46) & 3) != 0) {
+                ready = true;
+            } else {
+                const u64 now = globaltimer_ns();
+                if (t0 == 0) t0 = now;
+                if (++spins > kMaxSpin || now - t0 > kWaitLimitNs) gave_up = true;
+                else __nanosleep(20);
+            }
+        }
+        if (gave_up) {
+            set_error(st, ERR_TIMEOUT);
+            break;
+        }
+        spins = 0;
+        t0 = 0;
     }
     return prefix;
 }
@@ -172,6 +226,7 @@ struct ScatterSmem {
     u32 wsum[NW];
     u32 total;
     u32 tile;
+    u32 abort;
     u64 bar;
 };
 
@@ -180,8 +235,8 @@ struct ScatterSmem {
 // ragged tail (< 4 elements); otherwise all threads load.  Packed mode stages
 // the two uint32 columns side by side in the key buffer's bytes.
 template <typename K, bool HAS_V, int LOAD, int NT, int IT>
-__device__ __forceinline__ void stage_tile(const SortIn& in, ScatterSmem<K, HAS_V, NT, IT>& sm, u64 base, u32 tile_n,
-                                           bool bulk, DevStats* st) {
+__device__ __forceinline__ bool stage_tile(const SortIn& in, ScatterSmem<K, HAS_V, NT, IT>& sm, u64 base, u32 tile_n,
+                                           bool bulk, u32 parity, DevStats* st) {
     constexpr int kTile = NT * IT;
     u32* s32 = reinterpret_cast<u32*>(sm.keys);
     constexpr u32 kq = (LOAD == LOAD_PACK) ? 4u : (16u / (u32)sizeof(K));
@@ -217,7 +272,7 @@ __device__ __forceinline__ void stage_tile(const SortIn& in, ScatterSmem<K, HAS_
     if constexpr (HAS_V && LOAD != LOAD_PACK) {
         for (u32 i = nv + threadIdx.x; i < tile_n; i += NT) sm.vals[i] = in.vals[base + i];
     }
-    if (bulk) mbar_wait_bounded(&sm.bar, 0, st);
+    return bulk ? mbar_wait_bounded(&sm.bar, parity, st) : true;
 }
 
 // exclusive scan of one u32 per thread over an NT-thread block
@@ -249,7 +304,8 @@ __device__ __forceinline__ u32 block_excl_scan_nt(u32 v, u32* wsum, u32* total) 
 template <typename K, bool HAS_V, int LOAD, int NT, int IT>
 __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >= 384) ? 2 : (HAS_V ? 3 : 4))
     k_onesweep(SortIn in, K* __restrict__ kout, u64* __restrict__ vout, u64 n_arg, int shift,
-               const u64* __restrict__ offs, u64* __restrict__ status, u32* tile_counter, u32 tag, DevStats* st) {
+               const u64* __restrict__ offs, u64* __restrict__ status, u32* tile_counter, u32 tag, DevStats* st,
+               u32 pf_tiles) {
     constexpr int kWarps = NT / 32, kTile = NT * IT, kItems = IT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem<K, HAS_V, NT, IT>& sm = *reinterpret_cast<ScatterSmem<K, HAS_V, NT, IT>*>(smem_raw);
@@ -260,106 +316,144 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
     const bool bulk = in.bulk && LOAD != LOAD_DST_OF;
 
     if (threadIdx.x == 0) {
-        sm.tile = atomicAdd(tile_counter, 1u);
         mbar_init(&sm.bar, 1);
+        sm.abort = 0;
     }
-    for (int i = threadIdx.x; i < kWarps * kRadix; i += NT) (&sm.whist[0][0])[i] = 0;
-    __syncthreads();
-    const u64 tile = sm.tile;
-    const u64 base = tile * kTile;
-    if (base >= n) return;  // launched for an upper bound; nothing to publish
-    const u32 tile_n = (u32)((n - base) < (u64)kTile ? (n - base) : (u64)kTile);
+    u32 parity = 0;
+    // Persistent: take tiles in order until none are left.  Every tile a
+    // look-back waits on was taken earlier by a running CTA, and the grid
+    // never outnumbers the CTAs that fit at once, so a launch for an upper
+    // bound on n costs no empty CTAs.
+    for (;;) {
+        if (threadIdx.x == 0) sm.tile = atomicAdd(tile_counter, 1u);
+        for (int i = threadIdx.x; i < kWarps * kRadix; i += NT) (&sm.whist[0][0])[i] = 0;
+        __syncthreads();
+        const u64 tile = sm.tile;
+        const u64 base = tile * kTile;
+        if (base >= n) break;  // no tiles left
+        const u32 tile_n = (u32)((n - base) < (u64)kTile ? (n - base) : (u64)kTile);
 
-    stage_tile<K, HAS_V, LOAD, NT, IT>(in, sm, base, tile_n, bulk, st);
-    __syncthreads();
-
-    // warp w owns tile items [w*kItems*32, +kItems*32), read consecutively
-    K k[kItems];
-    u64 v[kItems];
-    u32 rank[kItems];
-    const u32 w0 = w * kItems * 32;
-    const u32* s32 = reinterpret_cast<const u32*>(sm.keys);
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-        const u32 li = w0 + j * 32 + lane;
-        if (li < tile_n) {
-            if constexpr (LOAD == LOAD_PACK) k[j] = (K)(((u64)s32[li] << 32) | (u64)s32[kTile + li]);
-            else k[j] = sm.keys[li];
-            if constexpr (HAS_V) v[j] = sm.vals[li];
-        } else {
-            k[j] = 0;
-            if constexpr (HAS_V) v[j] = 0;
-        }
-    }
-    // stable rank within the warp, item by item
-    const u32 lt = lanemask_lt();
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-        const u32 li = w0 + j * 32 + lane;
-        const bool valid = li < tile_n;
-        const u32 d = valid ? ((u32)(k[j] >> shift) & 0xFF) : 0x100u;
-        const u32 peers = __match_any_sync(FULL, d);
-        u32 before = 0;
-        if (valid) before = sm.whist[w][d];
-        __syncwarp();
-        if (valid) {
-            rank[j] = before + __popc(peers & lt);
-            if ((peers & lt) == 0) sm.whist[w][d] = (unsigned short)(before + __popc(peers));
-        }
-        __syncwarp();
-    }
-    __syncthreads();
-
-    // per digit (thread = digit): exclusive over warps, tile count
-    const u32 d = threadIdx.x;
-    u32 run = 0;
-    if (d < (u32)kRadix) {
-#pragma unroll
-        for (int ww = 0; ww < kWarps; ++ww) {
-            const u32 c = sm.whist[ww][d];
-            sm.whist[ww][d] = (unsigned short)run;
-            run += c;
-        }
-        // publish this tile's count early so successors can proceed
-        st_volatile(&status[tile * kRadix + d], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, run));
-    }
-    const u32 ls = block_excl_scan_nt<NT>(run, sm.wsum, &sm.total);
-    if (d < (u32)kRadix) {
-        sm.lstart[d] = ls;
-        u64 prefix = 0;
-        if (tile > 0) {
-            prefix = lookback(status + d, kRadix, tile, tag, st);
-            st_volatile(&status[tile * kRadix + d], pack_status(tag, kFlagPrefix, prefix + run));
-        }
-        sm.gbase[d] = offs[d] + prefix;
-    }
-    __syncthreads();
-
-    // place keys in tile-local digit order
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-        const u32 li = w0 + j * 32 + lane;
-        if (li < tile_n) {
-            const u32 dj = (u32)(k[j] >> shift) & 0xFF;
-            const u32 pos = sm.lstart[dj] + sm.whist[w][dj] + rank[j];
-            if (pos < (u32)kTile) {
-                sm.keys[pos] = k[j];
-                if constexpr (HAS_V) sm.vals[pos] = v[j];
+        // Tiles are taken in order, so the tile pf_tiles ahead will be taken by
+        // some CTA about one residency later: start moving it into L2 now, and
+        // its staging copy then reads L2 instead of waiting on HBM.
+        if (bulk && pf_tiles && threadIdx.x == 0) {
+            const u64 pb = base + (u64)pf_tiles * kTile;
+            if (pb < n) {
+                const u64 cnt = (n - pb) < (u64)kTile ? (n - pb) : (u64)kTile;
+                if constexpr (LOAD == LOAD_PACK) {
+                    const u32 bytes = (u32)(cnt * 4u) & ~15u;
+                    if (bytes) {
+                        bulk_prefetch_l2(in.src + pb, bytes);
+                        bulk_prefetch_l2(in.dst + pb, bytes);
+                    }
+                } else {
+                    const u32 bytes = (u32)(cnt * sizeof(K)) & ~15u;
+                    if (bytes) bulk_prefetch_l2(reinterpret_cast<const K*>(in.keys) + pb, bytes);
+                    if constexpr (HAS_V) {
+                        const u32 vb = (u32)(cnt * 8u) & ~15u;
+                        if (vb) bulk_prefetch_l2(in.vals + pb, vb);
+                    }
+                }
             }
         }
-    }
-    __syncthreads();
 
-    // write out: consecutive smem positions of one digit go to consecutive
-    // global positions
-    for (u32 i = threadIdx.x; i < tile_n; i += NT) {
-        const K key = sm.keys[i];
-        const u32 dk = (u32)(key >> shift) & 0xFF;
-        const u64 dst = sm.gbase[dk] + (i - sm.lstart[dk]);
-        if (dst < n) {  // always true unless a look-back gave up
-            kout[dst] = key;
-            if constexpr (HAS_V) vout[dst] = sm.vals[i];
+        {
+            const bool ok = stage_tile<K, HAS_V, LOAD, NT, IT>(in, sm, base, tile_n, bulk, parity, st);
+            if (threadIdx.x == 0 && !ok) sm.abort = 1;
         }
+        parity ^= bulk ? 1u : 0u;
+        __syncthreads();
+        if (sm.abort) break;  // a staging copy never completed (recorded); stop taking tiles
+
+        // warp w owns tile items [w*kItems*32, +kItems*32), read consecutively
+        K k[kItems];
+        u64 v[kItems];
+        u32 rank[kItems];
+        const u32 w0 = w * kItems * 32;
+        const u32* s32 = reinterpret_cast<const u32*>(sm.keys);
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            const u32 li = w0 + j * 32 + lane;
+            if (li < tile_n) {
+                if constexpr (LOAD == LOAD_PACK) k[j] = (K)(((u64)s32[li] << 32) | (u64)s32[kTile + li]);
+                else k[j] = sm.keys[li];
+                if constexpr (HAS_V) v[j] = sm.vals[li];
+            } else {
+                k[j] = 0;
+                if constexpr (HAS_V) v[j] = 0;
+            }
+        }
+        // stable rank within the warp, item by item
+        const u32 lt = lanemask_lt();
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            const u32 li = w0 + j * 32 + lane;
+            const bool valid = li < tile_n;
+            const u32 d = valid ? ((u32)(k[j] >> shift) & 0xFF) : 0x100u;
+            const u32 peers = __match_any_sync(FULL, d);
+            u32 before = 0;
+            if (valid) before = sm.whist[w][d];
+            __syncwarp();
+            if (valid) {
+                rank[j] = before + __popc(peers & lt);
+                if ((peers & lt) == 0) sm.whist[w][d] = (unsigned short)(before + __popc(peers));
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+
+        // per digit (thread = digit): exclusive over warps, tile count
+        const u32 d = threadIdx.x;
+        u32 run = 0;
+        if (d < (u32)kRadix) {
+#pragma unroll
+            for (int ww = 0; ww < kWarps; ++ww) {
+                const u32 c = sm.whist[ww][d];
+                sm.whist[ww][d] = (unsigned short)run;
+                run += c;
+            }
+            // publish this tile's count early so successors can proceed
+            st_volatile(&status[tile * kRadix + d], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, run));
+        }
+        const u32 ls = block_excl_scan_nt<NT>(run, sm.wsum, &sm.total);
+        if (d < (u32)kRadix) {
+            sm.lstart[d] = ls;
+            u64 prefix = 0;
+            if (tile > 0) {
+                prefix = lookback<kLookDigits>(status + d, kRadix, tile, tag, st);
+                st_volatile(&status[tile * kRadix + d], pack_status(tag, kFlagPrefix, prefix + run));
+            }
+            sm.gbase[d] = offs[d] + prefix;
+        }
+        __syncthreads();
+
+        // place keys in tile-local digit order
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            const u32 li = w0 + j * 32 + lane;
+            if (li < tile_n) {
+                const u32 dj = (u32)(k[j] >> shift) & 0xFF;
+                const u32 pos = sm.lstart[dj] + sm.whist[w][dj] + rank[j];
+                if (pos < (u32)kTile) {
+                    sm.keys[pos] = k[j];
+                    if constexpr (HAS_V) sm.vals[pos] = v[j];
+                }
+            }
+        }
+        __syncthreads();
+
+        // write out: consecutive smem positions of one digit go to consecutive
+        // global positions
+        for (u32 i = threadIdx.x; i < tile_n; i += NT) {
+            const K key = sm.keys[i];
+            const u32 dk = (u32)(key >> shift) & 0xFF;
+            const u64 dst = sm.gbase[dk] + (i - sm.lstart[dk]);
+            if (dst < n) {  // always true unless a look-back gave up
+                kout[dst] = key;
+                if constexpr (HAS_V) vout[dst] = sm.vals[i];
+            }
+        }
+        __syncthreads();  // the tile's shared memory is reused by the next one
     }
 }
 
@@ -368,7 +462,8 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
 template <int KEYMODE>
 __device__ __forceinline__ u64 run_key(const void* keys, u64 i) {
     if constexpr (KEYMODE == RUN_U64) return reinterpret_cast<const u64*>(keys)[i];
-    else if constexpr (KEYMODE == RUN_SRC_OF_U64) return reinterpret_cast<const u64*>(keys)[i] >> 32;
+    else if constexpr (KEYMODE == RUN_SRC_OF_U64 || KEYMODE == RUN_HI_OF_PACKED)
+        return reinterpret_cast<const u64*>(keys)[i] >> 32;
     else return reinterpret_cast<const u32*>(keys)[i];
 }
 
@@ -399,135 +494,154 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
                                                     u64* __restrict__ head_keys, u64* __restrict__ pos,
                                                     u64* __restrict__ psum, u64* status_c,
                                                     u64* status_s, u32* tile_counter, u32 tag,
-                                                    u64* R_out, DevStats* st) {
+                                                    u64* R_out, DevStats* st, u64* __restrict__ pack_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RunsSmem<HAS_V>& sm = *reinterpret_cast<RunsSmem<HAS_V>*>(smem_raw);
     const u32 FULL = 0xFFFFFFFFu;
     const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const u64 n = n_dev ? *n_dev : n_arg;
-    if (threadIdx.x == 0) sm.tile = atomicAdd(tile_counter, 1u);
-    __syncthreads();
-    const u64 tile = sm.tile;
-    const u64 base = tile * kTile;
-    if (base >= n) {
-        // an empty sequence still needs its terminal entry
-        if (n == 0 && tile == 0 && threadIdx.x == 0) {
-            pos[0] = 0;
-            if constexpr (HAS_V) psum[0] = 0;
-            *R_out = 0;
+    // Persistent: take tiles in order until none are left (a launch for an
+    // upper bound on n costs no empty CTAs).
+    for (;;) {
+        if (threadIdx.x == 0) sm.tile = atomicAdd(tile_counter, 1u);
+        __syncthreads();
+        const u64 tile = sm.tile;
+        const u64 base = tile * kTile;
+        if (base >= n) {
+            // an empty sequence still needs its terminal entry
+            if (n == 0 && tile == 0 && threadIdx.x == 0) {
+                pos[0] = 0;
+                if constexpr (HAS_V) psum[0] = 0;
+                *R_out = 0;
+            }
+            break;
         }
-        return;
-    }
-    const u64 tile_n = (n - base) < (u64)kTile ? (n - base) : (u64)kTile;
+        const u64 tile_n = (n - base) < (u64)kTile ? (n - base) : (u64)kTile;
 
-    for (u32 i = threadIdx.x; i < tile_n; i += kThreads) {
-        sm.key[i + 1] = run_key<KEYMODE>(keys, base + i);
-        if constexpr (HAS_V) sm.val[i] = vals[base + i];
-    }
-    if (threadIdx.x == 0) sm.key[0] = base > 0 ? run_key<KEYMODE>(keys, base - 1) : ~0ull;
-    __syncthreads();
-
-    // sweep 1: heads and value sums per warp
-    const u32 w0 = w * (kItems * 32);
-    u32 cnt = 0;
-    u64 vs = 0;
-#pragma unroll 4
-    for (int r = 0; r < kItems; ++r) {
-        const u32 li = w0 + r * 32 + lane;
-        bool h = false;
-        if (li < tile_n) {
-            h = (base + li == 0) || sm.key[li + 1] != sm.key[li];
-            if constexpr (HAS_V) vs += sm.val[li];
-        }
-        cnt += __popc(__ballot_sync(FULL, h));
-    }
-    if constexpr (HAS_V) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) vs += __shfl_xor_sync(FULL, vs, o);
-    }
-    if (lane == 0) {
-        sm.wcnt[w] = cnt;
-        if constexpr (HAS_V) sm.wsum[w] = vs;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        u32 c = 0;
-        u64 s = 0;
-        for (int i = 0; i < kWarps; ++i) {
-            const u32 tc = sm.wcnt[i];
-            sm.wcnt[i] = c;
-            c += tc;
-            if constexpr (HAS_V) {
-                const u64 ts = sm.wsum[i];
-                sm.wsum[i] = s;
-                s += ts;
+        for (u32 i = threadIdx.x; i < tile_n; i += kThreads) {
+            if constexpr (KEYMODE == RUN_HI_OF_PACKED) {
+                const u64 wd = reinterpret_cast<const u64*>(keys)[base + i];
+                sm.key[i + 1] = wd >> 32;
+                sm.val[i] = wd & 0xFFFFFFFFull;
+            } else if constexpr (KEYMODE == RUN_SRC_OF_U64) {
+                // with pack_out, also emit (dst << 32 | value) for a sort by dst
+                // (values < 2^32)
+                const u64 wd = reinterpret_cast<const u64*>(keys)[base + i];
+                const u64 v = vals[base + i];
+                sm.key[i + 1] = wd >> 32;
+                sm.val[i] = v;
+                if (pack_out) pack_out[base + i] = (wd << 32) | (v & 0xFFFFFFFFull);
+            } else {
+                sm.key[i + 1] = run_key<KEYMODE>(keys, base + i);
+                if constexpr (HAS_V) sm.val[i] = vals[base + i];
             }
         }
-        sm.tot = c;
-        sm.tot64 = s;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        st_volatile(&status_c[tile], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, sm.tot));
-        u64 c = 0;
-        if (tile > 0) {
-            c = lookback(status_c, 1, tile, tag, st);
-            st_volatile(&status_c[tile], pack_status(tag, kFlagPrefix, c + sm.tot));
-        }
-        sm.cbase = c;
-    }
-    if (HAS_V && threadIdx.x == 32) {
-        st_volatile(&status_s[tile], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, sm.tot64));
-        u64 s = 0;
-        if (tile > 0) {
-            s = lookback(status_s, 1, tile, tag, st);
-            st_volatile(&status_s[tile], pack_status(tag, kFlagPrefix, s + sm.tot64));
-        }
-        sm.sbase = s;
-    }
-    __syncthreads();
+        if (threadIdx.x == 0) sm.key[0] = base > 0 ? run_key<KEYMODE>(keys, base - 1) : ~0ull;
+        __syncthreads();
 
-    // sweep 2: write heads in order
-    u64 r_run = sm.cbase + sm.wcnt[w];
-    u64 s_run = HAS_V ? sm.sbase + sm.wsum[w] : 0;
-    const u32 lt = lanemask_lt();
+        // sweep 1: heads and value sums per warp
+        const u32 w0 = w * (kItems * 32);
+        u32 cnt = 0;
+        u64 vs = 0;
 #pragma unroll 4
-    for (int r = 0; r < kItems; ++r) {
-        const u32 li = w0 + r * 32 + lane;
-        bool h = false;
-        u64 v = 0;
-        if (li < tile_n) {
-            h = (base + li == 0) || sm.key[li + 1] != sm.key[li];
-            if constexpr (HAS_V) v = sm.val[li];
+        for (int r = 0; r < kItems; ++r) {
+            const u32 li = w0 + r * 32 + lane;
+            bool h = false;
+            if (li < tile_n) {
+                h = (base + li == 0) || sm.key[li + 1] != sm.key[li];
+                if constexpr (HAS_V) vs += sm.val[li];
+            }
+            cnt += __popc(__ballot_sync(FULL, h));
         }
-        const u32 bal = __ballot_sync(FULL, h);
-        u64 vex = 0, vtot = 0;
         if constexpr (HAS_V) {
-            u64 x = v;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const u64 y = __shfl_up_sync(FULL, x, o);
-                if (lane >= (u32)o) x += y;
-            }
-            vex = x - v;
-            vtot = __shfl_sync(FULL, x, 31);
+            for (int o = 16; o > 0; o >>= 1) vs += __shfl_xor_sync(FULL, vs, o);
         }
-        if (h) {
-            const u64 rr = r_run + __popc(bal & lt);
-            if (rr < n) {  // R <= n unless a look-back gave up
-                pos[rr] = base + li;
-                if constexpr (HAS_V) psum[rr] = s_run + vex;
-                if (head_keys) head_keys[rr] = sm.key[li + 1];
-            }
+        if (lane == 0) {
+            sm.wcnt[w] = cnt;
+            if constexpr (HAS_V) sm.wsum[w] = vs;
         }
-        r_run += __popc(bal);
-        s_run += vtot;
-    }
-    if (base + tile_n == n && threadIdx.x == 0) {
-        const u64 R = min(sm.cbase + sm.tot, n);
-        pos[R] = n;
-        if constexpr (HAS_V) psum[R] = sm.sbase + sm.tot64;
-        *R_out = R;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            u32 c = 0;
+            u64 s = 0;
+            for (int i = 0; i < kWarps; ++i) {
+                const u32 tc = sm.wcnt[i];
+                sm.wcnt[i] = c;
+                c += tc;
+                if constexpr (HAS_V) {
+                    const u64 ts = sm.wsum[i];
+                    sm.wsum[i] = s;
+                    s += ts;
+                }
+            }
+            sm.tot = c;
+            sm.tot64 = s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            st_volatile(&status_c[tile], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, sm.tot));
+            u64 c = 0;
+            if (tile > 0) {
+                c = lookback<8>(status_c, 1, tile, tag, st);
+                st_volatile(&status_c[tile], pack_status(tag, kFlagPrefix, c + sm.tot));
+            }
+            sm.cbase = c;
+        }
+        if (HAS_V && threadIdx.x == 32) {
+            st_volatile(&status_s[tile], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, sm.tot64));
+            u64 s = 0;
+            if (tile > 0) {
+                s = lookback<8>(status_s, 1, tile, tag, st);
+                st_volatile(&status_s[tile], pack_status(tag, kFlagPrefix, s + sm.tot64));
+            }
+            sm.sbase = s;
+        }
+        __syncthreads();
+
+        // sweep 2: write heads in order
+        u64 r_run = sm.cbase + sm.wcnt[w];
+        u64 s_run = HAS_V ? sm.sbase + sm.wsum[w] : 0;
+        const u32 lt = lanemask_lt();
+#pragma unroll 4
+        for (int r = 0; r < kItems; ++r) {
+            const u32 li = w0 + r * 32 + lane;
+            bool h = false;
+            u64 v = 0;
+            if (li < tile_n) {
+                h = (base + li == 0) || sm.key[li + 1] != sm.key[li];
+                if constexpr (HAS_V) v = sm.val[li];
+            }
+            const u32 bal = __ballot_sync(FULL, h);
+            u64 vex = 0, vtot = 0;
+            if constexpr (HAS_V) {
+                u64 x = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const u64 y = __shfl_up_sync(FULL, x, o);
+                    if (lane >= (u32)o) x += y;
+                }
+                vex = x - v;
+                vtot = __shfl_sync(FULL, x, 31);
+            }
+            if (h) {
+                const u64 rr = r_run + __popc(bal & lt);
+                if (rr < n) {  // R <= n unless a look-back gave up
+                    pos[rr] = base + li;
+                    if constexpr (HAS_V) psum[rr] = s_run + vex;
+                    if (head_keys) head_keys[rr] = sm.key[li + 1];
+                }
+            }
+            r_run += __popc(bal);
+            s_run += vtot;
+        }
+        if (base + tile_n == n && threadIdx.x == 0) {
+            const u64 R = min(sm.cbase + sm.tot, n);
+            pos[R] = n;
+            if constexpr (HAS_V) psum[R] = sm.sbase + sm.tot64;
+            *R_out = R;
+        }
+        __syncthreads();  // the tile's shared memory is reused by the next one
     }
 }
 
@@ -603,12 +717,21 @@ void launch_onesweep_nt(const SortIn& in, K* kout, u64* vout, u64 n, int shift, 
                              (int)smem);
         configured = true;
     }
+    static u32 resident = 0;  // CTAs of this instantiation resident on the whole GPU
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K, HAS_V, LOAD, NT, IT>, NT, smem);
+        resident = (u32)std::max(1, sms * std::max(per_sm, 1));
+    }
     constexpr u64 tile = (u64)NT * IT;
     const u64 tiles = (n + tile - 1) / tile;
     if (tiles == 0) return;
-    TraceScope ts(tr, onesweep_name<K, HAS_V>(), s);
-    k_onesweep<K, HAS_V, LOAD, NT, IT><<<(unsigned)tiles, NT, smem, s>>>(in, kout, vout, n, shift, offs, status,
-                                                                     tile_counter, tag, st);
+    const unsigned grid = (unsigned)std::min<u64>(tiles, resident);
+    TraceScope ts(tr, in.trace_name ? in.trace_name : onesweep_name<K, HAS_V>(), s);
+    k_onesweep<K, HAS_V, LOAD, NT, IT><<<grid, NT, smem, s>>>(in, kout, vout, n, shift, offs, status, tile_counter,
+                                                             tag, st, (u32)NS_ONESWEEP_PF * resident);
 }
 
 // 64-bit keys without values use 8192-key tiles (512 threads): half the
@@ -628,7 +751,7 @@ void launch_onesweep(const SortIn& in, K* kout, u64* vout, u64 n, int shift, con
 template <int KEYMODE, bool HAS_V>
 void launch_runs_t(const void* keys, const u64* vals, u64 n, const u64* n_dev, u64* head_keys, u64* pos, u64* psum,
                    u64* status_c, u64* status_s, u32* tile_counter, u32 tag, u64* R_out, DevStats* st,
-                   Tracer* tr, cudaStream_t s) {
+                   Tracer* tr, cudaStream_t s, u64* pack_out) {
     const size_t smem = sizeof(RunsSmem<HAS_V>);
     static bool configured = false;
     if (!configured) {
@@ -636,12 +759,21 @@ void launch_runs_t(const void* keys, const u64* vals, u64 n, const u64* n_dev, u
                              (int)smem);
         configured = true;
     }
+    static u32 resident = 0;  // CTAs of this instantiation resident on the whole GPU
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_runs<KEYMODE, HAS_V>, kThreads, smem);
+        resident = (u32)std::max(1, sms * std::max(per_sm, 1));
+    }
     u64 tiles = (n + kTile - 1) / kTile;
     if (tiles == 0) tiles = 1;
+    tiles = std::min<u64>(tiles, resident);
     TraceScope ts(tr, KEYMODE == RUN_U64 ? "k_runs<links>" : (KEYMODE == RUN_SRC_OF_U64 ? "k_runs<rows>" : "k_runs<cols>"),
                   s);
     k_runs<KEYMODE, HAS_V><<<(unsigned)tiles, kThreads, smem, s>>>(
-        keys, vals, n, n_dev, head_keys, pos, psum, status_c, status_s, tile_counter, tag, R_out, st);
+        keys, vals, n, n_dev, head_keys, pos, psum, status_c, status_s, tile_counter, tag, R_out, st, pack_out);
 }
 
 // Diagnostics: the library's bounded waits run against something nothing
@@ -649,7 +781,7 @@ void launch_runs_t(const void* keys, const u64* vals, u64 n, const u64* n_dev, u
 // mbarrier phase expecting bytes that no copy delivers -- so that they time
 // out and record ERR_TIMEOUT.  No fault, trap or unbounded wait is involved.
 __global__ void k_diag_lookback(u64* status, DevStats* st) {
-    if (threadIdx.x == 0) lookback(status, 1, 1, 0x7777u, st);
+    if (threadIdx.x == 0) lookback<8>(status, 1, 1, 0x7777u, st);
 }
 
 __global__ void k_diag_mbarrier(DevStats* st) {
@@ -703,6 +835,7 @@ int radix_sort_t(const SortIn& in, K* kbuf[2], u64* vbuf[2], u64 n, int begin_bi
             mid.keys = kbuf[(p - 1) & 1];
             mid.vals = vbuf[(p - 1) & 1];
             mid.n_dev = in.n_dev;
+            mid.trace_name = in.trace_name;
             // a caller's output buffer can be one of the ping-pong buffers:
             // stage with bulk copies only from 16-byte-aligned addresses
             mid.bulk = (((uintptr_t)kbuf[(p - 1) & 1] | (uintptr_t)vbuf[(p - 1) & 1]) & 15) == 0;
@@ -744,9 +877,20 @@ int radix_sort_dst_pairs(const u64* link_keys, const u64* counts, const u64* n_d
     return radix_sort_t<u32, true, LOAD_DST_OF>(in, (u32**)kbuf, (u64**)vbuf, n, 0, 4, sc, st, s);
 }
 
+int radix_sort_hi32(const u64* packed, const u64* n_dev, u64* kbuf[2], u64 n, SortScratch& sc, DevStats* st,
+                    cudaStream_t s) {
+    SortIn in{};
+    in.keys = packed;
+    in.n_dev = (const u64*)n_dev;
+    in.bulk = ((uintptr_t)packed & 15) == 0;
+    in.trace_name = "k_onesweep<u64 key, by dst>";
+    u64* vb[2] = {nullptr, nullptr};
+    return radix_sort_t<u64, false, LOAD_KEYS>(in, (u64**)kbuf, vb, n, 32, 4, sc, st, s);
+}
+
 void launch_runs(int keymode, bool has_v, const void* keys, const u64* vals, u64 n,
                  const u64* n_dev, u64* head_keys, u64* pos, u64* psum,
-                 u64* R_out, SortScratch& sc, DevStats* st, cudaStream_t s) {
+                 u64* R_out, SortScratch& sc, DevStats* st, cudaStream_t s, u64* pack_out) {
     cudaMemsetAsync(sc.tile_counters + 8, 0, sizeof(u32), s);
     const u32 tag = next_tag(sc, s);
     const u64* nd = (const u64*)n_dev;
@@ -755,13 +899,16 @@ void launch_runs(int keymode, bool has_v, const void* keys, const u64* vals, u64
     u32* tc = sc.tile_counters + 8;
     if (keymode == RUN_U64 && !has_v)
         launch_runs_t<RUN_U64, false>(keys, (const u64*)vals, n, nd, (u64*)head_keys, (u64*)pos,
-                                      (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, sc.tr, s);
+                                      (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, sc.tr, s, nullptr);
     else if (keymode == RUN_SRC_OF_U64 && has_v)
         launch_runs_t<RUN_SRC_OF_U64, true>(keys, (const u64*)vals, n, nd, (u64*)head_keys, (u64*)pos,
-                                            (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, sc.tr, s);
+                                            (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, sc.tr, s, pack_out);
     else if (keymode == RUN_U32 && has_v)
         launch_runs_t<RUN_U32, true>(keys, (const u64*)vals, n, nd, (u64*)head_keys, (u64*)pos,
-                                     (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, sc.tr, s);
+                                     (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, sc.tr, s, nullptr);
+    else if (keymode == RUN_HI_OF_PACKED && has_v)
+        launch_runs_t<RUN_HI_OF_PACKED, true>(keys, nullptr, n, nd, (u64*)head_keys, (u64*)pos,
+                                              (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, sc.tr, s, nullptr);
 }
 
 void launch_run_stats(int mode, const u64* pos, const u64* psum, const u64* R_ptr,

@@ -4,8 +4,9 @@ Every quantity and A's sorted nonzero list must match bit-exactly (all values
 are uint64 counts).  Sizes span several 4096-element tiles with ragged tails;
 edge cases cover the empty window, one packet, a single repeated key, the
 extreme keys 0 and 2^64-1, a star, self-loops and an all-distinct window.
-Both aggregation paths (sort, hash) are checked, and the windowed forms
-(build + accumulate, fused ingest) are checked after every window.
+Both aggregation paths (sort, hash) are checked, the sort path in both of
+its per-destination forms, and the windowed forms (build + accumulate,
+fused ingest) are checked after every window.
 """
 from __future__ import annotations
 
@@ -21,12 +22,18 @@ from gpu_util import assert_matrix_equal, export_np, stats_row, to_dev
 
 pytestmark = pytest.mark.gpu
 
-PATHS = ["hash", "sort"]
+# "sort_pairs": the sort path with its per-destination side forced onto
+# (dst, count) pairs, the form it takes from 2^32 packets on.  "hash_dense":
+# the hash path with tables sized at load 0.9, so that probe sequences run
+# long and the read-ahead probing is exercised throughout.
+PATHS = ["hash", "sort", "sort_pairs", "hash_dense"]
 
 
 @pytest.fixture(scope="module")
 def ctxs():
-    c = {p: ns.Context(0, path=p) for p in PATHS}
+    c = {"hash": ns.Context(0, path="hash"), "sort": ns.Context(0, path="sort"),
+         "sort_pairs": ns.Context(0, path="sort", column_sort="pairs"),
+         "hash_dense": ns.Context(0, path="hash", hash_load=0.9)}
     yield c
     for x in c.values():
         x.close()
@@ -213,16 +220,24 @@ def test_ingest_stats_after_every_window(ctxs):
     assert_matrix_equal(acc, *want)
 
 
-def test_trace_counts_kernels(ctxs):
-    ctx = ctxs["sort"]
+@pytest.mark.parametrize("form", ["sort", "sort_pairs"])
+def test_trace_counts_kernels(ctxs, form):
+    """Eight 64-bit digit passes for the links; the per-destination side adds
+    four passes over one u64 word per link, or four over (dst, count) pairs."""
+    ctx = ctxs[form]
     ns.trace_enable(ctx, True)
     m = ns.Matrix(ctx)
     s, d = W.single_window(50000)
     ns.window_build(ctx, to_dev(s), to_dev(d), m)
     tr = ns.trace_read(ctx)
     ns.trace_enable(ctx, False)
-    assert tr["k_onesweep<u64 key>"][0] == 8
-    assert tr["k_onesweep<u32 key, u64 value>"][0] == 4
+    if form == "sort":
+        assert tr["k_onesweep<u64 key>"][0] == 8
+        assert tr["k_onesweep<u64 key, by dst>"][0] == 4
+        assert "k_onesweep<u32 key, u64 value>" not in tr
+    else:
+        assert tr["k_onesweep<u64 key>"][0] == 8
+        assert tr["k_onesweep<u32 key, u64 value>"][0] == 4
     assert tr["k_runs<links>"][0] == 1 and tr["k_run_stats<cols>"][0] == 1
     assert all(v[1] >= 0 and v[2] >= 0 for v in tr.values())
     assert ns.trace_read(ctx) == {}
@@ -309,3 +324,25 @@ def test_random_atomic_ceiling_diagnostic():
     assert 0.0 < us < 1e6
     with pytest.raises(ns.NsError):
         ns.diag_random_atomics(1000, 10, 1)  # not a power of two
+
+
+@pytest.mark.parametrize("load", [0.01, 0.95, -1.0])
+def test_hash_load_out_of_range(load):
+    with pytest.raises(ns.NsError) as e:
+        ns.Context(0, path="hash", hash_load=load)
+    assert e.value.name == "NS_ERR_INVALID"
+
+
+def test_accumulator_growth_at_high_load():
+    """An accumulator sized at load 0.9 that outgrows its tables is rehashed
+    and stays exact."""
+    ctx = ns.Context(0, path="hash", hash_load=0.9)
+    acc = ns.Matrix(ctx)
+    ns.matrix_reserve(acc, 1000)
+    want = (np.zeros(0, np.uint64), np.zeros(0, np.uint64))
+    for w in range(4):
+        s, d = W.rmat_stream(30000, i0=w * 30000)
+        ns.window_ingest(ctx, acc, to_dev(s), to_dev(d))
+        want = oracle.accumulate(want, oracle.build_matrix(s, d))
+    assert ns.network_stats(ctx, acc) == oracle.stats(*want)
+    assert_matrix_equal(acc, *want)
