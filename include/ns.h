@@ -359,7 +359,8 @@ ns_status ns_trace_read(ns_ctx* ctx, ns_trace_entry* out, int cap, int* count);
 /* Diagnostic of the device-side wait bounds (no counterpart in the paper):
  * runs one of the library's bounded waits against something nothing will
  * signal -- which = 0: a decoupled look-back on a status word that is never
- * published; which = 1: an mbarrier phase expecting bytes no copy delivers --
+ * published; which = 1: an mbarrier phase expecting bytes no copy delivers;
+ * which = 2: the warp-wide look-back of the run kernels, likewise --
  * and returns NS_ERR_TIMEOUT once the wait gives up (about one second for
  * the look-back, two for the mbarrier, which waits a second time so that no
  * copy can still be in flight).  Blocking; the context stays usable. */

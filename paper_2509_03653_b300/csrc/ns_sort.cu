@@ -129,6 +129,52 @@ __device__ u64 lookback(u64* status, u64 stride, u64 tile, u32 tag, DevStats* st
     return prefix;
 }
 
+// The same walk by a whole warp (every lane must call it): lane l reads
+// predecessor k - l, so one round trip covers 32 predecessors.  Aggregates
+// are summed up to the nearest prefix; if an unpublished predecessor comes
+// first, the aggregates before it are taken and the warp waits (bounded) for
+// it.  Returns the prefix in every lane.
+__device__ u64 warp_lookback(const u64* status, u64 tile, u32 tag, DevStats* st) {
+    const u32 FULL = 0xFFFFFFFFu;
+    const u32 lane = threadIdx.x & 31;
+    u64 prefix = 0;
+    long long k = (long long)tile - 1;
+    u32 spins = 0;
+    u64 t0 = 0;
+    while (k >= 0) {
+        const long long j = k - (long long)lane;
+        // before tile 0 there is nothing: read as a prefix of 0
+        const u64 sw = j >= 0 ? ld_volatile(&status[j]) : pack_status(tag, kFlagPrefix, 0);
+        const bool ready = (u32)(sw >> 48) == tag && ((sw >> 46) & 3) != 0;
+        const bool is_prefix = ready && ((sw >> 46) & 3) == kFlagPrefix;
+        const u32 not_ready = __ballot_sync(FULL, !ready);
+        const u32 prefixes = __ballot_sync(FULL, is_prefix);
+        const u32 first_nr = not_ready ? (u32)(__ffs(not_ready) - 1) : 32u;
+        const u32 first_pf = prefixes ? (u32)(__ffs(prefixes) - 1) : 32u;
+        // lanes before the first unpublished one, through the first prefix
+        const u32 take = first_pf < first_nr ? first_pf + 1 : first_nr;
+        u64 v = lane < take ? (sw & kValMask) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        prefix += v;
+        if (first_pf < first_nr) break;  // reached a prefix
+        k -= (long long)take;
+        if (take > 0) {
+            spins = 0;
+            t0 = 0;
+            continue;
+        }
+        const u64 now = globaltimer_ns();
+        if (t0 == 0) t0 = now;
+        if (++spins > kMaxSpin || now - t0 > kWaitLimitNs) {
+            if (lane == 0) set_error(st, ERR_TIMEOUT);
+            break;
+        }
+        __nanosleep(20);
+    }
+    return prefix;
+}
+
 __device__ __forceinline__ u64 block_excl_scan64(u64 v, u64* wsum, u64* total) {
     const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     u64 x = v;
@@ -170,6 +216,7 @@ __device__ __forceinline__ K load_key(const SortIn& in, u64 i) {
 // Each warp counts into its own copy of the histograms (fewer shared-memory
 // atomic collisions on skewed keys); the copies are summed before the one
 // global addition per bin and CTA.
+constexpr int kHistUnroll = 8;
 template <typename K, int LOAD>
 __global__ void __launch_bounds__(kThreads) k_sort_hist(SortIn in, u64 n_arg, int begin_bit, int passes,
                                                          u32* __restrict__ ghist) {
@@ -178,10 +225,24 @@ __global__ void __launch_bounds__(kThreads) k_sort_hist(SortIn in, u64 n_arg, in
     for (int i = threadIdx.x; i < kWarps * passes * kRadix; i += kThreads) hs[i] = 0;
     __syncthreads();
     u32* h = hs + (threadIdx.x >> 5) * passes * kRadix;
+    // kHistUnroll keys per thread per round, loaded before any is counted, so
+    // that enough loads are in flight to cover HBM latency (one key at a time
+    // left this kernel latency-bound)
     const u64 stride = (u64)gridDim.x * kThreads;
-    for (u64 i = (u64)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
-        const K k = load_key<K, LOAD>(in, i);
-        for (int p = 0; p < passes; ++p) atomicAdd(&h[p * kRadix + ((u32)(k >> (begin_bit + 8 * p)) & 0xFF)], 1u);
+    for (u64 i0 = (u64)blockIdx.x * kThreads + threadIdx.x; i0 < n; i0 += stride * kHistUnroll) {
+        K k[kHistUnroll];
+#pragma unroll
+        for (int u = 0; u < kHistUnroll; ++u) {
+            const u64 i = i0 + (u64)u * stride;
+            k[u] = i < n ? load_key<K, LOAD>(in, i) : (K)0;
+        }
+#pragma unroll
+        for (int u = 0; u < kHistUnroll; ++u) {
+            if (i0 + (u64)u * stride < n) {
+                for (int p = 0; p < passes; ++p)
+                    atomicAdd(&h[p * kRadix + ((u32)(k[u] >> (begin_bit + 8 * p)) & 0xFF)], 1u);
+            }
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * kRadix; i += kThreads) {
@@ -518,22 +579,38 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
         }
         const u64 tile_n = (n - base) < (u64)kTile ? (n - base) : (u64)kTile;
 
-        for (u32 i = threadIdx.x; i < tile_n; i += kThreads) {
-            if constexpr (KEYMODE == RUN_HI_OF_PACKED) {
-                const u64 wd = reinterpret_cast<const u64*>(keys)[base + i];
-                sm.key[i + 1] = wd >> 32;
-                sm.val[i] = wd & 0xFFFFFFFFull;
-            } else if constexpr (KEYMODE == RUN_SRC_OF_U64) {
-                // with pack_out, also emit (dst << 32 | value) for a sort by dst
-                // (values < 2^32)
-                const u64 wd = reinterpret_cast<const u64*>(keys)[base + i];
-                const u64 v = vals[base + i];
-                sm.key[i + 1] = wd >> 32;
-                sm.val[i] = v;
-                if (pack_out) pack_out[base + i] = (wd << 32) | (v & 0xFFFFFFFFull);
-            } else {
-                sm.key[i + 1] = run_key<KEYMODE>(keys, base + i);
-                if constexpr (HAS_V) sm.val[i] = vals[base + i];
+        // stage the tile: all of a thread's loads are issued before any is
+        // stored, so that kItems of them are in flight at once
+        {
+            u64 wd[kItems], vv[kItems];
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                const u32 i = threadIdx.x + r * kThreads;
+                wd[r] = vv[r] = 0;
+                if (i < tile_n) {
+                    if constexpr (KEYMODE == RUN_U32) wd[r] = reinterpret_cast<const u32*>(keys)[base + i];
+                    else wd[r] = reinterpret_cast<const u64*>(keys)[base + i];
+                    if constexpr (HAS_V && KEYMODE != RUN_HI_OF_PACKED) vv[r] = vals[base + i];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kItems; ++r) {
+                const u32 i = threadIdx.x + r * kThreads;
+                if (i < tile_n) {
+                    if constexpr (KEYMODE == RUN_HI_OF_PACKED) {
+                        sm.key[i + 1] = wd[r] >> 32;
+                        sm.val[i] = wd[r] & 0xFFFFFFFFull;
+                    } else if constexpr (KEYMODE == RUN_SRC_OF_U64) {
+                        // with pack_out, also emit (dst << 32 | value) for a
+                        // sort by dst (values < 2^32)
+                        sm.key[i + 1] = wd[r] >> 32;
+                        sm.val[i] = vv[r];
+                        if (pack_out) pack_out[base + i] = (wd[r] << 32) | (vv[r] & 0xFFFFFFFFull);
+                    } else {
+                        sm.key[i + 1] = wd[r];
+                        if constexpr (HAS_V) sm.val[i] = vv[r];
+                    }
+                }
             }
         }
         if (threadIdx.x == 0) sm.key[0] = base > 0 ? run_key<KEYMODE>(keys, base - 1) : ~0ull;
@@ -579,23 +656,26 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
             sm.tot64 = s;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            st_volatile(&status_c[tile], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, sm.tot));
+        // look-back: warp 0 for the head count, warp 1 for the value sum
+        if (w == 0) {
+            if (lane == 0)
+                st_volatile(&status_c[tile], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, sm.tot));
             u64 c = 0;
             if (tile > 0) {
-                c = lookback<8>(status_c, 1, tile, tag, st);
-                st_volatile(&status_c[tile], pack_status(tag, kFlagPrefix, c + sm.tot));
+                c = warp_lookback(status_c, tile, tag, st);
+                if (lane == 0) st_volatile(&status_c[tile], pack_status(tag, kFlagPrefix, c + sm.tot));
             }
-            sm.cbase = c;
+            if (lane == 0) sm.cbase = c;
         }
-        if (HAS_V && threadIdx.x == 32) {
-            st_volatile(&status_s[tile], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, sm.tot64));
-            u64 s = 0;
+        if (HAS_V && w == 1) {
+            if (lane == 0)
+                st_volatile(&status_s[tile], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, sm.tot64));
+            u64 sv = 0;
             if (tile > 0) {
-                s = lookback<8>(status_s, 1, tile, tag, st);
-                st_volatile(&status_s[tile], pack_status(tag, kFlagPrefix, s + sm.tot64));
+                sv = warp_lookback(status_s, tile, tag, st);
+                if (lane == 0) st_volatile(&status_s[tile], pack_status(tag, kFlagPrefix, sv + sm.tot64));
             }
-            sm.sbase = s;
+            if (lane == 0) sm.sbase = sv;
         }
         __syncthreads();
 
@@ -784,6 +864,10 @@ __global__ void k_diag_lookback(u64* status, DevStats* st) {
     if (threadIdx.x == 0) lookback<8>(status, 1, 1, 0x7777u, st);
 }
 
+__global__ void k_diag_lookback_warp(u64* status, DevStats* st) {
+    warp_lookback(status, 1, 0x7777u, st);  // tile 1 waits on status[0], never published
+}
+
 __global__ void k_diag_mbarrier(DevStats* st) {
     __shared__ u64 bar;
     if (threadIdx.x == 0) {
@@ -934,6 +1018,7 @@ void launch_run_stats(int mode, const u64* pos, const u64* psum, const u64* R_pt
 namespace ns {
 void launch_diag_wait(int which, u64* status_word, DevStats* st, cudaStream_t s) {
     if (which == 0) k_diag_lookback<<<1, 32, 0, s>>>(status_word, st);
-    else k_diag_mbarrier<<<1, 32, 0, s>>>(st);
+    else if (which == 1) k_diag_mbarrier<<<1, 32, 0, s>>>(st);
+    else k_diag_lookback_warp<<<1, 32, 0, s>>>(status_word, st);
 }
 }  // namespace ns

@@ -105,7 +105,7 @@ ns_status ns_trace_read(ns_ctx* c, ns_trace_entry* out, int cap, int* count) {
 }
 
 ns_status ns_diag_wait_timeout(int which, ns_stream_t stream) {
-    if (which != 0 && which != 1) return ns::set_fail(NS_ERR_INVALID, "ns_diag_wait_timeout: which must be 0 or 1");
+    if (which < 0 || which > 2) return ns::set_fail(NS_ERR_INVALID, "ns_diag_wait_timeout: which must be 0, 1 or 2");
     cudaStream_t s = (cudaStream_t)stream;
     ns::Buf b;
     ns_status st = ns::buf_reserve(b, sizeof(ns::DevStats) + 64);

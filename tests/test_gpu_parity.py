@@ -297,11 +297,12 @@ def test_skewed_windows_cache_modes(cache, s_exp, K, n):
     assert_matrix_equal(acc, *want)
 
 
-@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("which", [0, 1, 2])
 def test_bounded_device_waits_time_out(which):
-    """A look-back on a status word nobody publishes, and an mbarrier phase
-    expecting bytes no copy delivers: the bounded waits give up with
-    NS_ERR_TIMEOUT within seconds and the device stays usable."""
+    """A look-back on a status word nobody publishes (one thread, and a whole
+    warp), and an mbarrier phase expecting bytes no copy delivers: the
+    bounded waits give up with NS_ERR_TIMEOUT within seconds and the device
+    stays usable."""
     import ctypes
     import time
     from paper_2509_03653_b300 import _native
