@@ -282,8 +282,7 @@ struct ScatterSmem {
     K keys[TILE];  // staged tile, then the tile in digit order
     u64 vals[HAS_V ? TILE : 1];
     unsigned short whist[NW][kRadix];  // per-warp digit counts (<= 512)
-    u32 lstart[kRadix];
-    u64 gbase[kRadix];
+    u64 gdelta[kRadix];  // global position of a digit's first key minus its tile-local start
     u32 wsum[NW];
     u32 total;
     u32 tile;
@@ -478,13 +477,15 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
         }
         const u32 ls = block_excl_scan_nt<NT>(run, sm.wsum, &sm.total);
         if (d < (u32)kRadix) {
-            sm.lstart[d] = ls;
+            // each warp's first slot for digit d in the tile's digit order
+#pragma unroll
+            for (int ww = 0; ww < kWarps; ++ww) sm.whist[ww][d] = (unsigned short)(sm.whist[ww][d] + ls);
             u64 prefix = 0;
             if (tile > 0) {
                 prefix = lookback<kLookDigits>(status + d, kRadix, tile, tag, st);
                 st_volatile(&status[tile * kRadix + d], pack_status(tag, kFlagPrefix, prefix + run));
             }
-            sm.gbase[d] = offs[d] + prefix;
+            sm.gdelta[d] = offs[d] + prefix - ls;  // modulo 2^64; + i below lands in range
         }
         __syncthreads();
 
@@ -494,7 +495,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
             const u32 li = w0 + j * 32 + lane;
             if (li < tile_n) {
                 const u32 dj = (u32)(k[j] >> shift) & 0xFF;
-                const u32 pos = sm.lstart[dj] + sm.whist[w][dj] + rank[j];
+                const u32 pos = sm.whist[w][dj] + rank[j];
                 if (pos < (u32)kTile) {
                     sm.keys[pos] = k[j];
                     if constexpr (HAS_V) sm.vals[pos] = v[j];
@@ -508,7 +509,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
         for (u32 i = threadIdx.x; i < tile_n; i += NT) {
             const K key = sm.keys[i];
             const u32 dk = (u32)(key >> shift) & 0xFF;
-            const u64 dst = sm.gbase[dk] + (i - sm.lstart[dk]);
+            const u64 dst = sm.gdelta[dk] + i;
             if (dst < n) {  // always true unless a look-back gave up
                 kout[dst] = key;
                 if constexpr (HAS_V) vout[dst] = sm.vals[i];
