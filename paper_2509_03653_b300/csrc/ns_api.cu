@@ -663,7 +663,7 @@ ns_status ns_window_ingest(ns_ctx* c, ns_matrix* acc, const uint32_t* d_src, con
     TRY(to_hash(acc, n, s));
     if (n == 0) return NS_OK;
     TraceScope ts(&c->tracer, "k_insert_packets", s);
-    launch_insert_packets(d_src, d_dst, n, hash_view(acc), c->sms, use_cta_cache(c, n), s);
+    launch_insert_packets(d_src, d_dst, n, hash_view(acc), c->sms, use_cta_cache(c, n), s, true);
     acc->bound += n;
     return check_launch();
 }

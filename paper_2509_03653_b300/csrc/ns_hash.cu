@@ -218,7 +218,7 @@ __device__ __forceinline__ u64 degree_add_cached(u32* cids, u32* cdeg, NodeSlot*
 // (2) the count additions of entries that already existed and, for a new
 // link, the degree increments of its row and column, again issued together.
 // With a cache, the parts that find room in it stay in shared memory.
-template <bool CACHE>
+template <bool CACHE, bool SNAP>
 __device__ __forceinline__ void insert_item(const HashView& M, bool valid, u64 key, u64 c, bool dedup,
                                             BlockStats& bs, CtaCache* C) {
     const u32 FULL = 0xFFFFFFFFu;
@@ -267,14 +267,17 @@ __device__ __forceinline__ void insert_item(const HashView& M, bool valid, u64 k
         if (cdir && ck == 2) Cl = node_probe(M.cols, M.col_mask, did + 1, cs, ci0, M.stats);
         // a found link cannot have count 0, so "new" is known now
         newlink = ldir && ((lk == 0) || (lk == 2 && L.slot != kNoSlot && L.prev == 0));
-        // round trip 2.  A node found at its home slot by the claim returned
-        // its contents: when the link is new, one 128-bit CAS from that
-        // snapshot adds the packets and the partner together (falling back
-        // to two additions if another update got there first).
+        // round trip 2.  With SNAP, a node found at its home slot by the
+        // claim returned its contents: when the link is new, one 128-bit CAS
+        // from that snapshot adds the packets and the partner together
+        // (falling back to two additions if another update got there first).
+        // That pays when inserts go to a large resident matrix whose nodes
+        // are rarely updated twice at once; in small per-window tables with
+        // hot nodes the CAS mostly fails and costs a third round trip.
         if (ldir && lk == 1) L.prev = atomicAdd(&M.links[li0].count, cs);
         if (ldir && lside) newlink = (L.prev == 0);  // the key-0 slot is only added to
         bool rdone = false, cdone = false;
-        if (newlink && rdir && rk == 1 && !rside && (u32)(ro.lo >> 32) != 0xFFFFFFFFu) {
+        if (SNAP && newlink && rdir && rk == 1 && !rside && (u32)(ro.lo >> 32) != 0xFFFFFFFFu) {
             const W128 w = cas128(&M.rows[ri0], ro.lo, ro.hi, ro.lo + (1ull << 32), ro.hi + cs);
             if (w.lo == ro.lo && w.hi == ro.hi) {
                 R.prev = ro.hi;
@@ -282,7 +285,7 @@ __device__ __forceinline__ void insert_item(const HashView& M, bool valid, u64 k
                 rdone = true;
             }
         }
-        if (newlink && cdir && ck == 1 && !cside && (u32)(co.lo >> 32) != 0xFFFFFFFFu) {
+        if (SNAP && newlink && cdir && ck == 1 && !cside && (u32)(co.lo >> 32) != 0xFFFFFFFFu) {
             const W128 w = cas128(&M.cols[ci0], co.lo, co.hi, co.lo + (1ull << 32), co.hi + cs);
             if (w.lo == co.lo && w.hi == co.hi) {
                 Cl.prev = co.hi;
@@ -431,7 +434,7 @@ __device__ __forceinline__ void last_block_snapshot(DevStats* st, u64* out) {
 
 // Raw packets: two uint32 columns (the paper's src and dst), count 1 each.
 // With `out` set, the statistics after this launch are written there.
-template <bool CACHE>
+template <bool CACHE, bool SNAP>
 __global__ void __launch_bounds__(kInsertThreads) k_insert_packets(const u32* __restrict__ src,
                                                                    const u32* __restrict__ dst, u64 n,
                                                                    HashView M, u64* __restrict__ out) {
@@ -465,7 +468,7 @@ __global__ void __launch_bounds__(kInsertThreads) k_insert_packets(const u32* __
             valid = i < n;
             key = valid ? (((u64)__ldg(src + i) << 32) | (u64)__ldg(dst + i)) : 0ull;
         }
-        insert_item<CACHE>(M, valid, key, 1, true, bs, C);
+        insert_item<CACHE, SNAP>(M, valid, key, 1, true, bs, C);
     }
     if constexpr (CACHE) cache_flush(M, *C, bs);
     __syncthreads();
@@ -495,7 +498,7 @@ __global__ void __launch_bounds__(kInsertThreads) k_insert_slots(const LinkSlot*
             c = s.count;
             key = (i == in_cap) ? 0ull : s.key;
         }
-        insert_item<CACHE>(M, c > 0, key, c, false, bs, C);
+        insert_item<CACHE, false>(M, c > 0, key, c, false, bs, C);
     }
     if constexpr (CACHE) cache_flush(M, *C, bs);
     __syncthreads();
@@ -524,7 +527,7 @@ __global__ void __launch_bounds__(kInsertThreads) k_insert_list(const u64* __res
             key = keys[i];
             c = counts[i];
         }
-        insert_item<CACHE>(M, c > 0, key, c, false, bs, C);
+        insert_item<CACHE, false>(M, c > 0, key, c, false, bs, C);
     }
     if constexpr (CACHE) cache_flush(M, *C, bs);
     __syncthreads();
@@ -620,7 +623,7 @@ __global__ void __launch_bounds__(kInsertThreads) k_batch_insert(BatchDev B, u32
             const bool valid = i < p1;
             u64 key = 0;
             if (valid) key = ((u64)__ldg(B.src + i) << 32) | (u64)__ldg(B.dst + i);
-            insert_item<CACHE>(M, valid, key, 1, true, bs, C);
+            insert_item<CACHE, false>(M, valid, key, 1, true, bs, C);
         }
         if constexpr (CACHE) cache_flush(M, *C, bs);
         __syncthreads();
@@ -660,12 +663,14 @@ int grid_for(u64 n, int threads, int sms, int per_sm) {
 }  // namespace
 
 void launch_insert_packets(const u32* src, const u32* dst, u64 n, const HashView& M,
-                           int sms, bool cache, cudaStream_t s) {
+                           int sms, bool cache, cudaStream_t s, bool snap) {
     if (n == 0) return;
-    if (cache)
-        k_insert_packets<true><<<grid_for(n, kInsertThreads, sms, 8), kInsertThreads, sizeof(CtaCache), s>>>(src, dst, n, M, nullptr);
-    else
-        k_insert_packets<false><<<grid_for(n, kInsertThreads, sms, 8), kInsertThreads, 0, s>>>(src, dst, n, M, nullptr);
+    const int grid = grid_for(n, kInsertThreads, sms, 8);
+    const size_t smem = cache ? sizeof(CtaCache) : 0;
+    if (cache && snap) k_insert_packets<true, true><<<grid, kInsertThreads, smem, s>>>(src, dst, n, M, nullptr);
+    else if (cache) k_insert_packets<true, false><<<grid, kInsertThreads, smem, s>>>(src, dst, n, M, nullptr);
+    else if (snap) k_insert_packets<false, true><<<grid, kInsertThreads, smem, s>>>(src, dst, n, M, nullptr);
+    else k_insert_packets<false, false><<<grid, kInsertThreads, smem, s>>>(src, dst, n, M, nullptr);
 }
 
 void launch_insert_packets_snapshot(const u32* src, const u32* dst, u64 n, const HashView& M,
@@ -686,8 +691,8 @@ void launch_insert_packets_snapshot(const u32* src, const u32* dst, u64 n, const
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cache) cudaLaunchKernelEx(&cfg, k_insert_packets<true>, src, dst, n, M, out);
-    else cudaLaunchKernelEx(&cfg, k_insert_packets<false>, src, dst, n, M, out);
+    if (cache) cudaLaunchKernelEx(&cfg, k_insert_packets<true, true>, src, dst, n, M, out);
+    else cudaLaunchKernelEx(&cfg, k_insert_packets<false, true>, src, dst, n, M, out);
 }
 
 void launch_insert_slots(const LinkSlot* in, u64 in_cap, const HashView& M, int sms,

@@ -99,9 +99,11 @@ struct BatchDev {
 };
 
 // hash path (ns_hash.cu)
-// `cache`: stage skewed keys in per-CTA shared-memory tables first
+// `cache`: stage skewed keys in per-CTA shared-memory tables first.
+// `snap`: update existing nodes from the claim's snapshot with one CAS (for
+// inserts into a large resident matrix; the snapshot launch always does).
 void launch_insert_packets(const u32* src, const u32* dst, u64 n, const HashView& M,
-                           int sms, bool cache, cudaStream_t s);
+                           int sms, bool cache, cudaStream_t s, bool snap = false);
 void launch_insert_packets_snapshot(const u32* src, const u32* dst, u64 n, const HashView& M,
                                     u64* out, int sms, bool cache, cudaStream_t s);
 void launch_insert_slots(const LinkSlot* in, u64 in_cap, const HashView& M, int sms,
