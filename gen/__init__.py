@@ -58,8 +58,17 @@ def lib():
         L.nsg_uniform_doubles.argtypes = [_f64p, _U64, ctypes.c_double, ctypes.c_double, _U64, _U64]
         L.nsg_poisson_arrivals.argtypes = [_f64p, _U64, ctypes.c_double, _U64, _U64]
         L.nsg_uniform_pairs.argtypes = [_u32p, _u32p, _U64, ctypes.c_int, _U64]
+        L.nsg_rand64_fill.argtypes = [_u64p, _U64, _U64, _U64]
         _lib = L
     return _lib
+
+
+def random_u64(n: int, seed: int, stream: int, out=None) -> np.ndarray:
+    """n random 64-bit keys (counter-based: key i = splitmix64(seed ^ stream << 40 ^ i))."""
+    out = np.empty(n, np.uint64) if out is None else out
+    if n:
+        lib().nsg_rand64_fill(out, n, seed, stream)
+    return out
 
 
 def splitmix64(x: int) -> int:

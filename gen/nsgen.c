@@ -45,6 +45,12 @@ uint64_t nsg_rand64(uint64_t seed, uint64_t stream, uint64_t i) {
     return nsg_splitmix64(seed ^ (stream << 40) ^ i);
 }
 
+/* out[i] = nsg_rand64(seed, stream, i): random 64-bit keys, e.g. the ones an
+ * anonymizing permutation is drawn from */
+void nsg_rand64_fill(uint64_t* out, uint64_t n, uint64_t seed, uint64_t stream) {
+    for (uint64_t i = 0; i < n; ++i) out[i] = nsg_rand64(seed, stream, i);
+}
+
 /* uniform double in [0, 1) with 53 random bits */
 static inline double u01(uint64_t r) { return (double)(r >> 11) * 0x1.0p-53; }
 

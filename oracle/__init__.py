@@ -63,6 +63,10 @@ def load(path: str | None = None):
     L.oracle_rows.argtypes = [_u64p, _u64p, _U64, _u32p, _u64p, _u64p, _P64]
     L.oracle_digest.argtypes = [_u64p, _u64p, _U64]
     L.oracle_digest.restype = _U64
+    L.oracle_cols.argtypes = [_u64p, _u64p, _U64, _u32p, _u64p, _u64p, _P64]
+    L.oracle_unique_addresses.argtypes = [_u64p, _U64, _u32p, _P64]
+    L.oracle_anonymize.argtypes = [_u32p, _u32p, _U64, _u64p, _U64, _u32p, _u32p, _P64]
+    L.oracle_anonymize.restype = ctypes.c_int
     return L
 
 
@@ -135,6 +139,52 @@ def rows(keys, counts, L=None):
                   ctypes.byref(ns))
     m = ns.value
     return s[:m].copy(), p[:m].copy(), f[:m].copy()
+
+
+def cols(keys, counts, L=None):
+    """Per-destination (dst, packets 1^T A, fan-in 1^T |A|_0), ascending by dst."""
+    L = L or lib()
+    keys = _c(keys, np.uint64)
+    counts = _c(counts, np.uint64)
+    n = max(keys.size, 1)
+    d = np.empty(n, np.uint32)
+    p = np.empty(n, np.uint64)
+    f = np.empty(n, np.uint64)
+    nd = ctypes.c_uint64(0)
+    L.oracle_cols(keys if keys.size else np.zeros(1, np.uint64),
+                  counts if counts.size else np.zeros(1, np.uint64), keys.size, d, p, f,
+                  ctypes.byref(nd))
+    m = nd.value
+    return d[:m].copy(), p[:m].copy(), f[:m].copy()
+
+
+def unique_addresses(keys, L=None) -> np.ndarray:
+    """Distinct addresses of src and dst together, ascending (|src u dst|)."""
+    L = L or lib()
+    keys = _c(keys, np.uint64)
+    out = np.empty(max(2 * keys.size, 1), np.uint32)
+    cnt = ctypes.c_uint64(0)
+    L.oracle_unique_addresses(keys if keys.size else np.zeros(1, np.uint64), keys.size, out,
+                              ctypes.byref(cnt))
+    return out[:cnt.value].copy()
+
+
+def anonymize(src, dst, rnd, L=None):
+    """(out_src, out_dst, n_unique): every address replaced by its label under
+    the random permutation that the random keys rnd define."""
+    L = L or lib()
+    src = _c(src, np.uint32)
+    dst = _c(dst, np.uint32)
+    rnd = _c(rnd, np.uint64)
+    n = src.size
+    os_ = np.empty(max(n, 1), np.uint32)
+    od = np.empty(max(n, 1), np.uint32)
+    nu = ctypes.c_uint64(0)
+    rc = L.oracle_anonymize(src if n else np.zeros(1, np.uint32), dst if n else np.zeros(1, np.uint32), n,
+                            rnd if rnd.size else np.zeros(1, np.uint64), rnd.size, os_, od, ctypes.byref(nu))
+    if rc != 0:
+        raise ValueError("fewer random keys than distinct addresses")
+    return os_[:n].copy(), od[:n].copy(), nu.value
 
 
 def digest(keys, counts, L=None) -> int:

@@ -189,4 +189,83 @@ uint64_t oracle_digest(const uint64_t* keys, const uint64_t* counts, uint64_t nn
     return h;
 }
 
+/* Columns (the reverse operation of oracle_rows, Table 2 caption): per
+ * destination j, ascending by j: packets 1^T A (j) and fan-in 1^T |A|_0 (j).
+ * The (dst, count) pairs of the nonzero list are std::sort-ed by dst, then
+ * equal destinations are summed in one scan.  Outputs hold nnz entries. */
+int oracle_cols(const uint64_t* keys, const uint64_t* counts, uint64_t nnz, uint32_t* dst_out,
+                uint64_t* packets_out, uint64_t* fanin_out, uint64_t* nd_out) {
+    std::vector<std::pair<uint32_t, uint64_t>> col(nnz);
+    for (uint64_t u = 0; u < nnz; ++u) col[u] = {(uint32_t)keys[u], counts[u]};
+    std::sort(col.begin(), col.end());
+    uint64_t u = 0, d_idx = 0;
+    while (u < nnz) {
+        const uint32_t d = col[u].first;
+        uint64_t packets = 0, fanin = 0;
+        while (u < nnz && col[u].first == d) {
+            packets += col[u].second;
+            fanin += 1;
+            ++u;
+        }
+        dst_out[d_idx] = d;
+        packets_out[d_idx] = packets;
+        fanin_out[d_idx] = fanin;
+        ++d_idx;
+    }
+    *nd_out = d_idx;
+    return 0;
+}
+
+/* Globally unique addresses (section "Graph Analytics"): the distinct values
+ * of the src and dst columns together -- each column's distinct values with
+ * the ones common to both counted once.  From A's nonzero list: every key
+ * contributes its source and its destination; std::sort, std::unique.
+ * out holds 2 * nnz entries; *n_out receives the count, out the addresses
+ * ascending. */
+int oracle_unique_addresses(const uint64_t* keys, uint64_t nnz, uint32_t* out, uint64_t* n_out) {
+    std::vector<uint32_t> a;
+    a.reserve(2 * nnz);
+    for (uint64_t u = 0; u < nnz; ++u) {
+        a.push_back((uint32_t)(keys[u] >> 32));
+        a.push_back((uint32_t)keys[u]);
+    }
+    std::sort(a.begin(), a.end());
+    a.erase(std::unique(a.begin(), a.end()), a.end());
+    std::copy(a.begin(), a.end(), out);
+    *n_out = a.size();
+    return 0;
+}
+
+/* Address anonymization (section "Implementation", paragraph "IP Address
+ * Anonymization"): the N distinct addresses of src and dst get the labels of
+ * a random permutation of 0..N-1, and every packet's addresses are replaced
+ * by their labels (a gather).
+ *   1. u = the distinct values of src and dst, ascending (std::sort, std::unique);
+ *   2. the permutation: u[i] is given label t when rnd[i] is the t-th
+ *      smallest of rnd[0..N) (ties by i) -- sorting independent random keys
+ *      yields a uniformly random permutation, as the shuffle of 0..N-1 does;
+ *      rnd is the caller's array of random 64-bit keys (at least N of them);
+ *   3. out[k] = label of src[k] (resp. dst[k]), found by binary search in u.
+ * Returns -1 (and writes nothing) if rnd_n < N. */
+int oracle_anonymize(const uint32_t* src, const uint32_t* dst, uint64_t n, const uint64_t* rnd,
+                     uint64_t rnd_n, uint32_t* out_src, uint32_t* out_dst, uint64_t* n_unique) {
+    std::vector<uint32_t> u(src, src + n);
+    u.insert(u.end(), dst, dst + n);
+    std::sort(u.begin(), u.end());
+    u.erase(std::unique(u.begin(), u.end()), u.end());
+    const uint64_t N = u.size();
+    *n_unique = N;
+    if (rnd_n < N) return -1;
+    std::vector<uint64_t> order(N);
+    for (uint64_t i = 0; i < N; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](uint64_t a, uint64_t b) { return rnd[a] < rnd[b]; });
+    std::vector<uint32_t> label(N);
+    for (uint64_t t = 0; t < N; ++t) label[order[t]] = (uint32_t)t;
+    for (uint64_t k = 0; k < n; ++k) {
+        out_src[k] = label[std::lower_bound(u.begin(), u.end(), src[k]) - u.begin()];
+        out_dst[k] = label[std::lower_bound(u.begin(), u.end(), dst[k]) - u.begin()];
+    }
+    return 0;
+}
+
 }  // extern "C"

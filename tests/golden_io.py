@@ -45,3 +45,28 @@ def read_worked_example(name: str = "worked_example.txt"):
     keys = np.array([k for k, _ in nz], np.uint64)
     counts = np.array([c for _, c in nz], np.uint64)
     return wins, (keys, counts), stats
+
+
+def read_anonymize_example(name: str = "anonymize_example.txt"):
+    """Returns (src, dst, rnd, out_src, out_dst) of the hand-worked
+    anonymization fixture."""
+    sec, cur = {}, None
+    with open(os.path.join(GOLDEN, name)) as f:
+        for raw in f:
+            line = raw.split("#", 1)[0].strip()
+            if not line:
+                continue
+            tok = line.split()
+            if tok[0] in ("packets", "random", "anonymized"):
+                cur = tok[0]
+                sec[cur] = []
+                continue
+            if tok[0] == "end":
+                cur = None
+                continue
+            sec[cur].append([int(x) for x in tok])
+    p = np.array(sec["packets"], dtype=np.uint64)
+    a = np.array(sec["anonymized"], dtype=np.uint64)
+    r = np.array([x[0] for x in sec["random"]], dtype=np.uint64)
+    return (p[:, 0].astype(np.uint32), p[:, 1].astype(np.uint32), r,
+            a[:, 0].astype(np.uint32), a[:, 1].astype(np.uint32))

@@ -13,6 +13,11 @@ The oracle is checked against things other than itself:
     fan-in <= S, concatenated windows = summed matrices, packet-order and
     address-relabelling invariance, src/dst exchange swaps the quantities,
     monotone running statistics),
+  * per-source / per-destination vectors and the distinct addresses against
+    the dense model's row and column sums and counts,
+  * address anonymization: a hand-worked fixture
+    (tests/golden/anonymize_example.txt), bijectivity, invariance of the nine
+    quantities, and the order-preserving special case,
   * planted mistakes: variants of the oracle source with a dropped term, a
     transposed operand or a wrong index must each fail one of the pins.
 """
@@ -28,7 +33,7 @@ import pytest
 import gen
 import gen.workloads as W
 import oracle
-from golden_io import read_worked_example
+from golden_io import read_anonymize_example, read_worked_example
 
 F = oracle.FIELDS
 
@@ -127,12 +132,65 @@ def check_swap(L, seed):
         (b["unique_sources"], b["max_src_packets"], b["max_src_fanout"])
 
 
+def check_vectors_bruteforce(L, n, seed):
+    """Per-source and per-destination vectors and the distinct addresses,
+    against the dense matrix: row sums and row nonzero counts (A 1,
+    |A|_0 1), column sums and counts (1^T A, 1^T |A|_0), and the union of
+    live rows and live columns."""
+    s8, d8 = skewed_pairs(n, seed)
+    M = dense_matrix(s8, d8)
+    k, c = oracle.build_matrix(widen8(s8), widen8(d8), L)
+    live_r = np.nonzero(M.sum(axis=1))[0]
+    live_c = np.nonzero(M.sum(axis=0))[0]
+    src, pk, fo = oracle.rows(k, c, L)
+    np.testing.assert_array_equal(src, widen8(live_r.astype(np.uint32)))
+    np.testing.assert_array_equal(pk, M.sum(axis=1)[live_r])
+    np.testing.assert_array_equal(fo, (M > 0).sum(axis=1)[live_r].astype(np.uint64))
+    dst, cp, fi = oracle.cols(k, c, L)
+    np.testing.assert_array_equal(dst, widen8(live_c.astype(np.uint32)))
+    np.testing.assert_array_equal(cp, M.sum(axis=0)[live_c])
+    np.testing.assert_array_equal(fi, (M > 0).sum(axis=0)[live_c].astype(np.uint64))
+    both = np.union1d(live_r, live_c).astype(np.uint32)
+    np.testing.assert_array_equal(oracle.unique_addresses(k, L), widen8(both))
+
+
+def check_anonymize(L, seed):
+    """The hand-worked fixture; then, on a skewed stream: the labels are a
+    bijection of the distinct addresses onto 0..N-1, equal addresses get
+    equal labels, the nine quantities are unchanged, and increasing keys
+    give the order-preserving relabelling (labels = ranks)."""
+    s, d, r, want_s, want_d = read_anonymize_example()
+    got_s, got_d, nu = oracle.anonymize(s, d, r, L)
+    np.testing.assert_array_equal(got_s, want_s)
+    np.testing.assert_array_equal(got_d, want_d)
+    assert nu == 4
+    s8, d8 = skewed_pairs(20000, seed)
+    src, dst = widen8(s8), widen8(d8)
+    u = np.union1d(src, dst)
+    rnd = gen.random_u64(u.size + 5, seed, 3)
+    a_s, a_d, nu = oracle.anonymize(src, dst, rnd, L)
+    assert nu == u.size
+    lab = np.full(u.size, -1, np.int64)
+    for addr, out in ((src, a_s), (dst, a_d)):
+        idx = np.searchsorted(u, addr)
+        assert np.all((lab[idx] == -1) | (lab[idx] == out))  # one label per address
+        lab[idx] = out
+    assert np.array_equal(np.sort(lab), np.arange(u.size))  # a permutation of 0..N-1
+    assert tup(oracle.stats_of_packets(a_s, a_d, L)) == tup(oracle.stats_of_packets(src, dst, L))
+    ranks_s, ranks_d, _ = oracle.anonymize(src, dst, np.arange(u.size, dtype=np.uint64), L)
+    np.testing.assert_array_equal(ranks_s, np.searchsorted(u, src).astype(np.uint32))
+    np.testing.assert_array_equal(ranks_d, np.searchsorted(u, dst).astype(np.uint32))
+
+
 def all_pins(L):
     check_golden(L)
     for n, seed in ((1, 1), (2, 2), (255, 3), (4099, 4), (40000, 5)):
         check_bruteforce(L, n, seed)
     check_windows_bruteforce(L, (700, 0, 1, 3000), 11)
     check_swap(L, 21)
+    for n, seed in ((1, 31), (3000, 32), (30000, 33)):
+        check_vectors_bruteforce(L, n, seed)
+    check_anonymize(L, 41)
 
 
 def test_golden_worked_example():
@@ -309,6 +367,14 @@ MUTANTS = {
                           "if (fanin > stats[MAX_DST_FANIN]) stats[MAX_DST_FANIN] = packets;"),
     # unique sources counted per entry rather than per run
     "sources_per_entry": ("stats[UNIQUE_SOURCES] += 1;", "stats[UNIQUE_SOURCES] += fanout;"),
+    # column fan-in summing packets instead of entries
+    "cols_fanin_sums_packets": ("fanin += 1;\n            ++u;", "fanin += col[u].second;\n            ++u;"),
+    # distinct addresses taken from the source half only
+    "unique_addresses_src_only": ("a.push_back((uint32_t)keys[u]);", "a.push_back((uint32_t)(keys[u] >> 32));"),
+    # the inverse permutation applied instead of the permutation
+    "anonymize_inverse_permutation": ("label[order[t]] = (uint32_t)t;", "label[t] = (uint32_t)order[t];"),
+    # random keys indexed from the end of the array
+    "anonymize_wrong_random_index": ("return rnd[a] < rnd[b];", "return rnd[rnd_n - 1 - a] < rnd[rnd_n - 1 - b];"),
 }
 
 
