@@ -58,15 +58,16 @@ def parse():
                     help="seconds of oracle work for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="stream", choices=["stream", "oneshot", "batched", "serve"],
+    ap.add_argument("--workload", default="stream", choices=["stream", "oneshot", "batched", "serve", "anonymize"],
                     help="stream: 512 windows of 2^17 with stats after each (default); "
                          "oneshot: one 2^30-packet build, sort path vs hash path; "
                          "batched: 8192 uneven windows, batched launch vs plain per-window launches; "
-                         "serve: Poisson arrivals at 80%% of capacity, p50/p99 window-to-stats latency")
+                         "serve: Poisson arrivals at 80%% of capacity, p50/p99 window-to-stats latency; "
+                         "anonymize: distinct addresses, random permutation and gather over the one-shot input")
     ap.add_argument("--serve-windows", type=int, default=448, help="serve: windows per phase")
     ap.add_argument("--batch-windows", type=int, default=8192, help="batched: number of windows")
     ap.add_argument("--tuner-cache", default=None, help="batched: autotuner cache file (default: none, tune now)")
-    ap.add_argument("--packets", type=int, default=1 << 30, help="oneshot: packets in the build")
+    ap.add_argument("--packets", type=int, default=1 << 30, help="oneshot / anonymize: packets in the input")
     ap.add_argument("--paths", default="sort,hash", help="oneshot: aggregation paths to run")
     ap.add_argument("--hash-load", type=float, default=0.25,
                     help="stream: load bound of the accumulated matrix's hash tables (sizes them for 2^26 links)")
@@ -550,6 +551,69 @@ def run_oneshot(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_anonymize(args, rank, world, local):
+    """Address anonymization (the paper's "IP Address Anonymization" step) of
+    N packets (default 2^30, the one-shot build's Zipf(1.2) input): distinct
+    addresses of both columns, a random permutation drawn from counter-based
+    random keys, and the gather that relabels every packet."""
+    import torch
+    import gen
+    import gen.workloads as W
+    import paper_2509_03653_b300 as ns
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    N = args.packets
+    h_src = torch.empty(N, dtype=torch.int32).pin_memory()
+    h_dst = torch.empty(N, dtype=torch.int32).pin_memory()
+    tg = time.time()
+    W.large_build(N, src=h_src.numpy().view(np.uint32), dst=h_dst.numpy().view(np.uint32))
+    h_rand = torch.empty(2 * N, dtype=torch.int64).pin_memory()
+    gen.random_u64(2 * N, W.seed_of(3), 9, out=h_rand.numpy().view(np.uint64))
+    gen_s = time.time() - tg
+    d_src, d_dst, d_rand = h_src.to(dev), h_dst.to(dev), h_rand.to(dev)
+    o_src = torch.empty_like(d_src)
+    o_dst = torch.empty_like(d_dst)
+    ctx = ns.Context(local)
+    for _ in range(max(args.warmup, 3)):
+        _, _, nu = ns.anonymize(ctx, d_src, d_dst, d_rand, o_src, o_dst)
+    ns.trace_enable(ctx, True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ns.anonymize(ctx, d_src, d_dst, d_rand, o_src, o_dst)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    tr = ns.trace_read(ctx)
+    ns.trace_enable(ctx, False)
+    peak, peak_src = peak_hbm()
+    # minimal bytes: both columns copied end to end (8N read + 8N written),
+    # the 2N keys' histogram (8N) and four 8-bit digit passes (4 x 16N), the
+    # run pass (8N + 16 nu), the permutation's sort of nu (key, position)
+    # pairs (8 digit passes x 32 nu), and the gather (8N read + 8N written)
+    path_bytes = 16 * N + 8 * N + 64 * N + 8 * N + 16 * nu + 256 * nu + 16 * N
+    kname = "k_onesweep<u32 key>"
+    kl, ktot, _ = tr.get(kname, (0, 0.0, 0.0))
+    kavg = ktot / kl if kl else float("nan")
+    line = {
+        "metric": "packets/s anonymized (distinct addresses, random permutation, gather)", "value": N / (ms / 1e3),
+        "unit": "packets/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"address anonymization of {N} packets, src/dst Zipf(1.2) over 2^24 addresses "
+                               "under a seeded bijection; counter-based random keys",
+                   "distinct_addresses": nu, "l2": "inputs larger than L2", "generator_s": round(gen_s, 1)},
+        "roofline": {"bound": "hbm", "achieved": path_bytes / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": path_bytes / (ms / 1e3) / 1e9 / peak, "traffic": None,
+                     "kernel": "whole step (minimal bytes of its passes)", "peak_source": peak_src,
+                     "digit_pass_frac": (16 * N / (kavg / 1e3) / 1e9 / peak) if kl else None},
+        "kernels_ms": {k: round(v[1] / args.steps, 4) for k, v in sorted(tr.items(), key=lambda kv: -kv[1][1])},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_batched(args, rank, world, local):
     """Workload 4: 8192 windows, sizes log-uniform in [2^10, 2^20], per-window
     Zipf exponent in [0.8, 1.4] over 2^20 addresses.  Per-window quantities
@@ -783,6 +847,10 @@ def main():
     if args.workload == "serve":
         if rank == 0:
             run_serve(args, rank, world, local)
+        return
+    if args.workload == "anonymize":
+        if rank == 0:
+            run_anonymize(args, rank, world, local)
         return
     run_ours(args, rank, world, local)
 

@@ -161,6 +161,40 @@ ns_status ns_matrix_nnz(const ns_matrix* m, uint64_t* h_nnz, ns_stream_t stream)
 ns_status ns_matrix_export(const ns_matrix* m, uint64_t* d_keys, uint64_t* d_counts,
                            uint64_t cap, uint64_t* h_nnz, ns_stream_t stream);
 
+/* Which vectors ns_matrix_nodes exports. */
+enum {
+    NS_NODES_SRC = 0, /* per source i: id, A 1 (i), |A|_0 1 (i)      (Table 2 rows 6, 8) */
+    NS_NODES_DST = 1, /* per destination j: id, 1^T A (j), 1^T |A|_0 (j) (their reverses) */
+    NS_NODES_ANY = 2  /* the distinct addresses of src and dst together: ids only */
+};
+
+/* Per-entity vectors of A, ascending by address, into device arrays of `cap`
+ * entries: d_ids (uint32), d_packets and d_degree (uint64; each may be NULL,
+ * and both are ignored for NS_NODES_ANY).  NS_NODES_ANY gives the globally
+ * unique addresses of section "Graph Analytics" (each column's distinct
+ * values, the ones common to both counted once).  *h_count receives the
+ * number of entries (S, D or |src u dst|); if it exceeds cap, the first cap
+ * are written and NS_ERR_CAPACITY is returned.  Allocates scratch for the
+ * call; blocking. */
+ns_status ns_matrix_nodes(ns_ctx* ctx, const ns_matrix* m, int which, uint32_t* d_ids, uint64_t* d_packets,
+                          uint64_t* d_degree, uint64_t cap, uint64_t* h_count, ns_stream_t stream);
+
+/* Address anonymization (section "Implementation", paragraph "IP Address
+ * Anonymization"): the N distinct addresses of d_src[0..n) and d_dst[0..n)
+ * are relabelled by a random permutation of 0..N-1 and every packet's
+ * addresses replaced by their labels: d_out_src[k] = label(d_src[k]),
+ * d_out_dst[k] = label(d_dst[k]).  The permutation is the one the caller's
+ * random keys define -- the address at position i of the ascending distinct
+ * list, whose key is d_rand[i], gets label t when d_rand[i] is the t-th
+ * smallest of d_rand[0..N) (ties by position) -- so the random draws are an
+ * input, and any source of independent keys yields a uniformly random
+ * permutation.  rand_count must be at least N (at most 2n); otherwise
+ * NS_ERR_CAPACITY, with *h_unique = N and nothing written.  The outputs may
+ * be the inputs.  Allocates scratch; blocking. */
+ns_status ns_anonymize(ns_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
+                       const uint64_t* d_rand, uint64_t rand_count, uint32_t* d_out_src, uint32_t* d_out_dst,
+                       uint64_t* h_unique, ns_stream_t stream);
+
 /* ---- the hot path (paper, Table 2) -------------------------------------- */
 
 /* out := A_t, the traffic matrix of one window of n packets given as two

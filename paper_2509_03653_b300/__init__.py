@@ -21,7 +21,7 @@ from ._native import (FIELDS, NsBatchParams, NsConfig, NsError, NsStats, NsStrea
 __all__ = [
     "FIELDS", "NsError", "Context", "Matrix", "window_build", "accumulate", "window_ingest",
     "window_ingest_stats", "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
-    "matrix_clear", "sync", "PATHS", "path_tune", "path_resolve", "window_stats_static", "STATIC_MAX_PACKETS",
+    "matrix_clear", "sync", "PATHS", "path_tune", "path_resolve", "matrix_nodes", "NODES", "anonymize", "window_stats_static", "STATIC_MAX_PACKETS",
     "trace_enable", "trace_read", "Batch", "batch_run", "batch_tune", "matrix_reserve_ex",
     "Server", "stream_submit", "stream_poll", "stream_wait", "diag_random_atomics",
 ]
@@ -194,6 +194,50 @@ def matrix_export(m: Matrix, stream=None, device=None):
     check(m._L.ns_matrix_export(m.handle, ctypes.c_void_p(keys.data_ptr()), ctypes.c_void_p(counts.data_ptr()),
                                 max(nnz, 1), ctypes.byref(got), _stream(stream)), "ns_matrix_export")
     return keys[: got.value], counts[: got.value]
+
+
+NODES = {"src": 0, "dst": 1, "any": 2}
+
+
+def matrix_nodes(m: Matrix, which: str = "src", stream=None):
+    """Per-entity vectors of A, ascending by address (ns_matrix_nodes):
+    which="src" -> (ids, A 1, |A|_0 1); "dst" -> (ids, 1^T A, 1^T |A|_0);
+    "any" -> the distinct addresses of src and dst together.  Device
+    tensors: ids int32 holding uint32 bit patterns, the others int64."""
+    nnz = matrix_nnz(m, stream)
+    dev = torch.device("cuda", m.ctx.device)
+    cap = max(2 * nnz, 1)
+    ids = torch.empty(cap, dtype=torch.int32, device=dev)
+    pk = torch.empty(cap, dtype=torch.int64, device=dev)
+    dg = torch.empty(cap, dtype=torch.int64, device=dev)
+    got = ctypes.c_uint64()
+    check(m._L.ns_matrix_nodes(m.ctx.handle, m.handle, NODES[which], ctypes.c_void_p(ids.data_ptr()),
+                               ctypes.c_void_p(pk.data_ptr()), ctypes.c_void_p(dg.data_ptr()), cap,
+                               ctypes.byref(got), _stream(stream)), "ns_matrix_nodes")
+    k = got.value
+    if which == "any":
+        return ids[:k]
+    return ids[:k], pk[:k], dg[:k]
+
+
+def anonymize(ctx: Context, src: torch.Tensor, dst: torch.Tensor, rand: torch.Tensor,
+              out_src: torch.Tensor | None = None, out_dst: torch.Tensor | None = None, stream=None):
+    """Relabels the addresses of both columns by the random permutation the
+    int64 (uint64 bit patterns) device tensor `rand` defines (ns_anonymize).
+    Returns (out_src, out_dst, number of distinct addresses)."""
+    n = src.numel()
+    if dst.numel() != n:
+        raise ValueError("src and dst differ in length")
+    if rand.dtype != torch.int64 or not rand.is_contiguous():
+        raise ValueError("rand must be a contiguous int64 tensor")
+    out_src = torch.empty_like(src) if out_src is None else out_src
+    out_dst = torch.empty_like(dst) if out_dst is None else out_dst
+    nu = ctypes.c_uint64()
+    check(ctx._L.ns_anonymize(ctx.handle, _column(src, "src"), _column(dst, "dst"), n,
+                              ctypes.c_void_p(rand.data_ptr() if rand.numel() else None), rand.numel(),
+                              _column(out_src, "out_src"), _column(out_dst, "out_dst"), ctypes.byref(nu),
+                              _stream(stream)), "ns_anonymize")
+    return out_src, out_dst, nu.value
 
 
 def matrix_reserve(m: Matrix, max_links: int, stream=None):

@@ -57,6 +57,8 @@ SIGNATURES = {
     "ns_path_tune": (ST, [P, P, P, U64, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                           ctypes.POINTER(ctypes.c_float)]),
     "ns_path_resolve": (ST, [P, U64, ctypes.POINTER(ctypes.c_int)]),
+    "ns_matrix_nodes": (ST, [P, P, ctypes.c_int, P, P, P, U64, ctypes.POINTER(U64), P]),
+    "ns_anonymize": (ST, [P, P, P, U64, P, U64, P, P, ctypes.POINTER(U64), P]),
     "ns_accumulate": (ST, [P, P, P, P]),
     "ns_window_ingest": (ST, [P, P, P, P, U64, P]),
     "ns_window_ingest_stats": (ST, [P, P, P, P, U64, P, P]),

@@ -26,6 +26,8 @@ HashView hash_view(const ns_matrix* m);
 void buf_free(Buf& b);
 ns_status check_launch();
 ns_status set_fail(ns_status s, const char* msg);
+// Sizes the context's look-back status words for sorts of up to n elements.
+ns_status sort_scratch(ns_ctx* c, u64 n);
 // Hash path: out := A_t.  cache: -1 = the context's rule, 0 = off, 1 = on.
 ns_status build_hash(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n, ns_matrix* out,
                      cudaStream_t s, int cache = -1);

@@ -128,6 +128,12 @@ int radix_sort_pairs64(const u64* keys, const u64* vals, const u64* n_dev,
 // passes, stable); returns the index of the buffer holding the result.
 int radix_sort_hi32(const u64* packed, const u64* n_dev, u64* kbuf[2], u64 n, SortScratch& sc, DevStats* st,
                     cudaStream_t s);
+// n_dev (<= n) uint32 keys (four 8-bit digit passes, stable).
+int radix_sort_u32(const u32* keys, const u64* n_dev, u32* kbuf[2], u64 n, SortScratch& sc, DevStats* st,
+                   cudaStream_t s);
+// The same by their lower 32 bits (words holding one uint32 each).
+int radix_sort_lo32(const u64* keys, const u64* n_dev, u64* kbuf[2], u64 n, SortScratch& sc, DevStats* st,
+                    cudaStream_t s);
 int radix_sort_dst_pairs(const u64* link_keys, const u64* counts, const u64* n_dev,
                          u32* kbuf[2], u64* vbuf[2], u64 n, SortScratch& sc,
                          DevStats* st, cudaStream_t s);

@@ -783,7 +783,8 @@ __global__ void __launch_bounds__(256) k_run_stats(const u64* __restrict__ pos,
 
 template <typename K, bool HAS_V>
 constexpr const char* onesweep_name() {
-    if constexpr (sizeof(K) == 4) return "k_onesweep<u32 key, u64 value>";
+    if constexpr (sizeof(K) == 4 && HAS_V) return "k_onesweep<u32 key, u64 value>";
+    else if constexpr (sizeof(K) == 4) return "k_onesweep<u32 key>";
     else if constexpr (HAS_V) return "k_onesweep<u64 key, u64 value>";
     else return "k_onesweep<u64 key>";
 }
@@ -815,13 +816,13 @@ void launch_onesweep_nt(const SortIn& in, K* kout, u64* vout, u64 n, int shift, 
                                                              tag, st, (u32)NS_ONESWEEP_PF * resident);
 }
 
-// 64-bit keys without values use 8192-key tiles (512 threads): half the
-// look-back hops and per-tile fixed work per key; pairs keep 4096-key tiles
-// (their shared memory would not fit twice).
+// Keys without values use 8192-key tiles (512 threads): half the look-back
+// hops and per-tile fixed work per key; pairs keep 4096-key tiles (their
+// shared memory would not fit twice).
 template <typename K, bool HAS_V, int LOAD>
 void launch_onesweep(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
                      u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s) {
-    if constexpr (sizeof(K) == 8 && !HAS_V)
+    if constexpr (!HAS_V)
         launch_onesweep_nt<K, HAS_V, LOAD, NS_ONESWEEP_NT, NS_ONESWEEP_ITEMS>(in, kout, vout, n, shift, offs, status,
                                                                               tile_counter, tag, st, tr, s);
     else
@@ -962,6 +963,28 @@ int radix_sort_dst_pairs(const u64* link_keys, const u64* counts, const u64* n_d
     return radix_sort_t<u32, true, LOAD_DST_OF>(in, (u32**)kbuf, (u64**)vbuf, n, 0, 4, sc, st, s);
 }
 
+int radix_sort_u32(const u32* keys, const u64* n_dev, u32* kbuf[2], u64 n, SortScratch& sc, DevStats* st,
+                   cudaStream_t s) {
+    SortIn in{};
+    in.keys = keys;
+    in.n_dev = (const u64*)n_dev;
+    in.bulk = ((uintptr_t)keys & 15) == 0;
+    in.trace_name = "k_onesweep<u32 key>";
+    u64* vb[2] = {nullptr, nullptr};
+    return radix_sort_t<u32, false, LOAD_KEYS>(in, (u32**)kbuf, vb, n, 0, 4, sc, st, s);
+}
+
+int radix_sort_lo32(const u64* keys, const u64* n_dev, u64* kbuf[2], u64 n, SortScratch& sc, DevStats* st,
+                    cudaStream_t s) {
+    SortIn in{};
+    in.keys = keys;
+    in.n_dev = (const u64*)n_dev;
+    in.bulk = ((uintptr_t)keys & 15) == 0;
+    in.trace_name = "k_onesweep<u64 key, low half>";
+    u64* vb[2] = {nullptr, nullptr};
+    return radix_sort_t<u64, false, LOAD_KEYS>(in, (u64**)kbuf, vb, n, 0, 4, sc, st, s);
+}
+
 int radix_sort_hi32(const u64* packed, const u64* n_dev, u64* kbuf[2], u64 n, SortScratch& sc, DevStats* st,
                     cudaStream_t s) {
     SortIn in{};
@@ -991,6 +1014,9 @@ void launch_runs(int keymode, bool has_v, const void* keys, const u64* vals, u64
     else if (keymode == RUN_U32 && has_v)
         launch_runs_t<RUN_U32, true>(keys, (const u64*)vals, n, nd, (u64*)head_keys, (u64*)pos,
                                      (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, sc.tr, s, nullptr);
+    else if (keymode == RUN_U32 && !has_v)
+        launch_runs_t<RUN_U32, false>(keys, nullptr, n, nd, (u64*)head_keys, (u64*)pos, nullptr, sc_c, sc_s, tc, tag,
+                                      (u64*)R_out, st, sc.tr, s, nullptr);
     else if (keymode == RUN_HI_OF_PACKED && has_v)
         launch_runs_t<RUN_HI_OF_PACKED, true>(keys, nullptr, n, nd, (u64*)head_keys, (u64*)pos,
                                               (u64*)psum, sc_c, sc_s, tc, tag, (u64*)R_out, st, sc.tr, s, nullptr);

@@ -180,3 +180,37 @@ def test_serving_448_windows():
     for w in (0, 7, 200, Wn - 1):
         s, d = wins[w]
         assert results[w][0] == oracle.stats_of_packets(s.numpy().view(np.uint32), d.numpy().view(np.uint32))
+
+
+def test_anonymize_2p30():
+    """Anonymization of the one-shot build's 2^30 packets, as bench.py times
+    it.  The distinct-address count equals numpy's; sampled packets carry the
+    label their address's random key ranks to (computed one by one from the
+    definition); labels are a bijection; the nine quantities are unchanged."""
+    import gen
+    N = W.W3_N
+    hs, hd, s, d = pinned_pair(N)
+    W.large_build(N, src=s, dst=d)
+    rnd = torch.empty(2 * N, dtype=torch.int64).pin_memory()
+    gen.random_u64(2 * N, W.seed_of(3), 9, out=rnd.numpy().view(np.uint64))
+    ds, dd, dr = hs.cuda(), hd.cuda(), rnd.cuda()
+    ctx = ns.Context(0)
+    os_, od, nu = ns.anonymize(ctx, ds, dd, dr)
+    u = np.union1d(np.unique(s), np.unique(d))
+    assert nu == u.size
+    r = rnd.numpy().view(np.uint64)[:nu]
+    rank = np.empty(nu, np.int64)
+    rank[np.argsort(r, kind="stable")] = np.arange(nu)
+    rng = np.random.default_rng(5)
+    pick = rng.integers(0, N, 4096)
+    got_s = os_[torch.from_numpy(pick).cuda()].cpu().numpy().view(np.uint32)
+    got_d = od[torch.from_numpy(pick).cuda()].cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(got_s, rank[np.searchsorted(u, s[pick])].astype(np.uint32))
+    np.testing.assert_array_equal(got_d, rank[np.searchsorted(u, d[pick])].astype(np.uint32))
+    # labels stay below nu, and the relabelled build has the same quantities
+    assert int(os_.view(torch.int32).max().item()) < nu or nu > 2**31
+    ctx_s = ns.Context(0, path="sort")
+    a, b = ns.Matrix(ctx_s), ns.Matrix(ctx_s)
+    ns.window_build(ctx_s, ds, dd, a)
+    ns.window_build(ctx_s, os_, od, b)
+    assert ns.network_stats(ctx_s, a) == ns.network_stats(ctx_s, b)
