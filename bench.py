@@ -58,17 +58,19 @@ def parse():
                     help="seconds of oracle work for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="stream", choices=["stream", "oneshot", "batched", "serve", "anonymize"],
+    ap.add_argument("--workload", default="stream", choices=["stream", "oneshot", "batched", "serve", "anonymize", "slide"],
                     help="stream: 512 windows of 2^17 with stats after each (default); "
                          "oneshot: one 2^30-packet build, sort path vs hash path; "
                          "batched: 8192 uneven windows, batched launch vs plain per-window launches; "
                          "serve: Poisson arrivals at 80%% of capacity, p50/p99 window-to-stats latency; "
-                         "anonymize: distinct addresses, random permutation and gather over the one-shot input")
+                         "anonymize: distinct addresses, random permutation and gather over the one-shot input; "
+                         "slide: the stream's windows with per-window and sliding-window quantities")
     ap.add_argument("--serve-windows", type=int, default=448, help="serve: windows per phase")
     ap.add_argument("--batch-windows", type=int, default=8192, help="batched: number of windows")
     ap.add_argument("--tuner-cache", default=None, help="batched: autotuner cache file (default: none, tune now)")
     ap.add_argument("--packets", type=int, default=1 << 30, help="oneshot / anonymize: packets in the input")
     ap.add_argument("--paths", default="sort,hash", help="oneshot: aggregation paths to run")
+    ap.add_argument("--slide-windows", type=int, default=8, help="slide: windows in the sliding sum (K)")
     ap.add_argument("--hash-load", type=float, default=0.25,
                     help="stream: load bound of the accumulated matrix's hash tables (sizes them for 2^26 links)")
     ap.add_argument("--windows", type=int, default=WINDOWS,
@@ -614,6 +616,63 @@ def run_anonymize(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_slide(args, rank, world, local):
+    """The stream workload's windows (512 x 2^17 RMAT packets) through a
+    slider over the last K windows: every window's own quantities and those
+    of the sum of the last K windows, after each window."""
+    import torch
+    import gen.workloads as W
+    import paper_2509_03653_b300 as ns
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    NW, K = args.windows, args.slide_windows
+    N = NW * WINDOW
+    h_src = torch.empty(N, dtype=torch.int32).pin_memory()
+    h_dst = torch.empty(N, dtype=torch.int32).pin_memory()
+    W.rmat_stream(N, src=h_src.numpy().view(np.uint32), dst=h_dst.numpy().view(np.uint32))
+    d_src, d_dst = h_src.to(dev), h_dst.to(dev)
+    ctx = ns.Context(local, path="hash")
+    out_w = torch.zeros(NW, 16, dtype=torch.int64, device=dev)
+    out_s = torch.zeros(NW, 16, dtype=torch.int64, device=dev)
+
+    def step(sl):
+        for w in range(NW):
+            a = w * WINDOW
+            ns.slider_push(ctx, sl, d_src[a:a + WINDOW], d_dst[a:a + WINDOW], out_w[w], out_s[w])
+
+    sl = ns.Slider(ctx, K)
+    for _ in range(max(args.warmup, 3)):
+        step(sl)  # also grows the sliding sum's tables to their final size
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step(sl)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    ns.trace_enable(ctx, True)  # one more step, traced, for the kernel breakdown
+    step(sl)
+    torch.cuda.synchronize()
+    tr = ns.trace_read(ctx)
+    ns.trace_enable(ctx, False)
+    line = {
+        "metric": "packets/s with per-window and sliding-window (last K windows) statistics after every window",
+        "value": N / (ms / 1e3), "unit": "packets/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": f"sliding windows: {NW} windows of 2^17 RMAT packets (the stream workload), "
+                               f"quantities of each window and of the sum of the last {K}",
+                   "windows": NW, "slide_windows": K, "l2": "inputs larger than L2"},
+        "ms_per_window": ms / NW,
+        "kernels_ms_traced_step": {k: round(v[1], 4) for k, v in sorted(tr.items(), key=lambda kv: -kv[1][1])},
+        "launches_per_step": sum(v[0] for v in tr.values()),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_batched(args, rank, world, local):
     """Workload 4: 8192 windows, sizes log-uniform in [2^10, 2^20], per-window
     Zipf exponent in [0.8, 1.4] over 2^20 addresses.  Per-window quantities
@@ -851,6 +910,10 @@ def main():
     if args.workload == "anonymize":
         if rank == 0:
             run_anonymize(args, rank, world, local)
+        return
+    if args.workload == "slide":
+        if rank == 0:
+            run_slide(args, rank, world, local)
         return
     run_ours(args, rank, world, local)
 

@@ -195,6 +195,32 @@ ns_status ns_anonymize(ns_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst
                        const uint64_t* d_rand, uint64_t rand_count, uint32_t* d_out_src, uint32_t* d_out_dst,
                        uint64_t* h_unique, ns_stream_t stream);
 
+/* ---- per-window and sliding-window statistics ---------------------------- */
+
+typedef struct ns_slider ns_slider;
+
+/* A slider over the last `windows` (K >= 1) windows: it keeps their matrices
+ * A_t (the time-indexed matrices of the Table 2 caption).  Owned by the
+ * caller; released with ns_slider_free. */
+ns_status ns_slider_create(ns_ctx* ctx, uint32_t windows, ns_slider** out);
+void ns_slider_free(ns_slider* slider);
+
+/* Builds A_t of the next window (as ns_window_build), writes its nine
+ * quantities to d_window and those of the sliding sum A_{t-K+1} + ... + A_t
+ * (of all windows pushed so far while fewer than K) to d_sliding; each may be
+ * NULL.  The sliding sum is re-formed from the K window matrices on every
+ * push, so every quantity is exact.  Asynchronous, except when the sliding
+ * sum's tables must grow.  Not from the paper: its analyses use one static
+ * matrix; the per-window and sliding forms follow from A_t being
+ * time-indexed. */
+ns_status ns_slider_push(ns_ctx* ctx, ns_slider* slider, const uint32_t* d_src, const uint32_t* d_dst,
+                         uint64_t n, ns_stats* d_window, ns_stats* d_sliding, ns_stream_t stream);
+
+/* The slider's current sliding-sum matrix (owned by the slider; valid until
+ * the next push or ns_slider_free), e.g. for ns_matrix_export or
+ * ns_matrix_nodes. */
+ns_status ns_slider_matrix(const ns_slider* slider, const ns_matrix** out);
+
 /* ---- the hot path (paper, Table 2) -------------------------------------- */
 
 /* out := A_t, the traffic matrix of one window of n packets given as two

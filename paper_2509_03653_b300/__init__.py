@@ -21,7 +21,8 @@ from ._native import (FIELDS, NsBatchParams, NsConfig, NsError, NsStats, NsStrea
 __all__ = [
     "FIELDS", "NsError", "Context", "Matrix", "window_build", "accumulate", "window_ingest",
     "window_ingest_stats", "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
-    "matrix_clear", "sync", "PATHS", "path_tune", "path_resolve", "matrix_nodes", "NODES", "anonymize", "window_stats_static", "STATIC_MAX_PACKETS",
+    "matrix_clear", "sync", "PATHS", "path_tune", "path_resolve", "matrix_nodes", "NODES", "anonymize", "Slider",
+    "slider_push", "window_stats_static", "STATIC_MAX_PACKETS",
     "trace_enable", "trace_read", "Batch", "batch_run", "batch_tune", "matrix_reserve_ex",
     "Server", "stream_submit", "stream_poll", "stream_wait", "diag_random_atomics",
 ]
@@ -288,6 +289,62 @@ def matrix_reserve_ex(m: Matrix, max_links: int, max_nodes: int, stream=None):
     """Reserve with a promise on the number of sources/destinations
     (ns_matrix_reserve_ex)."""
     check(m._L.ns_matrix_reserve_ex(m.handle, max_links, max_nodes, _stream(stream)), "ns_matrix_reserve_ex")
+
+
+class _BorrowedMatrix(Matrix):
+    """A matrix owned by another library object (not freed from Python)."""
+
+    def __init__(self, ctx: Context, handle):
+        self._L = ctx._L
+        self.ctx = ctx
+        self.handle = handle
+
+    def free(self):
+        self.handle = None
+
+
+class Slider:
+    """Per-window and sliding-window statistics over the last `windows`
+    windows (ns_slider_create / ns_slider_free)."""
+
+    def __init__(self, ctx: Context, windows: int):
+        self._L = ctx._L
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        check(self._L.ns_slider_create(ctx.handle, windows, ctypes.byref(h)), "ns_slider_create")
+        self.handle = h
+
+    def matrix(self) -> Matrix:
+        """The current sliding sum (valid until the next push)."""
+        h = ctypes.c_void_p()
+        check(self._L.ns_slider_matrix(self.handle, ctypes.byref(h)), "ns_slider_matrix")
+        return _BorrowedMatrix(self.ctx, h)
+
+    def free(self):
+        if getattr(self, "handle", None):
+            self._L.ns_slider_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def slider_push(ctx: Context, slider: Slider, src: torch.Tensor, dst: torch.Tensor,
+                out_window: torch.Tensor | None = None, out_sliding: torch.Tensor | None = None, stream=None):
+    """Builds the next window and writes its quantities and the sliding sum's
+    into int64 device tensors of at least 9 entries (ns_slider_push)."""
+    n = src.numel()
+    if dst.numel() != n:
+        raise ValueError("src and dst differ in length")
+    for t in (out_window, out_sliding):
+        if t is not None and (t.dtype != torch.int64 or t.numel() < 9 or not t.is_cuda):
+            raise ValueError("statistics outputs must be int64 CUDA tensors of >= 9 entries")
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+    check(ctx._L.ns_slider_push(ctx.handle, slider.handle, _column(src, "src"), _column(dst, "dst"), n,
+                                ptr(out_window), ptr(out_sliding), _stream(stream)), "ns_slider_push")
 
 
 class Batch:
