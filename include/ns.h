@@ -85,7 +85,9 @@ enum {
 };
 
 /* Per-CTA shared-memory staging of hot links, sources and destinations in
- * the hash path (see ns_config.cta_cache). */
+ * the hash path (see ns_config.cta_cache).  For ns_accumulate, AUTO and ON
+ * stage, OFF does not (staging pays when sources and destinations repeat,
+ * e.g. under Zipf skew, and costs time on nearly distinct RMAT windows). */
 enum {
     NS_CACHE_AUTO = 0, /* ns_path_tune's choice for the size, else on from 2^22 packets */
     NS_CACHE_ON = 1,

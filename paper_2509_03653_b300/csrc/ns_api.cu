@@ -644,7 +644,8 @@ ns_status ns_accumulate(ns_ctx* c, ns_matrix* acc, const ns_matrix* add, ns_stre
     TRY(to_hash(acc, add->bound, s));
     if (add->fmt == FMT_HASH) {
         TraceScope ts(&c->tracer, "k_insert_slots", s);
-        launch_insert_slots((const LinkSlot*)add->links.p, add->link_cap, hash_view(acc), c->sms, s);
+        launch_insert_slots((const LinkSlot*)add->links.p, add->link_cap, hash_view(acc), c->sms, s,
+                            c->cfg.cta_cache != NS_CACHE_OFF);
     } else if (add->fmt == FMT_LIST && add->bound > 0) {
         TraceScope ts(&c->tracer, "k_insert_list", s);
         launch_insert_list((const u64*)add->keys.p, (const u64*)add->counts.p, add->bound,

@@ -253,7 +253,8 @@ ns_status ns_batch_run(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uint
             // every window's link slots, side slots included (a side slot's
             // key field is 0, which is the key it holds)
             TraceScope ts(&c->tracer, "k_insert_slots", s);
-            launch_insert_slots((const LinkSlot*)b->links.p, ch.slots - 1, hash_view(acc), c->sms, s);
+            launch_insert_slots((const LinkSlot*)b->links.p, ch.slots - 1, hash_view(acc), c->sms, s,
+                                b->params.cta_cache != 0);
         }
     }
     {

@@ -696,8 +696,10 @@ void launch_insert_packets_snapshot(const u32* src, const u32* dst, u64 n, const
 }
 
 void launch_insert_slots(const LinkSlot* in, u64 in_cap, const HashView& M, int sms,
-                         cudaStream_t s) {
-    k_insert_slots<true><<<grid_for(in_cap + 1, kInsertThreads, sms, 8), kInsertThreads, sizeof(CtaCache), s>>>(in, in_cap, M);
+                         cudaStream_t s, bool cache) {
+    const int grid = grid_for(in_cap + 1, kInsertThreads, sms, 8);
+    if (cache) k_insert_slots<true><<<grid, kInsertThreads, sizeof(CtaCache), s>>>(in, in_cap, M);
+    else k_insert_slots<false><<<grid, kInsertThreads, 0, s>>>(in, in_cap, M);
 }
 
 void launch_insert_list(const u64* keys, const u64* counts, u64 n_bound,

@@ -106,8 +106,10 @@ void launch_insert_packets(const u32* src, const u32* dst, u64 n, const HashView
                            int sms, bool cache, cudaStream_t s, bool snap = false);
 void launch_insert_packets_snapshot(const u32* src, const u32* dst, u64 n, const HashView& M,
                                     u64* out, int sms, bool cache, cudaStream_t s);
+// `cache` (default on): stage rows and columns that repeat across the
+// inserted links in per-CTA shared-memory tables (pays under skew)
 void launch_insert_slots(const LinkSlot* in, u64 in_cap, const HashView& M, int sms,
-                         cudaStream_t s);
+                         cudaStream_t s, bool cache = true);
 void launch_insert_list(const u64* keys, const u64* counts, u64 n_bound,
                         const u64* n_dev, const HashView& M, int sms, cudaStream_t s);
 void launch_compact_links(const LinkSlot* in, u64 cap, u64* out_keys, u64* out_counts,
