@@ -816,9 +816,9 @@ def run_serve(args, rank, world, local):
         ns.matrix_clear(acc)
         torch.cuda.synchronize()
 
-    # warm-up: the 16 largest windows size every slot's buffers and tables
-    big = sorted(range(2 * Wn), key=lambda i: -int(sizes[i]))[:16]
-    for t in [ns.stream_submit(srv, wins[i][0], wins[i][1], i) for i in big]:
+    # every slot sized for the largest window, then a short warm-up
+    srv.reserve(int(sizes.max()))
+    for t in [ns.stream_submit(srv, s, d, i) for i, (s, d) in enumerate(wins[:16])]:
         ns.stream_wait(srv, t)
     restart()
 

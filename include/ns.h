@@ -353,6 +353,13 @@ typedef struct {
 
 ns_status ns_server_create(ns_ctx* ctx, ns_matrix* acc, ns_server** out);
 
+/* Sizes every slot's device buffers and tables for windows of up to
+ * max_window packets, so that no later window makes a slot grow (growing
+ * frees the old buffers, which synchronizes the device and stalls every
+ * window in flight).  Only while the service is idle (else NS_ERR_BUSY);
+ * blocking.  Optional: slots otherwise grow on demand. */
+ns_status ns_server_reserve(ns_server* server, uint64_t max_window);
+
 /* Finishes every submitted window, then stops the service's threads and
  * frees its slots (acc keeps the aggregate). */
 void ns_server_destroy(ns_server* server);

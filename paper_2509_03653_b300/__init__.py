@@ -427,6 +427,11 @@ class Server:
         self.handle = h
         self._keep = {}  # ticket -> host arrays that must outlive the window
 
+    def reserve(self, max_window: int):
+        """Sizes every slot for windows of up to max_window packets
+        (ns_server_reserve; while idle)."""
+        check(self._L.ns_server_reserve(self.handle, max_window), "ns_server_reserve")
+
     def close(self):
         if getattr(self, "handle", None):
             self._L.ns_server_destroy(self.handle)

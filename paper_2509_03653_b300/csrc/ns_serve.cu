@@ -274,6 +274,24 @@ ns_status ns_server_create(ns_ctx* c, ns_matrix* acc, ns_server** out) {
     return NS_OK;
 }
 
+ns_status ns_server_reserve(ns_server* S, uint64_t max_window) {
+    if (!S) return set_fail(NS_ERR_INVALID, "ns_server_reserve: NULL server");
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (!S->queue.empty() || !S->inflight.empty())
+        return set_fail(NS_ERR_BUSY, "ns_server_reserve: windows in flight");
+    for (auto& sl : S->slots) {
+        if (sl.busy) return set_fail(NS_ERR_BUSY, "ns_server_reserve: windows in flight");
+        ns_status st = slot_prepare(S, sl, max_window);
+        if (st == NS_OK) st = ns_matrix_reserve(sl.At, max_window, sl.stream);
+        if (st != NS_OK) return st;
+        if (cudaStreamSynchronize(sl.stream) != cudaSuccess) {
+            cudaGetLastError();
+            return set_fail(NS_ERR_CUDA, "ns_server_reserve: slot set-up failed");
+        }
+    }
+    return NS_OK;
+}
+
 void ns_server_destroy(ns_server* S) {
     if (!S) return;
     {

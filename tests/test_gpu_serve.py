@@ -111,3 +111,23 @@ def test_window_over_budget_is_rejected():
     pw, rn, _ = ns.stream_wait(srv, t2)
     assert pw == oracle.stats(*oracle.build_matrix(s2, d2))
     srv.close()
+
+
+def test_server_reserve_then_windows_match_oracle():
+    """Slots sized up front (ns_server_reserve) serve windows up to that size
+    with the oracle's per-window and running quantities; reserving again
+    once the service is idle is allowed."""
+    ctx = ns.Context(0, path="hash")
+    acc = ns.Matrix(ctx)
+    srv = ns.Server(ctx, acc)
+    sizes = [30000, 1, 0, 65536, 12345]
+    srv.reserve(max(sizes))
+    want = (np.zeros(0, np.uint64), np.zeros(0, np.uint64))
+    for w, n in enumerate(sizes):
+        s, d = W.serving_window(w, n)
+        pw, run, _ = ns.stream_wait(srv, ns.stream_submit(srv, s, d, w))
+        m = oracle.build_matrix(s, d)
+        want = oracle.accumulate(want, m)
+        assert pw == oracle.stats(*m) and run == oracle.stats(*want), w
+    srv.reserve(1 << 18)  # idle again: allowed
+    srv.close()
