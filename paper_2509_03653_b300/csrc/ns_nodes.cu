@@ -103,26 +103,33 @@ __global__ void k_buckets(const u64* __restrict__ u, u64 N, u64* __restrict__ bu
     }
 }
 
-// position of x in the ascending distinct list u[0..N) (x is in it)
-__device__ __forceinline__ u64 find_pos(const u64* __restrict__ u, const u64* __restrict__ bucket, u64 N, u32 x) {
+// u[i] := u[i] << 32 | label[i]: each distinct address carries its label,
+// so the lookup that finds it needs no further load
+__global__ void k_attach_labels(u64* __restrict__ u, const u32* __restrict__ label, u64 N) {
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) u[i] = (u[i] << 32) | label[i];
+}
+
+// the label of x, whose word is in the ascending list w[0..N) of
+// (address << 32 | label) (x is in it)
+__device__ __forceinline__ u32 find_label(const u64* __restrict__ w, const u64* __restrict__ bucket, u64 N, u32 x) {
     const u32 b = x >> (32 - kBucketBits);
     u64 lo = bucket[b], hi = bucket[b + 1];
     while (lo < hi) {
         const u64 mid = (lo + hi) >> 1;
-        if (u[mid] < (u64)x) lo = mid + 1;
+        if ((u32)(w[mid] >> 32) < x) lo = mid + 1;
         else hi = mid;
     }
-    return lo < N ? lo : N - 1;
+    return (u32)w[lo < N ? lo : N - 1];
 }
 
-__global__ void k_relabel(const u32* src, const u32* dst, u64 n, const u64* __restrict__ u,
-                          const u64* __restrict__ bucket, u64 N, const u32* __restrict__ label, u32* out_src,
-                          u32* out_dst) {
+__global__ void k_relabel(const u32* src, const u32* dst, u64 n, const u64* __restrict__ w,
+                          const u64* __restrict__ bucket, u64 N, u32* out_src, u32* out_dst) {
     const u64 stride = (u64)gridDim.x * blockDim.x;
     for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
         const u32 a = src[k], b = dst[k];
-        out_src[k] = label[find_pos(u, bucket, N, a)];
-        out_dst[k] = label[find_pos(u, bucket, N, b)];
+        out_src[k] = find_label(w, bucket, N, a);
+        out_dst[k] = find_label(w, bucket, N, b);
     }
 }
 
@@ -327,8 +334,12 @@ ns_status ns_anonymize(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, 
         k_buckets<<<grid_of((1ull << kBucketBits) + 1, c->sms), 256, 0, s>>>(uniq, N, bucket);
     }
     {
+        TraceScope t(&c->tracer, "k_attach_labels", s);
+        k_attach_labels<<<grid_of(N, c->sms), 256, 0, s>>>(uniq, label, N);
+    }
+    {
         TraceScope t(&c->tracer, "k_relabel", s);
-        k_relabel<<<grid_of(n, c->sms), 256, 0, s>>>(d_src, d_dst, n, uniq, bucket, N, label, d_out_src, d_out_dst);
+        k_relabel<<<grid_of(n, c->sms), 256, 0, s>>>(d_src, d_dst, n, uniq, bucket, N, d_out_src, d_out_dst);
     }
     if (cudaGetLastError() != cudaSuccess) return set_fail(NS_ERR_CUDA, "ns_anonymize: launch failed");
     return check_errors(err, s);

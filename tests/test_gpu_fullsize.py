@@ -31,7 +31,7 @@ def test_stream_512_windows_of_2p17():
     hs, hd, s, d = pinned_pair(N)
     W.rmat_stream(N, src=s, dst=d)
     ds, dd = hs.cuda(), hd.cuda()
-    ctx = ns.Context(0, path="hash")
+    ctx = ns.Context(0, path="hash", hash_load=0.25)  # bench.py's table sizing
     A = ns.Matrix(ctx)
     ns.matrix_reserve(A, N)
     rows = torch.zeros(NW, 16, dtype=torch.int64, device="cuda")
@@ -214,3 +214,31 @@ def test_anonymize_2p30():
     ns.window_build(ctx_s, ds, dd, a)
     ns.window_build(ctx_s, os_, od, b)
     assert ns.network_stats(ctx_s, a) == ns.network_stats(ctx_s, b)
+
+
+def test_slide_512_windows_k8():
+    """The slide workload as bench.py runs it (512 windows of 2^17 RMAT
+    packets, K = 8, no CTA staging): sampled windows' own and sliding-window
+    quantities against the oracle; every window's valid counts."""
+    NW, WIN, K = W.W2_WINDOWS, W.W2_WINDOW, 8
+    N = NW * WIN
+    hs, hd, s, d = pinned_pair(N)
+    W.rmat_stream(N, src=s, dst=d)
+    ds, dd = hs.cuda(), hd.cuda()
+    ctx = ns.Context(0, path="hash", cta_cache="off")
+    sl = ns.Slider(ctx, K)
+    ow = torch.zeros(NW, 16, dtype=torch.int64, device="cuda")
+    osl = torch.zeros(NW, 16, dtype=torch.int64, device="cuda")
+    for w in range(NW):
+        a = w * WIN
+        ns.slider_push(ctx, sl, ds[a:a + WIN], dd[a:a + WIN], ow[w], osl[w])
+    torch.cuda.synchronize()
+    rw = ow.cpu().numpy().view(np.uint64)[:, :9]
+    rs = osl.cpu().numpy().view(np.uint64)[:, :9]
+    assert np.all(rw[:, 0] == WIN)
+    assert np.array_equal(rs[:, 0], np.minimum(np.arange(NW) + 1, K).astype(np.uint64) * WIN)
+    for w in (0, 3, 7, 8, 300, NW - 1):
+        a, b = max(0, w + 1 - K) * WIN, (w + 1) * WIN
+        assert {f: int(x) for f, x in zip(oracle.FIELDS, rs[w])} == oracle.stats_of_packets(s[a:b], d[a:b]), w
+        c = w * WIN
+        assert {f: int(x) for f, x in zip(oracle.FIELDS, rw[w])} == oracle.stats_of_packets(s[c:c + WIN], d[c:c + WIN]), w
