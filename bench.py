@@ -813,8 +813,7 @@ def run_serve(args, rank, world, local):
     srv = ns.Server(ctx, acc)
 
     def restart():  # an empty aggregate between phases (the service is idle)
-        ns.matrix_clear(acc)
-        torch.cuda.synchronize()
+        srv.clear()
 
     # every slot sized for the largest window, then a short warm-up
     srv.reserve(int(sizes.max()))

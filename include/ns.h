@@ -360,6 +360,11 @@ ns_status ns_server_create(ns_ctx* ctx, ns_matrix* acc, ns_server** out);
  * blocking.  Optional: slots otherwise grow on demand. */
 ns_status ns_server_reserve(ns_server* server, uint64_t max_window);
 
+/* Empties the aggregate (A = 0) so that the next window's running
+ * quantities start afresh.  Only while the service is idle (else
+ * NS_ERR_BUSY); blocking. */
+ns_status ns_server_clear(ns_server* server);
+
 /* Finishes every submitted window, then stops the service's threads and
  * frees its slots (acc keeps the aggregate). */
 void ns_server_destroy(ns_server* server);

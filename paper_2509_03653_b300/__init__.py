@@ -432,6 +432,10 @@ class Server:
         (ns_server_reserve; while idle)."""
         check(self._L.ns_server_reserve(self.handle, max_window), "ns_server_reserve")
 
+    def clear(self):
+        """Empties the aggregate while idle (ns_server_clear)."""
+        check(self._L.ns_server_clear(self.handle), "ns_server_clear")
+
     def close(self):
         if getattr(self, "handle", None):
             self._L.ns_server_destroy(self.handle)

@@ -60,6 +60,7 @@ SIGNATURES = {
     "ns_matrix_nodes": (ST, [P, P, ctypes.c_int, P, P, P, U64, ctypes.POINTER(U64), P]),
     "ns_anonymize": (ST, [P, P, P, U64, P, U64, P, P, ctypes.POINTER(U64), P]),
     "ns_server_reserve": (ST, [P, U64]),
+    "ns_server_clear": (ST, [P]),
     "ns_slider_create": (ST, [P, ctypes.c_uint32, ctypes.POINTER(P)]),
     "ns_slider_free": (None, [P]),
     "ns_slider_push": (ST, [P, P, P, P, U64, P, P, P]),

@@ -292,6 +292,20 @@ ns_status ns_server_reserve(ns_server* S, uint64_t max_window) {
     return NS_OK;
 }
 
+ns_status ns_server_clear(ns_server* S) {
+    if (!S) return set_fail(NS_ERR_INVALID, "ns_server_clear: NULL server");
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (!S->queue.empty() || !S->inflight.empty())
+        return set_fail(NS_ERR_BUSY, "ns_server_clear: windows in flight");
+    ns_status st = ns_matrix_clear(S->acc, S->acc_stream);
+    if (st != NS_OK) return st;
+    if (cudaStreamSynchronize(S->acc_stream) != cudaSuccess) {
+        cudaGetLastError();
+        return set_fail(NS_ERR_CUDA, "ns_server_clear: clear failed");
+    }
+    return NS_OK;
+}
+
 void ns_server_destroy(ns_server* S) {
     if (!S) return;
     {

@@ -130,4 +130,8 @@ def test_server_reserve_then_windows_match_oracle():
         want = oracle.accumulate(want, m)
         assert pw == oracle.stats(*m) and run == oracle.stats(*want), w
     srv.reserve(1 << 18)  # idle again: allowed
+    srv.clear()  # A = 0: the next window's running quantities are its own
+    s, d = W.serving_window(99, 4000)
+    pw, run, _ = ns.stream_wait(srv, ns.stream_submit(srv, s, d, 99))
+    assert pw == run == oracle.stats_of_packets(s, d)
     srv.close()
