@@ -10,10 +10,11 @@
 //
 // Anonymization (section "Implementation", paragraph "IP Address
 // Anonymization"): the distinct addresses of the src and dst columns are
-// found by a sort of both columns and a run pass; the caller's random keys,
-// one per distinct address, are sorted with their positions attached, which
-// yields a uniformly random permutation (as the shuffle of 0..N-1 does);
-// every packet's addresses are then replaced by their labels, found by
+// found with a hash set (the paragraph's hash-table way of `unique`), then
+// compacted and sorted; the caller's random keys, one per distinct address,
+// are sorted with their positions attached, which yields a uniformly random
+// permutation (as the shuffle of 0..N-1 does); every packet's addresses are
+// then replaced by their labels, found through a prefix table and a short
 // binary search in the sorted distinct addresses (the gather).
 #include <algorithm>
 
@@ -130,6 +131,87 @@ __global__ void k_relabel(const u32* src, const u32* dst, u64 n, const u64* __re
         const u32 a = src[k], b = dst[k];
         out_src[k] = find_label(w, bucket, N, a);
         out_dst[k] = find_label(w, bucket, N, b);
+    }
+}
+
+// ---- the distinct addresses of both columns, by hashing ---------------------
+//
+// A set of addresses in open addressing: a slot holds address + 1 (0 =
+// empty); the address 0xFFFFFFFF sets a flag word instead.  Slots only ever
+// go from empty to an address, so a plain (possibly cached) load that shows
+// the address is final, and one that shows empty is settled by the CAS.
+// Skewed traffic repeats a few addresses, whose slots stay in L1/L2; the
+// distinct ones are then compacted and sorted, which is far less work than
+// sorting both columns.  When the distinct addresses outgrow half the table,
+// the kernel stops early and the host retries with a table for every
+// address being distinct.
+struct SetCounters {
+    u64 inserted;  // distinct addresses placed so far
+    u64 all_ones;  // address 0xFFFFFFFF seen
+    u64 full;      // more than half the slots taken: abandon this table
+    u64 out;       // compaction cursor
+};
+
+__global__ void k_set_insert(const u32* __restrict__ src, const u32* __restrict__ dst, u64 n, u32* __restrict__ T,
+                             u64 mask, SetCounters* sc, DevStats* st) {
+    const u32 FULL = 0xFFFFFFFFu;
+    const u64 limit = (mask + 1) / 2;
+    const u64 total = 2 * n;
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    const u64 wbase = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    u32 iter = 0;
+    for (u64 b = wbase; b < total; b += stride, ++iter) {
+        if ((iter & 15) == 0 && ld_volatile(&sc->full)) return;  // whole warps leave together
+        const u64 i = b + (threadIdx.x & 31);
+        bool inserted = false, ones = false;
+        if (i < total) {
+            const u32 x = i < n ? src[i] : dst[i - n];
+            if (x == 0xFFFFFFFFu) {
+                ones = true;
+            } else {
+                const u32 v = x + 1;
+                u64 h = mix32(x) & mask;
+                u32 p = 0;
+                for (; p < kMaxProbes; ++p) {
+                    const u32 cur = T[h];
+                    if (cur == v) break;
+                    if (cur == 0u) {
+                        const u32 old = atomicCAS(&T[h], 0u, v);
+                        if (old == 0u) {
+                            inserted = true;
+                            break;
+                        }
+                        if (old == v) break;
+                    }
+                    h = (h + 1) & mask;
+                }
+                if (p == kMaxProbes) set_error(st, ERR_CAPACITY);
+            }
+        }
+        const u32 ins = __ballot_sync(FULL, inserted);
+        if (__any_sync(FULL, ones) && (threadIdx.x & 31) == 0 && !ld_volatile(&sc->all_ones)) sc->all_ones = 1;
+        if (ins && (threadIdx.x & 31) == 0) {
+            const u64 before = atomicAdd((unsigned long long*)&sc->inserted, (unsigned long long)__popc(ins));
+            if (before + __popc(ins) > limit) st_volatile(&sc->full, 1ull);
+        }
+    }
+}
+
+// out[k] = the addresses in the set, in slot order (then sorted)
+__global__ void k_set_compact(const u32* __restrict__ T, u64 cap, SetCounters* sc, u32* __restrict__ out) {
+    const u32 FULL = 0xFFFFFFFFu;
+    const u32 lane = threadIdx.x & 31;
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    const u64 wbase = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    for (u64 b = wbase; b < cap; b += stride) {
+        const u64 i = b + lane;
+        const u32 v = i < cap ? T[i] : 0u;
+        const u32 has = __ballot_sync(FULL, v != 0u);
+        if (!has) continue;
+        u64 base = 0;
+        if (lane == 0) base = atomicAdd((unsigned long long*)&sc->out, (unsigned long long)__popc(has));
+        base = __shfl_sync(FULL, base, 0);
+        if (v != 0u) out[base + __popc(has & ((1u << lane) - 1u))] = v - 1u;
     }
 }
 
@@ -274,38 +356,70 @@ ns_status ns_anonymize(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, 
     if (n >= (1ull << 39)) return set_fail(NS_ERR_INVALID, "ns_anonymize: n too large");
     cudaStream_t s = (cudaStream_t)stream;
     const u64 m2 = 2 * n;
-    // 0 both columns, 1 stats + counters, 2 the gather's prefix table
+    // 0 the address set, 1 stats + set counters, 2 the gather's prefix table,
+    // 3 the distinct addresses (unsorted, then sorted ping-pong)
     Scratch x;
-    ns_status st = buf_reserve(x.b[0], m2 * sizeof(u32));
-    if (st == NS_OK) st = buf_reserve(x.b[1], sizeof(DevStats) + 8 * sizeof(u64));
-    if (st == NS_OK) st = buf_reserve(c->k32[0], m2 * sizeof(u32));
-    if (st == NS_OK) st = buf_reserve(c->k32[1], m2 * sizeof(u32));
-    if (st == NS_OK) st = buf_reserve(c->xk, m2 * sizeof(u64));
-    if (st == NS_OK) st = buf_reserve(c->pos, (m2 + 1) * sizeof(u64));
-    if (st == NS_OK) st = sort_scratch(c, m2);
+    ns_status st = buf_reserve(x.b[1], sizeof(DevStats) + sizeof(SetCounters));
     if (st != NS_OK) return st;
-    if (cudaMemsetAsync(x.b[1].p, 0, sizeof(DevStats) + 8 * sizeof(u64), s) != cudaSuccess)
-        return set_fail(NS_ERR_CUDA, "ns_anonymize: memset failed");
     DevStats* err = (DevStats*)x.b[1].p;
-    u64* R = (u64*)((char*)x.b[1].p + sizeof(DevStats));
-    // 1. the distinct addresses of both columns, ascending: the two columns
-    // end to end, sorted as uint32 keys, then the run heads
-    if (cudaMemcpyAsync(x.b[0].p, d_src, n * sizeof(u32), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync((u32*)x.b[0].p + n, d_dst, n * sizeof(u32), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return set_fail(NS_ERR_CUDA, "ns_anonymize: copy failed");
-    u32* kb32[2] = {(u32*)c->k32[0].p, (u32*)c->k32[1].p};
-    const int r = radix_sort_u32((const u32*)x.b[0].p, nullptr, kb32, m2, c->sc, err, s);
-    u64* uniq = (u64*)c->xk.p;
-    launch_runs(RUN_U32, false, kb32[r], nullptr, m2, nullptr, uniq, (u64*)c->pos.p, nullptr, R, c->sc, err, s);
-    if (cudaGetLastError() != cudaSuccess) return set_fail(NS_ERR_CUDA, "ns_anonymize: launch failed");
-    u64 N = 0;
-    st = read_u64(R, &N, s);
-    if (st == NS_OK) st = check_errors(err, s);
+    SetCounters* setc = (SetCounters*)((char*)x.b[1].p + sizeof(DevStats));
+    // 1. the distinct addresses of both columns: a hash set sized for up to
+    // 2^24 of them first, and for every address being distinct if that
+    // overflows; then compaction, and a sort of the distinct ones
+    const u64 first = std::min<u64>(m2, 1ull << 24);
+    u64 cap = 0;
+    SetCounters hs{};
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const u64 want = attempt == 0 ? first : m2;
+        cap = 1024;
+        while (cap < 2 * want) cap <<= 1;
+        st = buf_reserve(x.b[0], cap * sizeof(u32));
+        if (st != NS_OK) return st;
+        if (cudaMemsetAsync(x.b[0].p, 0, cap * sizeof(u32), s) != cudaSuccess ||
+            cudaMemsetAsync(x.b[1].p, 0, sizeof(DevStats) + sizeof(SetCounters), s) != cudaSuccess)
+            return set_fail(NS_ERR_CUDA, "ns_anonymize: memset failed");
+        {
+            TraceScope t(&c->tracer, "k_set_insert", s);
+            k_set_insert<<<grid_of(m2, c->sms), 256, 0, s>>>(d_src, d_dst, n, (u32*)x.b[0].p, cap - 1, setc, err);
+        }
+        if (cudaGetLastError() != cudaSuccess) return set_fail(NS_ERR_CUDA, "ns_anonymize: launch failed");
+        if (cudaMemcpyAsync(&hs, setc, sizeof hs, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return set_fail(NS_ERR_CUDA, "ns_anonymize: device read failed");
+        if (!hs.full) break;
+        if (attempt == 1) return set_fail(NS_ERR_CAPACITY, "ns_anonymize: address set overflowed");
+    }
+    st = check_errors(err, s);
     if (st != NS_OK) return st;
+    const u64 N = hs.inserted + (hs.all_ones ? 1 : 0);
     *h_unique = N;
     if (!d_rand || rand_count < N)
         return fail_fmt(NS_ERR_CAPACITY, "ns_anonymize: %llu distinct addresses, %llu random keys",
                         (unsigned long long)N, (unsigned long long)rand_count);
+    st = buf_reserve(x.b[3], std::max<u64>(N, 1) * sizeof(u32));
+    if (st == NS_OK) st = buf_reserve(c->k32[0], std::max<u64>(N, 1) * sizeof(u32));
+    if (st == NS_OK) st = buf_reserve(c->k32[1], std::max<u64>(N, 1) * sizeof(u32));
+    if (st == NS_OK) st = buf_reserve(c->xk, std::max<u64>(N, 1) * sizeof(u64));
+    if (st == NS_OK) st = sort_scratch(c, N);
+    if (st != NS_OK) return st;
+    {
+        TraceScope t(&c->tracer, "k_set_compact", s);
+        k_set_compact<<<grid_of(cap, c->sms), 256, 0, s>>>((const u32*)x.b[0].p, cap, setc, (u32*)x.b[3].p);
+    }
+    if (hs.all_ones) {
+        const u32 ones = 0xFFFFFFFFu;
+        if (cudaMemcpyAsync((u32*)x.b[3].p + hs.inserted, &ones, sizeof ones, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return set_fail(NS_ERR_CUDA, "ns_anonymize: copy failed");
+    }
+    u32* kb32[2] = {(u32*)c->k32[0].p, (u32*)c->k32[1].p};
+    const int r = radix_sort_u32((const u32*)x.b[3].p, nullptr, kb32, N, c->sc, err, s);
+    u64* uniq = (u64*)c->xk.p;
+    {
+        TraceScope t(&c->tracer, "k_concat_u32", s);
+        k_concat_u32<<<grid_of(N, c->sms), 256, 0, s>>>(kb32[r], N, nullptr, 0, uniq);
+    }
+    if (cudaGetLastError() != cudaSuccess) return set_fail(NS_ERR_CUDA, "ns_anonymize: launch failed");
     // 2. the permutation: positions sorted by their random keys (stable)
     st = buf_reserve(c->psum, (N + 1) * sizeof(u64));
     if (st == NS_OK) st = buf_reserve(c->v64[0], N * sizeof(u64));
@@ -313,7 +427,7 @@ ns_status ns_anonymize(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, 
     if (st == NS_OK) st = buf_reserve(c->k64[0], N * sizeof(u64));
     if (st == NS_OK) st = buf_reserve(c->k64[1], N * sizeof(u64));
     if (st == NS_OK) st = buf_reserve(x.b[2], ((1ull << kBucketBits) + 1) * sizeof(u64));
-    if (st == NS_OK) st = sort_scratch(c, m2);
+    if (st == NS_OK) st = sort_scratch(c, N);
     if (st != NS_OK) return st;
     {
         TraceScope t(&c->tracer, "k_iota", s);

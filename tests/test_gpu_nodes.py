@@ -130,3 +130,19 @@ def test_anonymized_stream_keeps_the_quantities():
     ns.window_build(ctx, to_dev(s), to_dev(d), a)
     ns.window_build(ctx, gs, gd, b)
     assert ns.network_stats(ctx, a) == ns.network_stats(ctx, b)
+
+
+@pytest.mark.slow
+def test_anonymize_high_cardinality_retries_the_set():
+    """2^24 packets of uniform 32-bit addresses: more than 2^24 distinct
+    addresses overflow the first address set, and the retry with a table
+    for all of them still gives the oracle's labels."""
+    s, d = gen.uniform_pairs(1 << 24, 32, 4242)
+    rnd = gen.random_u64(2 * s.size, 4243, 5)
+    ws, wd, wn = oracle.anonymize(s, d, rnd)
+    assert wn > (1 << 24)
+    ctx = ns.Context(0)
+    gs, gd, gn = ns.anonymize(ctx, to_dev(s), to_dev(d), torch.from_numpy(rnd.view(np.int64)).cuda())
+    assert gn == wn
+    np.testing.assert_array_equal(u32(gs), ws)
+    np.testing.assert_array_equal(u32(gd), wd)
