@@ -50,7 +50,7 @@ typedef enum {
     NS_ERR_CAPACITY = 3, /* a hash probe exceeded its bound */
     NS_ERR_CUDA = 4,     /* a CUDA runtime call failed */
     NS_ERR_TIMEOUT = 5,  /* a device-side wait gave up, or a host wait timed out */
-    NS_ERR_BUSY = 6,     /* serving queue full: retry later */
+    NS_ERR_BUSY = 6,     /* serving queue full (retry later), or the service is not idle */
     NS_ERR_STATE = 7     /* call not valid in the object's current state */
 } ns_status;
 
