@@ -403,7 +403,7 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
     load_path_choices(x);
     cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, device);
     x->sc.sms = x->sms;
-    ns_status st = buf_reserve(x->ghist, 8 * 256 * sizeof(u32));
+    ns_status st = buf_reserve(x->ghist, 8 * 256 * sizeof(u64));
     if (st == NS_OK) st = buf_reserve(x->offs, 8 * 256 * sizeof(u64));
     if (st == NS_OK) st = buf_reserve(x->tcount, 16 * sizeof(u32));
     if (st == NS_OK) st = buf_reserve(x->counters, 16 * sizeof(u64));
@@ -413,7 +413,7 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
         ns_destroy(x);
         return st;
     }
-    x->sc.ghist = (u32*)x->ghist.p;
+    x->sc.ghist = (u64*)x->ghist.p;
     x->sc.offs = (u64*)x->offs.p;
     x->sc.tile_counters = (u32*)x->tcount.p;
     x->sc.tag = 0;

@@ -215,16 +215,18 @@ __device__ __forceinline__ K load_key(const SortIn& in, u64 i) {
 
 // Each warp counts into its own copy of the histograms (fewer shared-memory
 // atomic collisions on skewed keys); the copies are summed before the one
-// global addition per bin and CTA.
+// global addition per bin and CTA.  The shared counters are 32-bit (the
+// launch keeps every CTA below 2^31 keys); the global ones are 64-bit, since
+// one digit value can hold every key of a sort of 2^32 or more.
 constexpr int kHistUnroll = 8;
-template <typename K, int LOAD>
-__global__ void __launch_bounds__(kThreads) k_sort_hist(SortIn in, u64 n_arg, int begin_bit, int passes,
-                                                         u32* __restrict__ ghist) {
-    extern __shared__ __align__(16) u32 hs[];  // [kWarps][passes][kRadix]
+template <typename K, int LOAD, int PASSES>
+__global__ void __launch_bounds__(kThreads) k_sort_hist(SortIn in, u64 n_arg, int begin_bit,
+                                                         u64* __restrict__ ghist) {
+    extern __shared__ __align__(16) u32 hs[];  // [kWarps][PASSES][kRadix]
     const u64 n = in.n_dev ? *in.n_dev : n_arg;
-    for (int i = threadIdx.x; i < kWarps * passes * kRadix; i += kThreads) hs[i] = 0;
+    for (int i = threadIdx.x; i < kWarps * PASSES * kRadix; i += kThreads) hs[i] = 0;
     __syncthreads();
-    u32* h = hs + (threadIdx.x >> 5) * passes * kRadix;
+    u32* h = hs + (threadIdx.x >> 5) * PASSES * kRadix;
     // kHistUnroll keys per thread per round, loaded before any is counted, so
     // that enough loads are in flight to cover HBM latency (one key at a time
     // left this kernel latency-bound)
@@ -238,23 +240,37 @@ __global__ void __launch_bounds__(kThreads) k_sort_hist(SortIn in, u64 n_arg, in
         }
 #pragma unroll
         for (int u = 0; u < kHistUnroll; ++u) {
-            if (i0 + (u64)u * stride < n) {
-                for (int p = 0; p < passes; ++p)
-                    atomicAdd(&h[p * kRadix + ((u32)(k[u] >> (begin_bit + 8 * p)) & 0xFF)], 1u);
+            const bool valid = i0 + (u64)u * stride < n;
+            const u64 kb = (u64)k[u] >> begin_bit;
+            if (valid) {
+#pragma unroll
+                for (int p = 0; p < PASSES; ++p) atomicAdd(&h[p * kRadix + ((u32)(kb >> (8 * p)) & 0xFF)], 1u);
             }
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * kRadix; i += kThreads) {
+    for (int i = threadIdx.x; i < PASSES * kRadix; i += kThreads) {
         u32 c = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) c += hs[w * passes * kRadix + i];
-        if (c) atomicAdd(&ghist[i], c);
+        for (int w = 0; w < kWarps; ++w) c += hs[w * PASSES * kRadix + i];
+        if (c) atomicAdd(reinterpret_cast<unsigned long long*>(&ghist[i]), (unsigned long long)c);
     }
 }
 
+template <typename K, int LOAD, int PASSES>
+void launch_hist(const SortIn& in, u64 n, int begin_bit, int grid, u64* ghist, Tracer* tr, cudaStream_t s) {
+    const size_t hsmem = sizeof(u32) * kWarps * PASSES * kRadix;
+    static bool hconf = false;
+    if (!hconf) {
+        cudaFuncSetAttribute(k_sort_hist<K, LOAD, PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
+        hconf = true;
+    }
+    TraceScope ts(tr, "k_sort_hist", s);
+    k_sort_hist<K, LOAD, PASSES><<<grid, kThreads, hsmem, s>>>(in, n, begin_bit, ghist);
+}
+
 // bucket starts: offs[p][d] = sum of ghist[p][0..d)
-__global__ void __launch_bounds__(kThreads) k_sort_offsets(const u32* __restrict__ ghist, int passes,
+__global__ void __launch_bounds__(kThreads) k_sort_offsets(const u64* __restrict__ ghist, int passes,
                                                             u64* __restrict__ offs) {
     __shared__ u64 wsum[kWarps];
     __shared__ u64 tot;
@@ -891,21 +907,15 @@ int sort_radix() { return kRadix; }
 template <typename K, bool HAS_V, int LOAD>
 int radix_sort_t(const SortIn& in, K* kbuf[2], u64* vbuf[2], u64 n, int begin_bit, int passes,
                  SortScratch& sc, DevStats* st, cudaStream_t s) {
-    cudaMemsetAsync(sc.ghist, 0, sizeof(u32) * 8 * kRadix, s);
+    cudaMemsetAsync(sc.ghist, 0, sizeof(u64) * 8 * kRadix, s);
     cudaMemsetAsync(sc.tile_counters, 0, sizeof(u32) * 8, s);
-    const int hist_grid = (int)std::min<u64>((n + kThreads * 8 - 1) / (kThreads * 8), (u64)sc.sms * 3);
-    {
-        const size_t hsmem = sizeof(u32) * kWarps * passes * kRadix;
-        static bool hconf = false;
-        if (!hconf) {
-            cudaFuncSetAttribute(k_sort_hist<K, LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(u32) * kWarps * 8 * kRadix));
-            hconf = true;
-        }
-        TraceScope ts(sc.tr, "k_sort_hist", s);
-        k_sort_hist<K, LOAD><<<hist_grid < 1 ? 1 : hist_grid, kThreads, hsmem, s>>>(in, n, begin_bit, passes,
-                                                                                   sc.ghist);
-    }
+    // three CTAs per SM, or more where that would leave a CTA 2^31 keys or more
+    const u64 hist_cap = std::max<u64>((u64)sc.sms * 3, (n >> 31) + 1);
+    const int hist_grid = (int)std::min<u64>((n + kThreads * 8 - 1) / (kThreads * 8), hist_cap);
+    if (passes == 8)
+        launch_hist<K, LOAD, 8>(in, n, begin_bit, hist_grid < 1 ? 1 : hist_grid, sc.ghist, sc.tr, s);
+    else  // 4: 32-bit keys, or one half of 64-bit ones
+        launch_hist<K, LOAD, 4>(in, n, begin_bit, hist_grid < 1 ? 1 : hist_grid, sc.ghist, sc.tr, s);
     {
         TraceScope ts(sc.tr, "k_sort_offsets", s);
         k_sort_offsets<<<1, kThreads, 0, s>>>(sc.ghist, passes, sc.offs);
