@@ -42,6 +42,10 @@ constexpr int kRadix = 256;
 #ifndef NS_ONESWEEP_PF
 #define NS_ONESWEEP_PF 1
 #endif
+// the same for the run kernels
+#ifndef NS_RUNS_PF
+#define NS_RUNS_PF 1
+#endif
 
 constexpr u64 kFlagAgg = 1, kFlagPrefix = 2;
 #ifndef NS_LOOK_DIGITS
@@ -213,60 +217,140 @@ __device__ __forceinline__ K load_key(const SortIn& in, u64 i) {
 
 // ---- histogram of every digit pass ------------------------------------------
 
-// Each warp counts into its own copy of the histograms (fewer shared-memory
-// atomic collisions on skewed keys); the copies are summed before the one
-// global addition per bin and CTA.  The shared counters are 32-bit (the
-// launch keeps every CTA below 2^31 keys); the global ones are 64-bit, since
-// one digit value can hold every key of a sort of 2^32 or more.
+// Counting is bound by the shared-memory atomic pipe, and with one counter
+// per bin, lanes holding different digits that share a bank replay (about
+// 2.8 wavefronts per atomic on random digits).  So every lane counts into
+// its own column instead: word (q, d, lane) is bank `lane`, so a warp's
+// atomic never conflicts.  The word holds two 16-bit counts, digit d of pass
+// q in the low half and of pass q + PASSES/2 in the high half (the added
+// constant is fixed per pass).  Each half counts at most kHistRounds rounds
+// of kHistUnroll keys from each of the CTA's warps (< 2^16) before the
+// counts are added to the 64-bit global histogram and cleared.
+constexpr int kHistThreads = 1024;
 constexpr int kHistUnroll = 8;
-template <typename K, int LOAD, int PASSES>
-__global__ void __launch_bounds__(kThreads) k_sort_hist(SortIn in, u64 n_arg, int begin_bit,
-                                                         u64* __restrict__ ghist) {
-    extern __shared__ __align__(16) u32 hs[];  // [kWarps][PASSES][kRadix]
-    const u64 n = in.n_dev ? *in.n_dev : n_arg;
-    for (int i = threadIdx.x; i < kWarps * PASSES * kRadix; i += kThreads) hs[i] = 0;
-    __syncthreads();
-    u32* h = hs + (threadIdx.x >> 5) * PASSES * kRadix;
-    // kHistUnroll keys per thread per round, loaded before any is counted, so
-    // that enough loads are in flight to cover HBM latency (one key at a time
-    // left this kernel latency-bound)
-    const u64 stride = (u64)gridDim.x * kThreads;
-    for (u64 i0 = (u64)blockIdx.x * kThreads + threadIdx.x; i0 < n; i0 += stride * kHistUnroll) {
-        K k[kHistUnroll];
-#pragma unroll
-        for (int u = 0; u < kHistUnroll; ++u) {
-            const u64 i = i0 + (u64)u * stride;
-            k[u] = i < n ? load_key<K, LOAD>(in, i) : (K)0;
+constexpr int kHistRounds = 128;
+static_assert(kHistRounds * kHistUnroll * (kHistThreads / 32) < 65536, "16-bit shared counters would wrap");
+
+template <int PASSES>
+__device__ __forceinline__ void hist_flush(u32* hs, u64* __restrict__ ghist) {
+    constexpr int kPairs = PASSES / 2;
+    const u32 lane = threadIdx.x & 31;
+    for (int c = threadIdx.x; c < kPairs * kRadix; c += kHistThreads) {
+        u32* row = hs + c * 32;
+        u64 lo = 0, hi = 0;
+#pragma unroll 8
+        for (int l = 0; l < 32; ++l) {
+            const int j = (l + lane) & 31;  // lanes start in different banks
+            const u32 x = row[j];
+            lo += x & 0xFFFFu;
+            hi += x >> 16;
+            row[j] = 0;
         }
-#pragma unroll
-        for (int u = 0; u < kHistUnroll; ++u) {
-            const bool valid = i0 + (u64)u * stride < n;
-            const u64 kb = (u64)k[u] >> begin_bit;
-            if (valid) {
-#pragma unroll
-                for (int p = 0; p < PASSES; ++p) atomicAdd(&h[p * kRadix + ((u32)(kb >> (8 * p)) & 0xFF)], 1u);
-            }
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < PASSES * kRadix; i += kThreads) {
-        u32 c = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) c += hs[w * PASSES * kRadix + i];
-        if (c) atomicAdd(reinterpret_cast<unsigned long long*>(&ghist[i]), (unsigned long long)c);
+        const int q = c / kRadix, d = c % kRadix;
+        if (lo) atomicAdd(reinterpret_cast<unsigned long long*>(&ghist[q * kRadix + d]), (unsigned long long)lo);
+        if (hi)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&ghist[(q + kPairs) * kRadix + d]), (unsigned long long)hi);
     }
 }
 
 template <typename K, int LOAD, int PASSES>
-void launch_hist(const SortIn& in, u64 n, int begin_bit, int grid, u64* ghist, Tracer* tr, cudaStream_t s) {
-    const size_t hsmem = sizeof(u32) * kWarps * PASSES * kRadix;
-    static bool hconf = false;
-    if (!hconf) {
-        cudaFuncSetAttribute(k_sort_hist<K, LOAD, PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
-        hconf = true;
+__global__ void __launch_bounds__(kHistThreads, 1) k_sort_hist(SortIn in, u64 n_arg, int begin_bit,
+                                                                u64* __restrict__ ghist) {
+    static_assert(PASSES % 2 == 0, "passes are counted in pairs");
+    constexpr int kPairs = PASSES / 2;
+    extern __shared__ __align__(16) u32 hs[];  // [kPairs][kRadix][32 lanes]
+    const u64 n = in.n_dev ? *in.n_dev : n_arg;
+    for (int i = threadIdx.x; i < kPairs * kRadix * 32; i += kHistThreads) hs[i] = 0;
+    __syncthreads();
+    u32* hl = hs + (threadIdx.x & 31);
+    // The CTA takes blocks of kHistThreads * kHistUnroll consecutive keys;
+    // each thread loads its kHistUnroll keys before counting any, so that
+    // enough loads are in flight to cover HBM latency.
+    const u64 per_block = (u64)kHistThreads * kHistUnroll;
+    // full blocks of 16-byte-aligned inputs are read with 16-byte loads
+    const bool vec = in.bulk && LOAD != LOAD_DST_OF;
+    const u32 t = threadIdx.x;
+    int rounds = 0;
+    for (u64 blk = (u64)blockIdx.x * per_block; blk < n; blk += (u64)gridDim.x * per_block) {
+        K k[kHistUnroll];
+        u32 valid = 0;  // bit u: k[u] is a key
+        if (vec && n - blk >= per_block) {
+            valid = (1u << kHistUnroll) - 1;
+            if constexpr (LOAD == LOAD_PACK) {
+#pragma unroll
+                for (int h = 0; h < kHistUnroll / 4; ++h) {
+                    const u64 i = blk + (u64)h * (4 * kHistThreads) + 4 * t;
+                    const uint4 a = __ldg(reinterpret_cast<const uint4*>(in.src + i));
+                    const uint4 b = __ldg(reinterpret_cast<const uint4*>(in.dst + i));
+                    k[4 * h + 0] = (K)(((u64)a.x << 32) | b.x);
+                    k[4 * h + 1] = (K)(((u64)a.y << 32) | b.y);
+                    k[4 * h + 2] = (K)(((u64)a.z << 32) | b.z);
+                    k[4 * h + 3] = (K)(((u64)a.w << 32) | b.w);
+                }
+            } else if constexpr (sizeof(K) == 8) {
+#pragma unroll
+                for (int h = 0; h < kHistUnroll / 2; ++h) {
+                    const u64 i = blk + (u64)h * (2 * kHistThreads) + 2 * t;
+                    const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(reinterpret_cast<const u64*>(in.keys) + i));
+                    k[2 * h + 0] = (K)a.x;
+                    k[2 * h + 1] = (K)a.y;
+                }
+            } else {
+#pragma unroll
+                for (int h = 0; h < kHistUnroll / 4; ++h) {
+                    const u64 i = blk + (u64)h * (4 * kHistThreads) + 4 * t;
+                    const uint4 a = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const u32*>(in.keys) + i));
+                    k[4 * h + 0] = (K)a.x;
+                    k[4 * h + 1] = (K)a.y;
+                    k[4 * h + 2] = (K)a.z;
+                    k[4 * h + 3] = (K)a.w;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < kHistUnroll; ++u) {
+                const u64 i = blk + (u64)u * kHistThreads + t;
+                k[u] = i < n ? load_key<K, LOAD>(in, i) : (K)0;
+                valid |= (i < n ? 1u : 0u) << u;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kHistUnroll; ++u) {
+            if ((valid >> u) & 1u) {
+                const u64 kb = (u64)k[u] >> begin_bit;
+#pragma unroll
+                for (int p = 0; p < PASSES; ++p)
+                    atomicAdd(&hl[((p % kPairs) * kRadix + ((u32)(kb >> (8 * p)) & 0xFF)) * 32],
+                              p < kPairs ? 1u : 0x10000u);
+            }
+        }
+        if (++rounds == kHistRounds) {  // the same count in every thread of the CTA
+            rounds = 0;
+            __syncthreads();
+            hist_flush<PASSES>(hs, ghist);
+            __syncthreads();
+        }
     }
+    __syncthreads();
+    hist_flush<PASSES>(hs, ghist);
+}
+
+template <typename K, int LOAD, int PASSES>
+void launch_hist(const SortIn& in, u64 n, int begin_bit, u64* ghist, Tracer* tr, cudaStream_t s) {
+    const size_t hsmem = sizeof(u32) * (PASSES / 2) * kRadix * 32;
+    static int max_grid = 0;  // CTAs resident on the whole GPU
+    if (max_grid == 0) {
+        cudaFuncSetAttribute(k_sort_hist<K, LOAD, PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_hist<K, LOAD, PASSES>, kHistThreads, hsmem);
+        max_grid = std::max(1, sms * std::max(per_sm, 1));
+    }
+    const u64 blocks = (n + (u64)kHistThreads * kHistUnroll - 1) / ((u64)kHistThreads * kHistUnroll);
+    const int grid = (int)std::max<u64>(1, std::min<u64>(blocks, (u64)max_grid));
     TraceScope ts(tr, "k_sort_hist", s);
-    k_sort_hist<K, LOAD, PASSES><<<grid, kThreads, hsmem, s>>>(in, n, begin_bit, ghist);
+    k_sort_hist<K, LOAD, PASSES><<<grid, kHistThreads, hsmem, s>>>(in, n, begin_bit, ghist);
 }
 
 // bucket starts: offs[p][d] = sum of ghist[p][0..d)
@@ -572,7 +656,8 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
                                                     u64* __restrict__ head_keys, u64* __restrict__ pos,
                                                     u64* __restrict__ psum, u64* status_c,
                                                     u64* status_s, u32* tile_counter, u32 tag,
-                                                    u64* R_out, DevStats* st, u64* __restrict__ pack_out) {
+                                                    u64* R_out, DevStats* st, u64* __restrict__ pack_out,
+                                                    u32 pf_tiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RunsSmem<HAS_V>& sm = *reinterpret_cast<RunsSmem<HAS_V>*>(smem_raw);
     const u32 FULL = 0xFFFFFFFFu;
@@ -595,6 +680,23 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
             break;
         }
         const u64 tile_n = (n - base) < (u64)kTile ? (n - base) : (u64)kTile;
+
+        // the tile pf_tiles ahead is taken about one residency later: start
+        // moving it into L2 now (pf_tiles is 0 unless the inputs are 16-byte
+        // aligned)
+        if (pf_tiles && threadIdx.x == 0) {
+            const u64 pb = base + (u64)pf_tiles * kTile;
+            if (pb < n) {
+                const u64 cnt = (n - pb) < (u64)kTile ? (n - pb) : (u64)kTile;
+                constexpr u32 ksz = KEYMODE == RUN_U32 ? 4u : 8u;
+                const u32 kbytes = (u32)(cnt * ksz) & ~15u;
+                if (kbytes) bulk_prefetch_l2(reinterpret_cast<const unsigned char*>(keys) + pb * ksz, kbytes);
+                if constexpr (HAS_V && KEYMODE != RUN_HI_OF_PACKED) {
+                    const u32 vbytes = (u32)(cnt * 8u) & ~15u;
+                    if (vbytes) bulk_prefetch_l2(vals + pb, vbytes);
+                }
+            }
+        }
 
         // stage the tile: all of a thread's loads are issued before any is
         // stored, so that kItems of them are in flight at once
@@ -870,8 +972,10 @@ void launch_runs_t(const void* keys, const u64* vals, u64 n, const u64* n_dev, u
     tiles = std::min<u64>(tiles, resident);
     TraceScope ts(tr, KEYMODE == RUN_U64 ? "k_runs<links>" : (KEYMODE == RUN_SRC_OF_U64 ? "k_runs<rows>" : "k_runs<cols>"),
                   s);
+    const bool aligned = (((uintptr_t)keys | (uintptr_t)vals) & 15) == 0;
+    const u32 pf = aligned ? (u32)NS_RUNS_PF * resident : 0u;
     k_runs<KEYMODE, HAS_V><<<(unsigned)tiles, kThreads, smem, s>>>(
-        keys, vals, n, n_dev, head_keys, pos, psum, status_c, status_s, tile_counter, tag, R_out, st, pack_out);
+        keys, vals, n, n_dev, head_keys, pos, psum, status_c, status_s, tile_counter, tag, R_out, st, pack_out, pf);
 }
 
 // Diagnostics: the library's bounded waits run against something nothing
@@ -909,13 +1013,10 @@ int radix_sort_t(const SortIn& in, K* kbuf[2], u64* vbuf[2], u64 n, int begin_bi
                  SortScratch& sc, DevStats* st, cudaStream_t s) {
     cudaMemsetAsync(sc.ghist, 0, sizeof(u64) * 8 * kRadix, s);
     cudaMemsetAsync(sc.tile_counters, 0, sizeof(u32) * 8, s);
-    // three CTAs per SM, or more where that would leave a CTA 2^31 keys or more
-    const u64 hist_cap = std::max<u64>((u64)sc.sms * 3, (n >> 31) + 1);
-    const int hist_grid = (int)std::min<u64>((n + kThreads * 8 - 1) / (kThreads * 8), hist_cap);
     if (passes == 8)
-        launch_hist<K, LOAD, 8>(in, n, begin_bit, hist_grid < 1 ? 1 : hist_grid, sc.ghist, sc.tr, s);
+        launch_hist<K, LOAD, 8>(in, n, begin_bit, sc.ghist, sc.tr, s);
     else  // 4: 32-bit keys, or one half of 64-bit ones
-        launch_hist<K, LOAD, 4>(in, n, begin_bit, hist_grid < 1 ? 1 : hist_grid, sc.ghist, sc.tr, s);
+        launch_hist<K, LOAD, 4>(in, n, begin_bit, sc.ghist, sc.tr, s);
     {
         TraceScope ts(sc.tr, "k_sort_offsets", s);
         k_sort_offsets<<<1, kThreads, 0, s>>>(sc.ghist, passes, sc.offs);
