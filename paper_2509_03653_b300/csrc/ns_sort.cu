@@ -42,7 +42,11 @@ constexpr int kRadix = 256;
 #ifndef NS_ONESWEEP_PF
 #define NS_ONESWEEP_PF 1
 #endif
-// the same for the run kernels
+// rank the first pass of keys-only sorts without stability
+#ifndef NS_UNSTABLE_FIRST
+#define NS_UNSTABLE_FIRST 1
+#endif
+// L2 prefetch distance of the run kernels (as above)
 #ifndef NS_RUNS_PF
 #define NS_RUNS_PF 1
 #endif
@@ -376,12 +380,15 @@ __global__ void __launch_bounds__(kThreads) k_sort_offsets(const u64* __restrict
 // time for double buffering was measured slower: successors then wait on a
 // tile whose count cannot be published until its CTA gets to it.)
 
+typedef unsigned short WCount;  // a per-warp digit count (<= 512)
+
 template <typename K, bool HAS_V, int NT, int IT>
 struct ScatterSmem {
     static constexpr int NW = NT / 32, TILE = NT * IT;
     K keys[TILE];  // staged tile, then the tile in digit order
     u64 vals[HAS_V ? TILE : 1];
-    unsigned short whist[NW][kRadix];  // per-warp digit counts (<= 512)
+    WCount whist[NW][kRadix];  // per-warp digit counts (<= 512)
+    u32 tcount[kRadix];  // unstable ranking: the tile's digit counts, then their exclusive scan
     u64 gdelta[kRadix];  // global position of a digit's first key minus its tile-local start
     u32 wsum[NW];
     u32 total;
@@ -461,7 +468,7 @@ __device__ __forceinline__ u32 block_excl_scan_nt(u32 v, u32* wsum, u32* total) 
     return wsum[w] + x - v;
 }
 
-template <typename K, bool HAS_V, int LOAD, int NT, int IT>
+template <typename K, bool HAS_V, int LOAD, int NT, int IT, bool UNSTABLE>
 __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >= 384) ? 2 : (HAS_V ? 3 : 4))
     k_onesweep(SortIn in, K* __restrict__ kout, u64* __restrict__ vout, u64 n_arg, int shift,
                const u64* __restrict__ offs, u64* __restrict__ status, u32* tile_counter, u32 tag, DevStats* st,
@@ -486,7 +493,11 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
     // bound on n costs no empty CTAs.
     for (;;) {
         if (threadIdx.x == 0) sm.tile = atomicAdd(tile_counter, 1u);
-        for (int i = threadIdx.x; i < kWarps * kRadix; i += NT) (&sm.whist[0][0])[i] = 0;
+        if constexpr (UNSTABLE) {
+            for (int i = threadIdx.x; i < kRadix; i += NT) sm.tcount[i] = 0;
+        } else {
+            for (int i = threadIdx.x; i < kWarps * kRadix; i += NT) (&sm.whist[0][0])[i] = 0;
+        }
         __syncthreads();
         const u64 tile = sm.tile;
         const u64 base = tile * kTile;
@@ -543,8 +554,17 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
                 if constexpr (HAS_V) v[j] = 0;
             }
         }
-        // stable rank within the warp, item by item
         const u32 lt = lanemask_lt();
+        if constexpr (UNSTABLE) {
+            // any order within a digit: a slot from the tile's digit counter
+            // (shared atomics; no item waits on the previous one's result)
+#pragma unroll
+            for (int j = 0; j < kItems; ++j) {
+                const u32 li = w0 + j * 32 + lane;
+                if (li < tile_n) rank[j] = atomicAdd(&sm.tcount[(u32)(k[j] >> shift) & 0xFF], 1u);
+            }
+        } else {
+        // stable rank within the warp, item by item
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
             const u32 li = w0 + j * 32 + lane;
@@ -556,9 +576,10 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
             __syncwarp();
             if (valid) {
                 rank[j] = before + __popc(peers & lt);
-                if ((peers & lt) == 0) sm.whist[w][d] = (unsigned short)(before + __popc(peers));
+                if ((peers & lt) == 0) sm.whist[w][d] = (WCount)(before + __popc(peers));
             }
             __syncwarp();
+        }
         }
         __syncthreads();
 
@@ -566,20 +587,28 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
         const u32 d = threadIdx.x;
         u32 run = 0;
         if (d < (u32)kRadix) {
+            if constexpr (UNSTABLE) {
+                run = sm.tcount[d];
+            } else {
 #pragma unroll
-            for (int ww = 0; ww < kWarps; ++ww) {
-                const u32 c = sm.whist[ww][d];
-                sm.whist[ww][d] = (unsigned short)run;
-                run += c;
+                for (int ww = 0; ww < kWarps; ++ww) {
+                    const u32 c = sm.whist[ww][d];
+                    sm.whist[ww][d] = (WCount)run;
+                    run += c;
+                }
             }
             // publish this tile's count early so successors can proceed
             st_volatile(&status[tile * kRadix + d], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, run));
         }
         const u32 ls = block_excl_scan_nt<NT>(run, sm.wsum, &sm.total);
         if (d < (u32)kRadix) {
-            // each warp's first slot for digit d in the tile's digit order
+            if constexpr (UNSTABLE) {
+                sm.tcount[d] = ls;  // the digit's first slot in the tile's digit order
+            } else {
+                // each warp's first slot for digit d in the tile's digit order
 #pragma unroll
-            for (int ww = 0; ww < kWarps; ++ww) sm.whist[ww][d] = (unsigned short)(sm.whist[ww][d] + ls);
+                for (int ww = 0; ww < kWarps; ++ww) sm.whist[ww][d] = (WCount)(sm.whist[ww][d] + ls);
+            }
             u64 prefix = 0;
             if (tile > 0) {
                 prefix = lookback<kLookDigits>(status + d, kRadix, tile, tag, st);
@@ -595,7 +624,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
             const u32 li = w0 + j * 32 + lane;
             if (li < tile_n) {
                 const u32 dj = (u32)(k[j] >> shift) & 0xFF;
-                const u32 pos = sm.whist[w][dj] + rank[j];
+                const u32 pos = (UNSTABLE ? sm.tcount[dj] : (u32)sm.whist[w][dj]) + rank[j];
                 if (pos < (u32)kTile) {
                     sm.keys[pos] = k[j];
                     if constexpr (HAS_V) sm.vals[pos] = v[j];
@@ -907,14 +936,14 @@ constexpr const char* onesweep_name() {
     else return "k_onesweep<u64 key>";
 }
 
-template <typename K, bool HAS_V, int LOAD, int NT, int IT>
+template <typename K, bool HAS_V, int LOAD, int NT, int IT, bool UNSTABLE>
 void launch_onesweep_nt(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
                         u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s) {
     const size_t smem = sizeof(ScatterSmem<K, HAS_V, NT, IT>);
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_onesweep<K, HAS_V, LOAD, NT, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        cudaFuncSetAttribute(k_onesweep<K, HAS_V, LOAD, NT, IT, UNSTABLE>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = true;
     }
     static u32 resident = 0;  // CTAs of this instantiation resident on the whole GPU
@@ -922,7 +951,8 @@ void launch_onesweep_nt(const SortIn& in, K* kout, u64* vout, u64 n, int shift, 
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K, HAS_V, LOAD, NT, IT>, NT, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K, HAS_V, LOAD, NT, IT, UNSTABLE>, NT,
+                                                      smem);
         resident = (u32)std::max(1, sms * std::max(per_sm, 1));
     }
     constexpr u64 tile = (u64)NT * IT;
@@ -930,22 +960,28 @@ void launch_onesweep_nt(const SortIn& in, K* kout, u64* vout, u64 n, int shift, 
     if (tiles == 0) return;
     const unsigned grid = (unsigned)std::min<u64>(tiles, resident);
     TraceScope ts(tr, in.trace_name ? in.trace_name : onesweep_name<K, HAS_V>(), s);
-    k_onesweep<K, HAS_V, LOAD, NT, IT><<<grid, NT, smem, s>>>(in, kout, vout, n, shift, offs, status, tile_counter,
-                                                             tag, st, (u32)NS_ONESWEEP_PF * resident);
+    k_onesweep<K, HAS_V, LOAD, NT, IT, UNSTABLE><<<grid, NT, smem, s>>>(
+        in, kout, vout, n, shift, offs, status, tile_counter, tag, st, (u32)NS_ONESWEEP_PF * resident);
 }
 
 // Keys without values use 8192-key tiles (512 threads): half the look-back
 // hops and per-tile fixed work per key; pairs keep 4096-key tiles (their
-// shared memory would not fit twice).
+// shared memory would not fit twice).  `unstable` (keys only) ranks in any
+// order within a digit.
 template <typename K, bool HAS_V, int LOAD>
 void launch_onesweep(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
-                     u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s) {
-    if constexpr (!HAS_V)
-        launch_onesweep_nt<K, HAS_V, LOAD, NS_ONESWEEP_NT, NS_ONESWEEP_ITEMS>(in, kout, vout, n, shift, offs, status,
-                                                                              tile_counter, tag, st, tr, s);
-    else
-        launch_onesweep_nt<K, HAS_V, LOAD, 256, kItems>(in, kout, vout, n, shift, offs, status, tile_counter, tag, st,
-                                                        tr, s);
+                     u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s, bool unstable = false) {
+    if constexpr (!HAS_V) {
+        if (unstable)
+            launch_onesweep_nt<K, HAS_V, LOAD, NS_ONESWEEP_NT, NS_ONESWEEP_ITEMS, true>(
+                in, kout, vout, n, shift, offs, status, tile_counter, tag, st, tr, s);
+        else
+            launch_onesweep_nt<K, HAS_V, LOAD, NS_ONESWEEP_NT, NS_ONESWEEP_ITEMS, false>(
+                in, kout, vout, n, shift, offs, status, tile_counter, tag, st, tr, s);
+    } else {
+        launch_onesweep_nt<K, HAS_V, LOAD, 256, kItems, false>(in, kout, vout, n, shift, offs, status, tile_counter,
+                                                               tag, st, tr, s);
+    }
 }
 
 template <int KEYMODE, bool HAS_V>
@@ -1025,8 +1061,11 @@ int radix_sort_t(const SortIn& in, K* kbuf[2], u64* vbuf[2], u64 n, int begin_bi
         const u32 tag = next_tag(sc, s);
         const int shift = begin_bit + 8 * p;
         if (p == 0) {
+            // The first pass of a keys-only sort need not be stable: its
+            // input order carries no information.  (Keys equal in the sorted
+            // bits then come out in any order; no caller relies on theirs.)
             launch_onesweep<K, HAS_V, LOAD>(in, kbuf[0], vbuf[0], n, shift, sc.offs, sc.status,
-                                            sc.tile_counters + p, tag, st, sc.tr, s);
+                                            sc.tile_counters + p, tag, st, sc.tr, s, !HAS_V && NS_UNSTABLE_FIRST);
         } else {
             SortIn mid{};
             mid.keys = kbuf[(p - 1) & 1];
