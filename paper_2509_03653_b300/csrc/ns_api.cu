@@ -404,7 +404,7 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
     cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, device);
     x->sc.sms = x->sms;
     ns_status st = buf_reserve(x->ghist, 8 * 256 * sizeof(u64));
-    if (st == NS_OK) st = buf_reserve(x->offs, 8 * 256 * sizeof(u64));
+    if (st == NS_OK) st = buf_reserve(x->offs, 9 * 256 * sizeof(u64));  // [8][256] offsets + cursors
     if (st == NS_OK) st = buf_reserve(x->tcount, 16 * sizeof(u32));
     if (st == NS_OK) st = buf_reserve(x->counters, 16 * sizeof(u64));
     if (st == NS_OK && cudaMallocHost((void**)&x->host_stats, sizeof(DevStats)) != cudaSuccess)

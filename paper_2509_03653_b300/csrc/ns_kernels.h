@@ -58,7 +58,7 @@ void tracer_destroy(Tracer* t);
 // Per-context scratch of the sort path.
 struct SortScratch {
     u64* ghist;          // [8][256] digit histograms
-    u64* offs;           // [8][256] bucket starts
+    u64* offs;           // [8][256] bucket starts, then [256] slot cursors of an unstable first pass
     u64* status;         // look-back status words
     u64 status_words;
     u32* tile_counters;  // [16]

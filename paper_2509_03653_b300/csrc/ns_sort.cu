@@ -46,6 +46,13 @@ constexpr int kRadix = 256;
 #ifndef NS_UNSTABLE_FIRST
 #define NS_UNSTABLE_FIRST 1
 #endif
+// ranking of a stable digit pass: warp match, or per-bit ballots (passes in
+// the bit mask NS_BALLOT_PASSES)
+enum { RANK_MATCH = 0, RANK_BALLOT = 1, RANK_UNSTABLE = 2 };
+#ifndef NS_BALLOT_PASSES
+#define NS_BALLOT_PASSES 0x10
+#endif
+inline int pass_rank(int p) { return ((NS_BALLOT_PASSES >> p) & 1) ? RANK_BALLOT : RANK_MATCH; }
 // L2 prefetch distance of the run kernels (as above)
 #ifndef NS_RUNS_PF
 #define NS_RUNS_PF 1
@@ -358,6 +365,8 @@ void launch_hist(const SortIn& in, u64 n, int begin_bit, u64* ghist, Tracer* tr,
 }
 
 // bucket starts: offs[p][d] = sum of ghist[p][0..d)
+// and offs[8][d] = offs[0][d]: the slot cursors of a first pass ranked
+// without stability
 __global__ void __launch_bounds__(kThreads) k_sort_offsets(const u64* __restrict__ ghist, int passes,
                                                             u64* __restrict__ offs) {
     __shared__ u64 wsum[kWarps];
@@ -366,6 +375,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_offsets(const u64* __restrict
         const u64 v = ghist[p * kRadix + threadIdx.x];
         const u64 e = block_excl_scan64(v, wsum, &tot);
         offs[p * kRadix + threadIdx.x] = e;
+        if (p == 0) offs[8 * kRadix + threadIdx.x] = e;
         __syncthreads();
     }
 }
@@ -468,12 +478,13 @@ __device__ __forceinline__ u32 block_excl_scan_nt(u32 v, u32* wsum, u32* total) 
     return wsum[w] + x - v;
 }
 
-template <typename K, bool HAS_V, int LOAD, int NT, int IT, bool UNSTABLE>
+template <typename K, bool HAS_V, int LOAD, int NT, int IT, int RANK>
 __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >= 384) ? 2 : (HAS_V ? 3 : 4))
     k_onesweep(SortIn in, K* __restrict__ kout, u64* __restrict__ vout, u64 n_arg, int shift,
                const u64* __restrict__ offs, u64* __restrict__ status, u32* tile_counter, u32 tag, DevStats* st,
-               u32 pf_tiles) {
+               u32 pf_tiles, u64* __restrict__ cursor) {
     constexpr int kWarps = NT / 32, kTile = NT * IT, kItems = IT;
+    constexpr bool UNSTABLE = RANK == RANK_UNSTABLE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem<K, HAS_V, NT, IT>& sm = *reinterpret_cast<ScatterSmem<K, HAS_V, NT, IT>*>(smem_raw);
     const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -570,7 +581,20 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
             const u32 li = w0 + j * 32 + lane;
             const bool valid = li < tile_n;
             const u32 d = valid ? ((u32)(k[j] >> shift) & 0xFF) : 0x100u;
-            const u32 peers = __match_any_sync(FULL, d);
+            u32 peers;
+            if constexpr (RANK == RANK_BALLOT) {
+                // the lanes agreeing with this one on every bit of d
+                peers = __ballot_sync(FULL, valid);
+                if (!valid) peers = ~peers;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const bool bit = (d >> b) & 1u;
+                    const u32 bal = __ballot_sync(FULL, bit);
+                    peers &= bit ? bal : ~bal;
+                }
+            } else {
+                peers = __match_any_sync(FULL, d);
+            }
             u32 before = 0;
             if (valid) before = sm.whist[w][d];
             __syncwarp();
@@ -598,23 +622,31 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
                 }
             }
             // publish this tile's count early so successors can proceed
-            st_volatile(&status[tile * kRadix + d], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, run));
+            if constexpr (!UNSTABLE)
+                st_volatile(&status[tile * kRadix + d], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, run));
         }
         const u32 ls = block_excl_scan_nt<NT>(run, sm.wsum, &sm.total);
         if (d < (u32)kRadix) {
             if constexpr (UNSTABLE) {
                 sm.tcount[d] = ls;  // the digit's first slot in the tile's digit order
+                // Tiles may take their places in any order: the digit's
+                // global slots come from one atomic on its cursor (which
+                // starts at the digit's bucket start) instead of a look-back.
+                const u64 g = run ? atomicAdd(reinterpret_cast<unsigned long long*>(&cursor[d]),
+                                              (unsigned long long)run)
+                                  : 0ull;
+                sm.gdelta[d] = g - ls;  // modulo 2^64; + i below lands in range
             } else {
                 // each warp's first slot for digit d in the tile's digit order
 #pragma unroll
                 for (int ww = 0; ww < kWarps; ++ww) sm.whist[ww][d] = (WCount)(sm.whist[ww][d] + ls);
+                u64 prefix = 0;
+                if (tile > 0) {
+                    prefix = lookback<kLookDigits>(status + d, kRadix, tile, tag, st);
+                    st_volatile(&status[tile * kRadix + d], pack_status(tag, kFlagPrefix, prefix + run));
+                }
+                sm.gdelta[d] = offs[d] + prefix - ls;  // modulo 2^64; + i below lands in range
             }
-            u64 prefix = 0;
-            if (tile > 0) {
-                prefix = lookback<kLookDigits>(status + d, kRadix, tile, tag, st);
-                st_volatile(&status[tile * kRadix + d], pack_status(tag, kFlagPrefix, prefix + run));
-            }
-            sm.gdelta[d] = offs[d] + prefix - ls;  // modulo 2^64; + i below lands in range
         }
         __syncthreads();
 
@@ -936,13 +968,13 @@ constexpr const char* onesweep_name() {
     else return "k_onesweep<u64 key>";
 }
 
-template <typename K, bool HAS_V, int LOAD, int NT, int IT, bool UNSTABLE>
+template <typename K, bool HAS_V, int LOAD, int NT, int IT, int RANK>
 void launch_onesweep_nt(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
-                        u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s) {
+                        u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s, u64* cursor) {
     const size_t smem = sizeof(ScatterSmem<K, HAS_V, NT, IT>);
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_onesweep<K, HAS_V, LOAD, NT, IT, UNSTABLE>,
+        cudaFuncSetAttribute(k_onesweep<K, HAS_V, LOAD, NT, IT, RANK>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = true;
     }
@@ -951,7 +983,7 @@ void launch_onesweep_nt(const SortIn& in, K* kout, u64* vout, u64 n, int shift, 
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K, HAS_V, LOAD, NT, IT, UNSTABLE>, NT,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K, HAS_V, LOAD, NT, IT, RANK>, NT,
                                                       smem);
         resident = (u32)std::max(1, sms * std::max(per_sm, 1));
     }
@@ -960,28 +992,44 @@ void launch_onesweep_nt(const SortIn& in, K* kout, u64* vout, u64 n, int shift, 
     if (tiles == 0) return;
     const unsigned grid = (unsigned)std::min<u64>(tiles, resident);
     TraceScope ts(tr, in.trace_name ? in.trace_name : onesweep_name<K, HAS_V>(), s);
-    k_onesweep<K, HAS_V, LOAD, NT, IT, UNSTABLE><<<grid, NT, smem, s>>>(
-        in, kout, vout, n, shift, offs, status, tile_counter, tag, st, (u32)NS_ONESWEEP_PF * resident);
+    k_onesweep<K, HAS_V, LOAD, NT, IT, RANK><<<grid, NT, smem, s>>>(
+        in, kout, vout, n, shift, offs, status, tile_counter, tag, st, (u32)NS_ONESWEEP_PF * resident, cursor);
 }
 
 // Keys without values use 8192-key tiles (512 threads): half the look-back
 // hops and per-tile fixed work per key; pairs keep 4096-key tiles (their
-// shared memory would not fit twice).  `unstable` (keys only) ranks in any
-// order within a digit.
+// shared memory would not fit twice).  `rank` picks the ranking (RANK_*;
+// RANK_UNSTABLE for keys only).
+// `cursor` (RANK_UNSTABLE only): per digit, the next free global slot.
+template <typename K, bool HAS_V, int LOAD, int NT, int IT>
+void launch_onesweep_rank(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
+                          u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s, int rank,
+                          u64* cursor) {
+    if constexpr (!HAS_V) {
+        if (rank == RANK_UNSTABLE) {
+            launch_onesweep_nt<K, HAS_V, LOAD, NT, IT, RANK_UNSTABLE>(in, kout, vout, n, shift, offs, status,
+                                                                       tile_counter, tag, st, tr, s, cursor);
+            return;
+        }
+    }
+    if (rank == RANK_BALLOT)
+        launch_onesweep_nt<K, HAS_V, LOAD, NT, IT, RANK_BALLOT>(in, kout, vout, n, shift, offs, status,
+                                                                 tile_counter, tag, st, tr, s, nullptr);
+    else
+        launch_onesweep_nt<K, HAS_V, LOAD, NT, IT, RANK_MATCH>(in, kout, vout, n, shift, offs, status, tile_counter,
+                                                                tag, st, tr, s, nullptr);
+}
+
 template <typename K, bool HAS_V, int LOAD>
 void launch_onesweep(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
-                     u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s, bool unstable = false) {
-    if constexpr (!HAS_V) {
-        if (unstable)
-            launch_onesweep_nt<K, HAS_V, LOAD, NS_ONESWEEP_NT, NS_ONESWEEP_ITEMS, true>(
-                in, kout, vout, n, shift, offs, status, tile_counter, tag, st, tr, s);
-        else
-            launch_onesweep_nt<K, HAS_V, LOAD, NS_ONESWEEP_NT, NS_ONESWEEP_ITEMS, false>(
-                in, kout, vout, n, shift, offs, status, tile_counter, tag, st, tr, s);
-    } else {
-        launch_onesweep_nt<K, HAS_V, LOAD, 256, kItems, false>(in, kout, vout, n, shift, offs, status, tile_counter,
-                                                               tag, st, tr, s);
-    }
+                     u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s, int rank,
+                     u64* cursor = nullptr) {
+    if constexpr (!HAS_V)
+        launch_onesweep_rank<K, HAS_V, LOAD, NS_ONESWEEP_NT, NS_ONESWEEP_ITEMS>(
+            in, kout, vout, n, shift, offs, status, tile_counter, tag, st, tr, s, rank, cursor);
+    else
+        launch_onesweep_rank<K, HAS_V, LOAD, 256, kItems>(in, kout, vout, n, shift, offs, status, tile_counter, tag,
+                                                          st, tr, s, rank, cursor);
 }
 
 template <int KEYMODE, bool HAS_V>
@@ -1065,7 +1113,9 @@ int radix_sort_t(const SortIn& in, K* kbuf[2], u64* vbuf[2], u64 n, int begin_bi
             // input order carries no information.  (Keys equal in the sorted
             // bits then come out in any order; no caller relies on theirs.)
             launch_onesweep<K, HAS_V, LOAD>(in, kbuf[0], vbuf[0], n, shift, sc.offs, sc.status,
-                                            sc.tile_counters + p, tag, st, sc.tr, s, !HAS_V && NS_UNSTABLE_FIRST);
+                                            sc.tile_counters + p, tag, st, sc.tr, s,
+                                            !HAS_V && NS_UNSTABLE_FIRST ? RANK_UNSTABLE : pass_rank(0),
+                                            sc.offs + 8 * kRadix);
         } else {
             SortIn mid{};
             mid.keys = kbuf[(p - 1) & 1];
@@ -1076,7 +1126,7 @@ int radix_sort_t(const SortIn& in, K* kbuf[2], u64* vbuf[2], u64 n, int begin_bi
             // stage with bulk copies only from 16-byte-aligned addresses
             mid.bulk = (((uintptr_t)kbuf[(p - 1) & 1] | (uintptr_t)vbuf[(p - 1) & 1]) & 15) == 0;
             launch_onesweep<K, HAS_V, LOAD_KEYS>(mid, kbuf[p & 1], vbuf[p & 1], n, shift, sc.offs + p * kRadix,
-                                                 sc.status, sc.tile_counters + p, tag, st, sc.tr, s);
+                                                 sc.status, sc.tile_counters + p, tag, st, sc.tr, s, pass_rank(p));
         }
     }
     return (passes - 1) & 1;
