@@ -60,7 +60,7 @@ inline int pass_rank(int p) { return ((NS_BALLOT_PASSES >> p) & 1) ? RANK_BALLOT
 
 constexpr u64 kFlagAgg = 1, kFlagPrefix = 2;
 #ifndef NS_LOOK_DIGITS
-#define NS_LOOK_DIGITS 1
+#define NS_LOOK_DIGITS 3
 #endif
 constexpr int kLookDigits = NS_LOOK_DIGITS;  // look-back window of the digit passes
 constexpr u64 kValMask = (1ull << 46) - 1;
@@ -77,10 +77,9 @@ __device__ __forceinline__ u64 pack_status(u32 tag, u64 flag, u64 v) {
 // 2^30 keys), so the walk reads WIN predecessors per round trip (independent
 // loads) and sums aggregates until it meets a prefix.  A predecessor that has
 // published nothing yet is waited for (bounded), then the walk resumes from
-// it.  The digit passes walk one word at a time (their digit threads hold
-// the tile's keys in registers, which a wider window would spill; measured
-// no faster in any arrangement tried); the run kernels' single look-back
-// thread reads 8 at a time.
+// it.  The digit passes read 3 words per round trip (their digit threads
+// hold the tile's keys in registers: 4 or more spill, and 1 or 2 were
+// slower); the run kernels walk with a whole warp (warp_lookback).
 template <int WIN>
 __device__ u64 lookback(u64* status, u64 stride, u64 tile, u32 tag, DevStats* st) {
     constexpr int kLookWindow = WIN;
