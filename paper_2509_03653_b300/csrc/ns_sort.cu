@@ -689,12 +689,32 @@ __device__ __forceinline__ u64 run_key(const void* keys, u64 i) {
     else return reinterpret_cast<const u32*>(keys)[i];
 }
 
+// Run-kernel CTA shape: threads and keys per thread.  Keys alone take
+// 8192-key tiles (fewer look-backs per key); with values, 2048-key tiles
+// (the registers that stage a tile otherwise halve the resident CTAs).
+#ifndef NS_RUNS_NT
+#define NS_RUNS_NT 512
+#endif
+#ifndef NS_RUNS_VNT
+#define NS_RUNS_VNT 256
+#endif
+#ifndef NS_RUNS_VITEMS
+#define NS_RUNS_VITEMS 8
+#endif
+template <bool HAS_V>
+struct RunShape {
+    static constexpr int threads = HAS_V ? NS_RUNS_VNT : NS_RUNS_NT;
+    static constexpr int items = HAS_V ? NS_RUNS_VITEMS : kItems;
+    static constexpr int warps = threads / 32;
+    static constexpr int tile = threads * items;
+};
+
 template <bool HAS_V>
 struct RunsSmem {
-    u64 key[kTile + 1];         // key[0] = the element before the tile
-    u64 val[HAS_V ? kTile : 1];
-    u32 wcnt[kWarps];           // heads per warp -> exclusive offsets
-    u64 wsum[kWarps];           // value sums per warp -> exclusive offsets
+    u64 key[RunShape<HAS_V>::tile + 1];  // key[0] = the element before the tile
+    u64 val[HAS_V ? RunShape<HAS_V>::tile : 1];
+    u32 wcnt[RunShape<HAS_V>::warps];    // heads per warp -> exclusive offsets
+    u64 wsum[RunShape<HAS_V>::warps];    // value sums per warp -> exclusive offsets
     u64 cbase, sbase, tot64;
     u32 tot;
     u32 tile;
@@ -704,13 +724,13 @@ struct RunsSmem {
 //   pos[r] = i, psum[r] = sum of val[0..i) (if HAS_V), head_keys[r] = key(i)
 // and finally pos[R] = n, psum[R] = total, *R_out = R.
 //
-// Warp w owns the tile's items [512 w, 512 w + 512), visited as 16 rounds
+// Warp w owns the tile's kRunItems * 32 items from 32 kRunItems w, visited as kRunItems rounds
 // of 32 consecutive items, so every shared-memory access is consecutive
 // across the lanes; heads are counted with ballots, value prefixes with
 // shuffle scans.  Two sweeps over the tile: count, then (after the tile's
 // offsets are known by look-back) write.
 template <int KEYMODE, bool HAS_V>
-__global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys,
+__global__ void __launch_bounds__(RunShape<HAS_V>::threads) k_runs(const void* __restrict__ keys,
                                                     const u64* __restrict__ vals, u64 n_arg,
                                                     const u64* __restrict__ n_dev,
                                                     u64* __restrict__ head_keys, u64* __restrict__ pos,
@@ -718,6 +738,8 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
                                                     u64* status_s, u32* tile_counter, u32 tag,
                                                     u64* R_out, DevStats* st, u64* __restrict__ pack_out,
                                                     u32 pf_tiles) {
+    constexpr int kRunThreads = RunShape<HAS_V>::threads, kRunWarps = RunShape<HAS_V>::warps,
+                  kRunTile = RunShape<HAS_V>::tile, kRunItems = RunShape<HAS_V>::items;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RunsSmem<HAS_V>& sm = *reinterpret_cast<RunsSmem<HAS_V>*>(smem_raw);
     const u32 FULL = 0xFFFFFFFFu;
@@ -729,7 +751,7 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
         if (threadIdx.x == 0) sm.tile = atomicAdd(tile_counter, 1u);
         __syncthreads();
         const u64 tile = sm.tile;
-        const u64 base = tile * kTile;
+        const u64 base = tile * kRunTile;
         if (base >= n) {
             // an empty sequence still needs its terminal entry
             if (n == 0 && tile == 0 && threadIdx.x == 0) {
@@ -739,15 +761,15 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
             }
             break;
         }
-        const u64 tile_n = (n - base) < (u64)kTile ? (n - base) : (u64)kTile;
+        const u64 tile_n = (n - base) < (u64)kRunTile ? (n - base) : (u64)kRunTile;
 
         // the tile pf_tiles ahead is taken about one residency later: start
         // moving it into L2 now (pf_tiles is 0 unless the inputs are 16-byte
         // aligned)
         if (pf_tiles && threadIdx.x == 0) {
-            const u64 pb = base + (u64)pf_tiles * kTile;
+            const u64 pb = base + (u64)pf_tiles * kRunTile;
             if (pb < n) {
-                const u64 cnt = (n - pb) < (u64)kTile ? (n - pb) : (u64)kTile;
+                const u64 cnt = (n - pb) < (u64)kRunTile ? (n - pb) : (u64)kRunTile;
                 constexpr u32 ksz = KEYMODE == RUN_U32 ? 4u : 8u;
                 const u32 kbytes = (u32)(cnt * ksz) & ~15u;
                 if (kbytes) bulk_prefetch_l2(reinterpret_cast<const unsigned char*>(keys) + pb * ksz, kbytes);
@@ -759,12 +781,12 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
         }
 
         // stage the tile: all of a thread's loads are issued before any is
-        // stored, so that kItems of them are in flight at once
+        // stored, so that kRunItems of them are in flight at once
         {
-            u64 wd[kItems], vv[kItems];
+            u64 wd[kRunItems], vv[kRunItems];
 #pragma unroll
-            for (int r = 0; r < kItems; ++r) {
-                const u32 i = threadIdx.x + r * kThreads;
+            for (int r = 0; r < kRunItems; ++r) {
+                const u32 i = threadIdx.x + r * kRunThreads;
                 wd[r] = vv[r] = 0;
                 if (i < tile_n) {
                     if constexpr (KEYMODE == RUN_U32) wd[r] = reinterpret_cast<const u32*>(keys)[base + i];
@@ -773,8 +795,8 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
                 }
             }
 #pragma unroll
-            for (int r = 0; r < kItems; ++r) {
-                const u32 i = threadIdx.x + r * kThreads;
+            for (int r = 0; r < kRunItems; ++r) {
+                const u32 i = threadIdx.x + r * kRunThreads;
                 if (i < tile_n) {
                     if constexpr (KEYMODE == RUN_HI_OF_PACKED) {
                         sm.key[i + 1] = wd[r] >> 32;
@@ -796,11 +818,11 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
         __syncthreads();
 
         // sweep 1: heads and value sums per warp
-        const u32 w0 = w * (kItems * 32);
+        const u32 w0 = w * (kRunItems * 32);
         u32 cnt = 0;
         u64 vs = 0;
 #pragma unroll 4
-        for (int r = 0; r < kItems; ++r) {
+        for (int r = 0; r < kRunItems; ++r) {
             const u32 li = w0 + r * 32 + lane;
             bool h = false;
             if (li < tile_n) {
@@ -821,7 +843,7 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
         if (threadIdx.x == 0) {
             u32 c = 0;
             u64 s = 0;
-            for (int i = 0; i < kWarps; ++i) {
+            for (int i = 0; i < kRunWarps; ++i) {
                 const u32 tc = sm.wcnt[i];
                 sm.wcnt[i] = c;
                 c += tc;
@@ -863,7 +885,7 @@ __global__ void __launch_bounds__(kThreads) k_runs(const void* __restrict__ keys
         u64 s_run = HAS_V ? sm.sbase + sm.wsum[w] : 0;
         const u32 lt = lanemask_lt();
 #pragma unroll 4
-        for (int r = 0; r < kItems; ++r) {
+        for (int r = 0; r < kRunItems; ++r) {
             const u32 li = w0 + r * 32 + lane;
             bool h = false;
             u64 v = 0;
@@ -1035,6 +1057,7 @@ template <int KEYMODE, bool HAS_V>
 void launch_runs_t(const void* keys, const u64* vals, u64 n, const u64* n_dev, u64* head_keys, u64* pos, u64* psum,
                    u64* status_c, u64* status_s, u32* tile_counter, u32 tag, u64* R_out, DevStats* st,
                    Tracer* tr, cudaStream_t s, u64* pack_out) {
+    constexpr int kRunThreads = RunShape<HAS_V>::threads, kRunTile = RunShape<HAS_V>::tile;
     const size_t smem = sizeof(RunsSmem<HAS_V>);
     static bool configured = false;
     if (!configured) {
@@ -1047,17 +1070,17 @@ void launch_runs_t(const void* keys, const u64* vals, u64 n, const u64* n_dev, u
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_runs<KEYMODE, HAS_V>, kThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_runs<KEYMODE, HAS_V>, kRunThreads, smem);
         resident = (u32)std::max(1, sms * std::max(per_sm, 1));
     }
-    u64 tiles = (n + kTile - 1) / kTile;
+    u64 tiles = (n + kRunTile - 1) / kRunTile;
     if (tiles == 0) tiles = 1;
     tiles = std::min<u64>(tiles, resident);
     TraceScope ts(tr, KEYMODE == RUN_U64 ? "k_runs<links>" : (KEYMODE == RUN_SRC_OF_U64 ? "k_runs<rows>" : "k_runs<cols>"),
                   s);
     const bool aligned = (((uintptr_t)keys | (uintptr_t)vals) & 15) == 0;
     const u32 pf = aligned ? (u32)NS_RUNS_PF * resident : 0u;
-    k_runs<KEYMODE, HAS_V><<<(unsigned)tiles, kThreads, smem, s>>>(
+    k_runs<KEYMODE, HAS_V><<<(unsigned)tiles, kRunThreads, smem, s>>>(
         keys, vals, n, n_dev, head_keys, pos, psum, status_c, status_s, tile_counter, tag, R_out, st, pack_out, pf);
 }
 
