@@ -120,17 +120,20 @@ void launch_batch_insert(const BatchDev& B, u32* tile_counter, u64 total_tiles, 
 void launch_batch_stats_out(const DevStats* wstats, u64 W, u64* out, int sms, cudaStream_t s);
 
 // sort path (ns_sort.cu).  Each radix sort returns the index of kbuf/vbuf
-// holding the result.  n is an upper bound when n_dev is given.
+// holding the result.  n is an upper bound when n_dev is given.  Sorts with
+// values are stable; keys-only sorts order only the sorted bits.
 int radix_sort_packets(const u32* src, const u32* dst, u64* kbuf[2], u64 n,
                        SortScratch& sc, DevStats* st, cudaStream_t s);
 int radix_sort_pairs64(const u64* keys, const u64* vals, const u64* n_dev,
                        u64* kbuf[2], u64* vbuf[2], u64 n, SortScratch& sc,
                        DevStats* st, cudaStream_t s);
 // Sorts n_dev (<= n) u64 words by their upper 32 bits (four 8-bit digit
-// passes, stable); returns the index of the buffer holding the result.
+// passes; words with equal upper halves come out in any order, since the
+// first pass keeps none); returns the index of the buffer holding the result.
+// Keys-only sorts below share this: only the sorted bits are ordered.
 int radix_sort_hi32(const u64* packed, const u64* n_dev, u64* kbuf[2], u64 n, SortScratch& sc, DevStats* st,
                     cudaStream_t s);
-// n_dev (<= n) uint32 keys (four 8-bit digit passes, stable).
+// n_dev (<= n) uint32 keys (four 8-bit digit passes).
 int radix_sort_u32(const u32* keys, const u64* n_dev, u32* kbuf[2], u64 n, SortScratch& sc, DevStats* st,
                    cudaStream_t s);
 // The same by their lower 32 bits (words holding one uint32 each).

@@ -7,7 +7,10 @@
 //    per-digit offsets by decoupled look-back over its predecessors' published
 //    counts, and scatters.  Tile ids are handed out in launch order, so every
 //    predecessor a tile waits on is already resident; each wait is bounded
-//    and records ERR_TIMEOUT instead of spinning forever.
+//    and records ERR_TIMEOUT instead of spinning forever.  The first pass of
+//    a keys-only sort keeps no order within a digit: it ranks with shared
+//    atomics and takes its global slots from per-digit cursors, with no
+//    look-back.
 //  * Run kernels: over a sorted sequence, emit each run's first position, its
 //    key and the exclusive prefix sum of a value column at that position;
 //    run lengths and run sums are then differences of neighbours.  This one
