@@ -242,3 +242,26 @@ def test_slide_512_windows_k8():
         assert {f: int(x) for f, x in zip(oracle.FIELDS, rs[w])} == oracle.stats_of_packets(s[a:b], d[a:b]), w
         c = w * WIN
         assert {f: int(x) for f, x in zip(oracle.FIELDS, rw[w])} == oracle.stats_of_packets(s[c:c + WIN], d[c:c + WIN]), w
+
+
+def test_sort_one_repeated_key_2p28():
+    """2^28 copies of one packet through the sort path: the closed form
+    (N, 1, 1, 1, N, 1, N, 1) with max link N, and A = [(key, N)].  At this
+    size every histogram CTA flushes its shared counters mid-launch, and
+    each 16-bit half reaches its bound (one digit value takes every count);
+    the stable passes see one digit per warp and the unstable first pass
+    sends every key to one cursor."""
+    N = 1 << 28
+    s_val, d_val = 0xDEADBEEF, 0x12345678
+    ds = torch.full((N,), s_val - (1 << 32), dtype=torch.int32, device="cuda")
+    dd = torch.full((N,), d_val, dtype=torch.int32, device="cuda")
+    ctx = ns.Context(0, path="sort")
+    m = ns.Matrix(ctx)
+    ns.window_build(ctx, ds, dd, m)
+    st = ns.network_stats(ctx, m)
+    assert st == {"valid_packets": N, "unique_links": 1, "unique_sources": 1, "unique_destinations": 1,
+                  "max_src_packets": N, "max_src_fanout": 1, "max_dst_packets": N, "max_dst_fanin": 1,
+                  "max_link_packets": N}
+    k, c = export_np(m)
+    np.testing.assert_array_equal(k, np.array([(s_val << 32) | d_val], dtype=np.uint64))
+    np.testing.assert_array_equal(c, np.array([N], dtype=np.uint64))

@@ -1,7 +1,7 @@
 """Parity of the CUDA path with the CPU oracle, element by element.
 
 Every quantity and A's sorted nonzero list must match bit-exactly (all values
-are uint64 counts).  Sizes span several 4096-element tiles with ragged tails;
+are uint64 counts).  Sizes span several tiles with ragged tails;
 edge cases cover the empty window, one packet, a single repeated key, the
 extreme keys 0 and 2^64-1, a star, self-loops and an all-distinct window.
 Both aggregation paths (sort, hash) are checked, the sort path in both of
@@ -25,7 +25,7 @@ pytestmark = pytest.mark.gpu
 # "sort_pairs": the sort path with its per-destination side forced onto
 # (dst, count) pairs, the form it takes from 2^32 packets on.  "hash_dense":
 # the hash path with tables sized at load 0.9, so that probe sequences run
-# long and the read-ahead probing is exercised throughout.
+# long throughout.
 PATHS = ["hash", "sort", "sort_pairs", "hash_dense"]
 
 
