@@ -21,6 +21,9 @@
 // Status words for look-back: tag(16) | flag(2) | value(46).  The tag is a
 // per-launch number, so a status array never needs clearing between launches.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "ns_common.cuh"
 #include "ns_kernels.h"
@@ -28,6 +31,29 @@
 namespace ns {
 
 namespace {
+
+// CTAs of kernel `fn` (at `threads` threads and `smem` dynamic shared bytes)
+// resident at once on the whole current GPU.  The first call for a kernel on
+// a device also lets it take that much shared memory there (the attribute is
+// per device).  Cached per (kernel, device); callers on several host threads
+// or devices are safe.
+int resident_ctas(const void* fn, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(fn, dev);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int sms = 0, per_sm = 0;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+    const int r = std::max(1, sms * std::max(per_sm, 1));
+    cache[key] = r;
+    return r;
+}
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
@@ -351,15 +377,7 @@ __global__ void __launch_bounds__(kHistThreads, 1) k_sort_hist(SortIn in, u64 n_
 template <typename K, int LOAD, int PASSES>
 void launch_hist(const SortIn& in, u64 n, int begin_bit, u64* ghist, Tracer* tr, cudaStream_t s) {
     const size_t hsmem = sizeof(u32) * (PASSES / 2) * kRadix * 32;
-    static int max_grid = 0;  // CTAs resident on the whole GPU
-    if (max_grid == 0) {
-        cudaFuncSetAttribute(k_sort_hist<K, LOAD, PASSES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_hist<K, LOAD, PASSES>, kHistThreads, hsmem);
-        max_grid = std::max(1, sms * std::max(per_sm, 1));
-    }
+    const int max_grid = resident_ctas((const void*)k_sort_hist<K, LOAD, PASSES>, kHistThreads, hsmem);
     const u64 blocks = (n + (u64)kHistThreads * kHistUnroll - 1) / ((u64)kHistThreads * kHistUnroll);
     const int grid = (int)std::max<u64>(1, std::min<u64>(blocks, (u64)max_grid));
     TraceScope ts(tr, "k_sort_hist", s);
@@ -996,21 +1014,7 @@ template <typename K, bool HAS_V, int LOAD, int NT, int IT, int RANK>
 void launch_onesweep_nt(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
                         u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s, u64* cursor) {
     const size_t smem = sizeof(ScatterSmem<K, HAS_V, NT, IT>);
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_onesweep<K, HAS_V, LOAD, NT, IT, RANK>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = true;
-    }
-    static u32 resident = 0;  // CTAs of this instantiation resident on the whole GPU
-    if (resident == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K, HAS_V, LOAD, NT, IT, RANK>, NT,
-                                                      smem);
-        resident = (u32)std::max(1, sms * std::max(per_sm, 1));
-    }
+    const u32 resident = (u32)resident_ctas((const void*)k_onesweep<K, HAS_V, LOAD, NT, IT, RANK>, NT, smem);
     constexpr u64 tile = (u64)NT * IT;
     const u64 tiles = (n + tile - 1) / tile;
     if (tiles == 0) return;
@@ -1062,20 +1066,7 @@ void launch_runs_t(const void* keys, const u64* vals, u64 n, const u64* n_dev, u
                    Tracer* tr, cudaStream_t s, u64* pack_out) {
     constexpr int kRunThreads = RunShape<HAS_V>::threads, kRunTile = RunShape<HAS_V>::tile;
     const size_t smem = sizeof(RunsSmem<HAS_V>);
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_runs<KEYMODE, HAS_V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        configured = true;
-    }
-    static u32 resident = 0;  // CTAs of this instantiation resident on the whole GPU
-    if (resident == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_runs<KEYMODE, HAS_V>, kRunThreads, smem);
-        resident = (u32)std::max(1, sms * std::max(per_sm, 1));
-    }
+    const u32 resident = (u32)resident_ctas((const void*)k_runs<KEYMODE, HAS_V>, kRunThreads, smem);
     u64 tiles = (n + kRunTile - 1) / kRunTile;
     if (tiles == 0) tiles = 1;
     tiles = std::min<u64>(tiles, resident);

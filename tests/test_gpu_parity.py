@@ -297,6 +297,45 @@ def test_skewed_windows_cache_modes(cache, s_exp, K, n):
     assert_matrix_equal(acc, *want)
 
 
+def test_sort_contexts_on_two_host_threads():
+    """Two host threads, each with its own sort-path context, build windows at
+    the same time.  The library's per-kernel launch shapes are shared between
+    them (and locked); every result must equal the oracle's."""
+    import threading
+    cases = [W.zipf_window(300007, 1.1, 1 << 14, 0xA11CE), W.zipf_window(500009, 1.3, 1 << 16, 0xB0B)]
+    devs = [(to_dev(s), to_dev(d)) for s, d in cases]
+    torch.cuda.synchronize()
+    results, errors = [None, None], []
+
+    def work(t):
+        try:
+            ctx = ns.Context(0, path="sort")
+            out = []
+            for _ in range(3):
+                m = ns.Matrix(ctx)
+                ns.window_build(ctx, devs[t][0], devs[t][1], m)
+                out.append((ns.network_stats(ctx, m), export_np(m)))
+                m.free()
+            ctx.close()
+            results[t] = out
+        except Exception as e:  # reported below, on the test's thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(t,)) for t in range(2)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    for t, (s, d) in enumerate(cases):
+        wk, wc = oracle.build_matrix(s, d)
+        want = oracle.stats(wk, wc)
+        for st, (k, c) in results[t]:
+            assert st == want
+            np.testing.assert_array_equal(k, wk)
+            np.testing.assert_array_equal(c, wc)
+
+
 @pytest.mark.parametrize("which", [0, 1, 2])
 def test_bounded_device_waits_time_out(which):
     """A look-back on a status word nobody publishes (one thread, and a whole
