@@ -406,9 +406,12 @@ __global__ void __launch_bounds__(kThreads) k_sort_offsets(const u64* __restrict
 // The tile is staged into shared memory by the bulk-copy engine (no register
 // is held while it streams in), ranked stably per warp, given its global
 // per-digit offsets by decoupled look-back, placed in digit order in the same
-// buffer and written out in digit runs.  (Reserving a second tile ahead of
-// time for double buffering was measured slower: successors then wait on a
-// tile whose count cannot be published until its CTA gets to it.)
+// buffer and written out in digit runs.  With RANK_UNSTABLE (the first pass
+// of a keys-only sort) the ranks come from shared atomics on the tile's digit
+// counters and the global offsets from per-digit cursors instead.
+// (Reserving a second tile ahead of time for double buffering was measured
+// slower: successors then wait on a tile whose count cannot be published
+// until its CTA gets to it.)
 
 typedef unsigned short WCount;  // a per-warp digit count (<= 512)
 
