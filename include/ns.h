@@ -116,9 +116,11 @@ typedef struct {
 
 /* ---- context ----------------------------------------------------------- */
 
-/* Creates a context on CUDA device `device` (which becomes current on the
- * calling thread).  cfg may be NULL for defaults.  *ctx is owned by the
- * caller and released with ns_destroy. */
+/* Creates a context on CUDA device `device`.  cfg may be NULL for defaults.
+ * *ctx is owned by the caller and released with ns_destroy.  Every call that
+ * takes a context, or an object made from one, runs on the context's device
+ * and leaves the calling thread's current device as it found it; streams
+ * passed in must belong to that device. */
 ns_status ns_create(ns_ctx** ctx, const ns_config* cfg, int device);
 
 /* Waits for the context's own work, frees everything it owns (matrices

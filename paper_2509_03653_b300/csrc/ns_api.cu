@@ -163,6 +163,7 @@ ns_status hash_grow(ns_matrix* m, u64 extra, cudaStream_t s) {
     // rehash: rebuild rows/cols/statistics from the link entries
     ns_matrix tmp;
     tmp.ctx = m->ctx;
+    tmp.device = m->device;
     tmp.stats = m->stats;
     tmp.node_limit = m->node_limit;
     TRY(hash_alloc(&tmp, actual + extra));
@@ -392,6 +393,7 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
     if (c.hash_load == 0.0) c.hash_load = 0.5;
     if (!(c.hash_load >= 0.05 && c.hash_load <= 0.9))
         return fail(NS_ERR_INVALID, "ns_create: hash_load %g outside [0.05, 0.9]", c.hash_load);
+    DeviceGuard device_guard(device);
     CK(cudaSetDevice(device));
     ns_ctx* x = new ns_ctx();
     x->device = device;
@@ -426,7 +428,7 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
 
 void ns_destroy(ns_ctx* c) {
     if (!c) return;
-    cudaSetDevice(c->device);
+    DeviceGuard device_guard(c->device);
     cudaDeviceSynchronize();
     Buf* all[] = {&c->ghist, &c->offs, &c->tcount, &c->counters, &c->status, &c->k64[0], &c->k64[1],
                   &c->pos, &c->psum, &c->k32[0], &c->k32[1], &c->v64[0], &c->v64[1], &c->xk, &c->xv};
@@ -438,14 +440,17 @@ void ns_destroy(ns_ctx* c) {
 
 ns_status ns_sync(ns_ctx* c, ns_stream_t stream) {
     if (!c) return fail(NS_ERR_INVALID, "ns_sync: NULL context");
+    DeviceGuard device_guard(c->device);
     CK(cudaStreamSynchronize((cudaStream_t)stream));
     return check_launch();
 }
 
 ns_status ns_matrix_create(ns_ctx* c, ns_matrix** out) {
     if (!c || !out) return fail(NS_ERR_INVALID, "ns_matrix_create: NULL argument");
+    DeviceGuard device_guard(c->device);
     ns_matrix* m = new ns_matrix();
     m->ctx = c;
+    m->device = c->device;
     ns_status st = buf_reserve(m->stats, sizeof(DevStats));
     if (st == NS_OK && cudaMemset(m->stats.p, 0, sizeof(DevStats)) != cudaSuccess)
         st = fail(NS_ERR_CUDA, "cudaMemset failed");
@@ -459,6 +464,7 @@ ns_status ns_matrix_create(ns_ctx* c, ns_matrix** out) {
 
 ns_status ns_matrix_reserve(ns_matrix* m, uint64_t max_links, ns_stream_t stream) {
     if (!m) return fail(NS_ERR_INVALID, "ns_matrix_reserve: NULL matrix");
+    DeviceGuard device_guard(m->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (m->fmt == FMT_EMPTY) {
         TRY(hash_alloc(m, max_links));
@@ -473,6 +479,7 @@ ns_status ns_matrix_reserve(ns_matrix* m, uint64_t max_links, ns_stream_t stream
 
 ns_status ns_matrix_reserve_ex(ns_matrix* m, uint64_t max_links, uint64_t max_nodes, ns_stream_t stream) {
     if (!m) return fail(NS_ERR_INVALID, "ns_matrix_reserve_ex: NULL matrix");
+    DeviceGuard device_guard(m->device);
     if (m->fmt != FMT_EMPTY) return fail(NS_ERR_STATE, "ns_matrix_reserve_ex: matrix is not empty");
     m->node_limit = max_nodes;
     return ns_matrix_reserve(m, max_links, stream);
@@ -480,6 +487,7 @@ ns_status ns_matrix_reserve_ex(ns_matrix* m, uint64_t max_links, uint64_t max_no
 
 ns_status ns_matrix_clear(ns_matrix* m, ns_stream_t stream) {
     if (!m) return fail(NS_ERR_INVALID, "ns_matrix_clear: NULL matrix");
+    DeviceGuard device_guard(m->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (m->fmt == FMT_HASH) {
         TRY(hash_clear(m, s));
@@ -493,6 +501,7 @@ ns_status ns_matrix_clear(ns_matrix* m, ns_stream_t stream) {
 
 void ns_matrix_free(ns_matrix* m) {
     if (!m) return;
+    DeviceGuard device_guard(m->device);
     cudaDeviceSynchronize();
     buf_free(m->links);
     buf_free(m->rows);
@@ -505,6 +514,7 @@ void ns_matrix_free(ns_matrix* m) {
 
 ns_status ns_matrix_nnz(const ns_matrix* m, uint64_t* h_nnz, ns_stream_t stream) {
     if (!m || !h_nnz) return fail(NS_ERR_INVALID, "ns_matrix_nnz: NULL argument");
+    DeviceGuard device_guard(m->device);
     DevStats ds;
     ns_status st = read_stats(m, (cudaStream_t)stream, &ds);
     *h_nnz = ds.v[S_LINKS];
@@ -514,6 +524,7 @@ ns_status ns_matrix_nnz(const ns_matrix* m, uint64_t* h_nnz, ns_stream_t stream)
 ns_status ns_matrix_export(const ns_matrix* m, uint64_t* d_keys, uint64_t* d_counts, uint64_t cap,
                            uint64_t* h_nnz, ns_stream_t stream) {
     if (!m || !h_nnz) return fail(NS_ERR_INVALID, "ns_matrix_export: NULL argument");
+    DeviceGuard device_guard(m->device);
     cudaStream_t s = (cudaStream_t)stream;
     DevStats ds;
     TRY(read_stats(m, s, &ds));
@@ -554,6 +565,7 @@ ns_status ns_matrix_export(const ns_matrix* m, uint64_t* d_keys, uint64_t* d_cou
 ns_status ns_window_build(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
                           ns_matrix* out, ns_stream_t stream) {
     if (!c || !out) return fail(NS_ERR_INVALID, "ns_window_build: NULL context or matrix");
+    DeviceGuard device_guard(c->device);
     if (n > 0 && (!d_src || !d_dst)) return fail(NS_ERR_INVALID, "ns_window_build: NULL input with n > 0");
     if (n >= (1ull << 40)) return fail(NS_ERR_INVALID, "ns_window_build: n too large");
     if (out->ctx != c) return fail(NS_ERR_INVALID, "ns_window_build: matrix belongs to another context");
@@ -564,6 +576,7 @@ ns_status ns_window_build(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_ds
 ns_status ns_path_tune(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n, ns_stream_t stream,
                        int* chosen, float* sort_ms, float* hash_ms) {
     if (!c) return fail(NS_ERR_INVALID, "ns_path_tune: NULL context");
+    DeviceGuard device_guard(c->device);
     if (n == 0) return fail(NS_ERR_INVALID, "ns_path_tune: n == 0");
     if (!d_src || !d_dst) return fail(NS_ERR_INVALID, "ns_path_tune: NULL input");
     if (n >= (1ull << 40)) return fail(NS_ERR_INVALID, "ns_path_tune: n too large");
@@ -635,6 +648,7 @@ ns_status ns_path_resolve(const ns_ctx* c, uint64_t n, int* path) {
 
 ns_status ns_accumulate(ns_ctx* c, ns_matrix* acc, const ns_matrix* add, ns_stream_t stream) {
     if (!c || !acc || !add) return fail(NS_ERR_INVALID, "ns_accumulate: NULL argument");
+    DeviceGuard device_guard(c->device);
     if (acc == add) return fail(NS_ERR_INVALID, "ns_accumulate: acc and add must be distinct");
     if (acc->ctx != c || add->ctx != c) return fail(NS_ERR_INVALID, "ns_accumulate: foreign matrix");
     cudaStream_t s = (cudaStream_t)stream;
@@ -658,6 +672,7 @@ ns_status ns_accumulate(ns_ctx* c, ns_matrix* acc, const ns_matrix* add, ns_stre
 ns_status ns_window_ingest(ns_ctx* c, ns_matrix* acc, const uint32_t* d_src, const uint32_t* d_dst,
                            uint64_t n, ns_stream_t stream) {
     if (!c || !acc) return fail(NS_ERR_INVALID, "ns_window_ingest: NULL argument");
+    DeviceGuard device_guard(c->device);
     if (n > 0 && (!d_src || !d_dst)) return fail(NS_ERR_INVALID, "ns_window_ingest: NULL input with n > 0");
     if (acc->ctx != c) return fail(NS_ERR_INVALID, "ns_window_ingest: foreign matrix");
     cudaStream_t s = (cudaStream_t)stream;
@@ -672,6 +687,7 @@ ns_status ns_window_ingest(ns_ctx* c, ns_matrix* acc, const uint32_t* d_src, con
 ns_status ns_window_ingest_stats(ns_ctx* c, ns_matrix* acc, const uint32_t* d_src, const uint32_t* d_dst,
                                  uint64_t n, ns_stats* d_out, ns_stream_t stream) {
     if (!c || !acc || !d_out) return fail(NS_ERR_INVALID, "ns_window_ingest_stats: NULL argument");
+    DeviceGuard device_guard(c->device);
     if (n > 0 && (!d_src || !d_dst))
         return fail(NS_ERR_INVALID, "ns_window_ingest_stats: NULL input with n > 0");
     if (acc->ctx != c) return fail(NS_ERR_INVALID, "ns_window_ingest_stats: foreign matrix");
@@ -688,6 +704,7 @@ ns_status ns_window_ingest_stats(ns_ctx* c, ns_matrix* acc, const uint32_t* d_sr
 
 ns_status ns_network_stats(ns_ctx* c, const ns_matrix* m, ns_stats* h_out, ns_stream_t stream) {
     if (!c || !m || !h_out) return fail(NS_ERR_INVALID, "ns_network_stats: NULL argument");
+    DeviceGuard device_guard(c->device);
     DevStats ds;
     ns_status st = read_stats(m, (cudaStream_t)stream, &ds);
     static_assert(sizeof(ns_stats) == S_NFIELDS * sizeof(uint64_t), "ns_stats layout");
@@ -697,6 +714,7 @@ ns_status ns_network_stats(ns_ctx* c, const ns_matrix* m, ns_stats* h_out, ns_st
 
 ns_status ns_network_stats_async(ns_ctx* c, const ns_matrix* m, ns_stats* d_out, ns_stream_t stream) {
     if (!c || !m || !d_out) return fail(NS_ERR_INVALID, "ns_network_stats_async: NULL argument");
+    DeviceGuard device_guard(c->device);
     TraceScope ts(&c->tracer, "k_stats_out", (cudaStream_t)stream);
     launch_stats_out((const DevStats*)m->stats.p, (u64*)d_out, (cudaStream_t)stream);
     return check_launch();

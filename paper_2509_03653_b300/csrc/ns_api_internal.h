@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_runtime.h>
 #include <map>
 #include <string>
 
@@ -9,6 +10,27 @@
 #include "ns_kernels.h"
 
 namespace ns {
+
+// Makes `device` current for the guard's scope and gives the calling thread
+// its own current device back afterwards, so that an entry point works on
+// its context's GPU whichever device the caller had current.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int device) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != device && cudaSetDevice(device) != cudaSuccess) cudaGetLastError();
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev && cudaSetDevice(prev) != cudaSuccess)
+            cudaGetLastError();
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
 
 // A grow-only device allocation.
 struct Buf {
@@ -67,6 +89,7 @@ struct ns_ctx {
 // unique-links field is the number of nonzeros.
 struct ns_matrix {
     ns_ctx* ctx = nullptr;
+    int device = 0;  // the context's device (kept here: a matrix may be freed after its context)
     int fmt = ns::FMT_EMPTY;
     ns::Buf links, rows, cols;
     uint64_t link_cap = 0, node_cap = 0;

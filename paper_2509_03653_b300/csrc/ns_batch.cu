@@ -26,6 +26,7 @@ using namespace ns;
 
 struct ns_batch {
     ns_ctx* ctx = nullptr;
+    int device = 0;  // the context's device (kept here: a batch may be freed after its context)
     uint64_t max_windows = 0, max_packets = 0;
     ns_batch_params params{4096, 8, 0.5, 1};
     Buf meta;                  // win_off, tile_off, tab_off, tab_cap: 4 x (max_windows + 1) u64
@@ -131,10 +132,12 @@ extern "C" {
 
 ns_status ns_batch_create(ns_ctx* c, uint64_t max_windows, uint64_t max_packets, ns_batch** out) {
     if (!c || !out) return set_fail(NS_ERR_INVALID, "ns_batch_create: NULL argument");
+    DeviceGuard device_guard(c->device);
     if (max_windows == 0) return set_fail(NS_ERR_INVALID, "ns_batch_create: max_windows == 0");
     *out = nullptr;
     ns_batch* b = new ns_batch();
     b->ctx = c;
+    b->device = c->device;
     b->max_windows = max_windows;
     b->max_packets = max_packets;
     // tuned parameters for this shape, if the cache has them
@@ -169,6 +172,7 @@ ns_status ns_batch_create(ns_ctx* c, uint64_t max_windows, uint64_t max_packets,
 
 void ns_batch_free(ns_batch* b) {
     if (!b) return;
+    DeviceGuard device_guard(b->device);
     cudaDeviceSynchronize();
     buf_free(b->meta);
     buf_free(b->links);
@@ -198,6 +202,7 @@ ns_status ns_batch_run(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uint
                        const uint64_t* h_offsets, uint64_t windows, ns_stats* d_window_stats, ns_matrix* acc,
                        ns_stream_t stream) {
     if (!c || !b || !h_offsets || !d_window_stats) return set_fail(NS_ERR_INVALID, "ns_batch_run: NULL argument");
+    DeviceGuard device_guard(c->device);
     if (b->ctx != c || (acc && acc->ctx != c)) return set_fail(NS_ERR_INVALID, "ns_batch_run: foreign object");
     if (windows > b->max_windows) return set_fail(NS_ERR_INVALID, "ns_batch_run: more windows than the batch plan");
     if (windows == 0) return NS_OK;
@@ -269,6 +274,7 @@ ns_status ns_batch_tune(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uin
                         const uint64_t* h_offsets, uint64_t windows, ns_stats* d_scratch_stats, ns_stream_t stream,
                         ns_batch_params* chosen) {
     if (!c || !b || !d_scratch_stats) return set_fail(NS_ERR_INVALID, "ns_batch_tune: NULL argument");
+    DeviceGuard device_guard(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned Ts[] = {2048, 4096, 16384};
     const unsigned Cs[] = {4, 8, 16};

@@ -252,6 +252,7 @@ extern "C" {
 
 ns_status ns_server_create(ns_ctx* c, ns_matrix* acc, ns_server** out) {
     if (!c || !acc || !out) return set_fail(NS_ERR_INVALID, "ns_server_create: NULL argument");
+    DeviceGuard device_guard(c->device);
     if (acc->ctx != c) return set_fail(NS_ERR_INVALID, "ns_server_create: acc belongs to another context");
     *out = nullptr;
     ns_server* S = new ns_server();
@@ -276,6 +277,7 @@ ns_status ns_server_create(ns_ctx* c, ns_matrix* acc, ns_server** out) {
 
 ns_status ns_server_reserve(ns_server* S, uint64_t max_window) {
     if (!S) return set_fail(NS_ERR_INVALID, "ns_server_reserve: NULL server");
+    DeviceGuard device_guard(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
     if (!S->queue.empty() || !S->inflight.empty())
         return set_fail(NS_ERR_BUSY, "ns_server_reserve: windows in flight");
@@ -294,6 +296,7 @@ ns_status ns_server_reserve(ns_server* S, uint64_t max_window) {
 
 ns_status ns_server_clear(ns_server* S) {
     if (!S) return set_fail(NS_ERR_INVALID, "ns_server_clear: NULL server");
+    DeviceGuard device_guard(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
     if (!S->queue.empty() || !S->inflight.empty())
         return set_fail(NS_ERR_BUSY, "ns_server_clear: windows in flight");

@@ -69,6 +69,7 @@ ns_status ns_trace_enable(ns_ctx* c, int on) {
 
 ns_status ns_trace_read(ns_ctx* c, ns_trace_entry* out, int cap, int* count) {
     if (!c || !count || (cap > 0 && !out)) return ns::set_fail(NS_ERR_INVALID, "ns_trace_read: NULL argument");
+    ns::DeviceGuard device_guard(c->device);
     struct Agg {
         uint64_t n = 0;
         double total = 0, mx = 0;
