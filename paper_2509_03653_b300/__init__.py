@@ -93,6 +93,15 @@ class Matrix:
             self._L.ns_matrix_free(self.handle)
             self.handle = None
 
+    def live(self):
+        """The handle, while this matrix and its context are both open (the
+        library would otherwise reach the closed context's freed memory)."""
+        if not getattr(self, "handle", None):
+            raise RuntimeError("the matrix has been freed")
+        if not getattr(self.ctx, "handle", None):
+            raise RuntimeError("the matrix's context has been closed")
+        return self.handle
+
     def __del__(self):
         try:
             self.free()
@@ -105,7 +114,7 @@ def window_build(ctx: Context, src: torch.Tensor, dst: torch.Tensor, out: Matrix
     n = src.numel()
     if dst.numel() != n:
         raise ValueError("src and dst differ in length")
-    check(ctx._L.ns_window_build(ctx.handle, _column(src, "src"), _column(dst, "dst"), n, out.handle,
+    check(ctx._L.ns_window_build(ctx.handle, _column(src, "src"), _column(dst, "dst"), n, out.live(),
                                  _stream(stream)), "ns_window_build")
 
 
@@ -134,7 +143,7 @@ def path_resolve(ctx: Context, n: int) -> str:
 
 def accumulate(ctx: Context, acc: Matrix, add: Matrix, stream=None):
     """acc := acc + add (ns_accumulate)."""
-    check(ctx._L.ns_accumulate(ctx.handle, acc.handle, add.handle, _stream(stream)), "ns_accumulate")
+    check(ctx._L.ns_accumulate(ctx.handle, acc.live(), add.live(), _stream(stream)), "ns_accumulate")
 
 
 def window_ingest(ctx: Context, acc: Matrix, src: torch.Tensor, dst: torch.Tensor, stream=None):
@@ -142,7 +151,7 @@ def window_ingest(ctx: Context, acc: Matrix, src: torch.Tensor, dst: torch.Tenso
     n = src.numel()
     if dst.numel() != n:
         raise ValueError("src and dst differ in length")
-    check(ctx._L.ns_window_ingest(ctx.handle, acc.handle, _column(src, "src"), _column(dst, "dst"), n,
+    check(ctx._L.ns_window_ingest(ctx.handle, acc.live(), _column(src, "src"), _column(dst, "dst"), n,
                                   _stream(stream)), "ns_window_ingest")
 
 
@@ -156,7 +165,7 @@ def window_ingest_stats(ctx: Context, acc: Matrix, src: torch.Tensor, dst: torch
         raise ValueError("src and dst differ in length")
     if out.element_size() != 8 or out.numel() < 9 or not out.is_contiguous():
         raise ValueError("out must be a contiguous 64-bit tensor with >= 9 elements")
-    check(ctx._L.ns_window_ingest_stats(ctx.handle, acc.handle, _column(src, "src"), _column(dst, "dst"), n,
+    check(ctx._L.ns_window_ingest_stats(ctx.handle, acc.live(), _column(src, "src"), _column(dst, "dst"), n,
                                         ctypes.c_void_p(out.data_ptr()), _stream(stream)),
           "ns_window_ingest_stats")
 
@@ -164,7 +173,7 @@ def window_ingest_stats(ctx: Context, acc: Matrix, src: torch.Tensor, dst: torch
 def network_stats(ctx: Context, m: Matrix, stream=None) -> dict:
     """The nine Table 2 quantities (ns_network_stats; blocking)."""
     out = NsStats()
-    check(ctx._L.ns_network_stats(ctx.handle, m.handle, ctypes.byref(out), _stream(stream)),
+    check(ctx._L.ns_network_stats(ctx.handle, m.live(), ctypes.byref(out), _stream(stream)),
           "ns_network_stats")
     return {f: int(getattr(out, f)) for f in FIELDS}
 
@@ -174,13 +183,13 @@ def network_stats_async(ctx: Context, m: Matrix, out: torch.Tensor, stream=None)
     elements) when the stream gets there (ns_network_stats_async)."""
     if out.element_size() != 8 or out.numel() < 9 or not out.is_contiguous():
         raise ValueError("out must be a contiguous 64-bit tensor with >= 9 elements")
-    check(ctx._L.ns_network_stats_async(ctx.handle, m.handle, ctypes.c_void_p(out.data_ptr()),
+    check(ctx._L.ns_network_stats_async(ctx.handle, m.live(), ctypes.c_void_p(out.data_ptr()),
                                         _stream(stream)), "ns_network_stats_async")
 
 
 def matrix_nnz(m: Matrix, stream=None) -> int:
     v = ctypes.c_uint64()
-    check(m._L.ns_matrix_nnz(m.handle, ctypes.byref(v), _stream(stream)), "ns_matrix_nnz")
+    check(m._L.ns_matrix_nnz(m.live(), ctypes.byref(v), _stream(stream)), "ns_matrix_nnz")
     return int(v.value)
 
 
@@ -192,7 +201,7 @@ def matrix_export(m: Matrix, stream=None, device=None):
     keys = torch.empty(max(nnz, 1), dtype=torch.int64, device=dev)
     counts = torch.empty(max(nnz, 1), dtype=torch.int64, device=dev)
     got = ctypes.c_uint64()
-    check(m._L.ns_matrix_export(m.handle, ctypes.c_void_p(keys.data_ptr()), ctypes.c_void_p(counts.data_ptr()),
+    check(m._L.ns_matrix_export(m.live(), ctypes.c_void_p(keys.data_ptr()), ctypes.c_void_p(counts.data_ptr()),
                                 max(nnz, 1), ctypes.byref(got), _stream(stream)), "ns_matrix_export")
     return keys[: got.value], counts[: got.value]
 
@@ -212,7 +221,7 @@ def matrix_nodes(m: Matrix, which: str = "src", stream=None):
     pk = torch.empty(cap, dtype=torch.int64, device=dev)
     dg = torch.empty(cap, dtype=torch.int64, device=dev)
     got = ctypes.c_uint64()
-    check(m._L.ns_matrix_nodes(m.ctx.handle, m.handle, NODES[which], ctypes.c_void_p(ids.data_ptr()),
+    check(m._L.ns_matrix_nodes(m.ctx.handle, m.live(), NODES[which], ctypes.c_void_p(ids.data_ptr()),
                                ctypes.c_void_p(pk.data_ptr()), ctypes.c_void_p(dg.data_ptr()), cap,
                                ctypes.byref(got), _stream(stream)), "ns_matrix_nodes")
     k = got.value
@@ -242,11 +251,11 @@ def anonymize(ctx: Context, src: torch.Tensor, dst: torch.Tensor, rand: torch.Te
 
 
 def matrix_reserve(m: Matrix, max_links: int, stream=None):
-    check(m._L.ns_matrix_reserve(m.handle, max_links, _stream(stream)), "ns_matrix_reserve")
+    check(m._L.ns_matrix_reserve(m.live(), max_links, _stream(stream)), "ns_matrix_reserve")
 
 
 def matrix_clear(m: Matrix, stream=None):
-    check(m._L.ns_matrix_clear(m.handle, _stream(stream)), "ns_matrix_clear")
+    check(m._L.ns_matrix_clear(m.live(), _stream(stream)), "ns_matrix_clear")
 
 
 def sync(ctx: Context, stream=None):
@@ -288,16 +297,23 @@ def trace_read(ctx: Context) -> dict:
 def matrix_reserve_ex(m: Matrix, max_links: int, max_nodes: int, stream=None):
     """Reserve with a promise on the number of sources/destinations
     (ns_matrix_reserve_ex)."""
-    check(m._L.ns_matrix_reserve_ex(m.handle, max_links, max_nodes, _stream(stream)), "ns_matrix_reserve_ex")
+    check(m._L.ns_matrix_reserve_ex(m.live(), max_links, max_nodes, _stream(stream)), "ns_matrix_reserve_ex")
 
 
 class _BorrowedMatrix(Matrix):
-    """A matrix owned by another library object (not freed from Python)."""
+    """A matrix owned by another library object (not freed from Python); it
+    stays usable while that owner is open."""
 
-    def __init__(self, ctx: Context, handle):
+    def __init__(self, ctx: Context, handle, owner=None):
         self._L = ctx._L
         self.ctx = ctx
         self.handle = handle
+        self.owner = owner
+
+    def live(self):
+        if self.owner is not None and not getattr(self.owner, "handle", None):
+            raise RuntimeError("the matrix's owner has been freed")
+        return super().live()
 
     def free(self):
         self.handle = None
@@ -318,7 +334,7 @@ class Slider:
         """The current sliding sum (valid until the next push)."""
         h = ctypes.c_void_p()
         check(self._L.ns_slider_matrix(self.handle, ctypes.byref(h)), "ns_slider_matrix")
-        return _BorrowedMatrix(self.ctx, h)
+        return _BorrowedMatrix(self.ctx, h, owner=self)
 
     def free(self):
         if getattr(self, "handle", None):
@@ -397,7 +413,7 @@ def batch_run(ctx: Context, batch: Batch, src: torch.Tensor, dst: torch.Tensor, 
     if out.element_size() != 8 or out.numel() < 9 * W or not out.is_contiguous():
         raise ValueError("out must be a contiguous 64-bit tensor with >= 9 * windows elements")
     check(ctx._L.ns_batch_run(ctx.handle, batch.handle, _column(src, "src"), _column(dst, "dst"), ptr, W,
-                              ctypes.c_void_p(out.data_ptr()), acc.handle if acc is not None else None,
+                              ctypes.c_void_p(out.data_ptr()), acc.live() if acc is not None else None,
                               _stream(stream)), "ns_batch_run")
     return off
 
@@ -423,7 +439,7 @@ class Server:
         self._L = ctx._L
         self.ctx, self.acc = ctx, acc
         h = ctypes.c_void_p()
-        check(self._L.ns_server_create(ctx.handle, acc.handle, ctypes.byref(h)), "ns_server_create")
+        check(self._L.ns_server_create(ctx.handle, acc.live(), ctypes.byref(h)), "ns_server_create")
         self.handle = h
         self._keep = {}  # ticket -> host arrays that must outlive the window
 

@@ -76,3 +76,31 @@ def test_error_raises_in_python_binding():
     with pytest.raises(ns.NsError) as e:
         _native.check(1, "where")
     assert e.value.name == "NS_ERR_INVALID"
+
+
+def test_matrix_after_its_context_closed_raises_without_a_library_call():
+    """A matrix whose context (or owning slider) is gone must not reach the
+    library, which would follow the context's freed memory."""
+    class Closed:
+        handle = None
+
+    m = object.__new__(ns.Matrix)
+    m._L = _native.load()
+    m.ctx = Closed()
+    m.handle = ctypes.c_void_p(1)  # never passed on
+    for call in (lambda: ns.matrix_nnz(m), lambda: ns.matrix_clear(m), lambda: ns.matrix_reserve(m, 16),
+                 lambda: ns.matrix_export(m)):
+        with pytest.raises(RuntimeError, match="context has been closed"):
+            call()
+    m.handle = None
+    with pytest.raises(RuntimeError, match="freed"):
+        ns.matrix_nnz(m)
+
+    class Open:
+        handle = ctypes.c_void_p(1)
+        device = 0
+
+    b = ns._BorrowedMatrix.__new__(ns._BorrowedMatrix)
+    b._L, b.ctx, b.handle, b.owner = _native.load(), Open(), ctypes.c_void_p(1), Closed()
+    with pytest.raises(RuntimeError, match="owner has been freed"):
+        ns.matrix_nnz(b)
