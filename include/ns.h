@@ -51,7 +51,8 @@ typedef enum {
     NS_ERR_CUDA = 4,     /* a CUDA runtime call failed */
     NS_ERR_TIMEOUT = 5,  /* a device-side wait gave up, or a host wait timed out */
     NS_ERR_BUSY = 6,     /* serving queue full (retry later), or the service is not idle */
-    NS_ERR_STATE = 7     /* call not valid in the object's current state */
+    NS_ERR_STATE = 7,    /* call not valid in the object's current state */
+    NS_ERR_IO = 8        /* a file could not be opened, read or written */
 } ns_status;
 
 /* The nine quantities of Table 2 (matrix notation), all exact uint64:
@@ -387,6 +388,31 @@ ns_status ns_stream_poll(ns_server* server, uint64_t ticket, int* done);
  * ticket is forgotten. */
 ns_status ns_stream_wait(ns_server* server, uint64_t ticket, ns_stats* per_window, ns_stats* running,
                          int64_t timeout_us, ns_stream_timing* timing);
+
+/* ---- checkpoint / resume ------------------------------------------------ */
+
+/* Checkpoint file of a matrix: a 128-byte little-endian header (magic
+ * "NSMATRIX", format version 1, header size, nnz, the nine quantities of
+ * ns_stats, zero padding), then the nnz keys (src << 32 | dst, strictly
+ * ascending) and the nnz counts, each as uint64.  It is the paper's
+ * three-column frame (src, dst, n_packets; section "Implementation") with
+ * its Table 2 quantities, so an accumulated A can be carried across a
+ * restart of the process that serves the stream. */
+#define NS_CHECKPOINT_VERSION 1
+
+/* Writes matrix m to `path` (replaced atomically: written beside it, then
+ * renamed).  Allocates scratch; blocking.  NS_ERR_IO if the file cannot be
+ * written. */
+ns_status ns_matrix_save(const ns_matrix* m, const char* path, ns_stream_t stream);
+
+/* Replaces the contents of m (a matrix of ctx) with the matrix saved in
+ * `path`.  The entries are inserted afresh, so m's quantities are recomputed
+ * on the GPU; they must equal the saved ones.  NS_ERR_IO if the file cannot
+ * be read, and NS_ERR_INVALID if it is malformed (a bad magic, version or
+ * size, keys not strictly ascending, a zero count): m is then unchanged.
+ * NS_ERR_INVALID too if the recomputed quantities differ from the saved
+ * ones: m is then left empty.  Allocates scratch; blocking. */
+ns_status ns_matrix_load(ns_ctx* ctx, const char* path, ns_matrix* m, ns_stream_t stream);
 
 /* ---- statistics without device allocation ------------------------------ */
 

@@ -12,6 +12,7 @@ the keys in ``FIELDS``.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import torch
 
@@ -24,7 +25,7 @@ __all__ = [
     "matrix_clear", "sync", "PATHS", "path_tune", "path_resolve", "matrix_nodes", "NODES", "anonymize", "Slider",
     "slider_push", "window_stats_static", "STATIC_MAX_PACKETS",
     "trace_enable", "trace_read", "Batch", "batch_run", "batch_tune", "matrix_reserve_ex",
-    "Server", "stream_submit", "stream_poll", "stream_wait", "diag_random_atomics",
+    "Server", "stream_submit", "stream_poll", "stream_wait", "diag_random_atomics", "matrix_save", "matrix_load",
 ]
 
 STATIC_MAX_PACKETS = 32768  # NS_STATIC_MAX_PACKETS in include/ns.h
@@ -292,6 +293,19 @@ def trace_read(ctx: Context) -> dict:
     check(ctx._L.ns_trace_read(ctx.handle, buf, cap, ctypes.byref(cnt)), "ns_trace_read")
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms), float(buf[i].max_ms))
             for i in range(min(cnt.value, cap))}
+
+
+def matrix_save(m: Matrix, path: str, stream=None):
+    """Checkpoint: writes A's sorted nonzero list and its nine quantities to
+    `path` (ns_matrix_save)."""
+    check(m._L.ns_matrix_save(m.live(), os.fsencode(path), _stream(stream)), "ns_matrix_save")
+
+
+def matrix_load(ctx: Context, path: str, m: Matrix, stream=None):
+    """Resume: replaces m's contents with the checkpoint in `path`; its
+    quantities are recomputed and checked against the saved ones
+    (ns_matrix_load)."""
+    check(ctx._L.ns_matrix_load(ctx.handle, os.fsencode(path), m.live(), _stream(stream)), "ns_matrix_load")
 
 
 def matrix_reserve_ex(m: Matrix, max_links: int, max_nodes: int, stream=None):

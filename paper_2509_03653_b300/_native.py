@@ -74,6 +74,8 @@ SIGNATURES = {
     "ns_trace_enable": (ST, [P, I32]),
     "ns_trace_read": (ST, [P, ctypes.POINTER(NsTraceEntry), I32, ctypes.POINTER(I32)]),
     "ns_matrix_reserve_ex": (ST, [P, U64, U64, P]),
+    "ns_matrix_save": (ST, [P, ctypes.c_char_p, P]),
+    "ns_matrix_load": (ST, [P, ctypes.c_char_p, P, P]),
     "ns_batch_create": (ST, [P, U64, U64, ctypes.POINTER(P)]),
     "ns_batch_free": (None, [P]),
     "ns_batch_get_params": (ST, [P, ctypes.POINTER(NsBatchParams)]),

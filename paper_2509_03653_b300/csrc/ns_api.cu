@@ -372,6 +372,7 @@ const char* ns_status_string(ns_status s) {
         case NS_ERR_TIMEOUT: return "NS_ERR_TIMEOUT";
         case NS_ERR_BUSY: return "NS_ERR_BUSY";
         case NS_ERR_STATE: return "NS_ERR_STATE";
+        case NS_ERR_IO: return "NS_ERR_IO";
     }
     return "NS_ERR_?";
 }

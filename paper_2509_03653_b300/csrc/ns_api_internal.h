@@ -48,6 +48,9 @@ HashView hash_view(const ns_matrix* m);
 void buf_free(Buf& b);
 ns_status check_launch();
 ns_status set_fail(ns_status s, const char* msg);
+// Reads the matrix's statistics record (blocking); the device error word
+// comes back as a status.
+ns_status read_stats(const ns_matrix* m, cudaStream_t s, DevStats* out);
 // Sizes the context's look-back status words for sorts of up to n elements.
 ns_status sort_scratch(ns_ctx* c, u64 n);
 // Hash path: out := A_t.  cache: -1 = the context's rule, 0 = off, 1 = on.

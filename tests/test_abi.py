@@ -50,6 +50,7 @@ def test_status_strings():
     assert L.ns_status_string(0) == b"NS_OK"
     assert L.ns_status_string(1) == b"NS_ERR_INVALID"
     assert L.ns_status_string(5) == b"NS_ERR_TIMEOUT"
+    assert L.ns_status_string(8) == b"NS_ERR_IO"
 
 
 def test_null_arguments_are_invalid_without_gpu():
@@ -68,6 +69,8 @@ def test_null_arguments_are_invalid_without_gpu():
     assert L.ns_matrix_reserve(None, 10, None) == 1
     assert L.ns_matrix_clear(None, None) == 1
     assert L.ns_sync(None, None) == 1
+    assert L.ns_matrix_save(None, None, None) == 1
+    assert L.ns_matrix_load(None, None, None, None) == 1
     L.ns_destroy(None)
     L.ns_matrix_free(None)
 
