@@ -411,7 +411,9 @@ ns_status ns_matrix_save(const ns_matrix* m, const char* path, ns_stream_t strea
  * be read, and NS_ERR_INVALID if it is malformed (a bad magic, version or
  * size, keys not strictly ascending, a zero count): m is then unchanged.
  * NS_ERR_INVALID too if the recomputed quantities differ from the saved
- * ones: m is then left empty.  Allocates scratch; blocking. */
+ * ones, and any error after the file has been checked (a failed copy,
+ * allocation or insert): m is then left empty, never partly loaded.  The
+ * copies and the insert run on `stream`.  Allocates scratch; blocking. */
 ns_status ns_matrix_load(ns_ctx* ctx, const char* path, ns_matrix* m, ns_stream_t stream);
 
 /* ---- statistics without device allocation ------------------------------ */
@@ -429,7 +431,9 @@ ns_status ns_matrix_load(ns_ctx* ctx, const char* path, ns_matrix* m, ns_stream_
  * device array of about 3 MiB inside the library, which every GPU that loads
  * the library keeps until the process exits.  n must not exceed
  * NS_STATIC_MAX_PACKETS (larger n returns NS_ERR_INVALID and does nothing).
- * Runs on the calling thread's current device.  The first call on a device
+ * Runs on the calling thread's current device, and `stream` must belong to
+ * that device (a stream of another device returns NS_ERR_INVALID).  The
+ * first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) and caches it;
  * make that first call before any stream capture on that device.  All calls
  * on a device share the one array and each starts by clearing it, so calls

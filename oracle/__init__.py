@@ -44,10 +44,11 @@ _P64 = ctypes.POINTER(ctypes.c_uint64)
 
 
 def build(force: bool = False, src: str = _SRC, out: str = _LIB, defines=()) -> str:
-    """Compile the oracle (plain g++ -O2, single thread) when missing or stale."""
+    """Compile the oracle (plain g++ -O2; std::thread for the all-cores
+    variants) when missing or stale."""
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
         tmp = out + ".tmp%d" % os.getpid()
-        cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, src]
+        cmd = ["g++", "-O2", "-std=c++17", "-pthread", "-shared", "-fPIC", "-o", tmp, src]
         cmd += ["-D%s" % d for d in defines]
         subprocess.check_call(cmd)
         os.replace(tmp, out)
@@ -67,6 +68,9 @@ def load(path: str | None = None):
     L.oracle_unique_addresses.argtypes = [_u64p, _U64, _u32p, _P64]
     L.oracle_anonymize.argtypes = [_u32p, _u32p, _U64, _u64p, _U64, _u32p, _u32p, _P64]
     L.oracle_anonymize.restype = ctypes.c_int
+    L.oracle_build_parallel.argtypes = [_u32p, _u32p, _U64, _u64p, _u64p, _P64, ctypes.c_int]
+    L.oracle_stats_parallel.argtypes = [_u64p, _u64p, _U64, _u64p, ctypes.c_int]
+    L.oracle_hardware_threads.restype = ctypes.c_int
     return L
 
 
@@ -93,6 +97,41 @@ def build_matrix(src, dst, L=None):
     nnz = ctypes.c_uint64(0)
     L.oracle_build(src, dst, n, keys, counts, ctypes.byref(nnz))
     return keys[: nnz.value].copy(), counts[: nnz.value].copy()
+
+
+def hardware_threads(L=None) -> int:
+    """Threads the all-cores variants use by default (the host's hardware
+    concurrency)."""
+    return int((L or lib()).oracle_hardware_threads())
+
+
+def build_matrix_parallel(src, dst, threads: int = 0, L=None):
+    """build_matrix on all host cores (threads <= 0: every hardware thread):
+    chunk matrices by build_matrix's own step, summed pairwise by
+    accumulate's.  Same result as build_matrix."""
+    L = L or lib()
+    src = _c(src, np.uint32)
+    dst = _c(dst, np.uint32)
+    n = src.size
+    assert dst.size == n
+    # np.empty pages are touched only up to nnz
+    keys = np.empty(max(n, 1), dtype=np.uint64)
+    counts = np.empty(max(n, 1), dtype=np.uint64)
+    nnz = ctypes.c_uint64(0)
+    L.oracle_build_parallel(src if n else np.zeros(1, np.uint32), dst if n else np.zeros(1, np.uint32), n,
+                            keys, counts, ctypes.byref(nnz), int(threads))
+    return keys[: nnz.value].copy(), counts[: nnz.value].copy()
+
+
+def stats_parallel(keys, counts, threads: int = 0, L=None) -> dict:
+    """stats on all host cores (the columns' sort split over the threads)."""
+    L = L or lib()
+    keys = _c(keys, np.uint64)
+    counts = _c(counts, np.uint64)
+    out = np.zeros(len(FIELDS), dtype=np.uint64)
+    L.oracle_stats_parallel(keys if keys.size else np.zeros(1, np.uint64),
+                            counts if counts.size else np.zeros(1, np.uint64), keys.size, out, int(threads))
+    return {f: int(v) for f, v in zip(FIELDS, out)}
 
 
 def accumulate(a, b, L=None):

@@ -28,11 +28,21 @@
  * Accumulation (A += A_t) merges two sorted nonzero lists, adding the counts
  * of equal keys.
  *
+ * The all-cores variants (oracle_build_parallel, oracle_stats_parallel) use
+ * the same steps on every host core and nothing else: the packets are cut
+ * into one chunk per thread, each chunk's matrix is built by oracle_build,
+ * and the chunk matrices are summed pairwise by oracle_accumulate -- the
+ * matrix of a concatenated stream is the sum of its pieces' matrices, the
+ * summation rule above.  Columns: each thread sorts the (dst, count) pairs of
+ * one slice of the nonzero list and sums equal destinations; the per-slice
+ * lists are then merged pairwise, adding the sums of equal destinations.
+ *
  * Every count is uint64; no floating point is involved.
  */
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -267,5 +277,161 @@ int oracle_anonymize(const uint32_t* src, const uint32_t* dst, uint64_t n, const
     }
     return 0;
 }
+
+/* ---- all host cores ------------------------------------------------------ */
+
+}  // extern "C"
+
+namespace {
+
+int thread_count(int threads) {
+    if (threads > 0) return threads;
+    const unsigned h = std::thread::hardware_concurrency();
+    return h ? (int)h : 1;
+}
+
+struct List {
+    std::vector<uint64_t> keys, counts;
+};
+
+/* Runs f(i) for i in [0, m) on up to m threads and waits for all of them. */
+template <typename F>
+void run_all(int m, F f) {
+    std::vector<std::thread> pool;
+    for (int i = 0; i < m; ++i) pool.emplace_back(f, i);
+    for (auto& t : pool) t.join();
+}
+
+/* Per-destination sums of one part: destination, packets, entries. */
+struct ColSum {
+    uint32_t dst;
+    uint64_t packets, entries;
+};
+
+std::vector<ColSum> merge_cols(const std::vector<ColSum>& a, const std::vector<ColSum>& b) {
+    std::vector<ColSum> out;
+    out.reserve(a.size() + b.size());
+    size_t i = 0, j = 0;
+    while (i < a.size() || j < b.size()) {
+        if (j >= b.size() || (i < a.size() && a[i].dst < b[j].dst)) out.push_back(a[i++]);
+        else if (i >= a.size() || b[j].dst < a[i].dst) out.push_back(b[j++]);
+        else {
+            out.push_back({a[i].dst, a[i].packets + b[j].packets, a[i].entries + b[j].entries});
+            ++i;
+            ++j;
+        }
+    }
+    return out;
+}
+
+}  // namespace
+
+extern "C" {
+
+/* oracle_build on all host cores (threads <= 0: std::thread's
+ * hardware_concurrency): one chunk of packets per thread through
+ * oracle_build, then the chunk matrices summed pairwise by
+ * oracle_accumulate until one is left.  Same outputs as oracle_build. */
+int oracle_build_parallel(const uint32_t* src, const uint32_t* dst, uint64_t n, uint64_t* keys_out,
+                          uint64_t* counts_out, uint64_t* nnz_out, int threads) {
+    const int T = thread_count(threads);
+    const uint64_t chunks = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)T, n));
+    std::vector<List> part(chunks);
+    run_all((int)chunks, [&](int c) {
+        const uint64_t a = n * (uint64_t)c / chunks, b = n * (uint64_t)(c + 1) / chunks;
+        List& L = part[c];
+        L.keys.resize(b - a);
+        L.counts.resize(b - a);
+        uint64_t u = 0;
+        oracle_build(src + a, dst + a, b - a, L.keys.data(), L.counts.data(), &u);
+        L.keys.resize(u);
+        L.counts.resize(u);
+    });
+    while (part.size() > 1) {
+        const size_t pairs = part.size() / 2;
+        std::vector<List> next(pairs + (part.size() & 1));
+        run_all((int)pairs, [&](int i) {
+            const List& x = part[2 * i];
+            const List& y = part[2 * i + 1];
+            List& z = next[i];
+            z.keys.resize(x.keys.size() + y.keys.size());
+            z.counts.resize(z.keys.size());
+            uint64_t u = 0;
+            oracle_accumulate(x.keys.data(), x.counts.data(), x.keys.size(), y.keys.data(), y.counts.data(),
+                              y.keys.size(), z.keys.data(), z.counts.data(), &u);
+            z.keys.resize(u);
+            z.counts.resize(u);
+        });
+        if (part.size() & 1) next.back() = std::move(part.back());
+        part.swap(next);
+    }
+    const List& A = part[0];
+    std::copy(A.keys.begin(), A.keys.end(), keys_out);
+    std::copy(A.counts.begin(), A.counts.end(), counts_out);
+    *nnz_out = A.keys.size();
+    return 0;
+}
+
+/* oracle_stats on all host cores: the whole-matrix and row quantities by the
+ * same linear scans; the columns by per-thread sorts of slices of the (dst,
+ * count) pairs, each summed per destination, then merged pairwise. */
+int oracle_stats_parallel(const uint64_t* keys, const uint64_t* counts, uint64_t nnz, uint64_t* stats,
+                          int threads) {
+    for (int f = 0; f < N_FIELDS; ++f) stats[f] = 0;
+    for (uint64_t u = 0; u < nnz; ++u) {
+        stats[VALID_PACKETS] += counts[u];
+        if (counts[u] > stats[MAX_LINK_PACKETS]) stats[MAX_LINK_PACKETS] = counts[u];
+    }
+    stats[UNIQUE_LINKS] = nnz;
+    uint64_t u = 0;
+    while (u < nnz) {
+        const uint64_t s = keys[u] >> 32;
+        uint64_t packets = 0, fanout = 0;
+        while (u < nnz && (keys[u] >> 32) == s) {
+            packets += counts[u];
+            fanout += 1;
+            ++u;
+        }
+        stats[UNIQUE_SOURCES] += 1;
+        if (packets > stats[MAX_SRC_PACKETS]) stats[MAX_SRC_PACKETS] = packets;
+        if (fanout > stats[MAX_SRC_FANOUT]) stats[MAX_SRC_FANOUT] = fanout;
+    }
+    const int T = thread_count(threads);
+    const uint64_t slices = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)T, nnz));
+    std::vector<std::vector<ColSum>> part(slices);
+    run_all((int)slices, [&](int c) {
+        const uint64_t a = nnz * (uint64_t)c / slices, b = nnz * (uint64_t)(c + 1) / slices;
+        std::vector<std::pair<uint32_t, uint64_t>> col(b - a);
+        for (uint64_t v = a; v < b; ++v) col[v - a] = {(uint32_t)(keys[v] & 0xFFFFFFFFu), counts[v]};
+        std::sort(col.begin(), col.end());
+        std::vector<ColSum>& out = part[c];
+        uint64_t v = 0;
+        while (v < col.size()) {
+            ColSum cs{col[v].first, 0, 0};
+            while (v < col.size() && col[v].first == cs.dst) {
+                cs.packets += col[v].second;
+                cs.entries += 1;
+                ++v;
+            }
+            out.push_back(cs);
+        }
+    });
+    while (part.size() > 1) {
+        const size_t pairs = part.size() / 2;
+        std::vector<std::vector<ColSum>> next(pairs + (part.size() & 1));
+        run_all((int)pairs, [&](int i) { next[i] = merge_cols(part[2 * i], part[2 * i + 1]); });
+        if (part.size() & 1) next.back() = std::move(part.back());
+        part.swap(next);
+    }
+    for (const ColSum& cs : part[0]) {
+        stats[UNIQUE_DESTINATIONS] += 1;
+        if (cs.packets > stats[MAX_DST_PACKETS]) stats[MAX_DST_PACKETS] = cs.packets;
+        if (cs.entries > stats[MAX_DST_FANIN]) stats[MAX_DST_FANIN] = cs.entries;
+    }
+    return 0;
+}
+
+/* The thread count the all-cores variants use for threads <= 0. */
+int oracle_hardware_threads(void) { return thread_count(0); }
 
 }  // extern "C"

@@ -60,10 +60,14 @@ ns_status ns_matrix_save(const ns_matrix* m, const char* path, ns_stream_t strea
         uint64_t got = 0;
         if (st == NS_OK) st = ns_matrix_export(m, (uint64_t*)dk.p, (uint64_t*)dc.p, nnz, &got, stream);
         if (st == NS_OK && got != nnz) st = set_fail(NS_ERR_STATE, "ns_matrix_save: the matrix changed while saved");
+        // copies on the caller's stream, behind the export (a legacy-stream
+        // cudaMemcpy is not ordered with a non-blocking stream)
         cudaError_t e = cudaSuccess;
-        if (st == NS_OK) e = cudaMemcpy(keys.data(), dk.p, nnz * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+        if (st == NS_OK)
+            e = cudaMemcpyAsync(keys.data(), dk.p, nnz * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
         if (st == NS_OK && e == cudaSuccess)
-            e = cudaMemcpy(counts.data(), dc.p, nnz * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+            e = cudaMemcpyAsync(counts.data(), dc.p, nnz * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+        if (st == NS_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (st == NS_OK && e != cudaSuccess) st = cuda_fail("ns_matrix_save: copy to host", e);
         buf_free(dk);
         buf_free(dc);
@@ -139,25 +143,38 @@ ns_status ns_matrix_load(ns_ctx* c, const char* path, ns_matrix* m, ns_stream_t 
         st = buf_reserve(tmp.keys, nnz * sizeof(uint64_t));
         if (st == NS_OK) st = buf_reserve(tmp.counts, nnz * sizeof(uint64_t));
         if (st == NS_OK) st = buf_reserve(tmp.stats, sizeof(DevStats));
+        // The copies go on the caller's stream, ahead of the insert that
+        // reads them: a pageable cudaMemcpy may return before its transfer
+        // has landed, and the legacy stream it uses is not ordered with a
+        // non-blocking one.  The host vectors outlive the synchronization
+        // below.
         cudaError_t e = cudaSuccess;
-        if (st == NS_OK) e = cudaMemcpy(tmp.keys.p, keys.data(), nnz * sizeof(uint64_t), cudaMemcpyHostToDevice);
+        if (st == NS_OK)
+            e = cudaMemcpyAsync(tmp.keys.p, keys.data(), nnz * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
         if (st == NS_OK && e == cudaSuccess)
-            e = cudaMemcpy(tmp.counts.p, counts.data(), nnz * sizeof(uint64_t), cudaMemcpyHostToDevice);
-        if (st == NS_OK && e == cudaSuccess) e = cudaMemcpy(tmp.stats.p, &ts, sizeof ts, cudaMemcpyHostToDevice);
+            e = cudaMemcpyAsync(tmp.counts.p, counts.data(), nnz * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
+        if (st == NS_OK && e == cudaSuccess) e = cudaMemcpyAsync(tmp.stats.p, &ts, sizeof ts, cudaMemcpyHostToDevice, s);
         if (st == NS_OK && e != cudaSuccess) st = cuda_fail("ns_matrix_load: copy to device", e);
         if (st == NS_OK) st = ns_accumulate(c, m, &tmp, stream);
-        if (st == NS_OK) {
-            const cudaError_t se = cudaStreamSynchronize(s);
-            if (se != cudaSuccess) st = cuda_fail("ns_matrix_load: insert", se);
-        }
+        // the temporaries are freed only once the stream is past every
+        // command that reads them, also when a step above failed
+        const cudaError_t se = cudaStreamSynchronize(s);
+        if (st == NS_OK && se != cudaSuccess) st = cuda_fail("ns_matrix_load: insert", se);
         buf_free(tmp.keys);
         buf_free(tmp.counts);
         buf_free(tmp.stats);
-        if (st != NS_OK) return st;
+        if (st != NS_OK) {
+            // never leave a partly loaded matrix behind
+            ns_matrix_clear(m, stream);
+            return st;
+        }
     }
     DevStats got;
     st = read_stats(m, s, &got);
-    if (st != NS_OK) return st;
+    if (st != NS_OK) {
+        ns_matrix_clear(m, stream);
+        return st;
+    }
     for (int i = 0; i < S_NFIELDS; ++i) {
         if (got.v[i] != h.stats[i]) {
             ns_matrix_clear(m, stream);

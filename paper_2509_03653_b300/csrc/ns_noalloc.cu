@@ -92,6 +92,18 @@ extern "C" ns_status ns_window_stats_static(const uint32_t* d_src, const uint32_
         su = g_setup[dev];
     }
     cudaStream_t s = (cudaStream_t)stream;
+    // the array looked up above is the current device's: a stream of another
+    // device could not reach it
+    int sdev = dev;
+    if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) {
+        cudaGetLastError();
+        return ns::set_fail(NS_ERR_INVALID, "ns_window_stats_static: not a valid stream");
+    }
+    if (sdev != dev) {
+        snprintf(g_msg, sizeof g_msg,
+                 "ns_window_stats_static: the stream belongs to device %d, the current device is %d", sdev, dev);
+        return ns::set_fail(NS_ERR_INVALID, g_msg);
+    }
     // every call shares the array: start from empty tables and zero statistics
     cudaError_t e = cudaMemsetAsync(su.base, 0, kScratchBytes, s);
     if (e != cudaSuccess) {

@@ -300,6 +300,12 @@ ns_status ns_server_clear(ns_server* S) {
     std::unique_lock<std::mutex> lk(S->mu);
     if (!S->queue.empty() || !S->inflight.empty())
         return set_fail(NS_ERR_BUSY, "ns_server_clear: windows in flight");
+    // The scheduler pops a request and marks its slot busy under the lock,
+    // then issues the window's work (accumulation into acc included) without
+    // it; the request joins the in-flight list only afterwards.  A busy slot
+    // therefore means a window may be touching acc right now.
+    for (const auto& sl : S->slots)
+        if (sl.busy) return set_fail(NS_ERR_BUSY, "ns_server_clear: windows in flight");
     ns_status st = ns_matrix_clear(S->acc, S->acc_stream);
     if (st != NS_OK) return st;
     if (cudaStreamSynchronize(S->acc_stream) != cudaSuccess) {

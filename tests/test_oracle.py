@@ -182,8 +182,32 @@ def check_anonymize(L, seed):
     np.testing.assert_array_equal(ranks_d, np.searchsorted(u, dst).astype(np.uint32))
 
 
+def check_parallel(L, seed):
+    """The all-cores variants against the dense model (nonzero list and the
+    nine quantities, heavy collisions, keys 0 and 2^64-1) with more threads
+    than packets and with ragged chunks, and against the single-thread
+    oracle on a skewed stream."""
+    for n, threads in ((0, 4), (1, 4), (5, 16), (4099, 3), (40000, 7)):
+        s8, d8 = skewed_pairs(n, seed + n)
+        M = dense_matrix(s8, d8)
+        k, c = oracle.build_matrix_parallel(widen8(s8), widen8(d8), threads, L)
+        dk, dc = dense_nonzeros(M)
+        np.testing.assert_array_equal(k, dk)
+        np.testing.assert_array_equal(c, dc)
+        want = dense_stats(M) if n else (0,) * 9
+        assert tup(oracle.stats_parallel(k, c, threads, L)) == want
+    s, d = W.large_build(1 << 16)
+    k1, c1 = oracle.build_matrix(s, d, L)
+    for threads in (2, 5, 0):
+        k2, c2 = oracle.build_matrix_parallel(s, d, threads, L)
+        np.testing.assert_array_equal(k2, k1)
+        np.testing.assert_array_equal(c2, c1)
+        assert oracle.stats_parallel(k1, c1, threads, L) == oracle.stats(k1, c1, L)
+
+
 def all_pins(L):
     check_golden(L)
+    check_parallel(L, 51)
     for n, seed in ((1, 1), (2, 2), (255, 3), (4099, 4), (40000, 5)):
         check_bruteforce(L, n, seed)
     check_windows_bruteforce(L, (700, 0, 1, 3000), 11)
@@ -375,6 +399,13 @@ MUTANTS = {
     "anonymize_inverse_permutation": ("label[order[t]] = (uint32_t)t;", "label[t] = (uint32_t)order[t];"),
     # random keys indexed from the end of the array
     "anonymize_wrong_random_index": ("return rnd[a] < rnd[b];", "return rnd[rnd_n - 1 - a] < rnd[rnd_n - 1 - b];"),
+    # all-cores build: each chunk loses its last packet
+    "parallel_chunk_short": ("oracle_build(src + a, dst + a, b - a,", "oracle_build(src + a, dst + a, b - a - (b > a),"),
+    # all-cores build: an odd chunk matrix left out of the sum
+    "parallel_drops_odd_chunk": ("if (part.size() & 1) next.back() = std::move(part.back());\n        part.swap(next);\n    }\n    const List&",
+                                 "part.swap(next);\n    }\n    const List&"),
+    # all-cores columns: merged destinations keep one side's fan-in
+    "parallel_cols_merge_drops_entries": ("a[i].entries + b[j].entries", "a[i].entries"),
 }
 
 
@@ -389,7 +420,7 @@ def test_planted_mistake_is_caught(name):
         with open(src, "w") as f:
             f.write(text.replace(old, new, 1))
         so = os.path.join(tmp, "libmutant.so")
-        subprocess.check_call(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-o", so, src])
+        subprocess.check_call(["g++", "-O1", "-std=c++17", "-pthread", "-shared", "-fPIC", "-o", so, src])
         L = oracle.load(so)
         with pytest.raises(AssertionError):
             all_pins(L)

@@ -4,11 +4,12 @@ framework's caching allocator already holds the GPU's memory, or in a loop
 that must not block in cudaMalloc/cudaFree).  It keeps its tables in one
 fixed device array inside the library.
 
-Checked through the C ABI against the ordinary entry points
-(ns_window_build + ns_network_stats) on two calls in a row -- a large window
-of distinct links followed by a small skewed one, so that leftovers from the
-first call would show up in the second -- with exact equality, the tolerance
-every count in this library is held to.  Collected last on purpose.
+Checked through the C ABI, on two calls in a row -- a large window of
+distinct links followed by a small skewed one, so that leftovers from the
+first call would show up in the second -- against the CPU oracle and against
+the ordinary entry points (ns_window_build + ns_network_stats), with exact
+equality, the tolerance every count in this library is held to.  Collected
+last on purpose.
 """
 from __future__ import annotations
 
@@ -19,6 +20,7 @@ import pytest
 import torch
 
 import gen.workloads as W
+import oracle
 import paper_2509_03653_b300 as ns
 from paper_2509_03653_b300 import _native
 
@@ -34,7 +36,7 @@ def _row(t):
     return {f: int(x) for f, x in zip(ns.FIELDS, v[:9])}
 
 
-def test_static_entry_matches_window_build_twice():
+def test_static_entry_matches_oracle_and_window_build_twice():
     L = _native.load()
     ctx = ns.Context(0, path="hash")
     windows = [W.rmat_stream(ns.STATIC_MAX_PACKETS), W.single_window(1000)]
@@ -46,6 +48,7 @@ def test_static_entry_matches_window_build_twice():
                                       ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
         assert st == 0, L.ns_last_error()
         torch.cuda.synchronize()
+        assert _row(out) == oracle.stats_of_packets(s, d)
         m = ns.Matrix(ctx)
         ns.window_build(ctx, ds, dd, m)
         want = ns.network_stats(ctx, m)
