@@ -235,6 +235,19 @@ ns_status ns_slider_matrix(const ns_slider* slider, const ns_matrix** out);
 ns_status ns_window_build(ns_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
                           ns_matrix* out, ns_stream_t stream);
 
+/* ns_window_build for packets in host memory, with the quantities read
+ * back: h_src[0..n) and h_dst[0..n) are copied (on `stream`) into device
+ * buffers the context owns and keeps for later calls, out := A_t of those
+ * packets, and, if h_stats is not NULL, A_t's nine quantities are written to
+ * *h_stats (host memory).  Pinned host columns are copied by DMA at the
+ * link's full rate; pageable ones are staged by the driver.  This is the
+ * end-to-end form of the hot path (host columns in, statistics out).
+ * Blocking: returns once the statistics are on the host (or, with h_stats
+ * NULL, once the build is done), with any device-side error as its status.
+ * The host columns may be reused as soon as it returns. */
+ns_status ns_window_build_host(ns_ctx* ctx, const uint32_t* h_src, const uint32_t* h_dst, uint64_t n,
+                               ns_matrix* out, ns_stats* h_stats, ns_stream_t stream);
+
 /* Path tuner: builds A from d_src/d_dst (n > 0 packets, device memory)
  * with the sort path, the hash path without per-CTA caches and the hash path
  * with them (only the one the context's cta_cache forces, if it forces one),

@@ -346,6 +346,8 @@ int oracle_build_parallel(const uint32_t* src, const uint32_t* dst, uint64_t n, 
         oracle_build(src + a, dst + a, b - a, L.keys.data(), L.counts.data(), &u);
         L.keys.resize(u);
         L.counts.resize(u);
+        L.keys.shrink_to_fit();
+        L.counts.shrink_to_fit();
     });
     while (part.size() > 1) {
         const size_t pairs = part.size() / 2;

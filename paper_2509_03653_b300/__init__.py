@@ -20,7 +20,7 @@ from ._native import (FIELDS, NsBatchParams, NsConfig, NsError, NsStats, NsStrea
                       load)
 
 __all__ = [
-    "FIELDS", "NsError", "Context", "Matrix", "window_build", "accumulate", "window_ingest",
+    "FIELDS", "NsError", "Context", "Matrix", "window_build", "window_build_host", "accumulate", "window_ingest",
     "window_ingest_stats", "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
     "matrix_clear", "sync", "PATHS", "path_tune", "path_resolve", "matrix_nodes", "NODES", "anonymize", "Slider",
     "slider_push", "window_stats_static", "STATIC_MAX_PACKETS",
@@ -117,6 +117,31 @@ def window_build(ctx: Context, src: torch.Tensor, dst: torch.Tensor, out: Matrix
         raise ValueError("src and dst differ in length")
     check(ctx._L.ns_window_build(ctx.handle, _column(src, "src"), _column(dst, "dst"), n, out.live(),
                                  _stream(stream)), "ns_window_build")
+
+
+def _host_column(t, name: str) -> ctypes.c_void_p:
+    if isinstance(t, torch.Tensor):
+        if t.element_size() != 4 or not t.is_contiguous() or t.is_cuda:
+            raise ValueError(f"{name} must be a contiguous 32-bit host tensor")
+        return ctypes.c_void_p(t.data_ptr() if t.numel() else 0)
+    import numpy as np
+    if not isinstance(t, np.ndarray) or t.dtype.itemsize != 4 or not t.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{name} must be a contiguous 32-bit host array")
+    return ctypes.c_void_p(t.ctypes.data if t.size else 0)
+
+
+def window_build_host(ctx: Context, src, dst, out: Matrix, stream=None) -> dict:
+    """out := A_t of packets held in host memory (torch CPU tensors or numpy
+    arrays of 32-bit addresses), and its nine quantities, returned
+    (ns_window_build_host; blocking)."""
+    n = src.numel() if isinstance(src, torch.Tensor) else src.size
+    m = dst.numel() if isinstance(dst, torch.Tensor) else dst.size
+    if m != n:
+        raise ValueError("src and dst differ in length")
+    st = NsStats()
+    check(ctx._L.ns_window_build_host(ctx.handle, _host_column(src, "src"), _host_column(dst, "dst"), n, out.live(),
+                                      ctypes.byref(st), _stream(stream)), "ns_window_build_host")
+    return {f: int(getattr(st, f)) for f in FIELDS}
 
 
 _PATH_NAMES = {v: k for k, v in PATHS.items()}

@@ -54,6 +54,7 @@ SIGNATURES = {
     "ns_matrix_nnz": (ST, [P, ctypes.POINTER(U64), P]),
     "ns_matrix_export": (ST, [P, P, P, U64, ctypes.POINTER(U64), P]),
     "ns_window_build": (ST, [P, P, P, U64, P, P]),
+    "ns_window_build_host": (ST, [P, P, P, U64, P, ctypes.POINTER(NsStats), P]),
     "ns_path_tune": (ST, [P, P, P, U64, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                           ctypes.POINTER(ctypes.c_float)]),
     "ns_path_resolve": (ST, [P, U64, ctypes.POINTER(ctypes.c_int)]),

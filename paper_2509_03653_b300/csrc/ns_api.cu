@@ -432,7 +432,8 @@ void ns_destroy(ns_ctx* c) {
     DeviceGuard device_guard(c->device);
     cudaDeviceSynchronize();
     Buf* all[] = {&c->ghist, &c->offs, &c->tcount, &c->counters, &c->status, &c->k64[0], &c->k64[1],
-                  &c->pos, &c->psum, &c->k32[0], &c->k32[1], &c->v64[0], &c->v64[1], &c->xk, &c->xv};
+                  &c->pos, &c->psum, &c->k32[0], &c->k32[1], &c->v64[0], &c->v64[1], &c->xk, &c->xv,
+                  &c->stage[0], &c->stage[1]};
     for (Buf* b : all) buf_free(*b);
     if (c->host_stats) cudaFreeHost(c->host_stats);
     tracer_destroy(&c->tracer);
@@ -572,6 +573,30 @@ ns_status ns_window_build(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_ds
     if (out->ctx != c) return fail(NS_ERR_INVALID, "ns_window_build: matrix belongs to another context");
     if (resolve_path(c, n) == NS_PATH_SORT) return build_sort(c, d_src, d_dst, n, out, (cudaStream_t)stream);
     return build_hash(c, d_src, d_dst, n, out, (cudaStream_t)stream);
+}
+
+ns_status ns_window_build_host(ns_ctx* c, const uint32_t* h_src, const uint32_t* h_dst, uint64_t n,
+                               ns_matrix* out, ns_stats* h_stats, ns_stream_t stream) {
+    if (!c || !out) return fail(NS_ERR_INVALID, "ns_window_build_host: NULL context or matrix");
+    DeviceGuard device_guard(c->device);
+    if (n > 0 && (!h_src || !h_dst)) return fail(NS_ERR_INVALID, "ns_window_build_host: NULL input with n > 0");
+    if (n >= (1ull << 40)) return fail(NS_ERR_INVALID, "ns_window_build_host: n too large");
+    if (out->ctx != c) return fail(NS_ERR_INVALID, "ns_window_build_host: matrix belongs to another context");
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t* d_src = nullptr;
+    const uint32_t* d_dst = nullptr;
+    if (n > 0) {
+        TRY(buf_reserve(c->stage[0], n * sizeof(uint32_t)));
+        TRY(buf_reserve(c->stage[1], n * sizeof(uint32_t)));
+        CK(cudaMemcpyAsync(c->stage[0].p, h_src, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(c->stage[1].p, h_dst, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        d_src = (const uint32_t*)c->stage[0].p;
+        d_dst = (const uint32_t*)c->stage[1].p;
+    }
+    TRY(ns_window_build(c, d_src, d_dst, n, out, stream));
+    if (h_stats) return ns_network_stats(c, out, h_stats, stream);
+    CK(cudaStreamSynchronize(s));
+    return check_launch();
 }
 
 ns_status ns_path_tune(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n, ns_stream_t stream,

@@ -82,6 +82,7 @@ struct ns_ctx {
     ns::SortScratch sc{};
     ns::Buf ghist, offs, tcount, counters, status;
     ns::Buf k64[2], pos, psum, k32[2], v64[2], xk, xv;
+    ns::Buf stage[2];  // device copies of host columns (ns_window_build_host)
     ns::DevStats* host_stats = nullptr;  // pinned
     ns::Tracer tracer;
 };

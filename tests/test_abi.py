@@ -59,6 +59,7 @@ def test_null_arguments_are_invalid_without_gpu():
     assert L.ns_create(None, None, 0) == 1
     assert b"NULL" in L.ns_last_error()
     assert L.ns_window_build(None, None, None, 5, None, None) == 1
+    assert L.ns_window_build_host(None, None, None, 5, None, None, None) == 1
     assert L.ns_accumulate(None, None, None, None) == 1
     assert L.ns_window_ingest(None, None, None, None, 3, None) == 1
     assert L.ns_network_stats(None, None, None, None) == 1
