@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--no-sub", action="store_true", help="headline without the sub-records")
     ap.add_argument("--packets", type=int, default=1 << 30, help="oneshot / anonymize: packets in the input")
     ap.add_argument("--paths", default="sort,hash", help="oneshot: aggregation paths to run (first = value)")
+    ap.add_argument("--sort-split", default="auto", choices=["auto", "on", "off"],
+                    help="headline/oneshot: the sort path's hot-key split")
     ap.add_argument("--windows", type=int, default=WINDOWS, help="stream: windows (512 = the full workload)")
     ap.add_argument("--hash-load", type=float, default=0.25,
                     help="stream: load bound of the accumulated matrix's hash tables")
@@ -332,7 +334,7 @@ def c3_run(args, rank, world, local, clocks, N):
     peak, peak_src = peak_hbm()
     res, stats_by_path = {}, {}
     for path in args.paths.split(","):
-        ctx = ns.Context(local, path=path)
+        ctx = ns.Context(local, path=path, sort_split=args.sort_split)
         M = ns.Matrix(ctx)
         for _ in range(max(args.warmup, 3)):
             ns.window_build(ctx, d_src, d_dst, M)
@@ -355,7 +357,11 @@ def c3_run(args, rank, world, local, clocks, N):
         torch.cuda.synchronize()
         tr = ns.trace_read(ctx)
         ns.trace_enable(ctx, False)
-        info = ns.build_info(M) if hasattr(ns, "build_info") else {}
+        info = {}
+        if path == "sort":
+            si = ns.sort_split_info(ctx)
+            if si["used"]:
+                info = {"hot_keys": si["hot_keys"], "cold_packets": si["cold_packets"]}
         U, S, D = st["unique_links"], st["unique_sources"], st["unique_destinations"]
         alg_bytes = 8 * N + 32 * U + 16 * (S + D)
         if path == "sort":
@@ -395,7 +401,7 @@ def c3_run(args, rank, world, local, clocks, N):
     first = args.paths.split(",")[0]
     e2e = None
     if not args.no_e2e:
-        ctx = ns.Context(local, path=first)
+        ctx = ns.Context(local, path=first, sort_split=args.sort_split)
         M = ns.Matrix(ctx)
         ns.window_build_host(ctx, h_src, h_dst, M)  # sizes the staging buffers
         steps = max(1, min(args.steps, 5))

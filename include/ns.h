@@ -103,6 +103,17 @@ enum {
     NS_COLSORT_PAIRS = 1  /* always (u32 dst, u64 count) pairs */
 };
 
+/* The sort path's hot-key split (see ns_config.sort_split): before the
+ * radix sort, the links a sample of the packets shows to be the heaviest
+ * (up to 4096) are counted in shared memory during one pass over the
+ * packets, and only the other ("cold") packets are sorted; the two are then
+ * merged.  Exact either way; it saves sort work under skew. */
+enum {
+    NS_SPLIT_AUTO = 0, /* ns_path_tune's choice for the size, else on from 2^23 packets */
+    NS_SPLIT_ON = 1,   /* from 2^16 packets (smaller windows never split) */
+    NS_SPLIT_OFF = 2
+};
+
 typedef struct {
     int path;                  /* NS_PATH_* used by ns_window_build */
     uint64_t hbm_budget_bytes; /* serving admission and batch arena budget; 0 = 64 GiB */
@@ -113,6 +124,7 @@ typedef struct {
     double hash_load;          /* load bound of the link, source and destination tables the
                                   library sizes (builds, reserves, growth), in [0.05, 0.9];
                                   0 = 0.5.  Lower costs memory and shortens probe chains. */
+    int sort_split;            /* NS_SPLIT_* for the sort path */
 } ns_config;
 
 /* ---- context ----------------------------------------------------------- */
@@ -249,18 +261,29 @@ ns_status ns_window_build_host(ns_ctx* ctx, const uint32_t* h_src, const uint32_
                                ns_matrix* out, ns_stats* h_stats, ns_stream_t stream);
 
 /* Path tuner: builds A from d_src/d_dst (n > 0 packets, device memory)
- * with the sort path, the hash path without per-CTA caches and the hash path
- * with them (only the one the context's cta_cache forces, if it forces one),
- * three times each, and keeps the fastest of the last two timings of each.
- * The winner becomes the context's NS_PATH_AUTO / NS_CACHE_AUTO choice for
- * every n' with floor(log2 n') = floor(log2 n), and is stored in the tuner
- * cache file (if the context has one) keyed by GPU name and that power of
- * two, where later contexts on the same GPU find it.  *chosen (NS_PATH_SORT
- * or NS_PATH_HASH), *sort_ms and *hash_ms (the faster hash variant) may each
- * be NULL.  Allocates a temporary matrix; blocking.  The paper has no
- * counterpart: its two aggregation paths are this library's own. */
+ * with the sort path without and with the hot-key split (only the one the
+ * context's sort_split forces, if it forces one; no split below 2^16
+ * packets), the hash path without per-CTA caches and the hash path with them
+ * (only the one the context's cta_cache forces, if it forces one), three
+ * times each, and keeps the fastest of the last two timings of each.  The
+ * winner becomes the context's NS_PATH_AUTO / NS_CACHE_AUTO choice, and the
+ * faster sort variant its NS_SPLIT_AUTO choice, for every n' with
+ * floor(log2 n') = floor(log2 n); both are stored in the tuner cache file
+ * (if the context has one) keyed by GPU name and that power of two, where
+ * later contexts on the same GPU find them.  *chosen (NS_PATH_SORT or
+ * NS_PATH_HASH), *sort_ms (the faster sort variant) and *hash_ms (the faster
+ * hash variant) may each be NULL.  Allocates a temporary matrix; blocking.
+ * The paper has no counterpart: its two aggregation paths are this
+ * library's own. */
 ns_status ns_path_tune(ns_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
                        ns_stream_t stream, int* chosen, float* sort_ms, float* hash_ms);
+
+/* What the context's last sort-path build did with the hot-key split:
+ * *used = 1 if it split, then *hot_keys = the links counted apart from the
+ * sort and *cold_packets = the packets that went through the sort (each
+ * pointer may be NULL).  Blocking (reads two counters). */
+ns_status ns_sort_split_info(ns_ctx* ctx, int* used, uint64_t* hot_keys, uint64_t* cold_packets,
+                             ns_stream_t stream);
 
 /* The path ns_window_build would take for a window of n packets
  * (NS_PATH_SORT or NS_PATH_HASH). */
@@ -401,6 +424,41 @@ ns_status ns_stream_poll(ns_server* server, uint64_t ticket, int* done);
  * ticket is forgotten. */
 ns_status ns_stream_wait(ns_server* server, uint64_t ticket, ns_stats* per_window, ns_stats* running,
                          int64_t timeout_us, ns_stream_timing* timing);
+
+/* ---- sharding over several ranks ------------------------------------------ */
+
+/* A traffic matrix split over W ranks (one GPU each), the decomposition of
+ * the paper's whole-graph quantities into per-rank parts: every rank
+ * aggregates its own packets; entries are exchanged so that rank r holds
+ * every entry whose source r owns (its rows of A are then complete: the row
+ * quantities are local, and links, packets and sources add up over the
+ * ranks); a second exchange by destination owner gives rank r every entry
+ * of the destinations it owns (the keys are unique across ranks after the
+ * first exchange, so each received entry is one link of its column), whose
+ * column quantities are then local too.  The maxima reduce by max.  The
+ * exchange itself is the caller's (any transport).  The paper has no
+ * counterpart: it analyses one graph on one GPU. */
+enum { NS_BY_SRC = 0, NS_BY_DST = 1 };
+
+/* The rank in [0, parts) that owns an address: (addr * 0x9E3779B1 mod 2^32)
+ * * parts / 2^32, the same on every rank and in device code.  parts == 0
+ * gives 0. */
+uint32_t ns_owner(uint32_t addr, uint32_t parts);
+
+/* A's nonzeros grouped by owner: d_keys / d_counts (device, cap entries each)
+ * receive the nonzero list reordered so that group p holds the entries whose
+ * source (by = NS_BY_SRC) or destination (NS_BY_DST) is owned by rank p,
+ * ascending by key within the group; h_offsets (host, parts + 1 entries)
+ * receives the groups' starts and the total.  NS_ERR_CAPACITY (nothing
+ * written) if cap < nnz.  Allocates scratch; blocking. */
+ns_status ns_matrix_partition(ns_ctx* ctx, const ns_matrix* m, int by, uint32_t parts, uint64_t* d_keys,
+                              uint64_t* d_counts, uint64_t cap, uint64_t* h_offsets, ns_stream_t stream);
+
+/* m := m + the entries (d_keys[i], d_counts[i]), i < n (device arrays; keys
+ * in any order, repeated keys add up, zero counts are skipped): how a rank
+ * takes in the entries it received.  Asynchronous. */
+ns_status ns_matrix_add_entries(ns_ctx* ctx, ns_matrix* m, const uint64_t* d_keys, const uint64_t* d_counts,
+                                uint64_t n, ns_stream_t stream);
 
 /* ---- checkpoint / resume ------------------------------------------------ */
 

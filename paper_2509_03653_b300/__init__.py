@@ -22,10 +22,10 @@ from ._native import (FIELDS, NsBatchParams, NsConfig, NsError, NsStats, NsStrea
 __all__ = [
     "FIELDS", "NsError", "Context", "Matrix", "window_build", "window_build_host", "accumulate", "window_ingest",
     "window_ingest_stats", "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
-    "matrix_clear", "sync", "PATHS", "path_tune", "path_resolve", "matrix_nodes", "NODES", "anonymize", "Slider",
+    "matrix_clear", "sync", "PATHS", "path_tune", "path_resolve", "sort_split_info", "matrix_nodes", "NODES", "anonymize", "Slider",
     "slider_push", "window_stats_static", "STATIC_MAX_PACKETS",
     "trace_enable", "trace_read", "Batch", "batch_run", "batch_tune", "matrix_reserve_ex",
-    "Server", "stream_submit", "stream_poll", "stream_wait", "diag_random_atomics", "matrix_save", "matrix_load",
+    "owner", "matrix_partition", "matrix_add_entries", "Server", "stream_submit", "stream_poll", "stream_wait", "diag_random_atomics", "matrix_save", "matrix_load",
 ]
 
 STATIC_MAX_PACKETS = 32768  # NS_STATIC_MAX_PACKETS in include/ns.h
@@ -56,11 +56,11 @@ class Context:
 
     def __init__(self, device: int = 0, path: str = "auto", hbm_budget_bytes: int = 0,
                  max_slots: int = 0, tuner_cache: str | None = None, cta_cache: str = "auto",
-                 column_sort: str = "auto", hash_load: float = 0.0):
+                 column_sort: str = "auto", hash_load: float = 0.0, sort_split: str = "auto"):
         self._L = load()
         cfg = NsConfig(PATHS[path], hbm_budget_bytes, max_slots,
                        tuner_cache.encode() if tuner_cache else None, {"auto": 0, "on": 1, "off": 2}[cta_cache],
-                       {"auto": 0, "pairs": 1}[column_sort], hash_load)
+                       {"auto": 0, "pairs": 1}[column_sort], hash_load, {"auto": 0, "on": 1, "off": 2}[sort_split])
         h = ctypes.c_void_p()
         check(self._L.ns_create(ctypes.byref(h), ctypes.byref(cfg), device), "ns_create")
         self.handle = h
@@ -158,6 +158,16 @@ def path_tune(ctx: Context, src: torch.Tensor, dst: torch.Tensor, stream=None) -
     check(ctx._L.ns_path_tune(ctx.handle, _column(src, "src"), _column(dst, "dst"), n, _stream(stream),
                               ctypes.byref(chosen), ctypes.byref(ms_sort), ctypes.byref(ms_hash)), "ns_path_tune")
     return {"path": _PATH_NAMES[chosen.value], "sort_ms": ms_sort.value, "hash_ms": ms_hash.value}
+
+
+def sort_split_info(ctx: Context, stream=None) -> dict:
+    """What the context's last sort-path build did with the hot-key split
+    (ns_sort_split_info): {"used", "hot_keys", "cold_packets"}."""
+    used = ctypes.c_int(0)
+    h, cold = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    check(ctx._L.ns_sort_split_info(ctx.handle, ctypes.byref(used), ctypes.byref(h), ctypes.byref(cold),
+                                    _stream(stream)), "ns_sort_split_info")
+    return {"used": bool(used.value), "hot_keys": int(h.value), "cold_packets": int(cold.value)}
 
 
 def path_resolve(ctx: Context, n: int) -> str:
@@ -554,3 +564,42 @@ def diag_random_atomics(table_words: int, threads: int, reps: int = 5, stream=No
     check(L.ns_diag_random_atomics(table_words, threads, reps, ctypes.byref(us), _stream(stream)),
           "ns_diag_random_atomics")
     return float(us.value)
+
+
+_BY = {"src": 0, "dst": 1}
+
+
+def owner(addr: int, parts: int) -> int:
+    """The rank among `parts` that owns an address (ns_owner)."""
+    return int(load().ns_owner(addr & 0xFFFFFFFF, parts))
+
+
+def matrix_partition(ctx: Context, m: Matrix, by: str, parts: int, stream=None):
+    """A's nonzeros grouped by the owner of their source (by="src") or
+    destination (by="dst"): (keys, counts, offsets) -- two int64 device
+    tensors holding uint64 bit patterns, and the parts + 1 group starts
+    (ns_matrix_partition; blocking)."""
+    nnz = matrix_nnz(m, stream)
+    dev = torch.device("cuda", ctx.device)
+    keys = torch.empty(max(nnz, 1), dtype=torch.int64, device=dev)
+    counts = torch.empty(max(nnz, 1), dtype=torch.int64, device=dev)
+    offs = (ctypes.c_uint64 * (parts + 1))()
+    check(ctx._L.ns_matrix_partition(ctx.handle, m.live(), _BY[by], parts, ctypes.c_void_p(keys.data_ptr()),
+                                     ctypes.c_void_p(counts.data_ptr()), max(nnz, 1), offs, _stream(stream)),
+          "ns_matrix_partition")
+    return keys[:nnz], counts[:nnz], [int(x) for x in offs]
+
+
+def matrix_add_entries(ctx: Context, m: Matrix, keys: torch.Tensor, counts: torch.Tensor, stream=None):
+    """m := m + the (key, count) entries of two device tensors of 64-bit
+    elements (ns_matrix_add_entries)."""
+    n = keys.numel()
+    if counts.numel() != n:
+        raise ValueError("keys and counts differ in length")
+    for t, name in ((keys, "keys"), (counts, "counts")):
+        if n and (t.element_size() != 8 or not t.is_contiguous() or not t.is_cuda):
+            raise ValueError(f"{name} must be a contiguous 64-bit CUDA tensor")
+    check(ctx._L.ns_matrix_add_entries(ctx.handle, m.live(), ctypes.c_void_p(keys.data_ptr() if n else 0),
+                                       ctypes.c_void_p(counts.data_ptr() if n else 0), n, _stream(stream)),
+          "ns_matrix_add_entries")
+

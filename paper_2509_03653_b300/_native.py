@@ -16,7 +16,7 @@ ST = ctypes.c_int  # ns_status
 
 class NsConfig(ctypes.Structure):
     _fields_ = [("path", I32), ("hbm_budget_bytes", U64), ("max_slots", I32), ("tuner_cache", ctypes.c_char_p),
-                ("cta_cache", I32), ("column_sort", I32), ("hash_load", ctypes.c_double)]
+                ("cta_cache", I32), ("column_sort", I32), ("hash_load", ctypes.c_double), ("sort_split", I32)]
 
 
 class NsStats(ctypes.Structure):
@@ -58,6 +58,7 @@ SIGNATURES = {
     "ns_path_tune": (ST, [P, P, P, U64, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                           ctypes.POINTER(ctypes.c_float)]),
     "ns_path_resolve": (ST, [P, U64, ctypes.POINTER(ctypes.c_int)]),
+    "ns_sort_split_info": (ST, [P, ctypes.POINTER(I32), ctypes.POINTER(U64), ctypes.POINTER(U64), P]),
     "ns_matrix_nodes": (ST, [P, P, ctypes.c_int, P, P, P, U64, ctypes.POINTER(U64), P]),
     "ns_anonymize": (ST, [P, P, P, U64, P, U64, P, P, ctypes.POINTER(U64), P]),
     "ns_server_reserve": (ST, [P, U64]),
@@ -76,6 +77,9 @@ SIGNATURES = {
     "ns_trace_read": (ST, [P, ctypes.POINTER(NsTraceEntry), I32, ctypes.POINTER(I32)]),
     "ns_matrix_reserve_ex": (ST, [P, U64, U64, P]),
     "ns_matrix_save": (ST, [P, ctypes.c_char_p, P]),
+    "ns_owner": (ctypes.c_uint32, [ctypes.c_uint32, ctypes.c_uint32]),
+    "ns_matrix_partition": (ST, [P, P, I32, ctypes.c_uint32, P, P, U64, ctypes.POINTER(U64), P]),
+    "ns_matrix_add_entries": (ST, [P, P, P, P, U64, P]),
     "ns_matrix_load": (ST, [P, ctypes.c_char_p, P, P]),
     "ns_batch_create": (ST, [P, U64, U64, ctypes.POINTER(P)]),
     "ns_batch_free": (None, [P]),

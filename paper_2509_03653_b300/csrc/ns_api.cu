@@ -229,9 +229,23 @@ ns_status sort_scratch(ns_ctx* c, u64 n) {
     return NS_OK;
 }
 
+// Whether a sort-path build of n packets takes the hot-key split: the
+// context's setting, else ns_path_tune's measurement for the size, else on
+// from 2^23 packets.  Below 2^16 packets the sample would be too small.
+constexpr int kAutoSplitLog2 = 23;
+bool use_split(const ns_ctx* c, u64 n) {
+    if (n < (1ull << 16) || c->cfg.sort_split == NS_SPLIT_OFF) return false;
+    if (c->cfg.sort_split == NS_SPLIT_ON) return true;
+    const int lg = 63 - __builtin_clzll(n);
+    const auto it = c->path_choice.find(lg);
+    if (it != c->path_choice.end() && it->second.split >= 0) return it->second.split != 0;
+    return lg >= kAutoSplitLog2;
+}
+
 // Sort path: A_t's sorted nonzero list and its statistics.
+// split: -1 = use_split's rule, 0 = no split, 1 = split (from 2^16 packets).
 ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n, ns_matrix* out,
-                     cudaStream_t s) {
+                     cudaStream_t s, int split = -1) {
     out->fmt = FMT_LIST;
     out->bound = n;
     CK(cudaMemsetAsync(out->stats.p, 0, sizeof(DevStats), s));
@@ -258,13 +272,22 @@ ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n,
     u64* nnz = &st->v[S_LINKS];
     u64* runs_out = (u64*)c->counters.p;
 
-    // links: sort packed keys, then runs of equal keys (Table 2 row 3)
+    // links: sort packed keys, then runs of equal keys (Table 2 row 3);
+    // with the split, the heaviest sampled links are counted apart and only
+    // the other packets are sorted
     u64* kb[2] = {(u64*)c->k64[0].p, (u64*)c->k64[1].p};
-    const int r = radix_sort_packets(src, dst, kb, n, c->sc, st, s);
-    launch_runs(RUN_U64, false, kb[r], nullptr, n, nullptr, (u64*)out->keys.p,
-                (u64*)c->pos.p, nullptr, nnz, c->sc, st, s);
-    launch_run_stats(RS_LINKS, (const u64*)c->pos.p, nullptr, nnz, n, (u64*)out->counts.p,
-                     st, c->sms, &c->tracer, s);
+    c->last_split = split < 0 ? use_split(c, n) : (split != 0 && n >= (1ull << 16));
+    if (c->last_split) {
+        TRY(buf_reserve(c->split, split_state_bytes()));
+        sort_links_split(src, dst, n, kb, (u64*)c->v64[0].p, (u64*)c->pos.p, c->split.p, (u64*)out->keys.p,
+                         (u64*)out->counts.p, c->sc, st, c->sms, s);
+    } else {
+        const int r = radix_sort_packets(src, dst, kb, n, c->sc, st, s);
+        launch_runs(RUN_U64, false, kb[r], nullptr, n, nullptr, (u64*)out->keys.p,
+                    (u64*)c->pos.p, nullptr, nnz, c->sc, st, s);
+        launch_run_stats(RS_LINKS, (const u64*)c->pos.p, nullptr, nnz, n, (u64*)out->counts.p,
+                         st, c->sms, &c->tracer, s);
+    }
     // rows: runs of equal src over the source-major list (rows 5-9)
     u64* packed = packed_cols ? (u64*)c->v64[0].p : nullptr;
     launch_runs(RUN_SRC_OF_U64, true, out->keys.p, (const u64*)out->counts.p, n, nnz, nullptr,
@@ -324,11 +347,13 @@ void load_path_choices(ns_ctx* c) {
         if (kv.first.compare(0, prefix.size(), prefix) != 0) continue;
         const int lg = atoi(kv.first.c_str() + prefix.size());
         std::string p;
-        double cache = 0;
+        double cache = 0, split = -1;
         if (lg < 0 || lg > 40 || !json_string(kv.second, "path", &p)) continue;
         json_number(kv.second, "cta_cache", &cache);
-        if (p == "sort") c->path_choice[lg] = {NS_PATH_SORT, false};
-        if (p == "hash") c->path_choice[lg] = {NS_PATH_HASH, cache != 0};
+        json_number(kv.second, "sort_split", &split);
+        const int sp = split < 0 ? -1 : (split != 0 ? 1 : 0);
+        if (p == "sort") c->path_choice[lg] = {NS_PATH_SORT, false, sp};
+        if (p == "hash") c->path_choice[lg] = {NS_PATH_HASH, cache != 0, sp};
     }
 }
 
@@ -391,6 +416,8 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
         return fail(NS_ERR_INVALID, "ns_create: unknown cta_cache %d", c.cta_cache);
     if (c.column_sort < NS_COLSORT_AUTO || c.column_sort > NS_COLSORT_PAIRS)
         return fail(NS_ERR_INVALID, "ns_create: unknown column_sort %d", c.column_sort);
+    if (c.sort_split < NS_SPLIT_AUTO || c.sort_split > NS_SPLIT_OFF)
+        return fail(NS_ERR_INVALID, "ns_create: unknown sort_split %d", c.sort_split);
     if (c.hash_load == 0.0) c.hash_load = 0.5;
     if (!(c.hash_load >= 0.05 && c.hash_load <= 0.9))
         return fail(NS_ERR_INVALID, "ns_create: hash_load %g outside [0.05, 0.9]", c.hash_load);
@@ -433,7 +460,7 @@ void ns_destroy(ns_ctx* c) {
     cudaDeviceSynchronize();
     Buf* all[] = {&c->ghist, &c->offs, &c->tcount, &c->counters, &c->status, &c->k64[0], &c->k64[1],
                   &c->pos, &c->psum, &c->k32[0], &c->k32[1], &c->v64[0], &c->v64[1], &c->xk, &c->xv,
-                  &c->stage[0], &c->stage[1]};
+                  &c->stage[0], &c->stage[1], &c->split};
     for (Buf* b : all) buf_free(*b);
     if (c->host_stats) cudaFreeHost(c->host_stats);
     tracer_destroy(&c->tracer);
@@ -607,15 +634,21 @@ ns_status ns_path_tune(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, 
     if (!d_src || !d_dst) return fail(NS_ERR_INVALID, "ns_path_tune: NULL input");
     if (n >= (1ull << 40)) return fail(NS_ERR_INVALID, "ns_path_tune: n too large");
     cudaStream_t s = (cudaStream_t)stream;
-    // candidates: the sort path, then the hash path without and with per-CTA
-    // caches (only the forced one if the context fixes cta_cache)
+    // candidates: the sort path without and with the hot-key split (only the
+    // forced one if the context fixes sort_split; no split below 2^16
+    // packets), then the hash path without and with per-CTA caches (only the
+    // forced one if the context fixes cta_cache)
     struct Cand {
-        int path, cache;
+        int path, cache, split;
         float ms;
     };
-    std::vector<Cand> cand = {{NS_PATH_SORT, 0, 1e30f}};
-    if (c->cfg.cta_cache != NS_CACHE_ON) cand.push_back({NS_PATH_HASH, 0, 1e30f});
-    if (c->cfg.cta_cache != NS_CACHE_OFF) cand.push_back({NS_PATH_HASH, 1, 1e30f});
+    std::vector<Cand> cand;
+    const bool can_split = n >= (1ull << 16);
+    if (c->cfg.sort_split != NS_SPLIT_ON || !can_split) cand.push_back({NS_PATH_SORT, 0, 0, 1e30f});
+    if (c->cfg.sort_split != NS_SPLIT_OFF && can_split) cand.push_back({NS_PATH_SORT, 0, 1, 1e30f});
+    const size_t n_sort = cand.size();
+    if (c->cfg.cta_cache != NS_CACHE_ON) cand.push_back({NS_PATH_HASH, 0, -1, 1e30f});
+    if (c->cfg.cta_cache != NS_CACHE_OFF) cand.push_back({NS_PATH_HASH, 1, -1, 1e30f});
     ns_matrix* m = nullptr;
     TRY(ns_matrix_create(c, &m));
     cudaEvent_t e0, e1;
@@ -627,7 +660,7 @@ ns_status ns_path_tune(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, 
         // the next two are timed
         for (int rep = 0; rep < 3 && st == NS_OK; ++rep) {
             cudaEventRecord(e0, s);
-            st = k.path == NS_PATH_SORT ? build_sort(c, d_src, d_dst, n, m, s)
+            st = k.path == NS_PATH_SORT ? build_sort(c, d_src, d_dst, n, m, s, k.split)
                                         : build_hash(c, d_src, d_dst, n, m, s, k.cache);
             cudaEventRecord(e1, s);
             if (st != NS_OK) break;
@@ -647,22 +680,48 @@ ns_status ns_path_tune(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, 
     ns_matrix_free(m);
     TRY(st);
     const Cand* best = &cand[0];
-    float best_hash = 1e30f;
-    for (const Cand& k : cand) {
+    const Cand* best_sort = &cand[0];
+    float best_hash = 1e30f, split_ms = -1, plain_ms = -1;
+    for (size_t i = 0; i < cand.size(); ++i) {
+        const Cand& k = cand[i];
         if (k.ms < best->ms) best = &k;
+        if (i < n_sort && k.ms < best_sort->ms) best_sort = &k;
         if (k.path == NS_PATH_HASH) best_hash = std::min(best_hash, k.ms);
+        if (k.path == NS_PATH_SORT) (k.split ? split_ms : plain_ms) = k.ms;
     }
     const int lg = floor_log2(n);
-    c->path_choice[lg] = {best->path, best->cache != 0};
+    // the sort path's split choice is kept for the size whichever path wins
+    c->path_choice[lg] = {best->path, best->cache != 0, best_sort->split};
     if (chosen) *chosen = best->path;
-    if (sort_ms) *sort_ms = cand[0].ms;
+    if (sort_ms) *sort_ms = best_sort->ms;
     if (hash_ms) *hash_ms = best_hash;
     auto cache = tuner_load(c->tuner_cache);
-    char val[160];
-    snprintf(val, sizeof val, "{\"path\": \"%s\", \"cta_cache\": %d, \"sort_ms\": %.4f, \"hash_ms\": %.4f}",
-             best->path == NS_PATH_SORT ? "sort" : "hash", best->cache, cand[0].ms, best_hash);
+    char val[256];
+    snprintf(val, sizeof val,
+             "{\"path\": \"%s\", \"cta_cache\": %d, \"sort_split\": %d, \"sort_ms\": %.4f, \"hash_ms\": %.4f, "
+             "\"sort_split_ms\": %.4f, \"sort_plain_ms\": %.4f}",
+             best->path == NS_PATH_SORT ? "sort" : "hash", best->cache, best_sort->split, best_sort->ms, best_hash,
+             split_ms, plain_ms);
     cache[path_key(c->device, lg)] = val;
     tuner_store(c->tuner_cache, cache);
+    return NS_OK;
+}
+
+ns_status ns_sort_split_info(ns_ctx* c, int* used, uint64_t* hot_keys, uint64_t* cold_packets,
+                             ns_stream_t stream) {
+    if (!c) return fail(NS_ERR_INVALID, "ns_sort_split_info: NULL context");
+    DeviceGuard device_guard(c->device);
+    if (used) *used = c->last_split ? 1 : 0;
+    u64 h = 0, cold = 0;
+    if (c->last_split && c->split.p) {
+        const cudaError_t e = split_info(c->split.p, &h, &cold, (cudaStream_t)stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(NS_ERR_CUDA, "ns_sort_split_info: %s", cudaGetErrorString(e));
+        }
+    }
+    if (hot_keys) *hot_keys = h;
+    if (cold_packets) *cold_packets = cold;
     return NS_OK;
 }
 

@@ -77,12 +77,15 @@ struct ns_ctx {
     struct PathChoice {
         int path;
         bool cta_cache;
+        int split;  // sort path: 1 split, 0 not, -1 the size rule
     };
     std::map<int, PathChoice> path_choice;
     ns::SortScratch sc{};
     ns::Buf ghist, offs, tcount, counters, status;
     ns::Buf k64[2], pos, psum, k32[2], v64[2], xk, xv;
     ns::Buf stage[2];  // device copies of host columns (ns_window_build_host)
+    ns::Buf split;     // the hot-key split's device state
+    bool last_split = false;  // the last sort-path build split
     ns::DevStats* host_stats = nullptr;  // pinned
     ns::Tracer tracer;
 };

@@ -78,6 +78,15 @@ inline u32 next_tag(SortScratch& sc, cudaStream_t s) {
 }
 
 u64 sort_tiles(u64 n);
+// CTAs of kernel fn resident at once on the current GPU (the kernel's shared
+// memory attribute is set on first use, per device).
+int resident_ctas_of(const void* fn, int threads, size_t smem);
+// The sort path's hot-key split (ns_split.cu): A's sorted nonzero list of n
+// packets with the heaviest sampled links counted apart from the sort.
+u64 split_state_bytes();
+void sort_links_split(const u32* src, const u32* dst, u64 n, u64* kb[2], u64* heads, u64* pos, void* state,
+                      u64* keys_out, u64* counts_out, SortScratch& sc, DevStats* st, int sms, cudaStream_t s);
+cudaError_t split_info(const void* state, u64* hot_keys, u64* cold_packets, cudaStream_t s);
 void launch_diag_wait(int which, u64* status_word, DevStats* st, cudaStream_t s);
 void launch_diag_rand3(u64* a, u64* b, u64* c, u64 mask, u64 threads, u64 seed, cudaStream_t s);
 int sort_radix();
@@ -124,6 +133,10 @@ void launch_batch_stats_out(const DevStats* wstats, u64 W, u64* out, int sms, cu
 // values are stable; keys-only sorts order only the sorted bits.
 int radix_sort_packets(const u32* src, const u32* dst, u64* kbuf[2], u64 n,
                        SortScratch& sc, DevStats* st, cudaStream_t s);
+// n_dev (<= n) u64 keys from `keys` (which must not be kbuf[0]), all 64 bits.
+// trace_name labels the digit passes (NULL: "k_onesweep<u64 key>").
+int radix_sort_keys64(const u64* keys, const u64* n_dev, u64* kbuf[2], u64 n, SortScratch& sc, DevStats* st,
+                      cudaStream_t s, const char* trace_name);
 int radix_sort_pairs64(const u64* keys, const u64* vals, const u64* n_dev,
                        u64* kbuf[2], u64* vbuf[2], u64 n, SortScratch& sc,
                        DevStats* st, cudaStream_t s);

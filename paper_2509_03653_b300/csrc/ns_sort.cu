@@ -1106,6 +1106,7 @@ __global__ void k_diag_mbarrier(DevStats* st) {
 }  // namespace
 
 u64 sort_tiles(u64 n) { return (n + kTile - 1) / kTile; }
+int resident_ctas_of(const void* fn, int threads, size_t smem) { return resident_ctas(fn, threads, smem); }
 int sort_radix() { return kRadix; }
 
 // Sort n keys by bits [begin_bit, begin_bit + 8*passes).  Pass p reads
@@ -1159,6 +1160,17 @@ int radix_sort_packets(const u32* src, const u32* dst, u64* kbuf[2], u64 n,
     in.bulk = (((uintptr_t)src | (uintptr_t)dst) & 15) == 0;
     u64* vb[2] = {nullptr, nullptr};
     return radix_sort_t<u64, false, LOAD_PACK>(in, (u64**)kbuf, vb, n, 0, 8, sc, st, s);
+}
+
+int radix_sort_keys64(const u64* keys, const u64* n_dev, u64* kbuf[2], u64 n, SortScratch& sc, DevStats* st,
+                      cudaStream_t s, const char* trace_name) {
+    SortIn in{};
+    in.keys = keys;
+    in.n_dev = n_dev;
+    in.bulk = ((uintptr_t)keys & 15) == 0;
+    in.trace_name = trace_name;
+    u64* vb[2] = {nullptr, nullptr};
+    return radix_sort_t<u64, false, LOAD_KEYS>(in, kbuf, vb, n, 0, 8, sc, st, s);
 }
 
 int radix_sort_pairs64(const u64* keys, const u64* vals, const u64* n_dev,

@@ -1,0 +1,405 @@
+// ns_split.cu -- the sort path's hot-key split.
+//
+// Under skewed traffic a small set of links carries a large share of the
+// packets (Zipf(1.2) over 2^24 addresses per column: the 4096 heaviest of
+// ~1.5e8 distinct links carry about half of 2^30 packets).  Sorting their
+// copies is wasted work: every copy travels through all eight digit passes
+// only to be counted by the run kernel.  So, before the sort:
+//
+//   1. sample: 64 evenly spaced blocks of consecutive packets (2^21 packets
+//      at most) are packed into keys, sorted and cut into runs with the sort
+//      path's own kernels;
+//   2. select: the keys seen at least kMinHotSample times in the sample, the
+//      most frequent first, up to kHotMax of them, become the hot set
+//      (sorted ascending; a table of 2 kHotMax slots is built from it);
+//   3. split: one pass over all packets.  Each CTA holds the table in shared
+//      memory; a packet whose key is hot adds 1 to the CTA's count of that
+//      key, every other ("cold") key is appended to the cold-key buffer
+//      (warp-compacted, one global reservation per CTA chunk, in no
+//      particular order).  At the end each CTA adds its counts to the global
+//      per-slot counts;
+//   4. the cold keys are sorted (LSD onesweep, the count read on the device)
+//      and cut into runs;
+//   5. merge: the cold runs and the hot keys (disjoint key sets, both
+//      ascending) are merged into A's sorted nonzero list; each element's
+//      place is its own rank plus the number of keys of the other set below
+//      it.  The whole-matrix quantities come out of the same pass.
+//
+// The result does not depend on which keys are hot: any hot set gives the
+// same list, since a key's count is the sum of its hot and cold occurrences
+// and a hot key has no cold occurrence.  The sample only decides how much
+// work the split saves.  Every hot key occurs in the input (the sample is
+// drawn from it), so every hot count is at least 1.
+#include <algorithm>
+#include <cstddef>
+
+#include "ns_api_internal.h"
+#include "ns_common.cuh"
+#include "ns_kernels.h"
+
+namespace ns {
+
+namespace {
+
+constexpr int kHotMax = 4096;
+constexpr int kHotSlots = 2 * kHotMax;  // load <= 1/2
+constexpr int kHotSlotBits = 13;
+static_assert((1 << kHotSlotBits) == kHotSlots, "slot bits");
+constexpr u64 kEmpty = ~0ull;  // an empty slot (never a hot key)
+constexpr int kSampleBlocks = 64;
+constexpr u64 kSampleMax = 1ull << 21;
+constexpr u32 kHotBins = 2048;      // sample run lengths, the last bin holding >= kHotBins - 1
+constexpr u32 kMinHotSample = 4;    // fewest sample occurrences of a hot key
+static_assert(kSampleMax / (kHotBins - 1) < (u64)kHotMax, "the top bin alone never exceeds the hot set");
+
+// Device-side state of one split (one allocation per context).
+struct SplitDev {
+    u64 table[kHotSlots];       // slot -> hot key (kEmpty = free)
+    u64 slot_count[kHotSlots];  // packets of the slot's key
+    u64 hot[kHotMax];           // hot keys ascending
+    u32 hist[kHotBins];         // sample keys by run length
+    u64 H;                      // hot keys
+    u64 thresh;                 // least sample count of a hot key
+    u64 cold;                   // cold packets
+    u64 R_sample;               // distinct sample keys
+    u64 R_cold;                 // distinct cold keys
+};
+
+__device__ __forceinline__ u32 hot_home(u64 key) { return (u32)((key * 0x9E3779B97F4A7C15ull) >> (64 - kHotSlotBits)); }
+
+// Slot of `key` in a table of kHotSlots keys, or -1.  The table is at most
+// half full, so every probe sequence ends at a free slot.
+__device__ __forceinline__ int hot_find(const u64* table, u64 key) {
+    u32 h = hot_home(key);
+    for (int i = 0; i < kHotSlots; ++i) {
+        const u64 k = table[h];
+        if (k == key) return (int)h;
+        if (k == kEmpty) return -1;
+        h = (h + 1) & (kHotSlots - 1);
+    }
+    return -1;
+}
+
+__device__ __forceinline__ u64 pack_key(u32 s, u32 d) { return ((u64)s << 32) | (u64)d; }
+
+// 1. The sample: packets [b * (n / 64), + blen) of each block b, packed.
+__global__ void k_sample_gather(const u32* __restrict__ src, const u32* __restrict__ dst, u64 n, u64 blen,
+                                u64* __restrict__ out) {
+    const u64 m = blen * kSampleBlocks;
+    const u64 stride = n / kSampleBlocks;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (u64)gridDim.x * blockDim.x) {
+        const u64 p = (i / blen) * stride + (i % blen);
+        out[i] = pack_key(__ldg(src + p), __ldg(dst + p));
+    }
+}
+
+// 2a. Sample keys by run length (only lengths >= kMinHotSample).
+__global__ void __launch_bounds__(1024) k_hot_hist(const u64* __restrict__ pos, SplitDev* sd) {
+    __shared__ u32 h[kHotBins];
+    for (u32 i = threadIdx.x; i < kHotBins; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const u64 R = sd->R_sample;
+    for (u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (u64)gridDim.x * blockDim.x) {
+        const u64 len = pos[r + 1] - pos[r];
+        if (len >= kMinHotSample) atomicAdd(&h[len < kHotBins - 1 ? len : kHotBins - 1], 1u);
+    }
+    __syncthreads();
+    for (u32 i = threadIdx.x; i < kHotBins; i += blockDim.x)
+        if (h[i]) atomicAdd(&sd->hist[i], h[i]);
+}
+
+// 2b. The least sample count t >= kMinHotSample such that at most kHotMax
+// keys occur t or more times (none: t = 2^64 - 1).
+__global__ void k_hot_pick(SplitDev* sd) {
+    if (threadIdx.x != 0) return;
+    u64 cum = 0, t = kEmpty;
+    for (u32 b = kHotBins - 1; b >= kMinHotSample; --b) {
+        if (cum + sd->hist[b] > (u64)kHotMax) break;
+        cum += sd->hist[b];
+        if (cum) t = b;
+    }
+    sd->thresh = t;
+}
+
+// 2c. The hot keys, in any order.
+__global__ void k_hot_collect(const u64* __restrict__ heads, const u64* __restrict__ pos, SplitDev* sd) {
+    const u64 R = sd->R_sample, t = sd->thresh;
+    for (u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (u64)gridDim.x * blockDim.x) {
+        const u64 key = heads[r];
+        if (pos[r + 1] - pos[r] >= t && key != kEmpty) {
+            const u64 i = atomicAdd(&sd->H, 1ull);
+            if (i < (u64)kHotMax) sd->hot[i] = key;
+        }
+    }
+}
+
+// 2d. One CTA: sorts the hot keys (bitonic, in shared memory) and builds the
+// table from them; clears the per-slot counts.
+constexpr int kTableThreads = 1024;
+__global__ void __launch_bounds__(kTableThreads, 1) k_hot_table(SplitDev* sd) {
+    extern __shared__ __align__(16) u64 sh[];
+    u64* keys = sh;              // [kHotMax]
+    u64* table = sh + kHotMax;   // [kHotSlots]
+    const u64 H = sd->H < (u64)kHotMax ? sd->H : (u64)kHotMax;
+    for (int i = threadIdx.x; i < kHotMax; i += kTableThreads) keys[i] = (u64)i < H ? sd->hot[i] : kEmpty;
+    for (int i = threadIdx.x; i < kHotSlots; i += kTableThreads) table[i] = kEmpty;
+    __syncthreads();
+    for (int k = 2; k <= kHotMax; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < kHotMax; i += kTableThreads) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const bool up = (i & k) == 0;
+                    const u64 a = keys[i], b = keys[p];
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[p] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < (int)H; i += kTableThreads) {
+        const u64 key = keys[i];
+        sd->hot[i] = key;
+        u32 h = hot_home(key);
+        for (int q = 0; q < kHotSlots; ++q) {  // distinct keys, table half full: ends at a free slot
+            const u64 prev = atomicCAS(reinterpret_cast<unsigned long long*>(&table[h]), kEmpty, key);
+            if (prev == kEmpty) break;
+            h = (h + 1) & (kHotSlots - 1);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHotSlots; i += kTableThreads) {
+        sd->table[i] = table[i];
+        sd->slot_count[i] = 0;
+    }
+    if (threadIdx.x == 0) sd->H = H;
+}
+
+// 3. The split.  Persistent CTAs take chunks of kSplitThreads * 8 packets
+// (chunk c, c + grid, ...).  With 16-byte-aligned columns a thread loads its
+// eight packets as two 16-byte vectors per column.
+constexpr int kSplitThreads = 1024;
+constexpr int kSplitItems = 8;
+constexpr u64 kSplitChunk = (u64)kSplitThreads * kSplitItems;
+struct SplitSmem {
+    u64 table[kHotSlots];
+    u64 count[kHotSlots];
+    u32 wsum[kSplitThreads / 32];
+    u64 base;
+};
+
+__global__ void __launch_bounds__(kSplitThreads, 1) k_hot_split(const u32* __restrict__ src, const u32* __restrict__ dst,
+                                                                 u64 n, bool vec, SplitDev* sd, u64* __restrict__ cold) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SplitSmem& sm = *reinterpret_cast<SplitSmem*>(smem_raw);
+    const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5, t = threadIdx.x;
+    const u32 FULL = 0xFFFFFFFFu;
+    for (int i = t; i < kHotSlots; i += kSplitThreads) {
+        sm.table[i] = sd->table[i];
+        sm.count[i] = 0;
+    }
+    __syncthreads();
+    const u32 lt = lanemask_lt();
+    for (u64 base = (u64)blockIdx.x * kSplitChunk; base < n; base += (u64)gridDim.x * kSplitChunk) {
+        u64 key[kSplitItems];
+        u32 valid = 0;
+        if (vec && n - base >= kSplitChunk) {
+            valid = (1u << kSplitItems) - 1;
+#pragma unroll
+            for (int h = 0; h < kSplitItems / 4; ++h) {
+                const u64 i = base + (u64)h * (4 * kSplitThreads) + 4 * t;
+                const uint4 a = __ldg(reinterpret_cast<const uint4*>(src + i));
+                const uint4 b = __ldg(reinterpret_cast<const uint4*>(dst + i));
+                key[4 * h + 0] = pack_key(a.x, b.x);
+                key[4 * h + 1] = pack_key(a.y, b.y);
+                key[4 * h + 2] = pack_key(a.z, b.z);
+                key[4 * h + 3] = pack_key(a.w, b.w);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < kSplitItems; ++u) {
+                const u64 i = base + (u64)u * kSplitThreads + t;
+                key[u] = i < n ? pack_key(__ldg(src + i), __ldg(dst + i)) : 0;
+                valid |= (i < n ? 1u : 0u) << u;
+            }
+        }
+        // hot keys are counted here; the others are marked cold
+        u32 coldm = 0;
+#pragma unroll
+        for (int u = 0; u < kSplitItems; ++u) {
+            if ((valid >> u) & 1u) {
+                const int slot = hot_find(sm.table, key[u]);
+                if (slot >= 0) atomicAdd(reinterpret_cast<unsigned long long*>(&sm.count[slot]), 1ull);
+                else coldm |= 1u << u;
+            }
+        }
+        u32 bal[kSplitItems];
+        u32 wtot = 0;
+#pragma unroll
+        for (int u = 0; u < kSplitItems; ++u) {
+            bal[u] = __ballot_sync(FULL, (coldm >> u) & 1u);
+            wtot += __popc(bal[u]);
+        }
+        if (lane == 0) sm.wsum[w] = wtot;
+        __syncthreads();
+        if (t == 0) {
+            u32 run = 0;
+            for (int i = 0; i < kSplitThreads / 32; ++i) {
+                const u32 x = sm.wsum[i];
+                sm.wsum[i] = run;
+                run += x;
+            }
+            sm.base = run ? atomicAdd(&sd->cold, (u64)run) : 0;
+        }
+        __syncthreads();
+        u64 off = sm.base + sm.wsum[w];
+#pragma unroll
+        for (int u = 0; u < kSplitItems; ++u) {
+            if ((coldm >> u) & 1u) cold[off + __popc(bal[u] & lt)] = key[u];
+            off += __popc(bal[u]);
+        }
+        __syncthreads();  // wsum and base are rewritten by the next chunk
+    }
+    __syncthreads();
+    for (int i = t; i < kHotSlots; i += kSplitThreads)
+        if (sm.count[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&sd->slot_count[i]),
+                                   (unsigned long long)sm.count[i]);
+}
+
+// 5. Merge of the cold runs (heads[r], length pos[r+1] - pos[r]) with the
+// hot keys into keys/counts, and the whole-matrix quantities: unique links,
+// valid packets and the largest count.
+constexpr int kMergeThreads = 512;
+__device__ __forceinline__ u64 count_below(const u64* a, u64 len, u64 key) {
+    u64 lo = 0, hi = len;  // first index with a[i] >= key
+    while (lo < hi) {
+        const u64 mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kMergeThreads) k_hot_merge(const u64* __restrict__ heads, const u64* __restrict__ pos,
+                                                             const SplitDev* sd, u64* __restrict__ keys_out,
+                                                             u64* __restrict__ counts_out, DevStats* st) {
+    __shared__ u64 hot[kHotMax];
+    __shared__ u64 bmax;
+    const u64 H = sd->H, RC = sd->R_cold;
+    for (u64 i = threadIdx.x; i < H; i += kMergeThreads) hot[i] = sd->hot[i];
+    if (threadIdx.x == 0) bmax = 0;
+    __syncthreads();
+    u64 mx = 0, hot_sum = 0;
+    for (u64 i = (u64)blockIdx.x * kMergeThreads + threadIdx.x; i < RC + H; i += (u64)gridDim.x * kMergeThreads) {
+        if (i < RC) {
+            const u64 key = heads[i], c = pos[i + 1] - pos[i];
+            const u64 at = i + count_below(hot, H, key);
+            keys_out[at] = key;
+            counts_out[at] = c;
+            mx = c > mx ? c : mx;
+        } else {
+            const u64 h = i - RC, key = hot[h];
+            const int slot = hot_find(sd->table, key);
+            const u64 c = slot >= 0 ? sd->slot_count[slot] : 0;
+            const u64 at = h + count_below(heads, RC, key);
+            keys_out[at] = key;
+            counts_out[at] = c;
+            mx = c > mx ? c : mx;
+            hot_sum += c;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+        hot_sum += __shfl_xor_sync(0xFFFFFFFFu, hot_sum, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (mx) atomicMax(&bmax, mx);
+        if (hot_sum) atomicAdd(&st->v[S_VALID], hot_sum);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (bmax) atomicMax(&st->v[S_MAX_LINK], bmax);
+        if (blockIdx.x == 0) {
+            st->v[S_LINKS] = RC + H;
+            atomicAdd(&st->v[S_VALID], pos[RC]);  // the cold packets
+        }
+    }
+}
+
+}  // namespace
+
+u64 split_state_bytes() { return sizeof(SplitDev); }
+
+// The sort path's links with the hot-key split; see the top of this file.
+// kb: the two key buffers of n entries; heads/pos: run scratch (n and n + 1
+// entries); state: split_state_bytes() of device memory.  Writes A's sorted
+// nonzero list to keys_out/counts_out and the links, valid-packets and
+// max-link fields of st.
+void sort_links_split(const u32* src, const u32* dst, u64 n, u64* kb[2], u64* heads, u64* pos, void* state,
+                      u64* keys_out, u64* counts_out, SortScratch& sc, DevStats* st, int sms, cudaStream_t s) {
+    SplitDev* sd = (SplitDev*)state;
+    Tracer* tr = sc.tr;
+    // the histogram and the scalars after it start from zero
+    cudaMemsetAsync(&sd->hist, 0, sizeof(SplitDev) - offsetof(SplitDev, hist), s);
+    // 1. sample, sorted, in runs
+    const u64 m = std::min<u64>(kSampleMax, (n / 4) / kSampleBlocks * kSampleBlocks);
+    const u64 blen = m / kSampleBlocks;
+    {
+        TraceScope ts(tr, "k_sample_gather", s);
+        k_sample_gather<<<sms * 4, 256, 0, s>>>(src, dst, n, blen, kb[1]);
+    }
+    const int r = radix_sort_keys64(kb[1], nullptr, kb, m, sc, st, s, "k_onesweep<sample key>");
+    launch_runs(RUN_U64, false, kb[r], nullptr, m, nullptr, heads, pos, nullptr, &sd->R_sample, sc, st, s);
+    // 2. the hot set and its table
+    {
+        TraceScope ts(tr, "k_hot_select", s);
+        k_hot_hist<<<sms, 1024, 0, s>>>(pos, sd);
+        k_hot_pick<<<1, 32, 0, s>>>(sd);
+        k_hot_collect<<<sms * 2, 256, 0, s>>>(heads, pos, sd);
+        const size_t tsmem = sizeof(u64) * (kHotMax + kHotSlots);
+        static bool attr_set[64] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+            cudaFuncSetAttribute(k_hot_table, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem);
+            attr_set[dev] = true;
+        }
+        k_hot_table<<<1, kTableThreads, tsmem, s>>>(sd);
+    }
+    // 3. the split: hot keys counted, cold keys into kb[1]
+    {
+        const size_t smem = sizeof(SplitSmem);
+        const int grid = resident_ctas_of((const void*)k_hot_split, kSplitThreads, smem);
+        const u64 chunks = (n + kSplitChunk - 1) / kSplitChunk;
+        const bool vec = (((uintptr_t)src | (uintptr_t)dst) & 15) == 0;
+        TraceScope ts(tr, "k_hot_split", s);
+        k_hot_split<<<(unsigned)std::min<u64>(chunks, (u64)grid), kSplitThreads, smem, s>>>(src, dst, n, vec, sd,
+                                                                                            kb[1]);
+    }
+    // 4. the cold keys sorted (kb[1] -> kb[r2]) and in runs
+    const int r2 = radix_sort_keys64(kb[1], &sd->cold, kb, n, sc, st, s, nullptr);
+    launch_runs(RUN_U64, false, kb[r2], nullptr, n, &sd->cold, heads, pos, nullptr, &sd->R_cold, sc, st, s);
+    // 5. merged with the hot keys
+    {
+        TraceScope ts(tr, "k_hot_merge", s);
+        k_hot_merge<<<sms * 4, kMergeThreads, 0, s>>>(heads, pos, sd, keys_out, counts_out, st);
+    }
+}
+
+// Hot keys and cold packets of the last split (blocking read).
+cudaError_t split_info(const void* state, u64* hot_keys, u64* cold_packets, cudaStream_t s) {
+    const SplitDev* sd = (const SplitDev*)state;
+    u64 v[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(&v[0], &sd->H, sizeof(u64), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&v[1], &sd->cold, sizeof(u64), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (hot_keys) *hot_keys = v[0];
+    if (cold_packets) *cold_packets = v[1];
+    return e;
+}
+
+}  // namespace ns

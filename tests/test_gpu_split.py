@@ -1,0 +1,131 @@
+"""The sort path's hot-key split against the oracle: A's sorted nonzero list
+and the nine quantities, element by element, with the split forced on and
+off, on skewed and uniform windows of several sizes (ragged tails, sizes at
+the split's lower bound), unaligned columns, and the degenerate cases --
+every packet hot (nothing left to sort), no key hot, the extreme keys 0 and
+2^64 - 1 heavy (2^64 - 1 marks a free slot of the hot table and is never
+made hot)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import gen
+import gen.workloads as W
+import oracle
+import paper_2509_03653_b300 as ns
+from gpu_util import export_np, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def check(ctx, s, d, m=None):
+    m = m or ns.Matrix(ctx)
+    ns.window_build(ctx, to_dev(s), to_dev(d), m)
+    got = ns.network_stats(ctx, m)
+    wk, wc = oracle.build_matrix(s, d)
+    assert got == oracle.stats(wk, wc)
+    k, c = export_np(m)
+    np.testing.assert_array_equal(k, wk)
+    np.testing.assert_array_equal(c, wc)
+    return ns.sort_split_info(ctx)
+
+
+@pytest.mark.parametrize("n", [1 << 16, (1 << 16) + 1, 300001, 1 << 20, 3 * (1 << 20) + 17])
+@pytest.mark.parametrize("split", ["on", "off"])
+def test_split_matches_oracle_zipf(n, split):
+    ctx = ns.Context(0, path="sort", sort_split=split)
+    s, d = W.zipf_window(n, 1.2, 1 << 16, 77 + n)
+    info = check(ctx, s, d)
+    assert info["used"] == (split == "on")
+    if split == "on":
+        assert info["hot_keys"] > 0
+        assert 0 <= info["cold_packets"] < n
+    ctx.close()
+
+
+def test_split_small_window_never_splits():
+    ctx = ns.Context(0, path="sort", sort_split="on")
+    s, d = W.zipf_window((1 << 16) - 1, 1.2, 1 << 10, 5)
+    assert not check(ctx, s, d)["used"]
+    ctx.close()
+
+
+def test_split_uniform_has_no_hot_keys():
+    ctx = ns.Context(0, path="sort", sort_split="on")
+    s, d = gen.uniform_pairs(1 << 20, 32, 9)
+    info = check(ctx, s, d)
+    assert info["used"] and info["hot_keys"] == 0 and info["cold_packets"] == 1 << 20
+    ctx.close()
+
+
+def test_split_every_packet_hot():
+    n = (1 << 18) + 3
+    s = np.full(n, 0xDEADBEEF, np.uint32)
+    d = np.full(n, 0x01020304, np.uint32)
+    ctx = ns.Context(0, path="sort", sort_split="on")
+    info = check(ctx, s, d)
+    assert info["hot_keys"] == 1 and info["cold_packets"] == 0
+    ctx.close()
+
+
+def test_split_extreme_keys_heavy():
+    n = 1 << 20
+    s, d = W.zipf_window(n, 1.1, 1 << 12, 13)
+    s, d = s.copy(), d.copy()
+    s[::3] = 0xFFFFFFFF  # key 2^64 - 1 on a third of the packets
+    d[::3] = 0xFFFFFFFF
+    s[1::5] = 0  # key 0 on a fifth
+    d[1::5] = 0
+    ctx = ns.Context(0, path="sort", sort_split="on")
+    info = check(ctx, s, d)
+    assert info["hot_keys"] > 0
+    ctx.close()
+
+
+def test_split_unaligned_columns_and_rebuild():
+    n = (1 << 20) + 5
+    s, d = W.zipf_window(n + 1, 1.3, 1 << 14, 21)
+    ts, td = to_dev(s), to_dev(d)
+    ctx = ns.Context(0, path="sort", sort_split="on")
+    m = ns.Matrix(ctx)
+    for off in (1, 0):  # 4-byte offset: the split loads packets one by one
+        ns.window_build(ctx, ts[off:off + n], td[off:off + n], m)
+        wk, wc = oracle.build_matrix(s[off:off + n], d[off:off + n])
+        assert ns.network_stats(ctx, m) == oracle.stats(wk, wc)
+        k, c = export_np(m)
+        np.testing.assert_array_equal(k, wk)
+        np.testing.assert_array_equal(c, wc)
+    ctx.close()
+
+
+def test_split_rmat_and_accumulate():
+    """An RMAT window through the split, then summed with a second one."""
+    ctx = ns.Context(0, path="sort", sort_split="on")
+    s, d = W.rmat_stream(1 << 21)
+    a, b = ns.Matrix(ctx), ns.Matrix(ctx)
+    half = 1 << 20
+    ns.window_build(ctx, to_dev(s[:half]), to_dev(d[:half]), a)
+    ns.window_build(ctx, to_dev(s[half:]), to_dev(d[half:]), b)
+    ns.accumulate(ctx, a, b)
+    wk, wc = oracle.build_matrix(s, d)
+    assert ns.network_stats(ctx, a) == oracle.stats(wk, wc)
+    k, c = export_np(a)
+    np.testing.assert_array_equal(k, wk)
+    np.testing.assert_array_equal(c, wc)
+    ctx.close()
+
+
+def test_path_tune_records_split_choice(tmp_path):
+    cache = str(tmp_path / "tuner.json")
+    ctx = ns.Context(0, tuner_cache=cache)
+    s, d = W.zipf_window(1 << 22, 1.2, 1 << 20, 3)
+    ns.path_tune(ctx, to_dev(s), to_dev(d))
+    text = open(cache).read()
+    assert '"sort_split"' in text and '"sort_split_ms"' in text
+    # a context on the same cache takes the recorded choices, and still builds exactly
+    ctx2 = ns.Context(0, tuner_cache=cache)
+    check(ctx2, s, d)
+    ctx.close()
+    ctx2.close()

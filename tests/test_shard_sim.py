@@ -6,7 +6,7 @@ Each rank takes a disjoint share of the packets and aggregates it locally;
 the oracle stands in for the rank's GPU.  Then:
 
 1. every local (key, count) entry goes to the rank that owns its source
-   (owner = splitmix64(src) mod W), which merges equal keys.  Each rank now
+   (the library's ns_owner rule), which merges equal keys.  Each rank now
    holds whole rows of A, so its unique links, unique sources, max link
    packets, max source packets and max fan-out are exact for those rows;
 2. every owned entry goes on to the rank that owns its destination.  Links
@@ -46,8 +46,11 @@ def _packets(kind):
 
 
 def _owner(addr: np.ndarray, world: int) -> np.ndarray:
-    import gen
-    return np.array([gen.splitmix64(int(a)) % world for a in addr], dtype=np.int64)
+    """The library's owner rule (ns_owner, a host function of libns: no GPU
+    needed), so the CPU simulation splits exactly as the GPU ranks do."""
+    from paper_2509_03653_b300 import _native
+    L = _native.load()
+    return np.array([L.ns_owner(int(a), world) for a in addr], dtype=np.int64)
 
 
 def _exchange(dist, parts):
