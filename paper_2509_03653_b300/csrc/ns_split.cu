@@ -1,7 +1,7 @@
 // ns_split.cu -- the sort path's hot-key split.
 //
 // Under skewed traffic a small set of links carries a large share of the
-// packets (Zipf(1.2) over 2^24 addresses per column: the 4096 heaviest of
+// packets (Zipf(1.2) over 2^24 addresses per column: the 6144 heaviest of
 // ~1.5e8 distinct links carry about half of 2^30 packets).  Sorting their
 // copies is wasted work: every copy travels through all eight digit passes
 // only to be counted by the run kernel.  So, before the sort:
@@ -11,7 +11,8 @@
 //      path's own kernels;
 //   2. select: the keys seen at least kMinHotSample times in the sample, the
 //      most frequent first, up to kHotMax of them, become the hot set
-//      (sorted ascending; a table of 2 kHotMax slots is built from it);
+//      (sorted ascending; a cuckoo table of 4 kHotMax / 3 slots is built
+//      from it, and a key that finds no slot there stays cold);
 //   3. split: one pass over all packets.  Each CTA holds the table in shared
 //      memory; a packet whose key is hot adds 1 to the CTA's count of that
 //      key, every other ("cold") key is appended to the cold-key buffer
@@ -41,10 +42,22 @@ namespace ns {
 
 namespace {
 
-constexpr int kHotMax = 4096;
-constexpr int kHotSlots = 2 * kHotMax;  // load <= 1/2
-constexpr int kHotSlotBits = 13;
-static_assert((1 << kHotSlotBits) == kHotSlots, "slot bits");
+// The hot table: bucketized cuckoo hashing.  kBuckets buckets of kWays
+// key slots; a key lives in one of its two buckets, so a lookup reads two
+// 32-byte buckets (four 16-byte loads) and compares eight slots, with no
+// data-dependent loop.  Keys that cannot be placed (insertion gives up
+// after kMaxKicks evictions) simply stay cold.
+#ifndef NS_HOT_BUCKETS
+#define NS_HOT_BUCKETS 2048
+#endif
+constexpr int kWays = 4;
+constexpr int kBuckets = NS_HOT_BUCKETS;  // a power of two
+constexpr int kBucketBits = kBuckets == 1024 ? 10 : kBuckets == 2048 ? 11 : kBuckets == 4096 ? 12 : 0;
+static_assert(kBucketBits && (1 << kBucketBits) == kBuckets, "kBuckets: 1024, 2048 or 4096");
+constexpr int kHotSlots = kBuckets * kWays;
+constexpr int kHotMax = kHotSlots / 4 * 3;  // hot keys at most: table load <= 3/4
+constexpr int kHotPad = kHotSlots;          // the bitonic sort's power-of-two length (>= kHotMax)
+constexpr int kMaxKicks = 500;
 constexpr u64 kEmpty = ~0ull;  // an empty slot (never a hot key)
 constexpr int kSampleBlocks = 64;
 constexpr u64 kSampleMax = 1ull << 21;
@@ -54,9 +67,9 @@ static_assert(kSampleMax / (kHotBins - 1) < (u64)kHotMax, "the top bin alone nev
 
 // Device-side state of one split (one allocation per context).
 struct SplitDev {
-    u64 table[kHotSlots];       // slot -> hot key (kEmpty = free)
+    u64 table[kHotSlots];       // slot -> hot key (kEmpty = free); bucket b = slots [4b, 4b + 4)
     u64 slot_count[kHotSlots];  // packets of the slot's key
-    u64 hot[kHotMax];           // hot keys ascending
+    u64 hot[kHotMax];           // hot keys ascending (those in the table)
     u32 hist[kHotBins];         // sample keys by run length
     u64 H;                      // hot keys
     u64 thresh;                 // least sample count of a hot key
@@ -65,17 +78,65 @@ struct SplitDev {
     u64 R_cold;                 // distinct cold keys
 };
 
-__device__ __forceinline__ u32 hot_home(u64 key) { return (u32)((key * 0x9E3779B97F4A7C15ull) >> (64 - kHotSlotBits)); }
+// A 32-bit mix of the key (32-bit multiplies only), and from it the key's
+// two buckets (never the same one) and, in ns_split's filter, its
+// fingerprint.  Weak hashing only costs hot keys (a key that finds no slot
+// stays cold), never exactness.
+__device__ __forceinline__ u32 key_mix(u64 key) {
+    const u32 x = (u32)key * 0x9E3779B1u ^ (u32)(key >> 32) * 0x85EBCA77u;
+    return x ^ (x >> 16);
+}
+__device__ __forceinline__ u32 bucket1(u64 key) { return key_mix(key) >> (32 - kBucketBits); }
+__device__ __forceinline__ u32 bucket2_of_mix(u32 x, u32 b1) {
+    const u32 b = (x * 0xC2B2AE3Du) >> (32 - kBucketBits);
+    return b == b1 ? b ^ 1u : b;
+}
+__device__ __forceinline__ u32 bucket2(u64 key, u32 b1) { return bucket2_of_mix(key_mix(key), b1); }
 
-// Slot of `key` in a table of kHotSlots keys, or -1.  The table is at most
-// half full, so every probe sequence ends at a free slot.
+// Slot of `key` in the table, or -1.  kEmpty, the mark of a free slot, is
+// never a hot key (it would otherwise match a free slot).
 __device__ __forceinline__ int hot_find(const u64* table, u64 key) {
-    u32 h = hot_home(key);
-    for (int i = 0; i < kHotSlots; ++i) {
-        const u64 k = table[h];
-        if (k == key) return (int)h;
-        if (k == kEmpty) return -1;
-        h = (h + 1) & (kHotSlots - 1);
+    if (key == kEmpty) return -1;
+    const u32 b1 = bucket1(key), b2 = bucket2(key, b1);
+    const ulonglong2* t = reinterpret_cast<const ulonglong2*>(table);
+    const ulonglong2 a0 = t[2 * b1], a1 = t[2 * b1 + 1], c0 = t[2 * b2], c1 = t[2 * b2 + 1];
+    int slot = -1;
+    slot = a0.x == key ? (int)(4 * b1 + 0) : slot;
+    slot = a0.y == key ? (int)(4 * b1 + 1) : slot;
+    slot = a1.x == key ? (int)(4 * b1 + 2) : slot;
+    slot = a1.y == key ? (int)(4 * b1 + 3) : slot;
+    slot = c0.x == key ? (int)(4 * b2 + 0) : slot;
+    slot = c0.y == key ? (int)(4 * b2 + 1) : slot;
+    slot = c1.x == key ? (int)(4 * b2 + 2) : slot;
+    slot = c1.y == key ? (int)(4 * b2 + 3) : slot;
+    return slot;
+}
+
+// 8-bit fingerprint of a key (never 0, which marks a free slot); the split
+// kernel filters with the fingerprints of the key's two buckets -- one
+// 32-bit word each, byte w for slot w -- and reads a full key only where a
+// fingerprint matches.
+__device__ __forceinline__ u32 fingerprint_of_mix(u32 x) {
+    const u32 f = (x * 0x27D4EB2Fu) >> 24;
+    return f ? f : 1u;
+}
+__device__ __forceinline__ u32 fingerprint(u64 key) { return fingerprint_of_mix(key_mix(key)); }
+
+// hot_find with the fingerprint filter (shared-memory tables of the split
+// kernel): two 4-byte loads for almost every cold key, plus one 8-byte load
+// per fingerprint match.
+__device__ __forceinline__ int hot_find_fp(const u32* fpw, const u64* table, u64 key) {
+    if (key == kEmpty) return -1;
+    const u32 x = key_mix(key);
+    const u32 b1 = x >> (32 - kBucketBits), b2 = bucket2_of_mix(x, b1);
+    const u32 f4 = fingerprint_of_mix(x) * 0x01010101u;
+    const u32 m1 = __vcmpeq4(fpw[b1], f4), m2 = __vcmpeq4(fpw[b2], f4);  // 0xFF per matching byte
+    u32 cand = (m1 & 0x01010101u) | ((m2 & 0x01010101u) << 1);  // bit 8w: slot w of b1, bit 8w+1: of b2
+    while (cand) {
+        const u32 bit = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const u32 slot = 4 * ((bit & 1) ? b2 : b1) + (bit >> 3);
+        if (table[slot] == key) return (int)slot;
     }
     return -1;
 }
@@ -133,20 +194,21 @@ __global__ void k_hot_collect(const u64* __restrict__ heads, const u64* __restri
     }
 }
 
-// 2d. One CTA: sorts the hot keys (bitonic, in shared memory) and builds the
-// table from them; clears the per-slot counts.
+// 2d. One CTA: sorts the hot keys (bitonic, in shared memory), places them
+// in the cuckoo table (one thread, in ascending order), keeps in the hot
+// list only the keys that found a place, and clears the per-slot counts.
 constexpr int kTableThreads = 1024;
 __global__ void __launch_bounds__(kTableThreads, 1) k_hot_table(SplitDev* sd) {
     extern __shared__ __align__(16) u64 sh[];
-    u64* keys = sh;              // [kHotMax]
-    u64* table = sh + kHotMax;   // [kHotSlots]
+    u64* keys = sh;              // [kHotPad]
+    u64* table = sh + kHotPad;   // [kHotSlots]
     const u64 H = sd->H < (u64)kHotMax ? sd->H : (u64)kHotMax;
-    for (int i = threadIdx.x; i < kHotMax; i += kTableThreads) keys[i] = (u64)i < H ? sd->hot[i] : kEmpty;
+    for (int i = threadIdx.x; i < kHotPad; i += kTableThreads) keys[i] = (u64)i < H ? sd->hot[i] : kEmpty;
     for (int i = threadIdx.x; i < kHotSlots; i += kTableThreads) table[i] = kEmpty;
     __syncthreads();
-    for (int k = 2; k <= kHotMax; k <<= 1) {
+    for (int k = 2; k <= kHotPad; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < kHotMax; i += kTableThreads) {
+            for (int i = threadIdx.x; i < kHotPad; i += kTableThreads) {
                 const int p = i ^ j;
                 if (p > i) {
                     const bool up = (i & k) == 0;
@@ -160,38 +222,118 @@ __global__ void __launch_bounds__(kTableThreads, 1) k_hot_table(SplitDev* sd) {
             __syncthreads();
         }
     }
+    // first, in parallel: every key takes a free slot of its first bucket,
+    // else of its second (compare-and-swap on the slot); the few that find
+    // both buckets full are left to the evicting insertion below
+    __shared__ u32 n_left;
+    if (threadIdx.x == 0) n_left = 0;
+    __syncthreads();
     for (int i = threadIdx.x; i < (int)H; i += kTableThreads) {
         const u64 key = keys[i];
-        sd->hot[i] = key;
-        u32 h = hot_home(key);
-        for (int q = 0; q < kHotSlots; ++q) {  // distinct keys, table half full: ends at a free slot
-            const u64 prev = atomicCAS(reinterpret_cast<unsigned long long*>(&table[h]), kEmpty, key);
-            if (prev == kEmpty) break;
-            h = (h + 1) & (kHotSlots - 1);
+        const u32 b1 = bucket1(key), b2 = bucket2(key, b1);
+        bool placed = false;
+        for (int q = 0; q < 2 * kWays && !placed; ++q) {
+            const u32 slot = 4 * (q < kWays ? b1 : b2) + (q & (kWays - 1));
+            placed = atomicCAS(reinterpret_cast<unsigned long long*>(&table[slot]), kEmpty, key) == kEmpty;
+        }
+        if (!placed) {
+            // the left-over keys go after the sorted ones (index >= H); one
+            // that finds no room there stays cold
+            const u32 j = atomicAdd(&n_left, 1u);
+            if ((u64)j < (u64)kHotPad - H) keys[kHotPad - 1 - j] = key;
         }
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        const u32 left = (u64)n_left < (u64)kHotPad - H ? n_left : (u32)((u64)kHotPad - H);
+        for (u32 i = 0; i < left; ++i) {
+            u64 cur = keys[kHotPad - 1 - i];
+            for (int kick = 0; kick < kMaxKicks && cur != kEmpty; ++kick) {
+                const u32 b1 = bucket1(cur), b2 = bucket2(cur, b1);
+                int free_slot = -1;
+                for (int w = kWays - 1; w >= 0; --w) {
+                    if (table[4 * b2 + w] == kEmpty) free_slot = (int)(4 * b2 + w);
+                }
+                for (int w = kWays - 1; w >= 0; --w) {
+                    if (table[4 * b1 + w] == kEmpty) free_slot = (int)(4 * b1 + w);
+                }
+                if (free_slot >= 0) {
+                    table[free_slot] = cur;
+                    cur = kEmpty;
+                } else {  // evict a resident of one of the two buckets
+                    const u32 victim = 4 * ((kick & 1) ? b2 : b1) + (u32)((kick * 5 + (int)i) & (kWays - 1));
+                    // (cur is never kEmpty here)
+                    const u64 out = table[victim];
+                    table[victim] = cur;
+                    cur = out;
+                }
+            }
+            // a key still in hand after kMaxKicks stays cold
+        }
+    }
+    __syncthreads();
+    // the hot list: the sorted keys that have a slot, in order (a block-wide
+    // ordered compaction, kTableThreads keys per round)
+    __shared__ u32 wcount[kTableThreads / 32];
+    __shared__ u32 kept;
+    if (threadIdx.x == 0) kept = 0;
+    __syncthreads();
+    for (u64 r = 0; r < H; r += kTableThreads) {
+        const u64 i = r + threadIdx.x;
+        const bool keep = i < H && hot_find(table, keys[i]) >= 0;
+        const u32 bal = __ballot_sync(0xFFFFFFFFu, keep);
+        if ((threadIdx.x & 31) == 0) wcount[threadIdx.x >> 5] = __popc(bal);
+        __syncthreads();
+        u32 before = kept;
+        for (u32 w = 0; w < (threadIdx.x >> 5); ++w) before += wcount[w];
+        if (keep) sd->hot[before + __popc(bal & lanemask_lt())] = keys[i];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            u32 t = 0;
+            for (int w = 0; w < kTableThreads / 32; ++w) t += wcount[w];
+            kept += t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sd->H = kept;
     for (int i = threadIdx.x; i < kHotSlots; i += kTableThreads) {
         sd->table[i] = table[i];
         sd->slot_count[i] = 0;
     }
-    if (threadIdx.x == 0) sd->H = H;
 }
 
 // 3. The split.  Persistent CTAs take chunks of kSplitThreads * 8 packets
 // (chunk c, c + grid, ...).  With 16-byte-aligned columns a thread loads its
 // eight packets as two 16-byte vectors per column.
-constexpr int kSplitThreads = 1024;
+// Counts are 32-bit in shared memory (64-bit shared atomics are not native
+// and serialize badly on the hottest keys) and are added to the global
+// counts every kFlushChunks chunks, before any could pass 2^31.
+#ifndef NS_SPLIT_THREADS
+#define NS_SPLIT_THREADS 512
+#endif
+constexpr int kSplitThreads = NS_SPLIT_THREADS;
 constexpr int kSplitItems = 8;
 constexpr u64 kSplitChunk = (u64)kSplitThreads * kSplitItems;
+constexpr u64 kFlushChunks = (1ull << 31) / kSplitChunk;
 struct SplitSmem {
     u64 table[kHotSlots];
-    u64 count[kHotSlots];
+    u32 count[kHotSlots];
+    u32 fpw[kBuckets];  // per bucket: the fingerprints of its kWays slots
     u32 wsum[kSplitThreads / 32];
     u64 base;
 };
 
-__global__ void __launch_bounds__(kSplitThreads, 1) k_hot_split(const u32* __restrict__ src, const u32* __restrict__ dst,
+__device__ __forceinline__ void split_flush(SplitSmem& sm, SplitDev* sd) {
+    for (int i = threadIdx.x; i < kHotSlots; i += kSplitThreads) {
+        const u32 c = sm.count[i];
+        if (c) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(&sd->slot_count[i]), (unsigned long long)c);
+            sm.count[i] = 0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSplitThreads, 1024 / kSplitThreads) k_hot_split(const u32* __restrict__ src, const u32* __restrict__ dst,
                                                                  u64 n, bool vec, SplitDev* sd, u64* __restrict__ cold) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SplitSmem& sm = *reinterpret_cast<SplitSmem*>(smem_raw);
@@ -201,9 +343,30 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_hot_split(const u32* __res
         sm.table[i] = sd->table[i];
         sm.count[i] = 0;
     }
+    for (int b = t; b < kBuckets; b += kSplitThreads) {
+        u32 w = 0;
+        for (int q = 0; q < kWays; ++q) {
+            const u64 k = sd->table[kWays * b + q];
+            w |= (k == kEmpty ? 0u : fingerprint(k)) << (8 * q);
+        }
+        sm.fpw[b] = w;
+    }
     __syncthreads();
     const u32 lt = lanemask_lt();
+    u64 since_flush = 0;  // the same in every thread of the CTA
     for (u64 base = (u64)blockIdx.x * kSplitChunk; base < n; base += (u64)gridDim.x * kSplitChunk) {
+        if (++since_flush == kFlushChunks) {
+            since_flush = 0;
+            __syncthreads();
+            split_flush(sm, sd);
+            __syncthreads();
+        }
+        // this CTA's next chunk starts moving into L2 now
+        const u64 nb = base + (u64)gridDim.x * kSplitChunk;
+        if (vec && t == 0 && nb + kSplitChunk <= n) {
+            bulk_prefetch_l2(src + nb, (u32)(kSplitChunk * 4));
+            bulk_prefetch_l2(dst + nb, (u32)(kSplitChunk * 4));
+        }
         u64 key[kSplitItems];
         u32 valid = 0;
         if (vec && n - base >= kSplitChunk) {
@@ -231,8 +394,8 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_hot_split(const u32* __res
 #pragma unroll
         for (int u = 0; u < kSplitItems; ++u) {
             if ((valid >> u) & 1u) {
-                const int slot = hot_find(sm.table, key[u]);
-                if (slot >= 0) atomicAdd(reinterpret_cast<unsigned long long*>(&sm.count[slot]), 1ull);
+                const int slot = hot_find_fp(sm.fpw, sm.table, key[u]);
+                if (slot >= 0) atomicAdd(&sm.count[slot], 1u);
                 else coldm |= 1u << u;
             }
         }
@@ -264,9 +427,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_hot_split(const u32* __res
         __syncthreads();  // wsum and base are rewritten by the next chunk
     }
     __syncthreads();
-    for (int i = t; i < kHotSlots; i += kSplitThreads)
-        if (sm.count[i]) atomicAdd(reinterpret_cast<unsigned long long*>(&sd->slot_count[i]),
-                                   (unsigned long long)sm.count[i]);
+    split_flush(sm, sd);
 }
 
 // 5. Merge of the cold runs (heads[r], length pos[r+1] - pos[r]) with the
@@ -286,21 +447,41 @@ __device__ __forceinline__ u64 count_below(const u64* a, u64 len, u64 key) {
 __global__ void __launch_bounds__(kMergeThreads) k_hot_merge(const u64* __restrict__ heads, const u64* __restrict__ pos,
                                                              const SplitDev* sd, u64* __restrict__ keys_out,
                                                              u64* __restrict__ counts_out, DevStats* st) {
-    __shared__ u64 hot[kHotMax];
+    extern __shared__ __align__(16) u64 hot[];  // [kHotMax]
     __shared__ u64 bmax;
-    const u64 H = sd->H, RC = sd->R_cold;
+    const u32 FULL = 0xFFFFFFFFu, lane = threadIdx.x & 31;
+    const u64 H = sd->H, RC = sd->R_cold, total = RC + H;
     for (u64 i = threadIdx.x; i < H; i += kMergeThreads) hot[i] = sd->hot[i];
     if (threadIdx.x == 0) bmax = 0;
     __syncthreads();
     u64 mx = 0, hot_sum = 0;
-    for (u64 i = (u64)blockIdx.x * kMergeThreads + threadIdx.x; i < RC + H; i += (u64)gridDim.x * kMergeThreads) {
-        if (i < RC) {
-            const u64 key = heads[i], c = pos[i + 1] - pos[i];
-            const u64 at = i + count_below(hot, H, key);
-            keys_out[at] = key;
-            counts_out[at] = c;
-            mx = c > mx ? c : mx;
-        } else {
+    // a warp takes 32 consecutive elements at a time (warp-uniform loop)
+    const u64 warp0 = ((u64)blockIdx.x * kMergeThreads + threadIdx.x) & ~31ull;
+    const u64 wstride = (u64)gridDim.x * kMergeThreads;
+    for (u64 base = warp0; base < total; base += wstride) {
+        const u64 i = base + lane;
+        if (base < RC) {
+            // cold runs of this warp: ascending keys heads[base .. base + last]
+            const u32 last = (u32)min((u64)31, RC - 1 - base);
+            const u64 key = i < RC ? heads[i] : 0;
+            const u64 kfirst = __shfl_sync(FULL, key, 0), klast = __shfl_sync(FULL, key, last);
+            // hot keys below the first and below the last run (two searches
+            // on two lanes); only the hot keys between them can fall in
+            // between the warp's runs, usually none
+            u64 b = 0;
+            if (lane < 2) b = count_below(hot, H, lane == 0 ? kfirst : klast);
+            const u64 lo = __shfl_sync(FULL, b, 0), hi = __shfl_sync(FULL, b, 1);
+            if (i < RC) {
+                u64 below = lo;
+                for (u64 j = lo; j < hi; ++j) below += hot[j] < key;
+                const u64 c = pos[i + 1] - pos[i];
+                const u64 at = i + below;
+                keys_out[at] = key;
+                counts_out[at] = c;
+                mx = c > mx ? c : mx;
+            }
+        }
+        if (i >= RC && i < total) {
             const u64 h = i - RC, key = hot[h];
             const int slot = hot_find(sd->table, key);
             const u64 c = slot >= 0 ? sd->slot_count[slot] : 0;
@@ -313,10 +494,10 @@ __global__ void __launch_bounds__(kMergeThreads) k_hot_merge(const u64* __restri
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
-        hot_sum += __shfl_xor_sync(0xFFFFFFFFu, hot_sum, o);
+        mx = max(mx, __shfl_xor_sync(FULL, mx, o));
+        hot_sum += __shfl_xor_sync(FULL, hot_sum, o);
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         if (mx) atomicMax(&bmax, mx);
         if (hot_sum) atomicAdd(&st->v[S_VALID], hot_sum);
     }
@@ -324,7 +505,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_hot_merge(const u64* __restri
     if (threadIdx.x == 0) {
         if (bmax) atomicMax(&st->v[S_MAX_LINK], bmax);
         if (blockIdx.x == 0) {
-            st->v[S_LINKS] = RC + H;
+            st->v[S_LINKS] = total;
             atomicAdd(&st->v[S_VALID], pos[RC]);  // the cold packets
         }
     }
@@ -360,14 +541,8 @@ void sort_links_split(const u32* src, const u32* dst, u64 n, u64* kb[2], u64* he
         k_hot_hist<<<sms, 1024, 0, s>>>(pos, sd);
         k_hot_pick<<<1, 32, 0, s>>>(sd);
         k_hot_collect<<<sms * 2, 256, 0, s>>>(heads, pos, sd);
-        const size_t tsmem = sizeof(u64) * (kHotMax + kHotSlots);
-        static bool attr_set[64] = {};
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-            cudaFuncSetAttribute(k_hot_table, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem);
-            attr_set[dev] = true;
-        }
+        const size_t tsmem = sizeof(u64) * (kHotPad + kHotSlots);
+        resident_ctas_of((const void*)k_hot_table, kTableThreads, tsmem);  // sets its shared-memory size
         k_hot_table<<<1, kTableThreads, tsmem, s>>>(sd);
     }
     // 3. the split: hot keys counted, cold keys into kb[1]
@@ -386,7 +561,9 @@ void sort_links_split(const u32* src, const u32* dst, u64 n, u64* kb[2], u64* he
     // 5. merged with the hot keys
     {
         TraceScope ts(tr, "k_hot_merge", s);
-        k_hot_merge<<<sms * 4, kMergeThreads, 0, s>>>(heads, pos, sd, keys_out, counts_out, st);
+        const size_t msmem = sizeof(u64) * kHotMax;
+        const int mgrid = resident_ctas_of((const void*)k_hot_merge, kMergeThreads, msmem);
+        k_hot_merge<<<mgrid, kMergeThreads, msmem, s>>>(heads, pos, sd, keys_out, counts_out, st);
     }
 }
 
