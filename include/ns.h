@@ -19,6 +19,13 @@
  *  - The caller owns the input buffers and must keep them valid and
  *    unmodified until the stream work completes.  The library owns matrices
  *    and all scratch memory it allocates.
+ *  - Device memory is stream-ordered: every buffer comes from the context's
+ *    memory pool and is allocated, grown and freed on the stream of the call
+ *    that needs it (calls without a stream -- the create calls -- use the
+ *    legacy default stream and wait for it).  No allocation or free waits for
+ *    the whole device.  A buffer cannot grow while its stream is being
+ *    captured into a CUDA graph: such a call returns NS_ERR_STATE (run it
+ *    once before the capture so that every buffer has its size).
  *  - n == 0 is legal everywhere and gives an empty matrix / zero statistics.
  *    Null pointers with n > 0, unknown enum values and mismatched devices
  *    return NS_ERR_INVALID.  No call aborts, traps or hangs: device-side
@@ -136,8 +143,10 @@ typedef struct {
  * passed in must belong to that device. */
 ns_status ns_create(ns_ctx** ctx, const ns_config* cfg, int device);
 
-/* Waits for the context's own work, frees everything it owns (matrices
- * created from it must be freed first). */
+/* Frees everything the context owns (matrices, batches, sliders and
+ * servers created from it must be freed first): its scratch is released in
+ * stream order behind the work of its last call, and its memory pool gives
+ * the memory back once those frees have run.  Does not wait for the device. */
 void ns_destroy(ns_ctx* ctx);
 
 /* Blocks until all work the context enqueued on `stream` is done, then
@@ -165,7 +174,11 @@ ns_status ns_matrix_reserve_ex(ns_matrix* m, uint64_t max_links, uint64_t max_no
 /* Makes the matrix empty (A = 0) keeping its memory.  Enqueued on stream. */
 ns_status ns_matrix_clear(ns_matrix* m, ns_stream_t stream);
 
-/* Frees the matrix after its pending work completes. */
+/* Frees the matrix's device memory in stream order, behind the work
+ * enqueued on the stream of the last call that used the matrix; the host does
+ * not wait.  Work that uses the matrix and was launched any other way (a
+ * replayed CUDA graph, a stream not ordered before that one) must be complete
+ * or ordered before that stream's current point. */
 void ns_matrix_free(ns_matrix* m);
 
 /* Number of nonzeros of A (unique links).  Blocking. */
@@ -343,6 +356,8 @@ typedef struct {
  * per-window metadata and statistics.  Parameters come from the context's
  * tuner cache when it has an entry for this GPU and batch shape. */
 ns_status ns_batch_create(ns_ctx* ctx, uint64_t max_windows, uint64_t max_packets, ns_batch** out);
+/* Frees the batch in stream order behind its last run (waiting only for
+ * that stream, whose copies read the batch's pinned staging). */
 void ns_batch_free(ns_batch* batch);
 ns_status ns_batch_get_params(const ns_batch* batch, ns_batch_params* out);
 ns_status ns_batch_set_params(ns_batch* batch, const ns_batch_params* params);
@@ -393,10 +408,10 @@ typedef struct {
 ns_status ns_server_create(ns_ctx* ctx, ns_matrix* acc, ns_server** out);
 
 /* Sizes every slot's device buffers and tables for windows of up to
- * max_window packets, so that no later window makes a slot grow (growing
- * frees the old buffers, which synchronizes the device and stalls every
- * window in flight).  Only while the service is idle (else NS_ERR_BUSY);
- * blocking.  Optional: slots otherwise grow on demand. */
+ * max_window packets, so that no later window makes a slot grow.  Only while
+ * the service is idle (else NS_ERR_BUSY); blocking.  Optional: slots
+ * otherwise grow on demand, in stream order on the slot's own stream (the
+ * slot is idle then), which stalls no other slot. */
 ns_status ns_server_reserve(ns_server* server, uint64_t max_window);
 
 /* Empties the aggregate (A = 0) so that the next window's running

@@ -51,29 +51,63 @@ u64 next_pow2(u64 x) {
 
 namespace ns {
 
+namespace {
+thread_local cudaMemPool_t t_pool = nullptr;
+thread_local cudaStream_t t_stream = nullptr;
+}  // namespace
+
+AllocScope::AllocScope(cudaMemPool_t pool, cudaStream_t s) : prev_pool(t_pool), prev_stream(t_stream) {
+    t_pool = pool;
+    t_stream = s;
+}
+AllocScope::~AllocScope() {
+    t_pool = prev_pool;
+    t_stream = prev_stream;
+}
+cudaStream_t alloc_stream() { return t_stream; }
+
 ns_status buf_reserve(Buf& b, size_t bytes) {
     if (b.bytes >= bytes && b.p) return NS_OK;
+    const cudaStream_t s = t_stream;
+    // Growing inside a CUDA graph capture would make the new buffer the
+    // graph's own allocation: refuse, as cudaMalloc would.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;
+    }
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(NS_ERR_STATE, "a buffer must grow (to %zu bytes) while its stream is being captured; "
+                                  "run the call once before the capture", bytes);
     if (b.p) {
-        cudaFree(b.p);
+        cudaFreeAsync(b.p, s);
         b.p = nullptr;
         b.bytes = 0;
     }
     if (bytes == 0) return NS_OK;
-    cudaError_t e = cudaMalloc(&b.p, bytes);
+    cudaError_t e = t_pool ? cudaMallocFromPoolAsync(&b.p, bytes, t_pool, s) : cudaMallocAsync(&b.p, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         b.p = nullptr;
-        return fail(NS_ERR_OOM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+        return fail(NS_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     }
     b.bytes = bytes;
     return NS_OK;
 }
 
-void buf_free(Buf& b) {
-    if (b.p) cudaFree(b.p);
+void buf_free_on(Buf& b, cudaStream_t s) {
+    if (b.p && cudaFreeAsync(b.p, s) != cudaSuccess) {
+        // the stream is gone: wait for the device, then free on the legacy stream
+        cudaGetLastError();
+        cudaDeviceSynchronize();
+        cudaFreeAsync(b.p, nullptr);
+        cudaGetLastError();
+    }
     b.p = nullptr;
     b.bytes = 0;
 }
+
+void buf_free(Buf& b) { buf_free_on(b, t_stream); }
 
 ns_status set_fail(ns_status s, const char* msg) { return fail(s, "%s", msg); }
 
@@ -192,6 +226,7 @@ ns_status hash_grow(ns_matrix* m, u64 extra, cudaStream_t s) {
 
 // Turns an accumulator into hash format (empty, or from its sorted list).
 ns_status to_hash(ns_matrix* m, u64 extra, cudaStream_t s) {
+    touch(m, s);
     if (m->fmt == FMT_HASH) return hash_grow(m, extra, s);
     ns_ctx* c = m->ctx;
     const u64 have = (m->fmt == FMT_LIST) ? m->bound : 0;
@@ -221,7 +256,7 @@ ns_status sort_scratch(ns_ctx* c, u64 n) {
     const u64 words = tiles * (u64)sort_radix();
     if (c->status.bytes < words * sizeof(u64)) {
         TRY(buf_reserve(c->status, words * sizeof(u64)));
-        CK(cudaMemset(c->status.p, 0, words * sizeof(u64)));
+        CK(cudaMemsetAsync(c->status.p, 0, words * sizeof(u64), alloc_stream()));
         c->sc.tag = 0;
     }
     c->sc.status = (u64*)c->status.p;
@@ -246,6 +281,7 @@ bool use_split(const ns_ctx* c, u64 n) {
 // split: -1 = use_split's rule, 0 = no split, 1 = split (from 2^16 packets).
 ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n, ns_matrix* out,
                      cudaStream_t s, int split = -1) {
+    touch(out, s);
     out->fmt = FMT_LIST;
     out->bound = n;
     CK(cudaMemsetAsync(out->stats.p, 0, sizeof(DevStats), s));
@@ -367,6 +403,7 @@ int resolve_path(const ns_ctx* c, u64 n) {
 
 ns_status build_hash(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n, ns_matrix* out,
                      cudaStream_t s, int cache) {
+    touch(out, s);
     TRY(hash_alloc(out, n));
     TRY(hash_clear(out, s));
     out->fmt = FMT_HASH;
@@ -433,12 +470,31 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
     load_path_choices(x);
     cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, device);
     x->sc.sms = x->sms;
+    // the context's memory pool: it keeps freed memory for reuse until the
+    // context is destroyed
+    {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        if (cudaMemPoolCreate(&x->pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            x->pool = nullptr;
+            ns_destroy(x);
+            return fail(NS_ERR_CUDA, "ns_create: memory pool creation failed");
+        }
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(x->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    AllocScope alloc(x->pool, nullptr);
     ns_status st = buf_reserve(x->ghist, 8 * 256 * sizeof(u64));
     if (st == NS_OK) st = buf_reserve(x->offs, 9 * 256 * sizeof(u64));  // [8][256] offsets + cursors
     if (st == NS_OK) st = buf_reserve(x->tcount, 16 * sizeof(u32));
     if (st == NS_OK) st = buf_reserve(x->counters, 16 * sizeof(u64));
     if (st == NS_OK && cudaMallocHost((void**)&x->host_stats, sizeof(DevStats)) != cudaSuccess)
         st = fail(NS_ERR_OOM, "cudaMallocHost failed");
+    if (st == NS_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) st = check_launch();
     if (st != NS_OK) {
         ns_destroy(x);
         return st;
@@ -457,13 +513,17 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
 void ns_destroy(ns_ctx* c) {
     if (!c) return;
     DeviceGuard device_guard(c->device);
-    cudaDeviceSynchronize();
+    // the scratch is freed behind the work of the context's last call, on
+    // that call's stream; the pool gives its memory back once those frees
+    // have run.  Nothing here waits for the device.
     Buf* all[] = {&c->ghist, &c->offs, &c->tcount, &c->counters, &c->status, &c->k64[0], &c->k64[1],
                   &c->pos, &c->psum, &c->k32[0], &c->k32[1], &c->v64[0], &c->v64[1], &c->xk, &c->xv,
                   &c->stage[0], &c->stage[1], &c->split};
-    for (Buf* b : all) buf_free(*b);
-    if (c->host_stats) cudaFreeHost(c->host_stats);
+    for (Buf* b : all) buf_free_on(*b, c->last_stream);
+    if (c->host_stats) cudaFreeHost(c->host_stats);  // used only by blocking reads, all complete
     tracer_destroy(&c->tracer);
+    if (c->pool) cudaMemPoolDestroy(c->pool);
+    cudaGetLastError();
     delete c;
 }
 
@@ -477,12 +537,17 @@ ns_status ns_sync(ns_ctx* c, ns_stream_t stream) {
 ns_status ns_matrix_create(ns_ctx* c, ns_matrix** out) {
     if (!c || !out) return fail(NS_ERR_INVALID, "ns_matrix_create: NULL argument");
     DeviceGuard device_guard(c->device);
+    AllocScope alloc(c->pool, nullptr);
     ns_matrix* m = new ns_matrix();
     m->ctx = c;
     m->device = c->device;
+    m->last_stream = nullptr;
     ns_status st = buf_reserve(m->stats, sizeof(DevStats));
-    if (st == NS_OK && cudaMemset(m->stats.p, 0, sizeof(DevStats)) != cudaSuccess)
-        st = fail(NS_ERR_CUDA, "cudaMemset failed");
+    if (st == NS_OK && (cudaMemsetAsync(m->stats.p, 0, sizeof(DevStats), nullptr) != cudaSuccess ||
+                        cudaStreamSynchronize(nullptr) != cudaSuccess)) {
+        cudaGetLastError();
+        st = fail(NS_ERR_CUDA, "ns_matrix_create: clearing the statistics record failed");
+    }
     if (st != NS_OK) {
         ns_matrix_free(m);
         return st;
@@ -493,8 +558,9 @@ ns_status ns_matrix_create(ns_ctx* c, ns_matrix** out) {
 
 ns_status ns_matrix_reserve(ns_matrix* m, uint64_t max_links, ns_stream_t stream) {
     if (!m) return fail(NS_ERR_INVALID, "ns_matrix_reserve: NULL matrix");
-    DeviceGuard device_guard(m->device);
     cudaStream_t s = (cudaStream_t)stream;
+    CallScope scope(m->ctx, s);
+    touch(m, s);
     if (m->fmt == FMT_EMPTY) {
         TRY(hash_alloc(m, max_links));
         TRY(hash_clear(m, s));
@@ -516,8 +582,9 @@ ns_status ns_matrix_reserve_ex(ns_matrix* m, uint64_t max_links, uint64_t max_no
 
 ns_status ns_matrix_clear(ns_matrix* m, ns_stream_t stream) {
     if (!m) return fail(NS_ERR_INVALID, "ns_matrix_clear: NULL matrix");
-    DeviceGuard device_guard(m->device);
     cudaStream_t s = (cudaStream_t)stream;
+    CallScope scope(m->ctx, s);
+    touch(m, s);
     if (m->fmt == FMT_HASH) {
         TRY(hash_clear(m, s));
     } else {
@@ -531,13 +598,15 @@ ns_status ns_matrix_clear(ns_matrix* m, ns_stream_t stream) {
 void ns_matrix_free(ns_matrix* m) {
     if (!m) return;
     DeviceGuard device_guard(m->device);
-    cudaDeviceSynchronize();
-    buf_free(m->links);
-    buf_free(m->rows);
-    buf_free(m->cols);
-    buf_free(m->keys);
-    buf_free(m->counts);
-    buf_free(m->stats);
+    // behind the matrix's pending work on the stream it was last used on;
+    // the host does not wait
+    const cudaStream_t s = m->last_stream;
+    buf_free_on(m->links, s);
+    buf_free_on(m->rows, s);
+    buf_free_on(m->cols, s);
+    buf_free_on(m->keys, s);
+    buf_free_on(m->counts, s);
+    buf_free_on(m->stats, s);
     delete m;
 }
 
@@ -553,8 +622,9 @@ ns_status ns_matrix_nnz(const ns_matrix* m, uint64_t* h_nnz, ns_stream_t stream)
 ns_status ns_matrix_export(const ns_matrix* m, uint64_t* d_keys, uint64_t* d_counts, uint64_t cap,
                            uint64_t* h_nnz, ns_stream_t stream) {
     if (!m || !h_nnz) return fail(NS_ERR_INVALID, "ns_matrix_export: NULL argument");
-    DeviceGuard device_guard(m->device);
     cudaStream_t s = (cudaStream_t)stream;
+    CallScope scope(m->ctx, s);
+    touch(m, s);
     DevStats ds;
     TRY(read_stats(m, s, &ds));
     const u64 nnz = ds.v[S_LINKS];
@@ -594,7 +664,7 @@ ns_status ns_matrix_export(const ns_matrix* m, uint64_t* d_keys, uint64_t* d_cou
 ns_status ns_window_build(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
                           ns_matrix* out, ns_stream_t stream) {
     if (!c || !out) return fail(NS_ERR_INVALID, "ns_window_build: NULL context or matrix");
-    DeviceGuard device_guard(c->device);
+    CallScope scope(c, (cudaStream_t)stream);
     if (n > 0 && (!d_src || !d_dst)) return fail(NS_ERR_INVALID, "ns_window_build: NULL input with n > 0");
     if (n >= (1ull << 40)) return fail(NS_ERR_INVALID, "ns_window_build: n too large");
     if (out->ctx != c) return fail(NS_ERR_INVALID, "ns_window_build: matrix belongs to another context");
@@ -605,7 +675,7 @@ ns_status ns_window_build(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_ds
 ns_status ns_window_build_host(ns_ctx* c, const uint32_t* h_src, const uint32_t* h_dst, uint64_t n,
                                ns_matrix* out, ns_stats* h_stats, ns_stream_t stream) {
     if (!c || !out) return fail(NS_ERR_INVALID, "ns_window_build_host: NULL context or matrix");
-    DeviceGuard device_guard(c->device);
+    CallScope scope(c, (cudaStream_t)stream);
     if (n > 0 && (!h_src || !h_dst)) return fail(NS_ERR_INVALID, "ns_window_build_host: NULL input with n > 0");
     if (n >= (1ull << 40)) return fail(NS_ERR_INVALID, "ns_window_build_host: n too large");
     if (out->ctx != c) return fail(NS_ERR_INVALID, "ns_window_build_host: matrix belongs to another context");
@@ -629,7 +699,7 @@ ns_status ns_window_build_host(ns_ctx* c, const uint32_t* h_src, const uint32_t*
 ns_status ns_path_tune(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n, ns_stream_t stream,
                        int* chosen, float* sort_ms, float* hash_ms) {
     if (!c) return fail(NS_ERR_INVALID, "ns_path_tune: NULL context");
-    DeviceGuard device_guard(c->device);
+    CallScope scope(c, (cudaStream_t)stream);
     if (n == 0) return fail(NS_ERR_INVALID, "ns_path_tune: n == 0");
     if (!d_src || !d_dst) return fail(NS_ERR_INVALID, "ns_path_tune: NULL input");
     if (n >= (1ull << 40)) return fail(NS_ERR_INVALID, "ns_path_tune: n too large");
@@ -733,7 +803,9 @@ ns_status ns_path_resolve(const ns_ctx* c, uint64_t n, int* path) {
 
 ns_status ns_accumulate(ns_ctx* c, ns_matrix* acc, const ns_matrix* add, ns_stream_t stream) {
     if (!c || !acc || !add) return fail(NS_ERR_INVALID, "ns_accumulate: NULL argument");
-    DeviceGuard device_guard(c->device);
+    CallScope scope(c, (cudaStream_t)stream);
+    touch(acc, (cudaStream_t)stream);
+    touch(add, (cudaStream_t)stream);
     if (acc == add) return fail(NS_ERR_INVALID, "ns_accumulate: acc and add must be distinct");
     if (acc->ctx != c || add->ctx != c) return fail(NS_ERR_INVALID, "ns_accumulate: foreign matrix");
     cudaStream_t s = (cudaStream_t)stream;
@@ -757,7 +829,8 @@ ns_status ns_accumulate(ns_ctx* c, ns_matrix* acc, const ns_matrix* add, ns_stre
 ns_status ns_window_ingest(ns_ctx* c, ns_matrix* acc, const uint32_t* d_src, const uint32_t* d_dst,
                            uint64_t n, ns_stream_t stream) {
     if (!c || !acc) return fail(NS_ERR_INVALID, "ns_window_ingest: NULL argument");
-    DeviceGuard device_guard(c->device);
+    CallScope scope(c, (cudaStream_t)stream);
+    touch(acc, (cudaStream_t)stream);
     if (n > 0 && (!d_src || !d_dst)) return fail(NS_ERR_INVALID, "ns_window_ingest: NULL input with n > 0");
     if (acc->ctx != c) return fail(NS_ERR_INVALID, "ns_window_ingest: foreign matrix");
     cudaStream_t s = (cudaStream_t)stream;
@@ -772,7 +845,8 @@ ns_status ns_window_ingest(ns_ctx* c, ns_matrix* acc, const uint32_t* d_src, con
 ns_status ns_window_ingest_stats(ns_ctx* c, ns_matrix* acc, const uint32_t* d_src, const uint32_t* d_dst,
                                  uint64_t n, ns_stats* d_out, ns_stream_t stream) {
     if (!c || !acc || !d_out) return fail(NS_ERR_INVALID, "ns_window_ingest_stats: NULL argument");
-    DeviceGuard device_guard(c->device);
+    CallScope scope(c, (cudaStream_t)stream);
+    touch(acc, (cudaStream_t)stream);
     if (n > 0 && (!d_src || !d_dst))
         return fail(NS_ERR_INVALID, "ns_window_ingest_stats: NULL input with n > 0");
     if (acc->ctx != c) return fail(NS_ERR_INVALID, "ns_window_ingest_stats: foreign matrix");
@@ -800,6 +874,7 @@ ns_status ns_network_stats(ns_ctx* c, const ns_matrix* m, ns_stats* h_out, ns_st
 ns_status ns_network_stats_async(ns_ctx* c, const ns_matrix* m, ns_stats* d_out, ns_stream_t stream) {
     if (!c || !m || !d_out) return fail(NS_ERR_INVALID, "ns_network_stats_async: NULL argument");
     DeviceGuard device_guard(c->device);
+    touch(m, (cudaStream_t)stream);
     TraceScope ts(&c->tracer, "k_stats_out", (cudaStream_t)stream);
     launch_stats_out((const DevStats*)m->stats.p, (u64*)d_out, (cudaStream_t)stream);
     return check_launch();

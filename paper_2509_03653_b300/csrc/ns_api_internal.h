@@ -32,11 +32,29 @@ struct DeviceGuard {
     DeviceGuard& operator=(const DeviceGuard&) = delete;
 };
 
-// A grow-only device allocation.
+// A grow-only device allocation.  Buffers are stream-ordered: they come
+// from the context's memory pool and are allocated, grown and freed on the
+// stream of the entry point that needs them (the AllocScope below), so that
+// no allocation or free synchronizes the device.
 struct Buf {
     void* p = nullptr;
     size_t bytes = 0;
 };
+
+// The pool and stream that buf_reserve / buf_free use on this host thread,
+// set by an entry point for its duration (nested scopes restore the outer
+// one).  Without a scope: the device's default pool and the legacy stream.
+struct AllocScope {
+    cudaMemPool_t prev_pool;
+    cudaStream_t prev_stream;
+    AllocScope(cudaMemPool_t pool, cudaStream_t s);
+    ~AllocScope();
+    AllocScope(const AllocScope&) = delete;
+    AllocScope& operator=(const AllocScope&) = delete;
+};
+cudaStream_t alloc_stream();
+// Frees b on stream s (after the work enqueued there so far).
+void buf_free_on(Buf& b, cudaStream_t s);
 
 enum { FMT_EMPTY = 0, FMT_HASH = 1, FMT_LIST = 2 };
 
@@ -83,6 +101,11 @@ struct ns_ctx {
     ns::SortScratch sc{};
     ns::Buf ghist, offs, tcount, counters, status;
     ns::Buf k64[2], pos, psum, k32[2], v64[2], xk, xv;
+    cudaMemPool_t pool = nullptr;  // every buffer of the context and its objects
+    // The stream of the last call that used the context's scratch.  Calls
+    // without a stream (creation) allocate on the legacy default stream and
+    // wait for it.
+    cudaStream_t last_stream = nullptr;
     ns::Buf stage[2];  // device copies of host columns (ns_window_build_host)
     ns::Buf split;     // the hot-key split's device state
     bool last_split = false;  // the last sort-path build split
@@ -104,4 +127,21 @@ struct ns_matrix {
     ns::Buf stats;       // ns::DevStats
     uint64_t bound = 0;       // host-side upper bound on the number of nonzeros
     uint64_t node_limit = 0;  // caller's bound on sources and destinations (0 = none)
+    cudaStream_t last_stream = nullptr;  // the stream of the last call that enqueued work on it
 };
+
+namespace ns {
+// Records that a call enqueues work on m on stream s (ns_matrix_free frees
+// the matrix's buffers on the last such stream).
+inline void touch(ns_matrix* m, cudaStream_t s) {
+    if (m) m->last_stream = s;
+}
+inline void touch(const ns_matrix* m, cudaStream_t s) { touch(const_cast<ns_matrix*>(m), s); }
+// An entry point's scope: its context's device, and its pool and stream for
+// buffer allocation; also records the stream as the context's last.
+struct CallScope {
+    DeviceGuard dev;
+    AllocScope alloc;
+    CallScope(ns_ctx* c, cudaStream_t s) : dev(c->device), alloc(c->pool, s) { c->last_stream = s; }
+};
+}  // namespace ns

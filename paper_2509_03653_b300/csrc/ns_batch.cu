@@ -35,6 +35,7 @@ struct ns_batch {
     uint64_t arena_slots = 0;  // slots per table kind
     Buf wstats;                // DevStats x max_windows
     Buf counter;               // tile counters, one per chunk
+    cudaStream_t last_stream = nullptr;  // the stream the batch last ran on
     uint64_t max_chunks = 0;
 };
 
@@ -133,6 +134,7 @@ extern "C" {
 ns_status ns_batch_create(ns_ctx* c, uint64_t max_windows, uint64_t max_packets, ns_batch** out) {
     if (!c || !out) return set_fail(NS_ERR_INVALID, "ns_batch_create: NULL argument");
     DeviceGuard device_guard(c->device);
+    AllocScope alloc(c->pool, nullptr);
     if (max_windows == 0) return set_fail(NS_ERR_INVALID, "ns_batch_create: max_windows == 0");
     *out = nullptr;
     ns_batch* b = new ns_batch();
@@ -162,6 +164,11 @@ ns_status ns_batch_create(ns_ctx* c, uint64_t max_windows, uint64_t max_packets,
         cudaGetLastError();
         st = set_fail(NS_ERR_OOM, "ns_batch_create: pinned staging allocation failed");
     }
+    if (st == NS_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) {
+        cudaGetLastError();
+        st = set_fail(NS_ERR_CUDA, "ns_batch_create: allocation failed");
+    }
+    b->last_stream = nullptr;
     if (st != NS_OK) {
         ns_batch_free(b);
         return st;
@@ -173,14 +180,22 @@ ns_status ns_batch_create(ns_ctx* c, uint64_t max_windows, uint64_t max_packets,
 void ns_batch_free(ns_batch* b) {
     if (!b) return;
     DeviceGuard device_guard(b->device);
-    cudaDeviceSynchronize();
-    buf_free(b->meta);
-    buf_free(b->links);
-    buf_free(b->rows);
-    buf_free(b->cols);
-    buf_free(b->wstats);
-    buf_free(b->counter);
-    if (b->h_meta) cudaFreeHost(b->h_meta);
+    // behind the batch's work on the stream it last ran on; the pinned
+    // staging is read by copies on that stream, so it waits for them
+    const cudaStream_t s = b->last_stream;
+    buf_free_on(b->meta, s);
+    buf_free_on(b->links, s);
+    buf_free_on(b->rows, s);
+    buf_free_on(b->cols, s);
+    buf_free_on(b->wstats, s);
+    buf_free_on(b->counter, s);
+    if (b->h_meta) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            cudaDeviceSynchronize();
+        }
+        cudaFreeHost(b->h_meta);
+    }
     delete b;
 }
 
@@ -202,7 +217,9 @@ ns_status ns_batch_run(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uint
                        const uint64_t* h_offsets, uint64_t windows, ns_stats* d_window_stats, ns_matrix* acc,
                        ns_stream_t stream) {
     if (!c || !b || !h_offsets || !d_window_stats) return set_fail(NS_ERR_INVALID, "ns_batch_run: NULL argument");
-    DeviceGuard device_guard(c->device);
+    CallScope scope(c, (cudaStream_t)stream);
+    b->last_stream = (cudaStream_t)stream;
+    touch(acc, (cudaStream_t)stream);
     if (b->ctx != c || (acc && acc->ctx != c)) return set_fail(NS_ERR_INVALID, "ns_batch_run: foreign object");
     if (windows > b->max_windows) return set_fail(NS_ERR_INVALID, "ns_batch_run: more windows than the batch plan");
     if (windows == 0) return NS_OK;
@@ -274,7 +291,8 @@ ns_status ns_batch_tune(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uin
                         const uint64_t* h_offsets, uint64_t windows, ns_stats* d_scratch_stats, ns_stream_t stream,
                         ns_batch_params* chosen) {
     if (!c || !b || !d_scratch_stats) return set_fail(NS_ERR_INVALID, "ns_batch_tune: NULL argument");
-    DeviceGuard device_guard(c->device);
+    CallScope scope(c, (cudaStream_t)stream);
+    b->last_stream = (cudaStream_t)stream;
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned Ts[] = {2048, 4096, 16384};
     const unsigned Cs[] = {4, 8, 16};

@@ -46,8 +46,9 @@ extern "C" {
 
 ns_status ns_matrix_save(const ns_matrix* m, const char* path, ns_stream_t stream) {
     if (!m || !path) return set_fail(NS_ERR_INVALID, "ns_matrix_save: NULL argument");
-    DeviceGuard device_guard(m->device);
     cudaStream_t s = (cudaStream_t)stream;
+    CallScope scope(m->ctx, s);
+    touch(m, s);
     DevStats ds;
     ns_status st = read_stats(m, s, &ds);
     if (st != NS_OK) return st;
@@ -97,8 +98,9 @@ ns_status ns_matrix_save(const ns_matrix* m, const char* path, ns_stream_t strea
 ns_status ns_matrix_load(ns_ctx* c, const char* path, ns_matrix* m, ns_stream_t stream) {
     if (!c || !path || !m) return set_fail(NS_ERR_INVALID, "ns_matrix_load: NULL argument");
     if (m->ctx != c) return set_fail(NS_ERR_INVALID, "ns_matrix_load: matrix belongs to another context");
-    DeviceGuard device_guard(c->device);
     cudaStream_t s = (cudaStream_t)stream;
+    CallScope scope(c, s);
+    touch(m, s);
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail_fmt(NS_ERR_IO, "ns_matrix_load: cannot open %s", path);
     Header h;

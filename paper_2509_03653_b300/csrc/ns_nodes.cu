@@ -248,7 +248,8 @@ extern "C" {
 ns_status ns_matrix_nodes(ns_ctx* c, const ns_matrix* m, int which, uint32_t* d_ids, uint64_t* d_packets,
                           uint64_t* d_degree, uint64_t cap, uint64_t* h_count, ns_stream_t stream) {
     if (!c || !m || !h_count) return set_fail(NS_ERR_INVALID, "ns_matrix_nodes: NULL argument");
-    DeviceGuard device_guard(c->device);
+    CallScope scope(c, (cudaStream_t)stream);
+    touch(m, (cudaStream_t)stream);
     if (which < NS_NODES_SRC || which > NS_NODES_ANY) return set_fail(NS_ERR_INVALID, "ns_matrix_nodes: unknown which");
     if (m->ctx != c) return set_fail(NS_ERR_INVALID, "ns_matrix_nodes: matrix belongs to another context");
     *h_count = 0;
@@ -351,7 +352,7 @@ ns_status ns_anonymize(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, 
                        uint64_t rand_count, uint32_t* d_out_src, uint32_t* d_out_dst, uint64_t* h_unique,
                        ns_stream_t stream) {
     if (!c || !h_unique) return set_fail(NS_ERR_INVALID, "ns_anonymize: NULL argument");
-    DeviceGuard device_guard(c->device);
+    CallScope scope(c, (cudaStream_t)stream);
     *h_unique = 0;
     if (n == 0) return NS_OK;
     if (!d_src || !d_dst || !d_out_src || !d_out_dst) return set_fail(NS_ERR_INVALID, "ns_anonymize: NULL column");

@@ -116,10 +116,13 @@ ns_status slot_prepare(ns_server* S, Slot& sl, u64 n) {
         }
         ns_status st = ns_matrix_create(S->ctx, &sl.At);
         if (st != NS_OK) return st;
-        st = buf_reserve(sl.d_stats, 2 * sizeof(ns_stats));
-        if (st != NS_OK) return st;
     }
-    ns_status st = buf_reserve(sl.d_src, std::max<u64>(n, 1) * sizeof(uint32_t));
+    // The slot's buffers are (re)allocated on its own stream.  A slot is only
+    // prepared while idle (its previous window has completed), so freeing the
+    // old buffers there is safe, and it stalls no other slot.
+    AllocScope alloc(S->ctx->pool, sl.stream);
+    ns_status st = buf_reserve(sl.d_stats, 2 * sizeof(ns_stats));
+    if (st == NS_OK) st = buf_reserve(sl.d_src, std::max<u64>(n, 1) * sizeof(uint32_t));
     if (st == NS_OK) st = buf_reserve(sl.d_dst, std::max<u64>(n, 1) * sizeof(uint32_t));
     return st;
 }
@@ -128,6 +131,8 @@ ns_status slot_prepare(ns_server* S, Slot& sl, u64 n) {
 ns_status launch_window(ns_server* S, Slot& sl, const Request& r) {
     ns_status st = slot_prepare(S, sl, r.n);
     if (st != NS_OK) return st;
+    // A_t's tables, too, grow on the slot's stream
+    AllocScope alloc(S->ctx->pool, sl.stream);
     if (r.n) {
         if (cudaMemcpyAsync(sl.d_src.p, r.src, r.n * sizeof(uint32_t), cudaMemcpyHostToDevice, sl.stream) != cudaSuccess ||
             cudaMemcpyAsync(sl.d_dst.p, r.dst, r.n * sizeof(uint32_t), cudaMemcpyHostToDevice, sl.stream) != cudaSuccess) {
@@ -340,9 +345,9 @@ void ns_server_destroy(ns_server* S) {
         }
         if (sl.h_stats) cudaFreeHost(sl.h_stats);
         if (sl.At) ns_matrix_free(sl.At);
-        buf_free(sl.d_src);
-        buf_free(sl.d_dst);
-        buf_free(sl.d_stats);
+        buf_free_on(sl.d_src, sl.stream);
+        buf_free_on(sl.d_dst, sl.stream);
+        buf_free_on(sl.d_stats, sl.stream);
     }
     cudaStreamDestroy(S->acc_stream);
     delete S;

@@ -131,8 +131,9 @@ ns_status ns_matrix_partition(ns_ctx* c, const ns_matrix* m, int by, uint32_t pa
     if (by != NS_BY_SRC && by != NS_BY_DST) return set_fail(NS_ERR_INVALID, "ns_matrix_partition: unknown `by`");
     if (parts == 0) return set_fail(NS_ERR_INVALID, "ns_matrix_partition: parts == 0");
     if (m->ctx != c) return set_fail(NS_ERR_INVALID, "ns_matrix_partition: matrix belongs to another context");
-    DeviceGuard device_guard(c->device);
     cudaStream_t s = (cudaStream_t)stream;
+    CallScope scope(c, s);
+    touch(m, s);
     uint64_t nnz = 0;
     ns_status st = ns_matrix_nnz(m, &nnz, stream);
     if (st != NS_OK) return st;
@@ -182,8 +183,8 @@ ns_status ns_matrix_add_entries(ns_ctx* c, ns_matrix* m, const uint64_t* d_keys,
     if (!c || !m) return set_fail(NS_ERR_INVALID, "ns_matrix_add_entries: NULL argument");
     if (n > 0 && (!d_keys || !d_counts)) return set_fail(NS_ERR_INVALID, "ns_matrix_add_entries: NULL input");
     if (m->ctx != c) return set_fail(NS_ERR_INVALID, "ns_matrix_add_entries: matrix belongs to another context");
-    DeviceGuard device_guard(c->device);
     cudaStream_t s = (cudaStream_t)stream;
+    CallScope scope(c, s);
     ns_status st = to_hash(m, n, s);
     if (st != NS_OK || n == 0) return st;
     {

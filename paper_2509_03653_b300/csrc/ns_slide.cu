@@ -58,7 +58,7 @@ void ns_slider_free(ns_slider* x) {
 ns_status ns_slider_push(ns_ctx* c, ns_slider* x, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n,
                          ns_stats* d_window, ns_stats* d_sliding, ns_stream_t stream) {
     if (!c || !x) return set_fail(NS_ERR_INVALID, "ns_slider_push: NULL argument");
-    DeviceGuard device_guard(c->device);
+    CallScope scope(c, (cudaStream_t)stream);
     if (x->ctx != c) return set_fail(NS_ERR_INVALID, "ns_slider_push: slider belongs to another context");
     const size_t K = x->ring.size();
     ns_matrix* at = x->ring[x->pushed % K];

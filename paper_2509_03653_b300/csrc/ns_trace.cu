@@ -108,6 +108,7 @@ ns_status ns_trace_read(ns_ctx* c, ns_trace_entry* out, int cap, int* count) {
 ns_status ns_diag_wait_timeout(int which, ns_stream_t stream) {
     if (which < 0 || which > 2) return ns::set_fail(NS_ERR_INVALID, "ns_diag_wait_timeout: which must be 0, 1 or 2");
     cudaStream_t s = (cudaStream_t)stream;
+    ns::AllocScope alloc(nullptr, s);
     ns::Buf b;
     ns_status st = ns::buf_reserve(b, sizeof(ns::DevStats) + 64);
     if (st != NS_OK) return st;
@@ -137,6 +138,7 @@ ns_status ns_diag_random_atomics(uint64_t table_words, uint64_t threads, int rep
     if (!best_us || reps < 1 || table_words < 1024 || (table_words & (table_words - 1)) || threads == 0)
         return ns::set_fail(NS_ERR_INVALID, "ns_diag_random_atomics: bad argument (table_words a power of two >= 1024)");
     cudaStream_t s = (cudaStream_t)stream;
+    ns::AllocScope alloc(nullptr, s);
     ns::Buf a, b, c;
     ns_status st = ns::buf_reserve(a, table_words * 8);
     if (st == NS_OK) st = ns::buf_reserve(b, table_words * 8);

@@ -135,3 +135,61 @@ def test_server_reserve_then_windows_match_oracle():
     pw, run, _ = ns.stream_wait(srv, ns.stream_submit(srv, s, d, 99))
     assert pw == run == oracle.stats_of_packets(s, d)
     srv.close()
+
+
+def test_slots_regrow_mid_stream_without_reserve():
+    """No ns_server_reserve: window sizes keep growing, so every slot frees
+    and regrows its buffers and tables (stream-ordered, on its own stream)
+    while other slots have windows in flight.  Every window's results still
+    equal the oracle's, alone and running."""
+    sizes = [int(64 * 1.6 ** k) for k in range(24)]  # 64 .. ~5.7e6 packets
+    ws = []
+    for w, n in enumerate(sizes):
+        ws.append(W.serving_window(w, n) if w % 3 else W.zipf_window(n, 1.1, 1 << 16, 77 + w))
+    per, run, acc_want = expected(ws)
+    ctx = ns.Context(0, path="hash", max_slots=4)
+    acc = ns.Matrix(ctx)
+    srv = ns.Server(ctx, acc)
+    host = [(torch.from_numpy(s.view(np.int32)).pin_memory(), torch.from_numpy(d.view(np.int32)).pin_memory())
+            for s, d in ws]
+    tickets = []
+    for w, (s, d) in enumerate(host):
+        while True:
+            try:
+                tickets.append(ns.stream_submit(srv, s, d, window_id=w))
+                break
+            except ns.NsError as e:
+                assert e.name == "NS_ERR_BUSY"
+                torch.cuda.synchronize()
+    results = [ns.stream_wait(srv, t) for t in tickets]
+    srv.close()
+    for w, (pw, rn, _) in enumerate(results):
+        assert pw == per[w], w
+        assert rn == run[w], w
+    assert_matrix_equal(acc, *acc_want)
+    acc.free()
+    ctx.close()
+
+
+def test_free_does_not_wait_for_other_streams():
+    """ns_matrix_free of a matrix last used on one stream returns while a
+    long build on another stream is still running (no device-wide wait)."""
+    ctx = ns.Context(0, path="sort")
+    big = ns.Matrix(ctx)
+    small = ns.Matrix(ctx)
+    n = 1 << 27
+    s, d = W.zipf_window(n, 1.2, 1 << 20, 5)
+    ds = torch.from_numpy(s.view(np.int32)).cuda()
+    dd = torch.from_numpy(d.view(np.int32)).cuda()
+    ns.window_build(ctx, ds[:4096], dd[:4096], small)  # on the current stream
+    torch.cuda.synchronize()
+    other = torch.cuda.Stream()
+    with torch.cuda.stream(other):
+        for _ in range(4):
+            ns.window_build(ctx, ds, dd, big)  # tens of ms of work on `other`
+    small.free()
+    assert not other.query(), "the free waited for another stream's work"
+    other.synchronize()
+    assert ns.network_stats(ctx, big)["valid_packets"] == n
+    big.free()
+    ctx.close()
