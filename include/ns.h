@@ -22,10 +22,13 @@
  *  - Device memory is stream-ordered: every buffer comes from the context's
  *    memory pool and is allocated, grown and freed on the stream of the call
  *    that needs it (calls without a stream -- the create calls -- use the
- *    legacy default stream and wait for it).  No allocation or free waits for
- *    the whole device.  A buffer cannot grow while its stream is being
- *    captured into a CUDA graph: such a call returns NS_ERR_STATE (run it
- *    once before the capture so that every buffer has its size).
+ *    legacy default stream and wait for it).  Freeing a matrix or a batch,
+ *    and growing a serving slot, never wait for the whole device; growing a
+ *    buffer that other streams may still read (the context's scratch, a
+ *    matrix's tables) and ns_destroy do, as cudaFree would.  A buffer cannot
+ *    grow while its stream is being captured into a CUDA graph: such a call
+ *    returns NS_ERR_STATE (run it once before the capture so that every
+ *    buffer has its size).
  *  - n == 0 is legal everywhere and gives an empty matrix / zero statistics.
  *    Null pointers with n > 0, unknown enum values and mismatched devices
  *    return NS_ERR_INVALID.  No call aborts, traps or hangs: device-side
@@ -143,10 +146,9 @@ typedef struct {
  * passed in must belong to that device. */
 ns_status ns_create(ns_ctx** ctx, const ns_config* cfg, int device);
 
-/* Frees everything the context owns (matrices, batches, sliders and
- * servers created from it must be freed first): its scratch is released in
- * stream order behind the work of its last call, and its memory pool gives
- * the memory back once those frees have run.  Does not wait for the device. */
+/* Waits for the device, then frees everything the context owns (matrices,
+ * batches, sliders and servers created from it must be freed first); its
+ * memory pool gives the memory back once every buffer from it is freed. */
 void ns_destroy(ns_ctx* ctx);
 
 /* Blocks until all work the context enqueued on `stream` is done, then

@@ -54,15 +54,19 @@ namespace ns {
 namespace {
 thread_local cudaMemPool_t t_pool = nullptr;
 thread_local cudaStream_t t_stream = nullptr;
+thread_local bool t_private = false;
 }  // namespace
 
-AllocScope::AllocScope(cudaMemPool_t pool, cudaStream_t s) : prev_pool(t_pool), prev_stream(t_stream) {
+AllocScope::AllocScope(cudaMemPool_t pool, cudaStream_t s, bool stream_private)
+    : prev_pool(t_pool), prev_stream(t_stream), prev_private(t_private) {
     t_pool = pool;
     t_stream = s;
+    t_private = stream_private;
 }
 AllocScope::~AllocScope() {
     t_pool = prev_pool;
     t_stream = prev_stream;
+    t_private = prev_private;
 }
 cudaStream_t alloc_stream() { return t_stream; }
 
@@ -80,6 +84,7 @@ ns_status buf_reserve(Buf& b, size_t bytes) {
         return fail(NS_ERR_STATE, "a buffer must grow (to %zu bytes) while its stream is being captured; "
                                   "run the call once before the capture", bytes);
     if (b.p) {
+        if (!t_private) cudaDeviceSynchronize();  // earlier readers on other streams are done
         cudaFreeAsync(b.p, s);
         b.p = nullptr;
         b.bytes = 0;
@@ -513,9 +518,10 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
 void ns_destroy(ns_ctx* c) {
     if (!c) return;
     DeviceGuard device_guard(c->device);
-    // the scratch is freed behind the work of the context's last call, on
-    // that call's stream; the pool gives its memory back once those frees
-    // have run.  Nothing here waits for the device.
+    // The context's scratch may have been used on several streams: wait for
+    // the device, then free it; the pool gives its memory back once every
+    // buffer allocated from it has been freed.
+    cudaDeviceSynchronize();
     Buf* all[] = {&c->ghist, &c->offs, &c->tcount, &c->counters, &c->status, &c->k64[0], &c->k64[1],
                   &c->pos, &c->psum, &c->k32[0], &c->k32[1], &c->v64[0], &c->v64[1], &c->xk, &c->xv,
                   &c->stage[0], &c->stage[1], &c->split};

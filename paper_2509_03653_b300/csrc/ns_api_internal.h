@@ -44,10 +44,16 @@ struct Buf {
 // The pool and stream that buf_reserve / buf_free use on this host thread,
 // set by an entry point for its duration (nested scopes restore the outer
 // one).  Without a scope: the device's default pool and the legacy stream.
+// Growing a buffer frees its old memory: unless the scope declares its
+// buffers private to its stream (every earlier use is on that stream or has
+// completed), the old memory may still be read by work on another stream,
+// so growth first waits for the device (as cudaFree would).  Frees of whole
+// objects (ns_matrix_free, ns_batch_free) are stream-ordered instead.
 struct AllocScope {
     cudaMemPool_t prev_pool;
     cudaStream_t prev_stream;
-    AllocScope(cudaMemPool_t pool, cudaStream_t s);
+    bool prev_private;
+    AllocScope(cudaMemPool_t pool, cudaStream_t s, bool stream_private = false);
     ~AllocScope();
     AllocScope(const AllocScope&) = delete;
     AllocScope& operator=(const AllocScope&) = delete;

@@ -120,7 +120,7 @@ ns_status slot_prepare(ns_server* S, Slot& sl, u64 n) {
     // The slot's buffers are (re)allocated on its own stream.  A slot is only
     // prepared while idle (its previous window has completed), so freeing the
     // old buffers there is safe, and it stalls no other slot.
-    AllocScope alloc(S->ctx->pool, sl.stream);
+    AllocScope alloc(S->ctx->pool, sl.stream, true);
     ns_status st = buf_reserve(sl.d_stats, 2 * sizeof(ns_stats));
     if (st == NS_OK) st = buf_reserve(sl.d_src, std::max<u64>(n, 1) * sizeof(uint32_t));
     if (st == NS_OK) st = buf_reserve(sl.d_dst, std::max<u64>(n, 1) * sizeof(uint32_t));
@@ -132,7 +132,7 @@ ns_status launch_window(ns_server* S, Slot& sl, const Request& r) {
     ns_status st = slot_prepare(S, sl, r.n);
     if (st != NS_OK) return st;
     // A_t's tables, too, grow on the slot's stream
-    AllocScope alloc(S->ctx->pool, sl.stream);
+    AllocScope alloc(S->ctx->pool, sl.stream, true);
     if (r.n) {
         if (cudaMemcpyAsync(sl.d_src.p, r.src, r.n * sizeof(uint32_t), cudaMemcpyHostToDevice, sl.stream) != cudaSuccess ||
             cudaMemcpyAsync(sl.d_dst.p, r.dst, r.n * sizeof(uint32_t), cudaMemcpyHostToDevice, sl.stream) != cudaSuccess) {
