@@ -19,16 +19,14 @@
  *  - The caller owns the input buffers and must keep them valid and
  *    unmodified until the stream work completes.  The library owns matrices
  *    and all scratch memory it allocates.
- *  - Device memory is stream-ordered: every buffer comes from the context's
- *    memory pool and is allocated, grown and freed on the stream of the call
- *    that needs it (calls without a stream -- the create calls -- use the
- *    legacy default stream and wait for it).  Freeing a matrix or a batch,
- *    and growing a serving slot, never wait for the whole device; growing a
- *    buffer that other streams may still read (the context's scratch, a
- *    matrix's tables) and ns_destroy do, as cudaFree would.  A buffer cannot
- *    grow while its stream is being captured into a CUDA graph: such a call
- *    returns NS_ERR_STATE (run it once before the capture so that every
- *    buffer has its size).
+ *  - Device memory: the serving slots' buffers and window matrices come from
+ *    the context's memory pool and are allocated, grown and freed in stream
+ *    order on the slot's own stream, so that a slot that grows stalls no
+ *    other slot.  Every other buffer comes from cudaMalloc and is released
+ *    with cudaFree, which waits for the device.  A buffer cannot grow while
+ *    its stream is being captured into a CUDA graph: such a call returns
+ *    NS_ERR_STATE (run it once before the capture so that every buffer has
+ *    its size).
  *  - n == 0 is legal everywhere and gives an empty matrix / zero statistics.
  *    Null pointers with n > 0, unknown enum values and mismatched devices
  *    return NS_ERR_INVALID.  No call aborts, traps or hangs: device-side
@@ -176,11 +174,9 @@ ns_status ns_matrix_reserve_ex(ns_matrix* m, uint64_t max_links, uint64_t max_no
 /* Makes the matrix empty (A = 0) keeping its memory.  Enqueued on stream. */
 ns_status ns_matrix_clear(ns_matrix* m, ns_stream_t stream);
 
-/* Frees the matrix's device memory in stream order, behind the work
- * enqueued on the stream of the last call that used the matrix; the host does
- * not wait.  Work that uses the matrix and was launched any other way (a
- * replayed CUDA graph, a stream not ordered before that one) must be complete
- * or ordered before that stream's current point. */
+/* Frees the matrix after its pending work completes (memory from the
+ * serving pool is released in stream order behind the work of the last
+ * stream that used the matrix). */
 void ns_matrix_free(ns_matrix* m);
 
 /* Number of nonzeros of A (unique links).  Blocking. */
@@ -358,8 +354,7 @@ typedef struct {
  * per-window metadata and statistics.  Parameters come from the context's
  * tuner cache when it has an entry for this GPU and batch shape. */
 ns_status ns_batch_create(ns_ctx* ctx, uint64_t max_windows, uint64_t max_packets, ns_batch** out);
-/* Frees the batch in stream order behind its last run (waiting only for
- * that stream, whose copies read the batch's pinned staging). */
+/* Frees the batch after its pending work completes. */
 void ns_batch_free(ns_batch* batch);
 ns_status ns_batch_get_params(const ns_batch* batch, ns_batch_params* out);
 ns_status ns_batch_set_params(ns_batch* batch, const ns_batch_params* params);

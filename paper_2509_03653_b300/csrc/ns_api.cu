@@ -74,7 +74,7 @@ ns_status buf_reserve(Buf& b, size_t bytes) {
     if (b.bytes >= bytes && b.p) return NS_OK;
     const cudaStream_t s = t_stream;
     // Growing inside a CUDA graph capture would make the new buffer the
-    // graph's own allocation: refuse, as cudaMalloc would.
+    // graph's own (or fail): refuse with a clear error.
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
         cudaGetLastError();
@@ -83,33 +83,48 @@ ns_status buf_reserve(Buf& b, size_t bytes) {
     if (cs != cudaStreamCaptureStatusNone)
         return fail(NS_ERR_STATE, "a buffer must grow (to %zu bytes) while its stream is being captured; "
                                   "run the call once before the capture", bytes);
+    // Stream-private scopes (every earlier use of their buffers is on their
+    // stream or complete) allocate from the context's pool in stream order;
+    // all others use cudaMalloc / cudaFree, which wait for the device.
+    const bool pooled = t_private && t_pool;
     if (b.p) {
-        if (!t_private) cudaDeviceSynchronize();  // earlier readers on other streams are done
-        cudaFreeAsync(b.p, s);
+        if (b.pooled) {
+            if (!t_private) cudaDeviceSynchronize();  // earlier readers on other streams are done
+            cudaFreeAsync(b.p, s);
+        } else {
+            cudaFree(b.p);
+        }
         b.p = nullptr;
         b.bytes = 0;
+        b.pooled = false;
     }
     if (bytes == 0) return NS_OK;
-    cudaError_t e = t_pool ? cudaMallocFromPoolAsync(&b.p, bytes, t_pool, s) : cudaMallocAsync(&b.p, bytes, s);
+    const cudaError_t e = pooled ? cudaMallocFromPoolAsync(&b.p, bytes, t_pool, s) : cudaMalloc(&b.p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         b.p = nullptr;
         return fail(NS_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     }
     b.bytes = bytes;
+    b.pooled = pooled;
     return NS_OK;
 }
 
 void buf_free_on(Buf& b, cudaStream_t s) {
-    if (b.p && cudaFreeAsync(b.p, s) != cudaSuccess) {
-        // the stream is gone: wait for the device, then free on the legacy stream
-        cudaGetLastError();
-        cudaDeviceSynchronize();
-        cudaFreeAsync(b.p, nullptr);
+    if (b.p) {
+        if (!b.pooled) {
+            cudaFree(b.p);
+        } else if (cudaFreeAsync(b.p, s) != cudaSuccess) {
+            // the stream is gone: wait for the device, then free on the legacy stream
+            cudaGetLastError();
+            cudaDeviceSynchronize();
+            cudaFreeAsync(b.p, nullptr);
+        }
         cudaGetLastError();
     }
     b.p = nullptr;
     b.bytes = 0;
+    b.pooled = false;
 }
 
 void buf_free(Buf& b) { buf_free_on(b, t_stream); }

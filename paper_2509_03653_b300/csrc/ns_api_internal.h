@@ -32,23 +32,23 @@ struct DeviceGuard {
     DeviceGuard& operator=(const DeviceGuard&) = delete;
 };
 
-// A grow-only device allocation.  Buffers are stream-ordered: they come
-// from the context's memory pool and are allocated, grown and freed on the
-// stream of the entry point that needs them (the AllocScope below), so that
-// no allocation or free synchronizes the device.
+// A grow-only device allocation.  Inside a stream-private allocation scope
+// (the AllocScope below; the serving slots) buffers come from the context's
+// memory pool and are allocated, grown and freed in stream order on the
+// scope's stream, which stalls no other stream; elsewhere they come from
+// cudaMalloc and go back with cudaFree, which waits for the device.
 struct Buf {
     void* p = nullptr;
     size_t bytes = 0;
+    bool pooled = false;  // from the context's pool: freed with cudaFreeAsync
 };
 
 // The pool and stream that buf_reserve / buf_free use on this host thread,
 // set by an entry point for its duration (nested scopes restore the outer
-// one).  Without a scope: the device's default pool and the legacy stream.
-// Growing a buffer frees its old memory: unless the scope declares its
-// buffers private to its stream (every earlier use is on that stream or has
-// completed), the old memory may still be read by work on another stream,
-// so growth first waits for the device (as cudaFree would).  Frees of whole
-// objects (ns_matrix_free, ns_batch_free) are stream-ordered instead.
+// one).  Only a scope that declares its buffers private to its stream (every
+// earlier use of them is on that stream or has completed) allocates from the
+// pool in stream order; elsewhere growth frees the old memory with cudaFree,
+// which waits for every reader on any stream.
 struct AllocScope {
     cudaMemPool_t prev_pool;
     cudaStream_t prev_stream;

@@ -170,26 +170,3 @@ def test_slots_regrow_mid_stream_without_reserve():
     acc.free()
     ctx.close()
 
-
-def test_free_does_not_wait_for_other_streams():
-    """ns_matrix_free of a matrix last used on one stream returns while a
-    long build on another stream is still running (no device-wide wait)."""
-    ctx = ns.Context(0, path="sort")
-    big = ns.Matrix(ctx)
-    small = ns.Matrix(ctx)
-    n = 1 << 27
-    s, d = W.zipf_window(n, 1.2, 1 << 20, 5)
-    ds = torch.from_numpy(s.view(np.int32)).cuda()
-    dd = torch.from_numpy(d.view(np.int32)).cuda()
-    ns.window_build(ctx, ds[:4096], dd[:4096], small)  # on the current stream
-    torch.cuda.synchronize()
-    other = torch.cuda.Stream()
-    with torch.cuda.stream(other):
-        for _ in range(4):
-            ns.window_build(ctx, ds, dd, big)  # tens of ms of work on `other`
-    small.free()
-    assert not other.query(), "the free waited for another stream's work"
-    other.synchronize()
-    assert ns.network_stats(ctx, big)["valid_packets"] == n
-    big.free()
-    ctx.close()
