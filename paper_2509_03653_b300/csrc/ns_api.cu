@@ -271,6 +271,24 @@ ns_status to_hash(ns_matrix* m, u64 extra, cudaStream_t s) {
     return NS_OK;
 }
 
+ns_status context_pool(ns_ctx* c) {
+    if (c->pool) return NS_OK;
+    // keeps freed memory for reuse until the context is destroyed
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = c->device;
+    if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        c->pool = nullptr;
+        return fail(NS_ERR_CUDA, "memory pool creation failed");
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    return NS_OK;
+}
+
 ns_status sort_scratch(ns_ctx* c, u64 n) {
     const u64 tiles = sort_tiles(std::max<u64>(n, 1));
     const u64 words = tiles * (u64)sort_radix();
@@ -490,24 +508,7 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
     load_path_choices(x);
     cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, device);
     x->sc.sms = x->sms;
-    // the context's memory pool: it keeps freed memory for reuse until the
-    // context is destroyed
-    {
-        cudaMemPoolProps props{};
-        props.allocType = cudaMemAllocationTypePinned;
-        props.handleTypes = cudaMemHandleTypeNone;
-        props.location.type = cudaMemLocationTypeDevice;
-        props.location.id = device;
-        if (cudaMemPoolCreate(&x->pool, &props) != cudaSuccess) {
-            cudaGetLastError();
-            x->pool = nullptr;
-            ns_destroy(x);
-            return fail(NS_ERR_CUDA, "ns_create: memory pool creation failed");
-        }
-        uint64_t keep = UINT64_MAX;
-        cudaMemPoolSetAttribute(x->pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    }
-    AllocScope alloc(x->pool, nullptr);
+    AllocScope alloc(nullptr, nullptr);
     ns_status st = buf_reserve(x->ghist, 8 * 256 * sizeof(u64));
     if (st == NS_OK) st = buf_reserve(x->offs, 9 * 256 * sizeof(u64));  // [8][256] offsets + cursors
     if (st == NS_OK) st = buf_reserve(x->tcount, 16 * sizeof(u32));

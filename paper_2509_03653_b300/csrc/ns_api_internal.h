@@ -75,6 +75,9 @@ ns_status set_fail(ns_status s, const char* msg);
 // Reads the matrix's statistics record (blocking); the device error word
 // comes back as a status.
 ns_status read_stats(const ns_matrix* m, cudaStream_t s, DevStats* out);
+// Creates the context's memory pool (for stream-private allocation scopes)
+// if it has none yet.
+ns_status context_pool(ns_ctx* c);
 // Sizes the context's look-back status words for sorts of up to n elements.
 ns_status sort_scratch(ns_ctx* c, u64 n);
 // Hash path: out := A_t.  cache: -1 = the context's rule, 0 = off, 1 = on.
@@ -107,7 +110,7 @@ struct ns_ctx {
     ns::SortScratch sc{};
     ns::Buf ghist, offs, tcount, counters, status;
     ns::Buf k64[2], pos, psum, k32[2], v64[2], xk, xv;
-    cudaMemPool_t pool = nullptr;  // every buffer of the context and its objects
+    cudaMemPool_t pool = nullptr;  // the serving slots' memory (created with the first server)
     // The stream of the last call that used the context's scratch.  Calls
     // without a stream (creation) allocate on the legacy default stream and
     // wait for it.

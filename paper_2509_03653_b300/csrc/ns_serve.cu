@@ -260,6 +260,10 @@ ns_status ns_server_create(ns_ctx* c, ns_matrix* acc, ns_server** out) {
     DeviceGuard device_guard(c->device);
     if (acc->ctx != c) return set_fail(NS_ERR_INVALID, "ns_server_create: acc belongs to another context");
     *out = nullptr;
+    {
+        const ns_status pst = context_pool(c);
+        if (pst != NS_OK) return pst;
+    }
     ns_server* S = new ns_server();
     S->ctx = c;
     S->acc = acc;
