@@ -340,18 +340,26 @@ void ns_server_destroy(ns_server* S) {
     S->completer.join();
     cudaSetDevice(S->device);
     cudaStreamSynchronize(S->acc_stream);
+    for (auto& sl : S->slots)
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+    // Every window has completed.  A slot's memory comes from the context's
+    // pool in stream order on the slot's stream, so it is freed there while
+    // that stream still exists; the stream is destroyed afterwards.
     for (auto& sl : S->slots) {
+        if (sl.At) {
+            touch(sl.At, sl.stream);
+            ns_matrix_free(sl.At);
+            sl.At = nullptr;
+        }
+        buf_free_on(sl.d_src, sl.stream);
+        buf_free_on(sl.d_dst, sl.stream);
+        buf_free_on(sl.d_stats, sl.stream);
         if (sl.stream) {
-            cudaStreamSynchronize(sl.stream);
             cudaStreamDestroy(sl.stream);
             cudaEventDestroy(sl.built);
             cudaEventDestroy(sl.done);
         }
         if (sl.h_stats) cudaFreeHost(sl.h_stats);
-        if (sl.At) ns_matrix_free(sl.At);
-        buf_free_on(sl.d_src, sl.stream);
-        buf_free_on(sl.d_dst, sl.stream);
-        buf_free_on(sl.d_stats, sl.stream);
     }
     cudaStreamDestroy(S->acc_stream);
     delete S;
