@@ -122,6 +122,15 @@ enum {
     NS_SPLIT_OFF = 2
 };
 
+/* The tile of the sort path's digit passes over 64-bit keys (threads x keys
+ * per thread; see ns_config.sort_tile).  Exact either way. */
+enum {
+    NS_TILE_AUTO = 0,   /* ns_path_tune's choice for the size, else 512 x 16 */
+    NS_TILE_512X16 = 1, /* 8192-key tiles, two CTAs per SM */
+    NS_TILE_512X12 = 2, /* 6144-key tiles */
+    NS_TILE_256X16 = 3  /* 4096-key tiles, four CTAs per SM */
+};
+
 typedef struct {
     int path;                  /* NS_PATH_* used by ns_window_build */
     uint64_t hbm_budget_bytes; /* serving admission and batch arena budget; 0 = 64 GiB */
@@ -133,6 +142,7 @@ typedef struct {
                                   library sizes (builds, reserves, growth), in [0.05, 0.9];
                                   0 = 0.5.  Lower costs memory and shortens probe chains. */
     int sort_split;            /* NS_SPLIT_* for the sort path */
+    int sort_tile;             /* NS_TILE_* for the sort path's digit passes */
 } ns_config;
 
 /* ---- context ----------------------------------------------------------- */
@@ -272,14 +282,15 @@ ns_status ns_window_build_host(ns_ctx* ctx, const uint32_t* h_src, const uint32_
                                ns_matrix* out, ns_stats* h_stats, ns_stream_t stream);
 
 /* Path tuner: builds A from d_src/d_dst (n > 0 packets, device memory)
- * with the sort path without and with the hot-key split (only the one the
- * context's sort_split forces, if it forces one; no split below 2^16
- * packets), the hash path without per-CTA caches and the hash path with them
- * (only the one the context's cta_cache forces, if it forces one), three
- * times each, and keeps the fastest of the last two timings of each.  The
- * winner becomes the context's NS_PATH_AUTO / NS_CACHE_AUTO choice, and the
- * faster sort variant its NS_SPLIT_AUTO choice, for every n' with
- * floor(log2 n') = floor(log2 n); both are stored in the tuner cache file
+ * with the sort path in every combination of hot-key split (without, with;
+ * no split below 2^16 packets) and digit-pass tile (the three NS_TILE_*
+ * shapes) -- only the ones the context's sort_split and sort_tile allow --
+ * and the hash path without and with per-CTA caches (only the one the
+ * context's cta_cache forces, if it forces one), three times each, and
+ * keeps the fastest of the last two timings of each.  The winner becomes
+ * the context's NS_PATH_AUTO / NS_CACHE_AUTO choice, and the fastest sort
+ * variant its NS_SPLIT_AUTO / NS_TILE_AUTO choice, for every n' with
+ * floor(log2 n') = floor(log2 n); all are stored in the tuner cache file
  * (if the context has one) keyed by GPU name and that power of two, where
  * later contexts on the same GPU find them.  *chosen (NS_PATH_SORT or
  * NS_PATH_HASH), *sort_ms (the faster sort variant) and *hash_ms (the faster

@@ -22,7 +22,7 @@ from ._native import (FIELDS, NsBatchParams, NsConfig, NsError, NsStats, NsStrea
 __all__ = [
     "FIELDS", "NsError", "Context", "Matrix", "window_build", "window_build_host", "accumulate", "window_ingest",
     "window_ingest_stats", "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
-    "matrix_clear", "sync", "PATHS", "path_tune", "path_resolve", "sort_split_info", "matrix_nodes", "NODES", "anonymize", "Slider",
+    "matrix_clear", "sync", "PATHS", "SORT_TILES", "path_tune", "path_resolve", "sort_split_info", "matrix_nodes", "NODES", "anonymize", "Slider",
     "slider_push", "window_stats_static", "STATIC_MAX_PACKETS",
     "trace_enable", "trace_read", "Batch", "batch_run", "batch_tune", "matrix_reserve_ex",
     "owner", "matrix_partition", "matrix_add_entries", "Server", "stream_submit", "stream_poll", "stream_wait", "diag_random_atomics", "matrix_save", "matrix_load",
@@ -31,6 +31,8 @@ __all__ = [
 STATIC_MAX_PACKETS = 32768  # NS_STATIC_MAX_PACKETS in include/ns.h
 
 PATHS = {"auto": 0, "sort": 1, "hash": 2}
+# digit-pass tiles of the sort path (ns_config.sort_tile): threads x keys per thread
+SORT_TILES = {"auto": 0, "512x16": 1, "512x12": 2, "256x16": 3}
 
 
 def _stream(stream) -> ctypes.c_void_p:
@@ -56,11 +58,13 @@ class Context:
 
     def __init__(self, device: int = 0, path: str = "auto", hbm_budget_bytes: int = 0,
                  max_slots: int = 0, tuner_cache: str | None = None, cta_cache: str = "auto",
-                 column_sort: str = "auto", hash_load: float = 0.0, sort_split: str = "auto"):
+                 column_sort: str = "auto", hash_load: float = 0.0, sort_split: str = "auto",
+                 sort_tile: str = "auto"):
         self._L = load()
         cfg = NsConfig(PATHS[path], hbm_budget_bytes, max_slots,
                        tuner_cache.encode() if tuner_cache else None, {"auto": 0, "on": 1, "off": 2}[cta_cache],
-                       {"auto": 0, "pairs": 1}[column_sort], hash_load, {"auto": 0, "on": 1, "off": 2}[sort_split])
+                       {"auto": 0, "pairs": 1}[column_sort], hash_load, {"auto": 0, "on": 1, "off": 2}[sort_split],
+                       SORT_TILES[sort_tile])
         h = ctypes.c_void_p()
         check(self._L.ns_create(ctypes.byref(h), ctypes.byref(cfg), device), "ns_create")
         self.handle = h

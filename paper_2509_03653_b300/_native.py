@@ -16,7 +16,8 @@ ST = ctypes.c_int  # ns_status
 
 class NsConfig(ctypes.Structure):
     _fields_ = [("path", I32), ("hbm_budget_bytes", U64), ("max_slots", I32), ("tuner_cache", ctypes.c_char_p),
-                ("cta_cache", I32), ("column_sort", I32), ("hash_load", ctypes.c_double), ("sort_split", I32)]
+                ("cta_cache", I32), ("column_sort", I32), ("hash_load", ctypes.c_double), ("sort_split", I32),
+                ("sort_tile", I32)]
 
 
 class NsStats(ctypes.Structure):

@@ -316,10 +316,21 @@ bool use_split(const ns_ctx* c, u64 n) {
 }
 
 // Sort path: A_t's sorted nonzero list and its statistics.
-// split: -1 = use_split's rule, 0 = no split, 1 = split (from 2^16 packets).
+// The digit passes' tile shape for n packets: the context's setting, else
+// ns_path_tune's measurement for the size, else 512 threads x 16 keys.
+int resolve_tile(const ns_ctx* c, u64 n) {
+    if (c->cfg.sort_tile != NS_TILE_AUTO) return c->cfg.sort_tile - 1;
+    const auto it = c->path_choice.find(n ? 63 - __builtin_clzll(n) : 0);
+    if (it != c->path_choice.end() && it->second.tile >= 0) return it->second.tile;
+    return 0;
+}
+
+// split: -1 = use_split's rule, 0 = no split, 1 = split (from 2^16 packets);
+// tile: -1 = resolve_tile's rule, else the digit passes' tile shape.
 ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n, ns_matrix* out,
-                     cudaStream_t s, int split = -1) {
+                     cudaStream_t s, int split = -1, int tile = -1) {
     touch(out, s);
+    c->sc.tile_shape = tile < 0 ? resolve_tile(c, n) : tile;
     out->fmt = FMT_LIST;
     out->bound = n;
     CK(cudaMemsetAsync(out->stats.p, 0, sizeof(DevStats), s));
@@ -421,13 +432,15 @@ void load_path_choices(ns_ctx* c) {
         if (kv.first.compare(0, prefix.size(), prefix) != 0) continue;
         const int lg = atoi(kv.first.c_str() + prefix.size());
         std::string p;
-        double cache = 0, split = -1;
+        double cache = 0, split = -1, tile = -1;
         if (lg < 0 || lg > 40 || !json_string(kv.second, "path", &p)) continue;
         json_number(kv.second, "cta_cache", &cache);
         json_number(kv.second, "sort_split", &split);
+        json_number(kv.second, "sort_tile", &tile);
         const int sp = split < 0 ? -1 : (split != 0 ? 1 : 0);
-        if (p == "sort") c->path_choice[lg] = {NS_PATH_SORT, false, sp};
-        if (p == "hash") c->path_choice[lg] = {NS_PATH_HASH, cache != 0, sp};
+        const int tl = (tile >= 0 && tile < kSortTileShapes) ? (int)tile : -1;
+        if (p == "sort") c->path_choice[lg] = {NS_PATH_SORT, false, sp, tl};
+        if (p == "hash") c->path_choice[lg] = {NS_PATH_HASH, cache != 0, sp, tl};
     }
 }
 
@@ -493,6 +506,8 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
         return fail(NS_ERR_INVALID, "ns_create: unknown column_sort %d", c.column_sort);
     if (c.sort_split < NS_SPLIT_AUTO || c.sort_split > NS_SPLIT_OFF)
         return fail(NS_ERR_INVALID, "ns_create: unknown sort_split %d", c.sort_split);
+    if (c.sort_tile < NS_TILE_AUTO || c.sort_tile > NS_TILE_256X16)
+        return fail(NS_ERR_INVALID, "ns_create: unknown sort_tile %d", c.sort_tile);
     if (c.hash_load == 0.0) c.hash_load = 0.5;
     if (!(c.hash_load >= 0.05 && c.hash_load <= 0.9))
         return fail(NS_ERR_INVALID, "ns_create: hash_load %g outside [0.05, 0.9]", c.hash_load);
@@ -731,16 +746,21 @@ ns_status ns_path_tune(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, 
     // packets), then the hash path without and with per-CTA caches (only the
     // forced one if the context fixes cta_cache)
     struct Cand {
-        int path, cache, split;
+        int path, cache, split, tile;
         float ms;
     };
     std::vector<Cand> cand;
     const bool can_split = n >= (1ull << 16);
-    if (c->cfg.sort_split != NS_SPLIT_ON || !can_split) cand.push_back({NS_PATH_SORT, 0, 0, 1e30f});
-    if (c->cfg.sort_split != NS_SPLIT_OFF && can_split) cand.push_back({NS_PATH_SORT, 0, 1, 1e30f});
+    std::vector<int> splits, tiles;
+    if (c->cfg.sort_split != NS_SPLIT_ON || !can_split) splits.push_back(0);
+    if (c->cfg.sort_split != NS_SPLIT_OFF && can_split) splits.push_back(1);
+    for (int t = 0; t < kSortTileShapes; ++t)
+        if (c->cfg.sort_tile == NS_TILE_AUTO || c->cfg.sort_tile - 1 == t) tiles.push_back(t);
+    for (int sp : splits)
+        for (int t : tiles) cand.push_back({NS_PATH_SORT, 0, sp, t, 1e30f});
     const size_t n_sort = cand.size();
-    if (c->cfg.cta_cache != NS_CACHE_ON) cand.push_back({NS_PATH_HASH, 0, -1, 1e30f});
-    if (c->cfg.cta_cache != NS_CACHE_OFF) cand.push_back({NS_PATH_HASH, 1, -1, 1e30f});
+    if (c->cfg.cta_cache != NS_CACHE_ON) cand.push_back({NS_PATH_HASH, 0, -1, -1, 1e30f});
+    if (c->cfg.cta_cache != NS_CACHE_OFF) cand.push_back({NS_PATH_HASH, 1, -1, -1, 1e30f});
     ns_matrix* m = nullptr;
     TRY(ns_matrix_create(c, &m));
     cudaEvent_t e0, e1;
@@ -752,7 +772,7 @@ ns_status ns_path_tune(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, 
         // the next two are timed
         for (int rep = 0; rep < 3 && st == NS_OK; ++rep) {
             cudaEventRecord(e0, s);
-            st = k.path == NS_PATH_SORT ? build_sort(c, d_src, d_dst, n, m, s, k.split)
+            st = k.path == NS_PATH_SORT ? build_sort(c, d_src, d_dst, n, m, s, k.split, k.tile)
                                         : build_hash(c, d_src, d_dst, n, m, s, k.cache);
             cudaEventRecord(e1, s);
             if (st != NS_OK) break;
@@ -779,21 +799,24 @@ ns_status ns_path_tune(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, 
         if (k.ms < best->ms) best = &k;
         if (i < n_sort && k.ms < best_sort->ms) best_sort = &k;
         if (k.path == NS_PATH_HASH) best_hash = std::min(best_hash, k.ms);
-        if (k.path == NS_PATH_SORT) (k.split ? split_ms : plain_ms) = k.ms;
+        if (k.path == NS_PATH_SORT) {
+            float& r = k.split ? split_ms : plain_ms;  // the best tile of each
+            if (r < 0 || k.ms < r) r = k.ms;
+        }
     }
     const int lg = floor_log2(n);
-    // the sort path's split choice is kept for the size whichever path wins
-    c->path_choice[lg] = {best->path, best->cache != 0, best_sort->split};
+    // the sort path's choices are kept for the size whichever path wins
+    c->path_choice[lg] = {best->path, best->cache != 0, best_sort->split, best_sort->tile};
     if (chosen) *chosen = best->path;
     if (sort_ms) *sort_ms = best_sort->ms;
     if (hash_ms) *hash_ms = best_hash;
     auto cache = tuner_load(c->tuner_cache);
     char val[256];
     snprintf(val, sizeof val,
-             "{\"path\": \"%s\", \"cta_cache\": %d, \"sort_split\": %d, \"sort_ms\": %.4f, \"hash_ms\": %.4f, "
-             "\"sort_split_ms\": %.4f, \"sort_plain_ms\": %.4f}",
-             best->path == NS_PATH_SORT ? "sort" : "hash", best->cache, best_sort->split, best_sort->ms, best_hash,
-             split_ms, plain_ms);
+             "{\"path\": \"%s\", \"cta_cache\": %d, \"sort_split\": %d, \"sort_tile\": %d, \"sort_ms\": %.4f, "
+             "\"hash_ms\": %.4f, \"sort_split_ms\": %.4f, \"sort_plain_ms\": %.4f}",
+             best->path == NS_PATH_SORT ? "sort" : "hash", best->cache, best_sort->split, best_sort->tile,
+             best_sort->ms, best_hash, split_ms, plain_ms);
     cache[path_key(c->device, lg)] = val;
     tuner_store(c->tuner_cache, cache);
     return NS_OK;

@@ -105,6 +105,7 @@ struct ns_ctx {
         int path;
         bool cta_cache;
         int split;  // sort path: 1 split, 0 not, -1 the size rule
+        int tile;   // sort path: digit-pass tile shape (0..kSortTileShapes-1), -1 the default
     };
     std::map<int, PathChoice> path_choice;
     ns::SortScratch sc{};

@@ -65,7 +65,10 @@ struct SortScratch {
     u32 tag;             // last look-back tag issued
     int sms;
     Tracer* tr;          // the context's tracer (may be off)
+    int tile_shape;      // digit passes over 64-bit keys: 0 = 512 threads x 16 keys,
+                         // 1 = 512 x 12, 2 = 256 x 16 (kSortTileShapes)
 };
+constexpr int kSortTileShapes = 3;
 
 // Look-back tags are 16 bits; when they wrap, the status words are cleared
 // on the stream so no stale word can carry a live tag.

@@ -1051,11 +1051,24 @@ void launch_onesweep_rank(const SortIn& in, K* kout, u64* vout, u64 n, int shift
                                                                 tag, st, tr, s, nullptr);
 }
 
+// `shape` (64-bit keys without values): the tile of a digit pass, 512
+// threads x 16 keys (0, the default), 512 x 12 (1) or 256 x 16 (2).  The
+// path tuner picks one per window size.
 template <typename K, bool HAS_V, int LOAD>
 void launch_onesweep(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
                      u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s, int rank,
-                     u64* cursor = nullptr) {
-    if constexpr (!HAS_V)
+                     u64* cursor = nullptr, int shape = 0) {
+    if constexpr (!HAS_V && sizeof(K) == 8) {
+        if (shape == 1)
+            launch_onesweep_rank<K, HAS_V, LOAD, 512, 12>(in, kout, vout, n, shift, offs, status, tile_counter, tag,
+                                                          st, tr, s, rank, cursor);
+        else if (shape == 2)
+            launch_onesweep_rank<K, HAS_V, LOAD, 256, 16>(in, kout, vout, n, shift, offs, status, tile_counter, tag,
+                                                          st, tr, s, rank, cursor);
+        else
+            launch_onesweep_rank<K, HAS_V, LOAD, NS_ONESWEEP_NT, NS_ONESWEEP_ITEMS>(
+                in, kout, vout, n, shift, offs, status, tile_counter, tag, st, tr, s, rank, cursor);
+    } else if constexpr (!HAS_V)
         launch_onesweep_rank<K, HAS_V, LOAD, NS_ONESWEEP_NT, NS_ONESWEEP_ITEMS>(
             in, kout, vout, n, shift, offs, status, tile_counter, tag, st, tr, s, rank, cursor);
     else
@@ -1135,7 +1148,7 @@ int radix_sort_t(const SortIn& in, K* kbuf[2], u64* vbuf[2], u64 n, int begin_bi
             launch_onesweep<K, HAS_V, LOAD>(in, kbuf[0], vbuf[0], n, shift, sc.offs, sc.status,
                                             sc.tile_counters + p, tag, st, sc.tr, s,
                                             !HAS_V && NS_UNSTABLE_FIRST ? RANK_UNSTABLE : pass_rank(0),
-                                            sc.offs + 8 * kRadix);
+                                            sc.offs + 8 * kRadix, sc.tile_shape);
         } else {
             SortIn mid{};
             mid.keys = kbuf[(p - 1) & 1];
@@ -1146,7 +1159,8 @@ int radix_sort_t(const SortIn& in, K* kbuf[2], u64* vbuf[2], u64 n, int begin_bi
             // stage with bulk copies only from 16-byte-aligned addresses
             mid.bulk = (((uintptr_t)kbuf[(p - 1) & 1] | (uintptr_t)vbuf[(p - 1) & 1]) & 15) == 0;
             launch_onesweep<K, HAS_V, LOAD_KEYS>(mid, kbuf[p & 1], vbuf[p & 1], n, shift, sc.offs + p * kRadix,
-                                                 sc.status, sc.tile_counters + p, tag, st, sc.tr, s, pass_rank(p));
+                                                 sc.status, sc.tile_counters + p, tag, st, sc.tr, s, pass_rank(p),
+                                                 nullptr, sc.tile_shape);
         }
     }
     return (passes - 1) & 1;

@@ -123,9 +123,23 @@ def test_path_tune_records_split_choice(tmp_path):
     s, d = W.zipf_window(1 << 22, 1.2, 1 << 20, 3)
     ns.path_tune(ctx, to_dev(s), to_dev(d))
     text = open(cache).read()
-    assert '"sort_split"' in text and '"sort_split_ms"' in text
+    assert '"sort_split"' in text and '"sort_split_ms"' in text and '"sort_tile"' in text
     # a context on the same cache takes the recorded choices, and still builds exactly
     ctx2 = ns.Context(0, tuner_cache=cache)
     check(ctx2, s, d)
     ctx.close()
     ctx2.close()
+
+
+@pytest.mark.parametrize("tile", ["512x16", "512x12", "256x16"])
+@pytest.mark.parametrize("split", ["on", "off"])
+def test_every_tile_shape_matches_oracle(tile, split):
+    """Each digit-pass tile the path tuner can choose (threads x keys per
+    thread), with and without the split, on a ragged skewed window and on a
+    window of all-distinct links."""
+    ctx = ns.Context(0, path="sort", sort_split=split, sort_tile=tile)
+    s, d = W.zipf_window((1 << 20) + 77, 1.2, 1 << 16, 31)
+    check(ctx, s, d)
+    s, d = gen.uniform_pairs(300007, 32, 12)
+    check(ctx, s, d)
+    ctx.close()
