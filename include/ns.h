@@ -379,6 +379,25 @@ ns_status ns_batch_run(ns_ctx* ctx, ns_batch* batch, const uint32_t* d_src, cons
                        const uint64_t* h_offsets, uint64_t windows, ns_stats* d_window_stats,
                        ns_matrix* acc, ns_stream_t stream);
 
+/* ns_batch_run with the window offsets in device memory: d_offsets holds
+ * windows + 1 uint64 entries (the same meaning as h_offsets).  The plan --
+ * each window's table capacity, tile and table offsets -- is computed on the
+ * device, so a CUDA graph captured around this call serves any new layout of
+ * the same number of windows written into d_offsets before a replay,
+ * without re-capture.  All windows of a run must fit the arena at once (one
+ * chunk) and total at most the plan's max_packets; offsets that break this,
+ * do not start at 0 or decrease make the run do nothing and set an error
+ * flag that ns_batch_sync reports as NS_ERR_CAPACITY.  If acc is given it
+ * must have room for max_packets more links (it is grown outside a capture
+ * if needed).  Asynchronous; allocates nothing once acc has its room. */
+ns_status ns_batch_run_device(ns_ctx* ctx, ns_batch* batch, const uint32_t* d_src, const uint32_t* d_dst,
+                              const uint64_t* d_offsets, uint64_t windows, ns_stats* d_window_stats,
+                              ns_matrix* acc, ns_stream_t stream);
+
+/* Waits for the stream and returns NS_ERR_CAPACITY if the batch's last
+ * ns_batch_run_device refused its offsets (see there), else NS_OK. */
+ns_status ns_batch_sync(ns_batch* batch, ns_stream_t stream);
+
 /* Autotuner: times ns_batch_run on this batch for every combination of tile
  * size {1024..16384}, CTAs per SM {4, 8, 16} and load bound {0.5, 0.7},
  * keeps the fastest in the plan, returns it in *chosen (may be NULL) and

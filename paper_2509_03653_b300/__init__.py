@@ -24,7 +24,7 @@ __all__ = [
     "window_ingest_stats", "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
     "matrix_clear", "sync", "PATHS", "SORT_TILES", "path_tune", "path_resolve", "sort_split_info", "matrix_nodes", "NODES", "anonymize", "Slider",
     "slider_push", "window_stats_static", "STATIC_MAX_PACKETS",
-    "trace_enable", "trace_read", "Batch", "batch_run", "batch_tune", "matrix_reserve_ex",
+    "trace_enable", "trace_read", "Batch", "batch_run", "batch_run_device", "batch_sync", "batch_tune", "matrix_reserve_ex",
     "owner", "matrix_partition", "matrix_add_entries", "Server", "stream_submit", "stream_poll", "stream_wait", "diag_random_atomics", "matrix_save", "matrix_load",
 ]
 
@@ -469,6 +469,28 @@ def batch_run(ctx: Context, batch: Batch, src: torch.Tensor, dst: torch.Tensor, 
                               ctypes.c_void_p(out.data_ptr()), acc.live() if acc is not None else None,
                               _stream(stream)), "ns_batch_run")
     return off
+
+
+def batch_run_device(ctx: Context, batch: Batch, src: torch.Tensor, dst: torch.Tensor, offsets: torch.Tensor,
+                     out: torch.Tensor, acc: Matrix | None = None, stream=None):
+    """ns_batch_run with the windows + 1 offsets in a device tensor (int64
+    holding uint64), planned on the device (ns_batch_run_device); a graph
+    captured around it replays any layout later written into `offsets`."""
+    W = offsets.numel() - 1
+    if W < 0 or not offsets.is_cuda or offsets.element_size() != 8 or not offsets.is_contiguous():
+        raise ValueError("offsets must be a contiguous 64-bit CUDA tensor of windows + 1 entries")
+    if out.element_size() != 8 or out.numel() < 9 * W or not out.is_contiguous():
+        raise ValueError("out must be a contiguous 64-bit tensor of >= 9 * windows elements")
+    check(ctx._L.ns_batch_run_device(ctx.handle, batch.handle, _column(src, "src"), _column(dst, "dst"),
+                                     ctypes.c_void_p(offsets.data_ptr()), W, ctypes.c_void_p(out.data_ptr()),
+                                     acc.live() if acc is not None else None, _stream(stream)),
+          "ns_batch_run_device")
+
+
+def batch_sync(batch: Batch, stream=None):
+    """Raises NS_ERR_CAPACITY if the batch's last device-planned run refused
+    its offsets (ns_batch_sync; blocking)."""
+    check(batch._L.ns_batch_sync(batch.handle, _stream(stream)), "ns_batch_sync")
 
 
 def batch_tune(ctx: Context, batch: Batch, src: torch.Tensor, dst: torch.Tensor, offsets, stream=None) -> dict:

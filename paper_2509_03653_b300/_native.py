@@ -88,6 +88,8 @@ SIGNATURES = {
     "ns_batch_set_params": (ST, [P, ctypes.POINTER(NsBatchParams)]),
     "ns_batch_run": (ST, [P, P, P, P, ctypes.POINTER(U64), U64, P, P, P]),
     "ns_batch_tune": (ST, [P, P, P, P, ctypes.POINTER(U64), U64, P, P, ctypes.POINTER(NsBatchParams)]),
+    "ns_batch_run_device": (ST, [P, P, P, P, P, U64, P, P, P]),
+    "ns_batch_sync": (ST, [P, P]),
     "ns_server_create": (ST, [P, P, ctypes.POINTER(P)]),
     "ns_server_destroy": (None, [P]),
     "ns_stream_submit": (ST, [P, P, P, U64, U64, ctypes.POINTER(U64)]),

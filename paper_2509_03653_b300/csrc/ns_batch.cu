@@ -35,6 +35,7 @@ struct ns_batch {
     uint64_t arena_slots = 0;  // slots per table kind
     Buf wstats;                // DevStats x max_windows
     Buf counter;               // tile counters, one per chunk
+    Buf dscal;                 // device-planned runs: total tiles, total slots, error flag
     cudaStream_t last_stream = nullptr;  // the stream the batch last ran on
     uint64_t max_chunks = 0;
 };
@@ -127,6 +128,103 @@ ns_status plan(ns_batch* b, const uint64_t* h_off, u64 W, std::vector<Chunk>& ch
     return NS_OK;
 }
 
+// ---- device-side planning (ns_batch_run_device) ------------------------------
+
+__device__ __forceinline__ u64 window_cap_dev(u64 n, double max_load) {
+    const double want = ceil((double)n / max_load);
+    u64 x = (u64)want > 64 ? (u64)want : 64;
+    u64 p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// One CTA: the same plan as the host's for one chunk, from offsets in device
+// memory -- each window's table capacity, its tile and table offsets
+// (exclusive scans over the windows), and the totals.  If the offsets do not
+// start at 0, decrease, exceed max_packets, or the tables do not fit the
+// arena in one chunk, the plan is empty and the error flag is set.
+constexpr int kPlanThreads = 1024;
+__global__ void __launch_bounds__(kPlanThreads) k_batch_plan(const u64* __restrict__ off, u64 W, u32 T, double max_load,
+                                                            u64 arena_slots, u64 max_packets, u64* __restrict__ win_off,
+                                                            u64* __restrict__ tile_off, u64* __restrict__ tab_off,
+                                                            u64* __restrict__ tab_cap, u64* __restrict__ scal) {
+    __shared__ u64 wt[kPlanThreads / 32], wsl[kPlanThreads / 32];
+    __shared__ u64 carry_t, carry_s;
+    __shared__ u32 bad;
+    const u32 lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        carry_t = carry_s = 0;
+        bad = off[0] != 0;
+    }
+    __syncthreads();
+    for (u64 base = 0; base < W; base += kPlanThreads) {
+        const u64 w = base + threadIdx.x;
+        u64 tiles = 0, slots = 0, cap = 0;
+        if (w < W) {
+            const u64 a = off[w], b = off[w + 1];
+            if (b < a) atomicOr(&bad, 1u);
+            const u64 n = b >= a ? b - a : 0;
+            cap = window_cap_dev(n, max_load);
+            tiles = (n + T - 1) / T;
+            slots = cap + 1;
+        }
+        // inclusive scans within the warp, then over the warps
+        u64 it = tiles, is = slots;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u64 yt = __shfl_up_sync(0xFFFFFFFFu, it, o), ys = __shfl_up_sync(0xFFFFFFFFu, is, o);
+            if (lane >= (u32)o) {
+                it += yt;
+                is += ys;
+            }
+        }
+        if (lane == 31) {
+            wt[wi] = it;
+            wsl[wi] = is;
+        }
+        __syncthreads();
+        u64 bt = carry_t, bs = carry_s;
+        for (u32 q = 0; q < wi; ++q) {
+            bt += wt[q];
+            bs += wsl[q];
+        }
+        if (w < W) {
+            win_off[w] = off[w];
+            tile_off[w] = bt + it - tiles;
+            tab_off[w] = bs + is - slots;
+            tab_cap[w] = cap;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < kPlanThreads / 32; ++q) {
+                carry_t += wt[q];
+                carry_s += wsl[q];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const u64 total = off[W];
+        win_off[W] = total;
+        tile_off[W] = carry_t;
+        const bool ok = !bad && total <= max_packets && carry_s <= arena_slots;
+        scal[0] = ok ? carry_t : 0;  // total tiles (none when the plan is refused)
+        scal[1] = ok ? carry_s : 0;  // arena slots in use
+        scal[2] = ok ? 0 : 1;        // error flag
+    }
+}
+
+// Clears the arena's slots [0, scal[1]) in all three tables.
+__global__ void k_arena_clear(LinkSlot* links, NodeSlot* rows, NodeSlot* cols, const u64* __restrict__ scal) {
+    const u64 n = scal[1];
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+        reinterpret_cast<uint4*>(links)[i] = z;
+        reinterpret_cast<uint4*>(rows)[i] = z;
+        reinterpret_cast<uint4*>(cols)[i] = z;
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -160,6 +258,11 @@ ns_status ns_batch_create(ns_ctx* c, uint64_t max_windows, uint64_t max_packets,
     if (st == NS_OK) st = buf_reserve(b->cols, b->arena_slots * sizeof(NodeSlot));
     if (st == NS_OK) st = buf_reserve(b->wstats, max_windows * sizeof(DevStats));
     if (st == NS_OK) st = buf_reserve(b->counter, max_windows * sizeof(u32));
+    if (st == NS_OK) st = buf_reserve(b->dscal, 4 * sizeof(u64));
+    if (st == NS_OK && cudaMemsetAsync(b->dscal.p, 0, 4 * sizeof(u64), nullptr) != cudaSuccess) {
+        cudaGetLastError();
+        st = set_fail(NS_ERR_CUDA, "ns_batch_create: clearing the device scalars failed");
+    }
     if (st == NS_OK && cudaMallocHost((void**)&b->h_meta, 4 * (max_windows + 1) * sizeof(u64)) != cudaSuccess) {
         cudaGetLastError();
         st = set_fail(NS_ERR_OOM, "ns_batch_create: pinned staging allocation failed");
@@ -189,6 +292,7 @@ void ns_batch_free(ns_batch* b) {
     buf_free_on(b->cols, s);
     buf_free_on(b->wstats, s);
     buf_free_on(b->counter, s);
+    buf_free_on(b->dscal, s);
     if (b->h_meta) {
         if (cudaStreamSynchronize(s) != cudaSuccess) {
             cudaGetLastError();
@@ -285,6 +389,92 @@ ns_status ns_batch_run(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uint
     }
     if (acc) acc->bound += total;
     return check_launch();
+}
+
+ns_status ns_batch_run_device(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uint32_t* d_dst,
+                              const uint64_t* d_offsets, uint64_t windows, ns_stats* d_window_stats, ns_matrix* acc,
+                              ns_stream_t stream) {
+    if (!c || !b || !d_offsets || !d_window_stats)
+        return set_fail(NS_ERR_INVALID, "ns_batch_run_device: NULL argument");
+    CallScope scope(c, (cudaStream_t)stream);
+    b->last_stream = (cudaStream_t)stream;
+    touch(acc, (cudaStream_t)stream);
+    if (b->ctx != c || (acc && acc->ctx != c)) return set_fail(NS_ERR_INVALID, "ns_batch_run_device: foreign object");
+    if (windows > b->max_windows)
+        return set_fail(NS_ERR_INVALID, "ns_batch_run_device: more windows than the batch plan");
+    if (windows == 0) return NS_OK;
+    if (b->max_packets > 0 && (!d_src || !d_dst)) return set_fail(NS_ERR_INVALID, "ns_batch_run_device: NULL input");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (acc) {
+        // room for the largest batch the plan allows (the host does not see the offsets)
+        const ns_status st = to_hash(acc, b->max_packets, s);
+        if (st != NS_OK) return st;
+    }
+    const u64 M1 = b->max_windows + 1;
+    u64* dm = (u64*)b->meta.p;
+    u64* scal = (u64*)b->dscal.p;
+    if (cudaMemsetAsync(b->wstats.p, 0, windows * sizeof(DevStats), s) != cudaSuccess ||
+        cudaMemsetAsync(b->counter.p, 0, sizeof(u32), s) != cudaSuccess) {
+        cudaGetLastError();
+        return set_fail(NS_ERR_CUDA, "ns_batch_run_device: clearing failed");
+    }
+    {
+        TraceScope ts(&c->tracer, "k_batch_plan", s);
+        k_batch_plan<<<1, kPlanThreads, 0, s>>>((const u64*)d_offsets, windows, b->params.tile_packets,
+                                                b->params.max_load, b->arena_slots, b->max_packets, dm, dm + M1,
+                                                dm + 2 * M1, dm + 3 * M1, scal);
+    }
+    {
+        TraceScope ts(&c->tracer, "k_arena_clear", s);
+        k_arena_clear<<<c->sms * 8, 256, 0, s>>>((LinkSlot*)b->links.p, (NodeSlot*)b->rows.p, (NodeSlot*)b->cols.p,
+                                                 scal);
+    }
+    BatchDev B;
+    B.src = d_src;
+    B.dst = d_dst;
+    B.win_off = dm;
+    B.tile_off = dm + M1;
+    B.tab_off = dm + 2 * M1;
+    B.tab_cap = dm + 3 * M1;
+    B.links = (LinkSlot*)b->links.p;
+    B.rows = (NodeSlot*)b->rows.p;
+    B.cols = (NodeSlot*)b->cols.p;
+    B.wstats = (DevStats*)b->wstats.p;
+    B.W = windows;
+    B.T = b->params.tile_packets;
+    const u64 tile_bound = b->max_packets / B.T + windows + 1;
+    {
+        TraceScope ts(&c->tracer, "k_batch_insert", s);
+        launch_batch_insert(B, (u32*)b->counter.p, tile_bound, c->sms, (int)b->params.ctas_per_sm,
+                            b->params.cta_cache != 0, s, scal);
+    }
+    if (acc) {
+        TraceScope ts(&c->tracer, "k_insert_slots", s);
+        launch_insert_slots((const LinkSlot*)b->links.p, b->arena_slots - 1, hash_view(acc), c->sms, s,
+                            b->params.cta_cache != 0, scal + 1);
+    }
+    {
+        TraceScope ts(&c->tracer, "k_batch_stats_out", s);
+        launch_batch_stats_out((const DevStats*)b->wstats.p, windows, (u64*)d_window_stats, c->sms, s);
+    }
+    if (acc) acc->bound += b->max_packets;
+    return check_launch();
+}
+
+ns_status ns_batch_sync(ns_batch* b, ns_stream_t stream) {
+    if (!b) return set_fail(NS_ERR_INVALID, "ns_batch_sync: NULL batch");
+    DeviceGuard device_guard(b->device);
+    u64 flag = 0;
+    if (cudaMemcpyAsync(&flag, (const u64*)b->dscal.p + 2, sizeof(u64), cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return set_fail(NS_ERR_CUDA, "ns_batch_sync: the batch's work failed");
+    }
+    if (flag)
+        return set_fail(NS_ERR_CAPACITY, "ns_batch_run_device: offsets that do not start at 0 or decrease, more "
+                                         "packets than the plan, or tables that do not fit the arena at once");
+    return NS_OK;
 }
 
 ns_status ns_batch_tune(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uint32_t* d_dst,

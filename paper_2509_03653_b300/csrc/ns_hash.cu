@@ -480,14 +480,17 @@ __global__ void __launch_bounds__(kInsertThreads) k_insert_packets(const u32* __
 // slot `cap` holds key 0).  Keys are unique, so no merging is needed.
 template <bool CACHE>
 __global__ void __launch_bounds__(kInsertThreads) k_insert_slots(const LinkSlot* __restrict__ in,
-                                                                 u64 in_cap, HashView M) {
+                                                                 u64 in_cap, HashView M,
+                                                                 const u64* __restrict__ total_dev) {
     __shared__ BlockStats bs;
     extern __shared__ __align__(16) unsigned char cache_smem[];  // sized sizeof(CtaCache) when CACHE
     CtaCache* C = CACHE ? reinterpret_cast<CtaCache*>(cache_smem) : nullptr;
     block_stats_init(bs);
     if constexpr (CACHE) cache_clear(*C);
     __syncthreads();
-    const u64 total = in_cap + 1;
+    // slots [0, total): the table's cap + 1, or a count on the device (an
+    // arena of tables whose extra slots hold key 0 in their key fields)
+    const u64 total = total_dev ? *total_dev : in_cap + 1;
     const u64 stride = (u64)gridDim.x * blockDim.x;
     const u64 warp_base = ((u64)blockIdx.x * blockDim.x) + (threadIdx.x & ~31u);
     for (u64 b = warp_base; b < total; b += stride) {
@@ -496,7 +499,7 @@ __global__ void __launch_bounds__(kInsertThreads) k_insert_slots(const LinkSlot*
         if (i < total) {
             LinkSlot s = in[i];
             c = s.count;
-            key = (i == in_cap) ? 0ull : s.key;
+            key = (i == total - 1) ? 0ull : s.key;
         }
         insert_item<CACHE, false>(M, c > 0, key, c, false, bs, C);
     }
@@ -579,7 +582,9 @@ __global__ void k_stats_out(const DevStats* __restrict__ st, u64* __restrict__ o
 // that window's own tables, carved from one arena at per-window offsets.
 // Each tile flushes its block totals into its window's statistics record.
 template <bool CACHE>
-__global__ void __launch_bounds__(kInsertThreads) k_batch_insert(BatchDev B, u32* tile_counter, u64 total_tiles) {
+__global__ void __launch_bounds__(kInsertThreads) k_batch_insert(BatchDev B, u32* tile_counter, u64 total_tiles_arg,
+                                                                 const u64* __restrict__ total_dev) {
+    const u64 total_tiles = total_dev ? *total_dev : total_tiles_arg;
     __shared__ BlockStats bs;
     __shared__ u64 s_tile, s_w, s_p0, s_p1;
     extern __shared__ __align__(16) unsigned char cache_smem[];  // sized sizeof(CtaCache) when CACHE
@@ -696,10 +701,10 @@ void launch_insert_packets_snapshot(const u32* src, const u32* dst, u64 n, const
 }
 
 void launch_insert_slots(const LinkSlot* in, u64 in_cap, const HashView& M, int sms,
-                         cudaStream_t s, bool cache) {
+                         cudaStream_t s, bool cache, const u64* total_dev) {
     const int grid = grid_for(in_cap + 1, kInsertThreads, sms, 8);
-    if (cache) k_insert_slots<true><<<grid, kInsertThreads, sizeof(CtaCache), s>>>(in, in_cap, M);
-    else k_insert_slots<false><<<grid, kInsertThreads, 0, s>>>(in, in_cap, M);
+    if (cache) k_insert_slots<true><<<grid, kInsertThreads, sizeof(CtaCache), s>>>(in, in_cap, M, total_dev);
+    else k_insert_slots<false><<<grid, kInsertThreads, 0, s>>>(in, in_cap, M, total_dev);
 }
 
 void launch_insert_list(const u64* keys, const u64* counts, u64 n_bound,
@@ -716,11 +721,13 @@ void launch_compact_links(const LinkSlot* in, u64 cap, u64* out_keys, u64* out_c
 }
 
 void launch_batch_insert(const BatchDev& B, u32* tile_counter, u64 total_tiles, int sms, int per_sm,
-                         bool cache, cudaStream_t s) {
+                         bool cache, cudaStream_t s, const u64* total_dev) {
     if (total_tiles == 0) return;
     const u64 grid = std::min<u64>(total_tiles, (u64)sms * (u64)per_sm);
-    if (cache) k_batch_insert<true><<<(unsigned)grid, kInsertThreads, sizeof(CtaCache), s>>>(B, tile_counter, total_tiles);
-    else k_batch_insert<false><<<(unsigned)grid, kInsertThreads, 0, s>>>(B, tile_counter, total_tiles);
+    if (cache)
+        k_batch_insert<true><<<(unsigned)grid, kInsertThreads, sizeof(CtaCache), s>>>(B, tile_counter, total_tiles,
+                                                                                      total_dev);
+    else k_batch_insert<false><<<(unsigned)grid, kInsertThreads, 0, s>>>(B, tile_counter, total_tiles, total_dev);
 }
 
 void launch_batch_stats_out(const DevStats* wstats, u64 W, u64* out, int sms, cudaStream_t s) {

@@ -120,15 +120,19 @@ void launch_insert_packets_snapshot(const u32* src, const u32* dst, u64 n, const
                                     u64* out, int sms, bool cache, cudaStream_t s);
 // `cache` (default on): stage rows and columns that repeat across the
 // inserted links in per-CTA shared-memory tables (pays under skew)
+// total_dev (optional): the number of slots to read, on the device (then
+// in_cap + 1 is only an upper bound that sizes the grid)
 void launch_insert_slots(const LinkSlot* in, u64 in_cap, const HashView& M, int sms,
-                         cudaStream_t s, bool cache = true);
+                         cudaStream_t s, bool cache = true, const u64* total_dev = nullptr);
 void launch_insert_list(const u64* keys, const u64* counts, u64 n_bound,
                         const u64* n_dev, const HashView& M, int sms, cudaStream_t s);
 void launch_compact_links(const LinkSlot* in, u64 cap, u64* out_keys, u64* out_counts,
                           u64* out_n, u64 out_cap, DevStats* st, int sms, cudaStream_t s);
 void launch_stats_out(const DevStats* st, u64* out, cudaStream_t s);
+// total_dev (optional): the tile count on the device (total_tiles is then an
+// upper bound that sizes the grid)
 void launch_batch_insert(const BatchDev& B, u32* tile_counter, u64 total_tiles, int sms, int per_sm,
-                         bool cache, cudaStream_t s);
+                         bool cache, cudaStream_t s, const u64* total_dev = nullptr);
 void launch_batch_stats_out(const DevStats* wstats, u64 W, u64* out, int sms, cudaStream_t s);
 
 // sort path (ns_sort.cu).  Each radix sort returns the index of kbuf/vbuf

@@ -157,3 +157,55 @@ def test_batch_in_cuda_graph():
         assert rows_of(out, 5) == per
         assert ns.network_stats(ctx, acc) == oracle.stats(*want_acc)
     del keep
+
+
+def test_device_offsets_new_layout_without_recapture():
+    """ns_batch_run_device in a captured CUDA graph: one capture, replayed
+    with two different window layouts written into the device offsets (the
+    same packets cut differently), each equal to the oracle per window and
+    in the running aggregate; then offsets past the plan are refused."""
+    src, dst, off_a = make_batch([9000, 1, 0, 25000, 4097, 12000, 333], seed0=70)
+    total = int(off_a[-1])
+    cuts = np.sort(np.random.default_rng(4).integers(0, total, size=6).astype(np.uint64))
+    off_b = np.concatenate([[0], cuts, [total]]).astype(np.uint64)  # 7 windows again, other sizes
+    Wn = off_a.size - 1
+    ctx = ns.Context(0, path="hash")
+    b = ns.Batch(ctx, Wn, total)
+    acc = ns.Matrix(ctx)
+    ns.matrix_reserve(acc, total)
+    ds, dd = to_dev(src), to_dev(dst)
+    d_off = torch.from_numpy(off_a.view(np.int64).copy()).cuda()
+    out = torch.full((Wn * 9,), -1, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ns.matrix_clear(acc)
+        ns.batch_run_device(ctx, b, ds, dd, d_off, out, acc)  # warm-up outside capture
+    torch.cuda.synchronize()
+    ns.batch_sync(b)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ns.matrix_clear(acc)
+        ns.batch_run_device(ctx, b, ds, dd, d_off, out, acc)
+    for off in (off_a, off_b, off_a):
+        d_off.copy_(torch.from_numpy(off.view(np.int64).copy()))
+        out.fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        ns.batch_sync(b)
+        per, want_acc = expected(src, dst, off)
+        assert rows_of(out, Wn) == per
+        assert ns.network_stats(ctx, acc) == oracle.stats(*want_acc)
+        assert_matrix_equal(acc, *want_acc)
+    # more packets than the plan allows: the run does nothing and reports it
+    bad = off_a.copy()
+    bad[-1] = total + 1
+    d_off.copy_(torch.from_numpy(bad.view(np.int64).copy()))
+    g.replay()
+    torch.cuda.synchronize()
+    with pytest.raises(ns.NsError) as e:
+        ns.batch_sync(b)
+    assert e.value.name == "NS_ERR_CAPACITY"
+    del g
+    b.free()
+    acc.free()
+    ctx.close()
