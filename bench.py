@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--paths", default="sort,hash", help="oneshot: aggregation paths to run (first = value)")
     ap.add_argument("--sort-split", default="auto", choices=["auto", "on", "off"],
                     help="headline/oneshot: the sort path's hot-key split")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="headline/oneshot: skip ns_path_tune before timing the sort path")
     ap.add_argument("--windows", type=int, default=WINDOWS, help="stream: windows (512 = the full workload)")
     ap.add_argument("--hash-load", type=float, default=0.25,
                     help="stream: load bound of the accumulated matrix's hash tables")
@@ -333,8 +335,21 @@ def c3_run(args, rank, world, local, clocks, N):
     out = torch.zeros(16, dtype=torch.int64, device=dev)
     peak, peak_src = peak_hbm()
     res, stats_by_path = {}, {}
+    tuned = None
     for path in args.paths.split(","):
-        ctx = ns.Context(local, path=path, sort_split=args.sort_split)
+        tuner_file = None
+        if path == "sort" and not args.no_tune:
+            import tempfile
+            tuner_file = os.path.join(tempfile.mkdtemp(prefix="ns_tune_"), "tuner.json")
+        ctx = ns.Context(local, path=path, sort_split=args.sort_split, tuner_cache=tuner_file)
+        if tuner_file:
+            # the path tuner on this input: the timed builds below take its
+            # split and tile choices for this size
+            tt = time.time()
+            ns.path_tune(ctx, d_src, d_dst)
+            entries = json.load(open(tuner_file))
+            tuned = {"seconds": round(time.time() - tt, 1), **{k.split("|", 1)[1]: json.loads(v) if isinstance(v, str)
+                                                               else v for k, v in entries.items()}}
         M = ns.Matrix(ctx)
         for _ in range(max(args.warmup, 3)):
             ns.window_build(ctx, d_src, d_dst, M)
@@ -419,7 +434,7 @@ def c3_run(args, rank, world, local, clocks, N):
         M.free()
         ctx.close()
         torch.cuda.empty_cache()
-    return {"res": res, "stats": stats_by_path[first], "paths_agree": same, "gen_s": gen_s, "e2e": e2e,
+    return {"res": res, "stats": stats_by_path[first], "paths_agree": same, "gen_s": gen_s, "e2e": e2e, "tuned": tuned,
             "h_src": h_src, "h_dst": h_dst, "peak": peak, "peak_src": peak_src}
 
 
@@ -465,7 +480,7 @@ def run_headline(args, rank, world, local, oneshot_only=False):
         },
         "clocks": b["clocks"],
         "gpu_launches": b["launches_per_build"] * b["steps"],
-        "path": first, "paths": res, "paths_agree": r["paths_agree"], "stats": r["stats"],
+        "path": first, "paths": res, "paths_agree": r["paths_agree"], "stats": r["stats"], "path_tuner": r["tuned"],
         "generator_s": round(r["gen_s"], 1),
     }
     if r["e2e"]:

@@ -124,18 +124,30 @@ __device__ __forceinline__ u32 fingerprint(u64 key) { return fingerprint_of_mix(
 
 // hot_find with the fingerprint filter (shared-memory tables of the split
 // kernel): two 4-byte loads for almost every cold key, plus one 8-byte load
-// per fingerprint match.
+// per fingerprint match.  A byte of a bucket word equal to the fingerprint
+// is found with the zero-byte test on (word ^ fingerprint x 4): bit 8w+7 of
+// (v - 0x01010101) & ~v & 0x80808080 is set for every zero byte w of v (and
+// possibly for a byte above a zero byte, a false candidate the key compare
+// rejects).  A false candidate can be a free slot, whose key field holds
+// kEmpty, so the key kEmpty (never hot) is refused before any compare.
+__device__ __forceinline__ u32 zero_bytes(u32 v) { return (v - 0x01010101u) & ~v & 0x80808080u; }
+
 __device__ __forceinline__ int hot_find_fp(const u32* fpw, const u64* table, u64 key) {
-    if (key == kEmpty) return -1;
     const u32 x = key_mix(key);
     const u32 b1 = x >> (32 - kBucketBits), b2 = bucket2_of_mix(x, b1);
     const u32 f4 = fingerprint_of_mix(x) * 0x01010101u;
-    const u32 m1 = __vcmpeq4(fpw[b1], f4), m2 = __vcmpeq4(fpw[b2], f4);  // 0xFF per matching byte
-    u32 cand = (m1 & 0x01010101u) | ((m2 & 0x01010101u) << 1);  // bit 8w: slot w of b1, bit 8w+1: of b2
+    // bit 8w+7: slot w of b1 may match; bit 8w+6: slot w of b2 may match
+    u32 cand = zero_bytes(fpw[b1] ^ f4) | (zero_bytes(fpw[b2] ^ f4) >> 1);
+    if (cand == 0 || key == kEmpty) return -1;
+    // almost always one candidate: check it without a loop
+    u32 bit = __ffs(cand) - 1;
+    u32 slot = 4 * ((bit & 1) ? b1 : b2) + (bit >> 3);
+    if (table[slot] == key) return (int)slot;
+    cand &= cand - 1;
     while (cand) {
-        const u32 bit = __ffs(cand) - 1;
+        bit = __ffs(cand) - 1;
         cand &= cand - 1;
-        const u32 slot = 4 * ((bit & 1) ? b2 : b1) + (bit >> 3);
+        slot = 4 * ((bit & 1) ? b1 : b2) + (bit >> 3);
         if (table[slot] == key) return (int)slot;
     }
     return -1;
@@ -444,6 +456,10 @@ __device__ __forceinline__ u64 count_below(const u64* a, u64 len, u64 key) {
     return lo;
 }
 
+// Each warp takes kMergeRounds x 32 consecutive elements at a time and
+// issues all their loads before any search, so that HBM latency is paid
+// once per group rather than once per element.
+constexpr int kMergeRounds = 4;
 __global__ void __launch_bounds__(kMergeThreads) k_hot_merge(const u64* __restrict__ heads, const u64* __restrict__ pos,
                                                              const SplitDev* sd, u64* __restrict__ keys_out,
                                                              u64* __restrict__ counts_out, DevStats* st) {
@@ -455,41 +471,39 @@ __global__ void __launch_bounds__(kMergeThreads) k_hot_merge(const u64* __restri
     if (threadIdx.x == 0) bmax = 0;
     __syncthreads();
     u64 mx = 0, hot_sum = 0;
-    // a warp takes 32 consecutive elements at a time (warp-uniform loop)
-    const u64 warp0 = ((u64)blockIdx.x * kMergeThreads + threadIdx.x) & ~31ull;
-    const u64 wstride = (u64)gridDim.x * kMergeThreads;
+    const u64 group = 32ull * kMergeRounds;
+    const u64 warp0 = (((u64)blockIdx.x * kMergeThreads + threadIdx.x) >> 5) * group;
+    const u64 wstride = ((u64)gridDim.x * kMergeThreads >> 5) * group;
     for (u64 base = warp0; base < total; base += wstride) {
-        const u64 i = base + lane;
-        if (base < RC) {
-            // cold runs of this warp: ascending keys heads[base .. base + last]
-            const u32 last = (u32)min((u64)31, RC - 1 - base);
-            const u64 key = i < RC ? heads[i] : 0;
-            const u64 kfirst = __shfl_sync(FULL, key, 0), klast = __shfl_sync(FULL, key, last);
-            // hot keys below the first and below the last run (two searches
-            // on two lanes); only the hot keys between them can fall in
-            // between the warp's runs, usually none
-            u64 b = 0;
-            if (lane < 2) b = count_below(hot, H, lane == 0 ? kfirst : klast);
-            const u64 lo = __shfl_sync(FULL, b, 0), hi = __shfl_sync(FULL, b, 1);
+        u64 key[kMergeRounds], c[kMergeRounds];
+#pragma unroll
+        for (int r = 0; r < kMergeRounds; ++r) {
+            const u64 i = base + (u64)r * 32 + lane;
+            key[r] = 0;
+            c[r] = 0;
             if (i < RC) {
-                u64 below = lo;
-                for (u64 j = lo; j < hi; ++j) below += hot[j] < key;
-                const u64 c = pos[i + 1] - pos[i];
-                const u64 at = i + below;
-                keys_out[at] = key;
-                counts_out[at] = c;
-                mx = c > mx ? c : mx;
+                key[r] = heads[i];
+                c[r] = pos[i + 1] - pos[i];
             }
         }
-        if (i >= RC && i < total) {
-            const u64 h = i - RC, key = hot[h];
-            const int slot = hot_find(sd->table, key);
-            const u64 c = slot >= 0 ? sd->slot_count[slot] : 0;
-            const u64 at = h + count_below(heads, RC, key);
-            keys_out[at] = key;
-            counts_out[at] = c;
-            mx = c > mx ? c : mx;
-            hot_sum += c;
+#pragma unroll
+        for (int r = 0; r < kMergeRounds; ++r) {
+            const u64 i = base + (u64)r * 32 + lane;
+            if (i < RC) {
+                const u64 at = i + count_below(hot, H, key[r]);
+                keys_out[at] = key[r];
+                counts_out[at] = c[r];
+                mx = c[r] > mx ? c[r] : mx;
+            } else if (i < total) {
+                const u64 h = i - RC, k = hot[h];
+                const int slot = hot_find(sd->table, k);
+                const u64 ch = slot >= 0 ? sd->slot_count[slot] : 0;
+                const u64 at = h + count_below(heads, RC, k);
+                keys_out[at] = k;
+                counts_out[at] = ch;
+                mx = ch > mx ? ch : mx;
+                hot_sum += ch;
+            }
         }
     }
 #pragma unroll
