@@ -9,19 +9,24 @@
 //   1. sample: 64 evenly spaced blocks of consecutive packets (2^21 packets
 //      at most) are packed into keys, sorted and cut into runs with the sort
 //      path's own kernels;
-//   2. select: the keys seen at least kMinHotSample times in the sample, the
-//      most frequent first, up to kHotMax of them, become the hot set
-//      (sorted ascending; a cuckoo table of 4 kHotMax / 3 slots is built
-//      from it, and a key that finds no slot there stays cold);
-//   3. split: one pass over all packets.  Each CTA holds the table in shared
-//      memory; a packet whose key is hot adds 1 to the CTA's count of that
-//      key, every other ("cold") key is appended to the cold-key buffer
-//      (warp-compacted, one global reservation per CTA chunk, in no
-//      particular order).  At the end each CTA adds its counts to the global
-//      per-slot counts;
+//   2. select: the keys seen most often in the sample become the hot set,
+//      in two tiers.  Tier 1: the keys seen at least kMinHotSample times,
+//      the most frequent first, up to kHotMax of them, go into a cuckoo
+//      table of 4 kHotMax / 3 slots that each CTA of the split holds in
+//      shared memory.  Tier 2 ("warm"): the next ones, seen at least
+//      kMinWarmSample times, up to kWarmMax of them, go into a larger cuckoo
+//      table in global memory (small enough to stay in L2).  A key that
+//      finds no slot in its tier stays cold.  The keys of both tables,
+//      sorted, form the hot list;
+//   3. split: one pass over all packets.  A packet whose key is in tier 1
+//      adds 1 to its CTA's count of that key; one whose key is in tier 2
+//      adds 1 to the key's global count (an L2 atomic); every other ("cold")
+//      key is appended to the cold-key buffer (warp-compacted, one global
+//      reservation per CTA chunk, in no particular order).  At the end each
+//      CTA adds its tier-1 counts to the global per-slot counts;
 //   4. the cold keys are sorted (LSD onesweep, the count read on the device)
 //      and cut into runs;
-//   5. merge: the cold runs and the hot keys (disjoint key sets, both
+//   5. merge: the cold runs and the hot list (disjoint key sets, both
 //      ascending) are merged into A's sorted nonzero list; each element's
 //      place is its own rank plus the number of keys of the other set below
 //      it.  The whole-matrix quantities come out of the same pass.
@@ -62,17 +67,46 @@ constexpr u64 kEmpty = ~0ull;  // an empty slot (never a hot key)
 constexpr int kSampleBlocks = 64;
 constexpr u64 kSampleMax = 1ull << 21;
 constexpr u32 kHotBins = 2048;      // sample run lengths, the last bin holding >= kHotBins - 1
-constexpr u32 kMinHotSample = 4;    // fewest sample occurrences of a hot key
+constexpr u32 kMinHotSample = 4;    // fewest sample occurrences of a tier-1 key
 static_assert(kSampleMax / (kHotBins - 1) < (u64)kHotMax, "the top bin alone never exceeds the hot set");
+
+// Tier 2: kWarmBuckets buckets of kWays slots in global memory, at most
+// kWarmMax keys (load <= 5/8, placed without evictions).
+#ifndef NS_WARM_BUCKETS
+#define NS_WARM_BUCKETS 16384
+#endif
+constexpr int kWarmBuckets = NS_WARM_BUCKETS;  // a power of two, 0 turns tier 2 off
+constexpr int kWarmBits = kWarmBuckets == 0 ? 0 : kWarmBuckets == 8192 ? 13 : kWarmBuckets == 16384 ? 14 : -1;
+static_assert(kWarmBits >= 0, "kWarmBuckets: 0, 8192 or 16384");
+constexpr int kWarmSlots = kWarmBuckets * kWays;
+constexpr int kWarmMax = kWarmSlots / 8 * 5;
+constexpr u32 kMinWarmSample = 2;   // fewest sample occurrences of a tier-2 key
+constexpr int kListMax = kHotMax + kWarmMax;
+// the hot list is sorted in the key buffers, which hold the window's
+// packets, and the split runs from 2^16 packets up
+static_assert(kListMax <= (1 << 16), "the hot list fits the smallest split window");
+constexpr int kArr = kWarmSlots > 0 ? kWarmSlots : 1;  // array extents of an absent tier 2
+constexpr int kWarmArr = kWarmMax > 0 ? kWarmMax : 1;
+constexpr int kIndexStride = 8;     // the merge's shared-memory index holds every 8th hot-list key
+constexpr int kIndexMax = (kListMax + kIndexStride - 1) / kIndexStride;
 
 // Device-side state of one split (one allocation per context).
 struct SplitDev {
-    u64 table[kHotSlots];       // slot -> hot key (kEmpty = free); bucket b = slots [4b, 4b + 4)
+    u64 table[kHotSlots];       // tier-1 slot -> key (kEmpty = free); bucket b = slots [4b, 4b + 4)
     u64 slot_count[kHotSlots];  // packets of the slot's key
-    u64 hot[kHotMax];           // hot keys ascending (those in the table)
+    u64 hot[kHotMax];           // tier-1 candidates, any order
+    u64 table2[kArr];           // tier-2 slot -> key (kEmpty = free)
+    u64 count2[kArr];           // packets of the tier-2 slot's key
+    u32 fpw2[kWarmBuckets > 0 ? kWarmBuckets : 1];  // tier-2 fingerprints, one word per bucket
+    u64 warm[kWarmArr];         // tier-2 candidates, any order
+    u64 list[kListMax];         // the hot list: the keys of both tables, ascending after the sort
     u32 hist[kHotBins];         // sample keys by run length
-    u64 H;                      // hot keys
-    u64 thresh;                 // least sample count of a hot key
+    u64 H1;                     // tier-1 keys (collected, then placed)
+    u64 W;                      // tier-2 candidates collected
+    u64 W2;                     // tier-2 keys placed
+    u64 H;                      // hot-list length (H1 + W2)
+    u64 thresh;                 // least sample count of a tier-1 key
+    u64 thresh2;                // least sample count of a tier-2 key
     u64 cold;                   // cold packets
     u64 R_sample;               // distinct sample keys
     u64 R_cold;                 // distinct cold keys
@@ -92,6 +126,12 @@ __device__ __forceinline__ u32 bucket2_of_mix(u32 x, u32 b1) {
     return b == b1 ? b ^ 1u : b;
 }
 __device__ __forceinline__ u32 bucket2(u64 key, u32 b1) { return bucket2_of_mix(key_mix(key), b1); }
+// The two tier-2 buckets of a key (from the same mix, other multipliers).
+__device__ __forceinline__ u32 warm_bucket1(u32 x) { return (x * 0x85EBCA6Bu) >> (32 - kWarmBits); }
+__device__ __forceinline__ u32 warm_bucket2(u32 x, u32 b1) {
+    const u32 b = (x * 0xCC9E2D51u) >> (32 - kWarmBits);
+    return b == b1 ? b ^ 1u : b;
+}
 
 // Slot of `key` in the table, or -1.  kEmpty, the mark of a free slot, is
 // never a hot key (it would otherwise match a free slot).
@@ -153,6 +193,23 @@ __device__ __forceinline__ int hot_find_fp(const u32* fpw, const u64* table, u64
     return -1;
 }
 
+// Slot of `key` in the tier-2 table, or -1: the same fingerprint filter
+// over the two tier-2 buckets, read through the read-only path.
+__device__ __forceinline__ int warm_find(const u32* __restrict__ fpw, const u64* __restrict__ table, u64 key) {
+    if (kWarmBuckets == 0 || key == kEmpty) return -1;
+    const u32 x = key_mix(key);
+    const u32 b1 = warm_bucket1(x), b2 = warm_bucket2(x, b1);
+    const u32 f4 = fingerprint_of_mix(x) * 0x01010101u;
+    u32 cand = zero_bytes(__ldg(fpw + b1) ^ f4) | (zero_bytes(__ldg(fpw + b2) ^ f4) >> 1);
+    while (cand) {
+        const u32 bit = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const u32 slot = 4 * ((bit & 1) ? b1 : b2) + (bit >> 3);
+        if (__ldg(table + slot) == key) return (int)slot;
+    }
+    return -1;
+}
+
 __device__ __forceinline__ u64 pack_key(u32 s, u32 d) { return ((u64)s << 32) | (u64)d; }
 
 // 1. The sample: packets [b * (n / 64), + blen) of each block b, packed.
@@ -166,7 +223,8 @@ __global__ void k_sample_gather(const u32* __restrict__ src, const u32* __restri
     }
 }
 
-// 2a. Sample keys by run length (only lengths >= kMinHotSample).
+// 2a. Sample keys by run length (only lengths >= the least of either tier).
+constexpr u32 kMinSample = kWarmBuckets > 0 ? kMinWarmSample : kMinHotSample;
 __global__ void __launch_bounds__(1024) k_hot_hist(const u64* __restrict__ pos, SplitDev* sd) {
     __shared__ u32 h[kHotBins];
     for (u32 i = threadIdx.x; i < kHotBins; i += blockDim.x) h[i] = 0;
@@ -174,34 +232,49 @@ __global__ void __launch_bounds__(1024) k_hot_hist(const u64* __restrict__ pos, 
     const u64 R = sd->R_sample;
     for (u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (u64)gridDim.x * blockDim.x) {
         const u64 len = pos[r + 1] - pos[r];
-        if (len >= kMinHotSample) atomicAdd(&h[len < kHotBins - 1 ? len : kHotBins - 1], 1u);
+        if (len >= kMinSample) atomicAdd(&h[len < kHotBins - 1 ? len : kHotBins - 1], 1u);
     }
     __syncthreads();
     for (u32 i = threadIdx.x; i < kHotBins; i += blockDim.x)
         if (h[i]) atomicAdd(&sd->hist[i], h[i]);
 }
 
-// 2b. The least sample count t >= kMinHotSample such that at most kHotMax
-// keys occur t or more times (none: t = 2^64 - 1).
+// 2b. Tier 1: the least sample count t1 >= kMinHotSample such that at most
+// kHotMax keys occur t1 or more times.  Tier 2 continues downwards from the
+// first count that tier 1 could not take: the least t2 >= kMinWarmSample
+// such that at most kWarmMax keys occur at least t2 and fewer than t1
+// times.  An empty tier has threshold 2^64 - 1.
 __global__ void k_hot_pick(SplitDev* sd) {
     if (threadIdx.x != 0) return;
-    u64 cum = 0, t = kEmpty;
-    for (u32 b = kHotBins - 1; b >= kMinHotSample; --b) {
+    u64 cum = 0, t1 = kEmpty;
+    u32 b = kHotBins - 1;
+    for (; b >= kMinHotSample; --b) {
         if (cum + sd->hist[b] > (u64)kHotMax) break;
         cum += sd->hist[b];
-        if (cum) t = b;
+        if (cum) t1 = b;
     }
-    sd->thresh = t;
+    u64 cum2 = 0, t2 = kEmpty;
+    for (; kWarmBuckets > 0 && b >= kMinWarmSample; --b) {
+        if (cum2 + sd->hist[b] > (u64)kWarmMax) break;
+        cum2 += sd->hist[b];
+        if (cum2) t2 = b;
+    }
+    sd->thresh = t1;
+    sd->thresh2 = t2;
 }
 
-// 2c. The hot keys, in any order.
+// 2c. The candidates of each tier, in any order.
 __global__ void k_hot_collect(const u64* __restrict__ heads, const u64* __restrict__ pos, SplitDev* sd) {
-    const u64 R = sd->R_sample, t = sd->thresh;
+    const u64 R = sd->R_sample, t1 = sd->thresh, t2 = sd->thresh2;
     for (u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (u64)gridDim.x * blockDim.x) {
-        const u64 key = heads[r];
-        if (pos[r + 1] - pos[r] >= t && key != kEmpty) {
-            const u64 i = atomicAdd(&sd->H, 1ull);
+        const u64 key = heads[r], len = pos[r + 1] - pos[r];
+        if (key == kEmpty) continue;
+        if (len >= t1) {
+            const u64 i = atomicAdd(&sd->H1, 1ull);
             if (i < (u64)kHotMax) sd->hot[i] = key;
+        } else if (len >= t2) {
+            const u64 i = atomicAdd(&sd->W, 1ull);
+            if (i < (u64)kWarmMax) sd->warm[i] = key;
         }
     }
 }
@@ -214,7 +287,7 @@ __global__ void __launch_bounds__(kTableThreads, 1) k_hot_table(SplitDev* sd) {
     extern __shared__ __align__(16) u64 sh[];
     u64* keys = sh;              // [kHotPad]
     u64* table = sh + kHotPad;   // [kHotSlots]
-    const u64 H = sd->H < (u64)kHotMax ? sd->H : (u64)kHotMax;
+    const u64 H = sd->H1 < (u64)kHotMax ? sd->H1 : (u64)kHotMax;
     for (int i = threadIdx.x; i < kHotPad; i += kTableThreads) keys[i] = (u64)i < H ? sd->hot[i] : kEmpty;
     for (int i = threadIdx.x; i < kHotSlots; i += kTableThreads) table[i] = kEmpty;
     __syncthreads();
@@ -298,7 +371,7 @@ __global__ void __launch_bounds__(kTableThreads, 1) k_hot_table(SplitDev* sd) {
         __syncthreads();
         u32 before = kept;
         for (u32 w = 0; w < (threadIdx.x >> 5); ++w) before += wcount[w];
-        if (keep) sd->hot[before + __popc(bal & lanemask_lt())] = keys[i];
+        if (keep) sd->list[before + __popc(bal & lanemask_lt())] = keys[i];
         __syncthreads();
         if (threadIdx.x == 0) {
             u32 t = 0;
@@ -307,11 +380,47 @@ __global__ void __launch_bounds__(kTableThreads, 1) k_hot_table(SplitDev* sd) {
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) sd->H = kept;
+    if (threadIdx.x == 0) {
+        sd->H1 = kept;
+        sd->H = kept;
+    }
     for (int i = threadIdx.x; i < kHotSlots; i += kTableThreads) {
         sd->table[i] = table[i];
         sd->slot_count[i] = 0;
     }
+}
+
+// 2e. Tier 2, many CTAs: each candidate takes a free slot of its first
+// tier-2 bucket, else of its second (compare-and-swap), and is appended to
+// the hot list after the tier-1 keys; one that finds both buckets full
+// stays cold.  The table starts all free and the counts zero.
+__global__ void k_warm_insert(SplitDev* sd) {
+    const u64 W = sd->W < (u64)kWarmMax ? sd->W : (u64)kWarmMax, H1 = sd->H1;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < W; i += (u64)gridDim.x * blockDim.x) {
+        const u64 key = sd->warm[i];
+        const u32 x = key_mix(key);
+        const u32 b1 = warm_bucket1(x), b2 = warm_bucket2(x, b1);
+        bool placed = false;
+        for (int q = 0; q < 2 * kWays && !placed; ++q) {
+            const u32 slot = 4 * (q < kWays ? b1 : b2) + (q & (kWays - 1));
+            placed = atomicCAS(reinterpret_cast<unsigned long long*>(&sd->table2[slot]), kEmpty, key) == kEmpty;
+        }
+        if (placed) sd->list[H1 + atomicAdd(&sd->W2, 1ull)] = key;
+    }
+}
+
+// 2f. The tier-2 fingerprint words, and the hot list's length.
+__global__ void k_warm_fp(SplitDev* sd) {
+    const u32 b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < (u32)kWarmBuckets) {
+        u32 w = 0;
+        for (int q = 0; q < kWays; ++q) {
+            const u64 k = sd->table2[kWays * b + q];
+            w |= (k == kEmpty ? 0u : fingerprint(k)) << (8 * q);
+        }
+        sd->fpw2[b] = w;
+    }
+    if (b == 0) sd->H = sd->H1 + sd->W2;
 }
 
 // 3. The split.  Persistent CTAs take chunks of kSplitThreads * 8 packets
@@ -321,7 +430,7 @@ __global__ void __launch_bounds__(kTableThreads, 1) k_hot_table(SplitDev* sd) {
 // and serialize badly on the hottest keys) and are added to the global
 // counts every kFlushChunks chunks, before any could pass 2^31.
 #ifndef NS_SPLIT_THREADS
-#define NS_SPLIT_THREADS 512
+#define NS_SPLIT_THREADS (NS_WARM_BUCKETS > 0 ? 1024 : 512)
 #endif
 constexpr int kSplitThreads = NS_SPLIT_THREADS;
 constexpr int kSplitItems = 8;
@@ -331,6 +440,7 @@ struct SplitSmem {
     u64 table[kHotSlots];
     u32 count[kHotSlots];
     u32 fpw[kBuckets];  // per bucket: the fingerprints of its kWays slots
+    u32 fpw2[kWarmBuckets > 0 ? kWarmBuckets : 1];  // the same for tier 2 (its keys stay in global memory)
     u32 wsum[kSplitThreads / 32];
     u64 base;
 };
@@ -363,8 +473,11 @@ __global__ void __launch_bounds__(kSplitThreads, 1024 / kSplitThreads) k_hot_spl
         }
         sm.fpw[b] = w;
     }
+    for (int b = t; b < kWarmBuckets; b += kSplitThreads) sm.fpw2[b] = sd->fpw2[b];
     __syncthreads();
     const u32 lt = lanemask_lt();
+    const u64* __restrict__ table2 = sd->table2;
+    u64* count2 = sd->count2;
     u64 since_flush = 0;  // the same in every thread of the CTA
     for (u64 base = (u64)blockIdx.x * kSplitChunk; base < n; base += (u64)gridDim.x * kSplitChunk) {
         if (++since_flush == kFlushChunks) {
@@ -401,7 +514,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1024 / kSplitThreads) k_hot_spl
                 valid |= (i < n ? 1u : 0u) << u;
             }
         }
-        // hot keys are counted here; the others are marked cold
+        // tier 1: counted in shared memory; the others are marked cold
         u32 coldm = 0;
 #pragma unroll
         for (int u = 0; u < kSplitItems; ++u) {
@@ -409,6 +522,49 @@ __global__ void __launch_bounds__(kSplitThreads, 1024 / kSplitThreads) k_hot_spl
                 const int slot = hot_find_fp(sm.fpw, sm.table, key[u]);
                 if (slot >= 0) atomicAdd(&sm.count[slot], 1u);
                 else coldm |= 1u << u;
+            }
+        }
+        if (kWarmBuckets > 0 && coldm) {
+            // tier 2: the fingerprints (shared memory) give each key still
+            // cold its first candidate slot, all candidates' keys are then
+            // loaded (L2) before any compare; a key whose first candidate
+            // is not it checks its others one by one (rare)
+            u32 cand[kSplitItems], sl[kSplitItems];
+#pragma unroll
+            for (int u = 0; u < kSplitItems; ++u) {
+                cand[u] = 0;
+                sl[u] = 0;
+                if (((coldm >> u) & 1u) && key[u] != kEmpty) {
+                    const u32 x = key_mix(key[u]);
+                    const u32 b1 = warm_bucket1(x), b2 = warm_bucket2(x, b1);
+                    const u32 f4 = fingerprint_of_mix(x) * 0x01010101u;
+                    cand[u] = zero_bytes(sm.fpw2[b1] ^ f4) | (zero_bytes(sm.fpw2[b2] ^ f4) >> 1);
+                    const u32 bit = __ffs(cand[u]) - 1;
+                    sl[u] = 4 * ((bit & 1) ? b1 : b2) + (bit >> 3);
+                }
+            }
+            u64 k2[kSplitItems];
+#pragma unroll
+            for (int u = 0; u < kSplitItems; ++u) k2[u] = cand[u] ? __ldg(table2 + sl[u]) : 0;
+#pragma unroll
+            for (int u = 0; u < kSplitItems; ++u) {
+                if (!cand[u]) continue;
+                int slot = k2[u] == key[u] ? (int)sl[u] : -1;
+                u32 c = cand[u] & (cand[u] - 1);
+                if (slot < 0 && c) {
+                    const u32 x = key_mix(key[u]);
+                    const u32 b1 = warm_bucket1(x), b2 = warm_bucket2(x, b1);
+                    while (c && slot < 0) {
+                        const u32 bit = __ffs(c) - 1;
+                        c &= c - 1;
+                        const u32 q = 4 * ((bit & 1) ? b1 : b2) + (bit >> 3);
+                        if (__ldg(table2 + q) == key[u]) slot = (int)q;
+                    }
+                }
+                if (slot >= 0) {
+                    atomicAdd(reinterpret_cast<unsigned long long*>(count2 + slot), 1ull);
+                    coldm &= ~(1u << u);
+                }
             }
         }
         u32 bal[kSplitItems];
@@ -443,7 +599,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1024 / kSplitThreads) k_hot_spl
 }
 
 // 5. Merge of the cold runs (heads[r], length pos[r+1] - pos[r]) with the
-// hot keys into keys/counts, and the whole-matrix quantities: unique links,
+// hot list into keys/counts, and the whole-matrix quantities: unique links,
 // valid packets and the largest count.
 constexpr int kMergeThreads = 512;
 __device__ __forceinline__ u64 count_below(const u64* a, u64 len, u64 key) {
@@ -456,18 +612,37 @@ __device__ __forceinline__ u64 count_below(const u64* a, u64 len, u64 key) {
     return lo;
 }
 
+// Hot-list keys below `key`.  idx (shared memory) holds list[0], list[S],
+// list[2S], ... (S = kIndexStride); if p index keys are below `key`, then
+// list[0 .. (p-1)S] all are and list[pS] is not, which leaves the S - 1 keys
+// between to compare (one or two cache lines of the list).
+__device__ __forceinline__ u64 hot_rank(const u64* idx, u64 NI, const u64* __restrict__ list, u64 H, u64 key) {
+    const u64 p = count_below(idx, NI, key);
+    if (p == 0) return 0;
+    const u64 b = (p - 1) * kIndexStride;
+    u64 r = b + 1;
+#pragma unroll
+    for (int q = 1; q < kIndexStride; ++q) r += (b + q < H && __ldg(list + b + q) < key) ? 1 : 0;
+    return r;
+}
+
 // Each warp takes kMergeRounds x 32 consecutive elements at a time and
 // issues all their loads before any search, so that HBM latency is paid
-// once per group rather than once per element.
+// once per group rather than once per element.  The hot keys below a cold
+// key of the group are those below the group's first key (lo) plus those
+// below it among the hot keys that fall between the group's first and last
+// keys (span of them: almost always none).
 constexpr int kMergeRounds = 4;
 __global__ void __launch_bounds__(kMergeThreads) k_hot_merge(const u64* __restrict__ heads, const u64* __restrict__ pos,
                                                              const SplitDev* sd, u64* __restrict__ keys_out,
                                                              u64* __restrict__ counts_out, DevStats* st) {
-    extern __shared__ __align__(16) u64 hot[];  // [kHotMax]
+    extern __shared__ __align__(16) u64 idx[];  // [kIndexMax]
     __shared__ u64 bmax;
     const u32 FULL = 0xFFFFFFFFu, lane = threadIdx.x & 31;
     const u64 H = sd->H, RC = sd->R_cold, total = RC + H;
-    for (u64 i = threadIdx.x; i < H; i += kMergeThreads) hot[i] = sd->hot[i];
+    const u64 NI = (H + kIndexStride - 1) / kIndexStride;
+    const u64* __restrict__ list = sd->list;
+    for (u64 i = threadIdx.x; i < NI; i += kMergeThreads) idx[i] = list[i * kIndexStride];
     if (threadIdx.x == 0) bmax = 0;
     __syncthreads();
     u64 mx = 0, hot_sum = 0;
@@ -475,7 +650,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_hot_merge(const u64* __restri
     const u64 warp0 = (((u64)blockIdx.x * kMergeThreads + threadIdx.x) >> 5) * group;
     const u64 wstride = ((u64)gridDim.x * kMergeThreads >> 5) * group;
     for (u64 base = warp0; base < total; base += wstride) {
-        u64 key[kMergeRounds], c[kMergeRounds];
+        u64 key[kMergeRounds], c[kMergeRounds], below[kMergeRounds];
 #pragma unroll
         for (int r = 0; r < kMergeRounds; ++r) {
             const u64 i = base + (u64)r * 32 + lane;
@@ -486,18 +661,46 @@ __global__ void __launch_bounds__(kMergeThreads) k_hot_merge(const u64* __restri
                 c[r] = pos[i + 1] - pos[i];
             }
         }
+        u64 lo = 0, hi = 0;
+        if (base < RC) {  // warp-uniform
+            const u64 last = min(base + group, RC) - 1;
+            u64 v = 0;
+            if (lane < 2) v = hot_rank(idx, NI, list, H, heads[lane == 0 ? base : last]);
+            lo = __shfl_sync(FULL, v, 0);
+            hi = __shfl_sync(FULL, v, 1);
+        }
+        const u64 span = hi - lo;
+#pragma unroll
+        for (int r = 0; r < kMergeRounds; ++r) below[r] = lo;
+        if (span > 0 && span <= 32) {
+            const u64 w = lane < span ? __ldg(list + lo + lane) : 0;
+            for (u32 j = 0; j < (u32)span; ++j) {
+                const u64 wj = __shfl_sync(FULL, w, j);
+#pragma unroll
+                for (int r = 0; r < kMergeRounds; ++r) below[r] += wj < key[r] ? 1 : 0;
+            }
+        } else if (span > 32) {
+#pragma unroll
+            for (int r = 0; r < kMergeRounds; ++r) below[r] = lo + count_below(list + lo, span, key[r]);
+        }
 #pragma unroll
         for (int r = 0; r < kMergeRounds; ++r) {
             const u64 i = base + (u64)r * 32 + lane;
             if (i < RC) {
-                const u64 at = i + count_below(hot, H, key[r]);
+                const u64 at = i + below[r];
                 keys_out[at] = key[r];
                 counts_out[at] = c[r];
                 mx = c[r] > mx ? c[r] : mx;
             } else if (i < total) {
-                const u64 h = i - RC, k = hot[h];
+                const u64 h = i - RC, k = list[h];
                 const int slot = hot_find(sd->table, k);
-                const u64 ch = slot >= 0 ? sd->slot_count[slot] : 0;
+                u64 ch = 0;
+                if (slot >= 0) {
+                    ch = sd->slot_count[slot];
+                } else {
+                    const int s2 = warm_find(sd->fpw2, sd->table2, k);
+                    ch = s2 >= 0 ? sd->count2[s2] : 0;
+                }
                 const u64 at = h + count_below(heads, RC, k);
                 keys_out[at] = k;
                 counts_out[at] = ch;
@@ -538,8 +741,13 @@ void sort_links_split(const u32* src, const u32* dst, u64 n, u64* kb[2], u64* he
                       u64* keys_out, u64* counts_out, SortScratch& sc, DevStats* st, int sms, cudaStream_t s) {
     SplitDev* sd = (SplitDev*)state;
     Tracer* tr = sc.tr;
-    // the histogram and the scalars after it start from zero
+    // the histogram and the scalars after it start from zero, the tier-2
+    // table free and its counts zero
     cudaMemsetAsync(&sd->hist, 0, sizeof(SplitDev) - offsetof(SplitDev, hist), s);
+    if (kWarmBuckets > 0) {
+        cudaMemsetAsync(sd->table2, 0xFF, sizeof(sd->table2), s);
+        cudaMemsetAsync(sd->count2, 0, sizeof(sd->count2), s);
+    }
     // 1. sample, sorted, in runs
     const u64 m = std::min<u64>(kSampleMax, (n / 4) / kSampleBlocks * kSampleBlocks);
     const u64 blen = m / kSampleBlocks;
@@ -558,6 +766,16 @@ void sort_links_split(const u32* src, const u32* dst, u64 n, u64* kb[2], u64* he
         const size_t tsmem = sizeof(u64) * (kHotPad + kHotSlots);
         resident_ctas_of((const void*)k_hot_table, kTableThreads, tsmem);  // sets its shared-memory size
         k_hot_table<<<1, kTableThreads, tsmem, s>>>(sd);
+        if (kWarmBuckets > 0) {
+            k_warm_insert<<<(kWarmMax + 255) / 256, 256, 0, s>>>(sd);
+            k_warm_fp<<<(kWarmBuckets + 255) / 256, 256, 0, s>>>(sd);
+        }
+    }
+    if (kWarmBuckets > 0) {
+        // the hot list ascending: both tiers' keys sorted together (kb is
+        // free until the split writes the cold keys)
+        const int rl = radix_sort_keys64(sd->list, &sd->H, kb, kListMax, sc, st, s, "k_onesweep<hot list>");
+        cudaMemcpyAsync(sd->list, kb[rl], sizeof(sd->list), cudaMemcpyDeviceToDevice, s);
     }
     // 3. the split: hot keys counted, cold keys into kb[1]
     {
@@ -575,7 +793,7 @@ void sort_links_split(const u32* src, const u32* dst, u64 n, u64* kb[2], u64* he
     // 5. merged with the hot keys
     {
         TraceScope ts(tr, "k_hot_merge", s);
-        const size_t msmem = sizeof(u64) * kHotMax;
+        const size_t msmem = sizeof(u64) * kIndexMax;
         const int mgrid = resident_ctas_of((const void*)k_hot_merge, kMergeThreads, msmem);
         k_hot_merge<<<mgrid, kMergeThreads, msmem, s>>>(heads, pos, sd, keys_out, counts_out, st);
     }

@@ -143,3 +143,13 @@ def test_every_tile_shape_matches_oracle(tile, split):
     s, d = gen.uniform_pairs(300007, 32, 12)
     check(ctx, s, d)
     ctx.close()
+
+
+def test_split_second_tier_takes_warm_keys():
+    """More heavy links than the shared-memory tier holds (6144 keys): the
+    global-memory tier takes the next ones, and A is still exact."""
+    s, d = W.zipf_window(1 << 22, 1.1, 1 << 18, 41)
+    ctx = ns.Context(0, path="sort", sort_split="on")
+    info = check(ctx, s, d)
+    assert info["hot_keys"] > 6144
+    ctx.close()
