@@ -565,6 +565,20 @@ def c2_record(args, local, clocks, steps=None, windows=None):
     last = rows[-1].cpu().numpy().view(np.uint64)
     assert int(last[0]) == N, "valid packets != N"
     ceiling_us = ns.diag_random_atomics(1 << 28, WINDOW, 5)
+    # the same window against the ingest's own two-round-trip structure, and
+    # what claiming stale slots (an epoch mark instead of the clear) would add
+    slots = 1 << 28  # the link, row and column tables' capacity here (load <= 1/4)
+    claim_add_us = ns.diag_random_claims(slots, WINDOW, "claim_add", 5)
+    stale_us = ns.diag_random_claims(slots, WINDOW, "claim_stale", 5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(cap):
+        ns.matrix_clear(A)
+        e0.record()
+        for _ in range(5):
+            ns.matrix_clear(A)
+        e1.record()
+    torch.cuda.synchronize()
+    clear_ms = e0.elapsed_time(e1) / 5
     peak, peak_src = peak_hbm()
     kus = float(np.mean(launch_ms)) * 1e3
     rec = {
@@ -578,7 +592,15 @@ def c2_record(args, local, clocks, steps=None, windows=None):
                      "traffic": (profile_traffic("k_insert_packets.stream_rmat_window_2p17.md",
                                                  ["ns_hash.cu", "ns_common.cuh"]) or {}).get("bytes")},
         "roofline_random_access": {"kernel_us": kus, "ceiling_us": ceiling_us, "frac": ceiling_us / kus,
-                                   "ceiling": "2^17 threads x 3 random 8-byte atomics into three 2 GiB tables"},
+                                   "ceiling": "2^17 threads x 3 random 8-byte atomics into three 2 GiB tables",
+                                   "structure_ceiling_us": claim_add_us, "structure_frac": claim_add_us / kus,
+                                   "structure_ceiling": "2^17 threads x 3 random 16-byte CAS claims into three "
+                                                        "4 GiB tables, then 2 dependent adds (the ingest's two "
+                                                        "round trips)"},
+        "clear_vs_epoch": {"clear_ms_per_step": clear_ms, "stale_claim_us": stale_us,
+                           "epoch_extra_ms_per_step": NW * max(stale_us - claim_add_us, 0.0) / 1e3,
+                           "note": "an epoch mark replaces the per-step clear of the three tables by a second "
+                                   "compare-and-swap on every slot's first touch after the clear"},
     }
     if not args.no_e2e:
         h_rows = torch.empty(NW, 16, dtype=torch.int64).pin_memory()

@@ -594,6 +594,29 @@ ns_status ns_diag_wait_timeout(int which, ns_stream_t stream);
 ns_status ns_diag_random_atomics(uint64_t table_words, uint64_t threads, int reps, double* best_us,
                                  ns_stream_t stream);
 
+/* Diagnostic of the ceiling set by the hash ingest's own access structure
+ * (no counterpart in the paper).  Three tables of table_slots 16-byte slots
+ * (a power of two >= 1024); `threads` threads each touch one pseudo-random
+ * slot of each table:
+ *   NS_DIAG_CLAIM       three 128-bit compare-and-swap claims from the empty
+ *                       value, issued together (one round trip);
+ *   NS_DIAG_CLAIM_ADD   the claims, then -- dependent on them -- an 8-byte
+ *                       add on the second and third slots: the two round
+ *                       trips an ingested packet takes (link, row and column
+ *                       claims; then the row and column updates);
+ *   NS_DIAG_CLAIM_STALE every slot holds an old entry: the claim from the
+ *                       empty value fails and a second compare-and-swap from
+ *                       the value it returned claims the slot, then the
+ *                       dependent adds -- what marking slots with an epoch,
+ *                       instead of clearing the tables, costs on a slot's
+ *                       first touch after a clear.
+ * *best_us receives the fastest of `reps` timed launches (after one
+ * warm-up).  Allocates (3 x 16 x table_slots bytes) and frees its tables;
+ * blocking.  NS_ERR_INVALID for a bad argument. */
+enum { NS_DIAG_CLAIM = 0, NS_DIAG_CLAIM_ADD = 1, NS_DIAG_CLAIM_STALE = 2 };
+ns_status ns_diag_random_claims(uint64_t table_slots, uint64_t threads, int mode, int reps, double* best_us,
+                                ns_stream_t stream);
+
 /* ---- errors ------------------------------------------------------------ */
 
 const char* ns_last_error(void);

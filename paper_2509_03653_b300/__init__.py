@@ -25,7 +25,7 @@ __all__ = [
     "matrix_clear", "sync", "PATHS", "SORT_TILES", "path_tune", "path_resolve", "sort_split_info", "matrix_nodes", "NODES", "anonymize", "Slider",
     "slider_push", "window_stats_static", "STATIC_MAX_PACKETS",
     "trace_enable", "trace_read", "Batch", "batch_run", "batch_run_device", "batch_sync", "batch_tune", "matrix_reserve_ex",
-    "owner", "matrix_partition", "matrix_add_entries", "Server", "stream_submit", "stream_poll", "stream_wait", "diag_random_atomics", "matrix_save", "matrix_load",
+    "owner", "matrix_partition", "matrix_add_entries", "Server", "stream_submit", "stream_poll", "stream_wait", "diag_random_atomics", "diag_random_claims", "matrix_save", "matrix_load",
 ]
 
 STATIC_MAX_PACKETS = 32768  # NS_STATIC_MAX_PACKETS in include/ns.h
@@ -589,6 +589,24 @@ def diag_random_atomics(table_words: int, threads: int, reps: int = 5, stream=No
     us = ctypes.c_double()
     check(L.ns_diag_random_atomics(table_words, threads, reps, ctypes.byref(us), _stream(stream)),
           "ns_diag_random_atomics")
+    return float(us.value)
+
+
+DIAG_CLAIM_MODES = {"claim": 0, "claim_add": 1, "claim_stale": 2}
+
+
+def diag_random_claims(table_slots: int, threads: int, mode: str = "claim_add", reps: int = 5,
+                       stream=None) -> float:
+    """Microseconds for `threads` x three random 16-byte slot claims into
+    three tables of `table_slots` slots (ns_diag_random_claims).  mode:
+    "claim" (one round trip), "claim_add" (the claims, then the dependent row
+    and column adds: the hash ingest's two round trips) or "claim_stale"
+    (claims of slots holding old entries, as an epoch mark instead of a
+    table clear would need, then the adds)."""
+    L = load()
+    us = ctypes.c_double()
+    check(L.ns_diag_random_claims(table_slots, threads, DIAG_CLAIM_MODES[mode], reps, ctypes.byref(us),
+                                  _stream(stream)), "ns_diag_random_claims")
     return float(us.value)
 
 

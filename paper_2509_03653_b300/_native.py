@@ -98,6 +98,7 @@ SIGNATURES = {
                            ctypes.POINTER(NsStreamTiming)]),
     "ns_diag_wait_timeout": (ST, [I32, P]),
     "ns_diag_random_atomics": (ST, [U64, U64, I32, ctypes.POINTER(ctypes.c_double), P]),
+    "ns_diag_random_claims": (ST, [U64, U64, I32, I32, ctypes.POINTER(ctypes.c_double), P]),
     "ns_last_error": (ctypes.c_char_p, []),
     "ns_status_string": (ctypes.c_char_p, [ST]),
 }

@@ -658,6 +658,38 @@ __global__ void k_diag_rand3(u64* a, u64* b, u64* c, u64 mask, u64 threads, u64 
     atomicAdd(&c[mix64(h + 2) & mask], 1ull);
 }
 
+// Diagnostic: the ingest's own access structure without hashing, probing or
+// statistics.  Each thread claims one pseudo-random 16-byte slot in each of
+// three tables with a 128-bit CAS from the empty value {0, 0}, the three
+// issued together (mode 0).  Mode 1 adds the dependent second round trip:
+// an 8-byte add on the row and column slots after the claims return.  Mode
+// 2 models claims of stale slots (what a per-slot epoch tag in place of a
+// table clear needs): the CAS from {0, 0} finds a stale entry, a second CAS
+// from the value it returned claims the slot, then mode 1's second round
+// trip.  The results feed a store that practically never happens (it keeps
+// them live without contention on one address).
+__global__ void k_diag_claims(u64* a, u64* b, u64* c, u64 mask, u64 threads, u64 seed, int mode, u64* sink) {
+    const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= threads) return;
+    const u64 h = mix64(seed ^ (i * 0x9E3779B97F4A7C15ull));
+    const u64 ia = h & mask, ib = mix64(h + 1) & mask, ic = mix64(h + 2) & mask;
+    const u64 key = h | 1;
+    W128 x = cas128(&a[2 * ia], 0ull, 0ull, key, 1ull);
+    W128 y = cas128(&b[2 * ib], 0ull, 0ull, key, 1ull);
+    W128 z = cas128(&c[2 * ic], 0ull, 0ull, key, 1ull);
+    if (mode == 2) {
+        x = cas128(&a[2 * ia], x.lo, x.hi, key, 1ull);
+        y = cas128(&b[2 * ib], y.lo, y.hi, key, 1ull);
+        z = cas128(&c[2 * ic], z.lo, z.hi, key, 1ull);
+    }
+    u64 r = x.lo + y.lo + z.lo;
+    if (mode >= 1) {
+        r += atomicAdd(&b[2 * ib + 1], 1ull);
+        r += atomicAdd(&c[2 * ic + 1], 1ull);
+    }
+    if (r == ~0ull) sink[0] = i;
+}
+
 int grid_for(u64 n, int threads, int sms, int per_sm) {
     u64 want = (n + threads - 1) / threads;
     u64 cap = (u64)sms * per_sm;
@@ -737,6 +769,11 @@ void launch_batch_stats_out(const DevStats* wstats, u64 W, u64* out, int sms, cu
 
 void launch_diag_rand3(u64* a, u64* b, u64* c, u64 mask, u64 threads, u64 seed, cudaStream_t s) {
     k_diag_rand3<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a, b, c, mask, threads, seed);
+}
+
+void launch_diag_claims(u64* a, u64* b, u64* c, u64 mask, u64 threads, u64 seed, int mode, u64* sink,
+                        cudaStream_t s) {
+    k_diag_claims<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a, b, c, mask, threads, seed, mode, sink);
 }
 
 void launch_stats_out(const DevStats* st, u64* out, cudaStream_t s) {

@@ -92,6 +92,9 @@ void sort_links_split(const u32* src, const u32* dst, u64 n, u64* kb[2], u64* he
 cudaError_t split_info(const void* state, u64* hot_keys, u64* cold_packets, cudaStream_t s);
 void launch_diag_wait(int which, u64* status_word, DevStats* st, cudaStream_t s);
 void launch_diag_rand3(u64* a, u64* b, u64* c, u64 mask, u64 threads, u64 seed, cudaStream_t s);
+// a, b, c: tables of mask + 1 16-byte slots (2 (mask + 1) words); mode 0..2
+void launch_diag_claims(u64* a, u64* b, u64* c, u64 mask, u64 threads, u64 seed, int mode, u64* sink,
+                        cudaStream_t s);
 int sort_radix();
 
 // Batched windows: per-window tables carved from one arena (ns_batch.cu).

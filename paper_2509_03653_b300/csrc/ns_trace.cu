@@ -133,6 +133,44 @@ ns_status ns_diag_wait_timeout(int which, ns_stream_t stream) {
     return ns::set_fail(NS_ERR_STATE, "ns_diag_wait_timeout: the wait did not report a timeout");
 }
 
+}  // extern "C"
+
+namespace {
+
+// Fastest of `reps` timed launches (after one warm-up) of launch(r) on s.
+template <typename F>
+ns_status time_best(const char* what, int reps, cudaStream_t s, F launch, double* best_us) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return ns::fail_fmt(NS_ERR_CUDA, "%s: event creation failed", what);
+    }
+    ns_status st = NS_OK;
+    float best = 1e30f;
+    for (int r = 0; r <= reps; ++r) {  // the first run warms up
+        cudaEventRecord(e0, s);
+        launch(r);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaGetLastError();
+            st = ns::fail_fmt(NS_ERR_CUDA, "%s: launch failed", what);
+            break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0 && ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == NS_OK) *best_us = best * 1e3;
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
 ns_status ns_diag_random_atomics(uint64_t table_words, uint64_t threads, int reps, double* best_us,
                                  ns_stream_t stream) {
     if (!best_us || reps < 1 || table_words < 1024 || (table_words & (table_words - 1)) || threads == 0)
@@ -143,37 +181,50 @@ ns_status ns_diag_random_atomics(uint64_t table_words, uint64_t threads, int rep
     ns_status st = ns::buf_reserve(a, table_words * 8);
     if (st == NS_OK) st = ns::buf_reserve(b, table_words * 8);
     if (st == NS_OK) st = ns::buf_reserve(c, table_words * 8);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (st == NS_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
-        cudaGetLastError();
-        st = ns::set_fail(NS_ERR_CUDA, "ns_diag_random_atomics: event creation failed");
-    }
-    float best = 1e30f;
     if (st == NS_OK) {
         cudaMemsetAsync(a.p, 0, table_words * 8, s);
         cudaMemsetAsync(b.p, 0, table_words * 8, s);
         cudaMemsetAsync(c.p, 0, table_words * 8, s);
-        for (int r = 0; r <= reps && st == NS_OK; ++r) {  // the first run warms up
-            cudaEventRecord(e0, s);
+        st = time_best("ns_diag_random_atomics", reps, s, [&](int r) {
             ns::launch_diag_rand3((ns::u64*)a.p, (ns::u64*)b.p, (ns::u64*)c.p, table_words - 1, threads,
                                   0x5EEDull + (ns::u64)r * 7919, s);
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                cudaGetLastError();
-                st = ns::set_fail(NS_ERR_CUDA, "ns_diag_random_atomics: launch failed");
-                break;
-            }
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (r > 0 && ms < best) best = ms;
-        }
+        }, best_us);
     }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
     ns::buf_free(a);
     ns::buf_free(b);
     ns::buf_free(c);
-    if (st == NS_OK) *best_us = best * 1e3;
+    return st;
+}
+
+ns_status ns_diag_random_claims(uint64_t table_slots, uint64_t threads, int mode, int reps, double* best_us,
+                                ns_stream_t stream) {
+    if (!best_us || reps < 1 || table_slots < 1024 || (table_slots & (table_slots - 1)) || threads == 0 ||
+        mode < NS_DIAG_CLAIM || mode > NS_DIAG_CLAIM_STALE)
+        return ns::set_fail(NS_ERR_INVALID, "ns_diag_random_claims: bad argument (table_slots a power of two >= "
+                                            "1024, mode 0..2)");
+    cudaStream_t s = (cudaStream_t)stream;
+    ns::AllocScope alloc(nullptr, s);
+    ns::Buf a, b, c, sink;
+    const ns::u64 bytes = table_slots * 16;
+    ns_status st = ns::buf_reserve(a, bytes);
+    if (st == NS_OK) st = ns::buf_reserve(b, bytes);
+    if (st == NS_OK) st = ns::buf_reserve(c, bytes);
+    if (st == NS_OK) st = ns::buf_reserve(sink, 16);
+    if (st == NS_OK) {
+        // empty slots, or (stale mode) every slot holding an old entry
+        const int fill = mode == NS_DIAG_CLAIM_STALE ? 0x11 : 0;
+        cudaMemsetAsync(a.p, fill, bytes, s);
+        cudaMemsetAsync(b.p, fill, bytes, s);
+        cudaMemsetAsync(c.p, fill, bytes, s);
+        st = time_best("ns_diag_random_claims", reps, s, [&](int r) {
+            ns::launch_diag_claims((ns::u64*)a.p, (ns::u64*)b.p, (ns::u64*)c.p, table_slots - 1, threads,
+                                   0xC1A1ull + (ns::u64)r * 7919, mode, (ns::u64*)sink.p, s);
+        }, best_us);
+    }
+    ns::buf_free(a);
+    ns::buf_free(b);
+    ns::buf_free(c);
+    ns::buf_free(sink);
     return st;
 }
 

@@ -366,6 +366,14 @@ def test_random_atomic_ceiling_diagnostic():
         ns.diag_random_atomics(1000, 10, 1)  # not a power of two
 
 
+@pytest.mark.parametrize("mode", ["claim", "claim_add", "claim_stale"])
+def test_random_claim_ceiling_diagnostic(mode):
+    us = ns.diag_random_claims(1 << 16, 1 << 14, mode, 2)
+    assert 0.0 < us < 1e6
+    with pytest.raises(ns.NsError):
+        ns.diag_random_claims(1 << 16 | 1, 10, mode, 1)  # not a power of two
+
+
 @pytest.mark.parametrize("load", [0.01, 0.95, -1.0])
 def test_hash_load_out_of_range(load):
     with pytest.raises(ns.NsError) as e:
