@@ -669,7 +669,10 @@ __global__ void __launch_bounds__(kMergeThreads) k_hot_merge(const u64* __restri
             lo = __shfl_sync(FULL, v, 0);
             hi = __shfl_sync(FULL, v, 1);
         }
-        const u64 span = hi - lo;
+        // hi >= lo for ascending inputs; clamped so that a list left out of
+        // order (a look-back that gave up, recorded as an error) cannot
+        // send the search outside the list
+        const u64 span = hi > lo ? hi - lo : 0;
 #pragma unroll
         for (int r = 0; r < kMergeRounds; ++r) below[r] = lo;
         if (span > 0 && span <= 32) {
