@@ -172,10 +172,9 @@ __device__ __forceinline__ u32 fingerprint(u64 key) { return fingerprint_of_mix(
 // kEmpty, so the key kEmpty (never hot) is refused before any compare.
 __device__ __forceinline__ u32 zero_bytes(u32 v) { return (v - 0x01010101u) & ~v & 0x80808080u; }
 
-__device__ __forceinline__ int hot_find_fp(const u32* fpw, const u64* table, u64 key) {
-    const u32 x = key_mix(key);
+// x: key_mix(key); f4: its fingerprint in all four bytes.
+__device__ __forceinline__ int hot_find_fp(const u32* fpw, const u64* table, u64 key, u32 x, u32 f4) {
     const u32 b1 = x >> (32 - kBucketBits), b2 = bucket2_of_mix(x, b1);
-    const u32 f4 = fingerprint_of_mix(x) * 0x01010101u;
     // bit 8w+7: slot w of b1 may match; bit 8w+6: slot w of b2 may match
     u32 cand = zero_bytes(fpw[b1] ^ f4) | (zero_bytes(fpw[b2] ^ f4) >> 1);
     if (cand == 0 || key == kEmpty) return -1;
@@ -514,35 +513,36 @@ __global__ void __launch_bounds__(kSplitThreads, 1024 / kSplitThreads) k_hot_spl
                 valid |= (i < n ? 1u : 0u) << u;
             }
         }
-        // tier 1: counted in shared memory; the others are marked cold
+        // tier 1: counted in shared memory; the others are marked cold.  A
+        // key missing tier 1 takes its tier-2 candidate slot from the same
+        // mix and fingerprint (fingerprint words in shared memory)
         u32 coldm = 0;
+        u32 cand[kSplitItems], sl[kSplitItems];
 #pragma unroll
         for (int u = 0; u < kSplitItems; ++u) {
+            cand[u] = 0;
+            sl[u] = 0;
             if ((valid >> u) & 1u) {
-                const int slot = hot_find_fp(sm.fpw, sm.table, key[u]);
-                if (slot >= 0) atomicAdd(&sm.count[slot], 1u);
-                else coldm |= 1u << u;
+                const u32 x = key_mix(key[u]);
+                const u32 f4 = fingerprint_of_mix(x) * 0x01010101u;
+                const int slot = hot_find_fp(sm.fpw, sm.table, key[u], x, f4);
+                if (slot >= 0) {
+                    atomicAdd(&sm.count[slot], 1u);
+                } else {
+                    coldm |= 1u << u;
+                    if (kWarmBuckets > 0 && key[u] != kEmpty) {
+                        const u32 b1 = warm_bucket1(x), b2 = warm_bucket2(x, b1);
+                        cand[u] = zero_bytes(sm.fpw2[b1] ^ f4) | (zero_bytes(sm.fpw2[b2] ^ f4) >> 1);
+                        const u32 bit = __ffs(cand[u]) - 1;
+                        sl[u] = 4 * ((bit & 1) ? b1 : b2) + (bit >> 3);
+                    }
+                }
             }
         }
         if (kWarmBuckets > 0 && coldm) {
-            // tier 2: the fingerprints (shared memory) give each key still
-            // cold its first candidate slot, all candidates' keys are then
-            // loaded (L2) before any compare; a key whose first candidate
-            // is not it checks its others one by one (rare)
-            u32 cand[kSplitItems], sl[kSplitItems];
-#pragma unroll
-            for (int u = 0; u < kSplitItems; ++u) {
-                cand[u] = 0;
-                sl[u] = 0;
-                if (((coldm >> u) & 1u) && key[u] != kEmpty) {
-                    const u32 x = key_mix(key[u]);
-                    const u32 b1 = warm_bucket1(x), b2 = warm_bucket2(x, b1);
-                    const u32 f4 = fingerprint_of_mix(x) * 0x01010101u;
-                    cand[u] = zero_bytes(sm.fpw2[b1] ^ f4) | (zero_bytes(sm.fpw2[b2] ^ f4) >> 1);
-                    const u32 bit = __ffs(cand[u]) - 1;
-                    sl[u] = 4 * ((bit & 1) ? b1 : b2) + (bit >> 3);
-                }
-            }
+            // tier 2: all candidates' keys are loaded (L2) before any
+            // compare; a key whose first candidate is not it checks its
+            // others one by one (rare)
             u64 k2[kSplitItems];
 #pragma unroll
             for (int u = 0; u < kSplitItems; ++u) k2[u] = cand[u] ? __ldg(table2 + sl[u]) : 0;
@@ -576,14 +576,18 @@ __global__ void __launch_bounds__(kSplitThreads, 1024 / kSplitThreads) k_hot_spl
         }
         if (lane == 0) sm.wsum[w] = wtot;
         __syncthreads();
-        if (t == 0) {
-            u32 run = 0;
-            for (int i = 0; i < kSplitThreads / 32; ++i) {
-                const u32 x = sm.wsum[i];
-                sm.wsum[i] = run;
-                run += x;
+        if (w == 0) {  // exclusive scan of the warp counts (one warp), and the CTA's reservation
+            constexpr u32 kW = kSplitThreads / 32;
+            const u32 v = lane < kW ? sm.wsum[lane] : 0u;
+            u32 x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const u32 y = __shfl_up_sync(FULL, x, o);
+                if (lane >= (u32)o) x += y;
             }
-            sm.base = run ? atomicAdd(&sd->cold, (u64)run) : 0;
+            const u32 run = __shfl_sync(FULL, x, 31);
+            if (lane < kW) sm.wsum[lane] = x - v;
+            if (lane == 0) sm.base = run ? atomicAdd(&sd->cold, (u64)run) : 0;
         }
         __syncthreads();
         u64 off = sm.base + sm.wsum[w];
