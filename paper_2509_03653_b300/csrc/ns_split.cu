@@ -422,35 +422,53 @@ __global__ void k_warm_fp(SplitDev* sd) {
     if (b == 0) sd->H = sd->H1 + sd->W2;
 }
 
-// 3. The split.  Persistent CTAs take chunks of kSplitThreads * 8 packets
-// (chunk c, c + grid, ...).  With 16-byte-aligned columns a thread loads its
-// eight packets as two 16-byte vectors per column.
+// 3. The split.  Each CTA holds the tables once and runs as kGroups
+// independent groups of kGroupThreads threads (named barriers): group g of
+// CTA b takes chunks of kGroupThreads * 8 packets (chunk b * kGroups + g,
+// then every gridDim.x * kGroups chunks), so that while one group waits on
+// its barrier or its tier-2 loads the other keeps the SM busy.  With
+// 16-byte-aligned columns a thread loads its eight packets as two 16-byte
+// vectors per column.
 // Counts are 32-bit in shared memory (64-bit shared atomics are not native
-// and serialize badly on the hottest keys) and are added to the global
-// counts every kFlushChunks chunks, before any could pass 2^31.
+// and serialize badly on the hottest keys).  Every kDrainChunks of its own
+// chunks a group drains all counts into the global per-slot counts (atomic
+// exchange, so the other group's additions are never lost); between two
+// drains no count can reach 2^31.
 #ifndef NS_SPLIT_THREADS
 #define NS_SPLIT_THREADS (NS_WARM_BUCKETS > 0 ? 1024 : 512)
 #endif
 constexpr int kSplitThreads = NS_SPLIT_THREADS;
+constexpr int kGroupThreads = 512;
+constexpr int kGroups = kSplitThreads / kGroupThreads;
+static_assert(kGroups >= 1 && kGroups * kGroupThreads == kSplitThreads, "groups of 512 threads");
 constexpr int kSplitItems = 8;
-constexpr u64 kSplitChunk = (u64)kSplitThreads * kSplitItems;
-constexpr u64 kFlushChunks = (1ull << 31) / kSplitChunk;
+constexpr u64 kGroupChunk = (u64)kGroupThreads * kSplitItems;
+constexpr u64 kDrainChunks = (1ull << 31) / (2 * kGroups * kGroupChunk);
 struct SplitSmem {
     u64 table[kHotSlots];
     u32 count[kHotSlots];
     u32 fpw[kBuckets];  // per bucket: the fingerprints of its kWays slots
     u32 fpw2[kWarmBuckets > 0 ? kWarmBuckets : 1];  // the same for tier 2 (its keys stay in global memory)
-    u32 wsum[kSplitThreads / 32];
-    u64 base;
+    u32 wsum[kGroups][kGroupThreads / 32];
+    u64 base[kGroups];
 };
 
+__device__ __forceinline__ void group_sync(u32 g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kGroupThreads) : "memory");
+}
+
+// All counts into the global ones: by one group while the other may still
+// be adding (drain), or by the whole CTA at the end (flush).
+__device__ __forceinline__ void split_drain(SplitSmem& sm, SplitDev* sd, u32 tg) {
+    for (int i = tg; i < kHotSlots; i += kGroupThreads) {
+        const u32 c = atomicExch(&sm.count[i], 0u);
+        if (c) atomicAdd(reinterpret_cast<unsigned long long*>(&sd->slot_count[i]), (unsigned long long)c);
+    }
+}
 __device__ __forceinline__ void split_flush(SplitSmem& sm, SplitDev* sd) {
     for (int i = threadIdx.x; i < kHotSlots; i += kSplitThreads) {
         const u32 c = sm.count[i];
-        if (c) {
-            atomicAdd(reinterpret_cast<unsigned long long*>(&sd->slot_count[i]), (unsigned long long)c);
-            sm.count[i] = 0;
-        }
+        if (c) atomicAdd(reinterpret_cast<unsigned long long*>(&sd->slot_count[i]), (unsigned long long)c);
     }
 }
 
@@ -458,46 +476,46 @@ __global__ void __launch_bounds__(kSplitThreads, 1024 / kSplitThreads) k_hot_spl
                                                                  u64 n, bool vec, SplitDev* sd, u64* __restrict__ cold) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SplitSmem& sm = *reinterpret_cast<SplitSmem*>(smem_raw);
-    const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5, t = threadIdx.x;
+    const u32 lane = threadIdx.x & 31, t = threadIdx.x;
+    const u32 g = t / kGroupThreads, tg = t % kGroupThreads, w = tg >> 5;  // group, thread and warp in it
     const u32 FULL = 0xFFFFFFFFu;
     for (int i = t; i < kHotSlots; i += kSplitThreads) {
         sm.table[i] = sd->table[i];
         sm.count[i] = 0;
     }
     for (int b = t; b < kBuckets; b += kSplitThreads) {
-        u32 w = 0;
+        u32 fw = 0;
         for (int q = 0; q < kWays; ++q) {
             const u64 k = sd->table[kWays * b + q];
-            w |= (k == kEmpty ? 0u : fingerprint(k)) << (8 * q);
+            fw |= (k == kEmpty ? 0u : fingerprint(k)) << (8 * q);
         }
-        sm.fpw[b] = w;
+        sm.fpw[b] = fw;
     }
     for (int b = t; b < kWarmBuckets; b += kSplitThreads) sm.fpw2[b] = sd->fpw2[b];
     __syncthreads();
     const u32 lt = lanemask_lt();
     const u64* __restrict__ table2 = sd->table2;
     u64* count2 = sd->count2;
-    u64 since_flush = 0;  // the same in every thread of the CTA
-    for (u64 base = (u64)blockIdx.x * kSplitChunk; base < n; base += (u64)gridDim.x * kSplitChunk) {
-        if (++since_flush == kFlushChunks) {
-            since_flush = 0;
-            __syncthreads();
-            split_flush(sm, sd);
-            __syncthreads();
+    const u64 step = (u64)gridDim.x * kGroups * kGroupChunk;
+    u64 since_drain = 0;  // the same in every thread of the group
+    for (u64 base = ((u64)blockIdx.x * kGroups + g) * kGroupChunk; base < n; base += step) {
+        if (++since_drain == kDrainChunks) {
+            since_drain = 0;
+            split_drain(sm, sd, tg);
         }
-        // this CTA's next chunk starts moving into L2 now
-        const u64 nb = base + (u64)gridDim.x * kSplitChunk;
-        if (vec && t == 0 && nb + kSplitChunk <= n) {
-            bulk_prefetch_l2(src + nb, (u32)(kSplitChunk * 4));
-            bulk_prefetch_l2(dst + nb, (u32)(kSplitChunk * 4));
+        // this group's next chunk starts moving into L2 now
+        const u64 nb = base + step;
+        if (vec && tg == 0 && nb + kGroupChunk <= n) {
+            bulk_prefetch_l2(src + nb, (u32)(kGroupChunk * 4));
+            bulk_prefetch_l2(dst + nb, (u32)(kGroupChunk * 4));
         }
         u64 key[kSplitItems];
         u32 valid = 0;
-        if (vec && n - base >= kSplitChunk) {
+        if (vec && n - base >= kGroupChunk) {
             valid = (1u << kSplitItems) - 1;
 #pragma unroll
             for (int h = 0; h < kSplitItems / 4; ++h) {
-                const u64 i = base + (u64)h * (4 * kSplitThreads) + 4 * t;
+                const u64 i = base + (u64)h * (4 * kGroupThreads) + 4 * tg;
                 const uint4 a = __ldg(reinterpret_cast<const uint4*>(src + i));
                 const uint4 b = __ldg(reinterpret_cast<const uint4*>(dst + i));
                 key[4 * h + 0] = pack_key(a.x, b.x);
@@ -508,7 +526,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1024 / kSplitThreads) k_hot_spl
         } else {
 #pragma unroll
             for (int u = 0; u < kSplitItems; ++u) {
-                const u64 i = base + (u64)u * kSplitThreads + t;
+                const u64 i = base + (u64)u * kGroupThreads + tg;
                 key[u] = i < n ? pack_key(__ldg(src + i), __ldg(dst + i)) : 0;
                 valid |= (i < n ? 1u : 0u) << u;
             }
@@ -574,11 +592,11 @@ __global__ void __launch_bounds__(kSplitThreads, 1024 / kSplitThreads) k_hot_spl
             bal[u] = __ballot_sync(FULL, (coldm >> u) & 1u);
             wtot += __popc(bal[u]);
         }
-        if (lane == 0) sm.wsum[w] = wtot;
-        __syncthreads();
-        if (w == 0) {  // exclusive scan of the warp counts (one warp), and the CTA's reservation
-            constexpr u32 kW = kSplitThreads / 32;
-            const u32 v = lane < kW ? sm.wsum[lane] : 0u;
+        if (lane == 0) sm.wsum[g][w] = wtot;
+        group_sync(g);
+        if (w == 0) {  // exclusive scan of the warp counts (one warp), and the group's reservation
+            constexpr u32 kW = kGroupThreads / 32;
+            const u32 v = lane < kW ? sm.wsum[g][lane] : 0u;
             u32 x = v;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -586,17 +604,17 @@ __global__ void __launch_bounds__(kSplitThreads, 1024 / kSplitThreads) k_hot_spl
                 if (lane >= (u32)o) x += y;
             }
             const u32 run = __shfl_sync(FULL, x, 31);
-            if (lane < kW) sm.wsum[lane] = x - v;
-            if (lane == 0) sm.base = run ? atomicAdd(&sd->cold, (u64)run) : 0;
+            if (lane < kW) sm.wsum[g][lane] = x - v;
+            if (lane == 0) sm.base[g] = run ? atomicAdd(&sd->cold, (u64)run) : 0;
         }
-        __syncthreads();
-        u64 off = sm.base + sm.wsum[w];
+        group_sync(g);
+        u64 off = sm.base[g] + sm.wsum[g][w];
 #pragma unroll
         for (int u = 0; u < kSplitItems; ++u) {
             if ((coldm >> u) & 1u) cold[off + __popc(bal[u] & lt)] = key[u];
             off += __popc(bal[u]);
         }
-        __syncthreads();  // wsum and base are rewritten by the next chunk
+        group_sync(g);  // wsum and base are rewritten by the group's next chunk
     }
     __syncthreads();
     split_flush(sm, sd);
@@ -788,7 +806,7 @@ void sort_links_split(const u32* src, const u32* dst, u64 n, u64* kb[2], u64* he
     {
         const size_t smem = sizeof(SplitSmem);
         const int grid = resident_ctas_of((const void*)k_hot_split, kSplitThreads, smem);
-        const u64 chunks = (n + kSplitChunk - 1) / kSplitChunk;
+        const u64 chunks = (n + kGroups * kGroupChunk - 1) / (kGroups * kGroupChunk);
         const bool vec = (((uintptr_t)src | (uintptr_t)dst) & 15) == 0;
         TraceScope ts(tr, "k_hot_split", s);
         k_hot_split<<<(unsigned)std::min<u64>(chunks, (u64)grid), kSplitThreads, smem, s>>>(src, dst, n, vec, sd,
