@@ -438,9 +438,13 @@ __global__ void k_warm_fp(SplitDev* sd) {
 #define NS_SPLIT_THREADS (NS_WARM_BUCKETS > 0 ? 1024 : 512)
 #endif
 constexpr int kSplitThreads = NS_SPLIT_THREADS;
-constexpr int kGroupThreads = 512;
+#ifndef NS_SPLIT_GROUP
+#define NS_SPLIT_GROUP 128
+#endif
+constexpr int kGroupThreads = NS_SPLIT_GROUP;  // 128 (eight groups) measured fastest at 2^30 packets
 constexpr int kGroups = kSplitThreads / kGroupThreads;
-static_assert(kGroups >= 1 && kGroups * kGroupThreads == kSplitThreads, "groups of 512 threads");
+static_assert(kGroups >= 1 && kGroups <= 15 && kGroups * kGroupThreads == kSplitThreads && kGroupThreads % 32 == 0,
+              "whole warps per group; named barriers 1..15");
 constexpr int kSplitItems = 8;
 constexpr u64 kGroupChunk = (u64)kGroupThreads * kSplitItems;
 constexpr u64 kDrainChunks = (1ull << 31) / (2 * kGroups * kGroupChunk);
