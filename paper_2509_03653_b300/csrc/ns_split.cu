@@ -242,24 +242,57 @@ __global__ void __launch_bounds__(1024) k_hot_hist(const u64* __restrict__ pos, 
 // kHotMax keys occur t1 or more times.  Tier 2 continues downwards from the
 // first count that tier 1 could not take: the least t2 >= kMinWarmSample
 // such that at most kWarmMax keys occur at least t2 and fewer than t1
-// times.  An empty tier has threshold 2^64 - 1.
-__global__ void k_hot_pick(SplitDev* sd) {
-    if (threadIdx.x != 0) return;
-    u64 cum = 0, t1 = kEmpty;
-    u32 b = kHotBins - 1;
-    for (; b >= kMinHotSample; --b) {
-        if (cum + sd->hist[b] > (u64)kHotMax) break;
-        cum += sd->hist[b];
-        if (cum) t1 = b;
+// times.  An empty tier has threshold 2^64 - 1.  One CTA: with S[b] the
+// number of sample keys seen b or more times (a suffix sum over the bins),
+// tier 1 stops below the largest b with S[b] > kHotMax, tier 2 likewise
+// with the counts below tier 1's.
+constexpr int kPickThreads = 1024;
+static_assert(kHotBins == 2 * kPickThreads, "two bins per thread");
+__global__ void __launch_bounds__(kPickThreads) k_hot_pick(SplitDev* sd) {
+    __shared__ u64 S[kHotBins + 1];
+    __shared__ u32 cut1, cut2;  // 1 + the largest bin over the limit, 0 = none
+    const u32 t = threadIdx.x;
+    for (u32 b = t; b < kHotBins; b += kPickThreads) S[b] = sd->hist[b];
+    if (t == 0) {
+        S[kHotBins] = 0;
+        cut1 = 0;
+        cut2 = 0;
     }
-    u64 cum2 = 0, t2 = kEmpty;
-    for (; kWarmBuckets > 0 && b >= kMinWarmSample; --b) {
-        if (cum2 + sd->hist[b] > (u64)kWarmMax) break;
-        cum2 += sd->hist[b];
-        if (cum2) t2 = b;
+    __syncthreads();
+    for (u32 o = 1; o < (u32)kHotBins; o <<= 1) {  // S[b] += S[b + o], Hillis-Steele
+        u64 v[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const u32 b = t + q * kPickThreads;
+            v[q] = b + o < (u32)kHotBins ? S[b + o] : 0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 2; ++q) S[t + q * kPickThreads] += v[q];
+        __syncthreads();
     }
-    sd->thresh = t1;
-    sd->thresh2 = t2;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const u32 b = t + q * kPickThreads;
+        if (b >= kMinHotSample && S[b] > (u64)kHotMax) atomicMax(&cut1, b + 1);
+    }
+    __syncthreads();
+    // tier 1 takes the bins from L up; tier 2 looks at [kMinWarmSample, L)
+    const u32 L = cut1 ? cut1 : kMinHotSample;  // cut1 = largest bin over the limit, + 1
+    const u64 above = S[L];                        // keys tier 1 takes (L <= kHotBins)
+    if (kWarmBuckets > 0) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const u32 b = t + q * kPickThreads;
+            if (b >= kMinWarmSample && b < L && S[b] - above > (u64)kWarmMax) atomicMax(&cut2, b + 1);
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        sd->thresh = (L < (u32)kHotBins && above > 0) ? (u64)L : kEmpty;
+        const u32 L2 = cut2 ? cut2 : kMinWarmSample;
+        sd->thresh2 = (kWarmBuckets > 0 && L2 < L && S[L2] - above > 0) ? (u64)L2 : kEmpty;
+    }
 }
 
 // 2c. The candidates of each tier, in any order.
@@ -290,7 +323,8 @@ __global__ void __launch_bounds__(kTableThreads, 1) k_hot_table(SplitDev* sd) {
     for (int i = threadIdx.x; i < kHotPad; i += kTableThreads) keys[i] = (u64)i < H ? sd->hot[i] : kEmpty;
     for (int i = threadIdx.x; i < kHotSlots; i += kTableThreads) table[i] = kEmpty;
     __syncthreads();
-    for (int k = 2; k <= kHotPad; k <<= 1) {
+    // (with tier 2 the hot list is sorted after both tiers are placed)
+    for (int k = 2; kWarmBuckets == 0 && k <= kHotPad; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
             for (int i = threadIdx.x; i < kHotPad; i += kTableThreads) {
                 const int p = i ^ j;
@@ -788,17 +822,30 @@ void sort_links_split(const u32* src, const u32* dst, u64 n, u64* kb[2], u64* he
     launch_runs(RUN_U64, false, kb[r], nullptr, m, nullptr, heads, pos, nullptr, &sd->R_sample, sc, st, s);
     // 2. the hot set and its table
     {
-        TraceScope ts(tr, "k_hot_select", s);
+        TraceScope ts(tr, "k_hot_hist", s);
         k_hot_hist<<<sms, 1024, 0, s>>>(pos, sd);
-        k_hot_pick<<<1, 32, 0, s>>>(sd);
+    }
+    {
+        TraceScope ts(tr, "k_hot_pick", s);
+        k_hot_pick<<<1, kPickThreads, 0, s>>>(sd);
+    }
+    {
+        TraceScope ts(tr, "k_hot_collect", s);
         k_hot_collect<<<sms * 2, 256, 0, s>>>(heads, pos, sd);
+    }
+    {
+        TraceScope ts(tr, "k_hot_table", s);
         const size_t tsmem = sizeof(u64) * (kHotPad + kHotSlots);
         resident_ctas_of((const void*)k_hot_table, kTableThreads, tsmem);  // sets its shared-memory size
         k_hot_table<<<1, kTableThreads, tsmem, s>>>(sd);
-        if (kWarmBuckets > 0) {
+    }
+    if (kWarmBuckets > 0) {
+        {
+            TraceScope ts(tr, "k_warm_insert", s);
             k_warm_insert<<<(kWarmMax + 255) / 256, 256, 0, s>>>(sd);
-            k_warm_fp<<<(kWarmBuckets + 255) / 256, 256, 0, s>>>(sd);
         }
+        TraceScope ts(tr, "k_warm_fp", s);
+        k_warm_fp<<<(kWarmBuckets + 255) / 256, 256, 0, s>>>(sd);
     }
     if (kWarmBuckets > 0) {
         // the hot list ascending: both tiers' keys sorted together (kb is

@@ -153,3 +153,44 @@ def test_split_second_tier_takes_warm_keys():
     info = check(ctx, s, d)
     assert info["hot_keys"] > 6144
     ctx.close()
+
+
+def test_split_tiers_with_tied_sample_counts():
+    """60,000 links of exactly 32 packets each, shuffled into uniform filler:
+    the sample sees them all about equally often, so the tier thresholds
+    fall inside a histogram bin's ties; whatever each tier takes, A is
+    exact."""
+    rng = np.random.default_rng(5)
+    k = 60000
+    hs = rng.integers(0, 1 << 32, k, dtype=np.uint64).astype(np.uint32)
+    hd = rng.integers(0, 1 << 32, k, dtype=np.uint64).astype(np.uint32)
+    n = 1 << 21
+    s = np.empty(n, np.uint32)
+    d = np.empty(n, np.uint32)
+    s[:32 * k] = np.repeat(hs, 32)
+    d[:32 * k] = np.repeat(hd, 32)
+    s[32 * k:] = rng.integers(0, 1 << 32, n - 32 * k, dtype=np.uint64).astype(np.uint32)
+    d[32 * k:] = rng.integers(0, 1 << 32, n - 32 * k, dtype=np.uint64).astype(np.uint32)
+    p = rng.permutation(n)
+    s, d = s[p], d[p]
+    ctx = ns.Context(0, path="sort", sort_split="on")
+    info = check(ctx, s, d)
+    assert info["hot_keys"] > 6144 and info["cold_packets"] < n
+    ctx.close()
+
+
+def test_split_extreme_keys_in_second_tier():
+    """Keys 0 and 2^64 - 1 at middling frequency (one packet in 500 each),
+    below the heaviest links: 0 can be a tier-2 key, 2^64 - 1 never is (it
+    marks free slots), and both still count exactly."""
+    n = 1 << 22
+    s, d = W.zipf_window(n, 1.2, 1 << 16, 23)
+    s, d = s.copy(), d.copy()
+    s[::500] = 0xFFFFFFFF
+    d[::500] = 0xFFFFFFFF
+    s[7::500] = 0
+    d[7::500] = 0
+    ctx = ns.Context(0, path="sort", sort_split="on")
+    info = check(ctx, s, d)
+    assert info["hot_keys"] > 6144
+    ctx.close()
