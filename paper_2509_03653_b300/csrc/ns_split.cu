@@ -2,13 +2,14 @@
 //
 // Under skewed traffic a small set of links carries a large share of the
 // packets (Zipf(1.2) over 2^24 addresses per column: the 6144 heaviest of
-// ~1.5e8 distinct links carry about half of 2^30 packets).  Sorting their
+// ~1.5e8 distinct links carry about half of 2^30 packets, the 60,000
+// heaviest about 62%).  Sorting their
 // copies is wasted work: every copy travels through all eight digit passes
 // only to be counted by the run kernel.  So, before the sort:
 //
-//   1. sample: 64 evenly spaced blocks of consecutive packets (2^21 packets
-//      at most) are packed into keys, sorted and cut into runs with the sort
-//      path's own kernels;
+//   1. sample: 64 evenly spaced blocks of consecutive packets (a quarter of
+//      the window, kSampleMax packets at most) are packed into keys, sorted
+//      and cut into runs with the sort path's own kernels;
 //   2. select: the keys seen most often in the sample become the hot set,
 //      in two tiers.  Tier 1: the keys seen at least kMinHotSample times,
 //      the most frequent first, up to kHotMax of them, go into a cuckoo
@@ -65,19 +66,24 @@ constexpr int kHotPad = kHotSlots;          // the bitonic sort's power-of-two l
 constexpr int kMaxKicks = 500;
 constexpr u64 kEmpty = ~0ull;  // an empty slot (never a hot key)
 constexpr int kSampleBlocks = 64;
-constexpr u64 kSampleMax = 1ull << 21;
+#ifndef NS_SAMPLE_LOG2
+#define NS_SAMPLE_LOG2 23
+#endif
+constexpr u64 kSampleMax = 1ull << NS_SAMPLE_LOG2;
 constexpr u32 kHotBins = 2048;      // sample run lengths, the last bin holding >= kHotBins - 1
 constexpr u32 kMinHotSample = 4;    // fewest sample occurrences of a tier-1 key
 static_assert(kSampleMax / (kHotBins - 1) < (u64)kHotMax, "the top bin alone never exceeds the hot set");
 
 // Tier 2: kWarmBuckets buckets of kWays slots in global memory, at most
-// kWarmMax keys (load <= 5/8, placed without evictions).
+// kWarmMax keys (load <= 5/8, placed without evictions).  Any multiple of
+// 256 buckets: a key's bucket is a 32-bit hash scaled to [0, kWarmBuckets)
+// (multiply-high), so the count is set by the shared memory the split
+// kernel has left for tier 2's fingerprint words, not by a power of two.
 #ifndef NS_WARM_BUCKETS
-#define NS_WARM_BUCKETS 16384
+#define NS_WARM_BUCKETS 23552
 #endif
-constexpr int kWarmBuckets = NS_WARM_BUCKETS;  // a power of two, 0 turns tier 2 off
-constexpr int kWarmBits = kWarmBuckets == 0 ? 0 : kWarmBuckets == 8192 ? 13 : kWarmBuckets == 16384 ? 14 : -1;
-static_assert(kWarmBits >= 0, "kWarmBuckets: 0, 8192 or 16384");
+constexpr int kWarmBuckets = NS_WARM_BUCKETS;  // 0 turns tier 2 off
+static_assert(kWarmBuckets >= 0 && kWarmBuckets % 256 == 0, "kWarmBuckets: a multiple of 256");
 constexpr int kWarmSlots = kWarmBuckets * kWays;
 constexpr int kWarmMax = kWarmSlots / 8 * 5;
 constexpr u32 kMinWarmSample = 2;   // fewest sample occurrences of a tier-2 key
@@ -126,11 +132,12 @@ __device__ __forceinline__ u32 bucket2_of_mix(u32 x, u32 b1) {
     return b == b1 ? b ^ 1u : b;
 }
 __device__ __forceinline__ u32 bucket2(u64 key, u32 b1) { return bucket2_of_mix(key_mix(key), b1); }
-// The two tier-2 buckets of a key (from the same mix, other multipliers).
-__device__ __forceinline__ u32 warm_bucket1(u32 x) { return (x * 0x85EBCA6Bu) >> (32 - kWarmBits); }
+// The two tier-2 buckets of a key (from the same mix, other multipliers,
+// scaled to the bucket count), never the same one.
+__device__ __forceinline__ u32 warm_bucket1(u32 x) { return __umulhi(x * 0x85EBCA6Bu, (u32)kWarmBuckets); }
 __device__ __forceinline__ u32 warm_bucket2(u32 x, u32 b1) {
-    const u32 b = (x * 0xCC9E2D51u) >> (32 - kWarmBits);
-    return b == b1 ? b ^ 1u : b;
+    const u32 b = __umulhi(x * 0xCC9E2D51u, (u32)kWarmBuckets);
+    return b != b1 ? b : (b + 1 == (u32)kWarmBuckets ? 0u : b + 1);
 }
 
 // Slot of `key` in the table, or -1.  kEmpty, the mark of a free slot, is

@@ -82,6 +82,34 @@ def test_sorted_list_matrix_and_empty_matrix_round_trip(tmp_path):
     ctx.close()
 
 
+def test_load_on_a_side_stream(tmp_path):
+    """Loading on a non-blocking stream: the entries' copies are ordered
+    with the insert that reads them, so the loaded matrix is exact however
+    busy the device is (a large kernel is queued on the same stream first)."""
+    import torch
+
+    ctx = ns.Context(0, path="hash")
+    s, d = W.rmat_stream(1 << 20)
+    m = ns.Matrix(ctx)
+    ns.window_build(ctx, to_dev(s), to_dev(d), m)
+    ck = str(tmp_path / "side.nsm")
+    ns.matrix_save(m, ck)
+    want = oracle.build_matrix(s, d)
+    side = torch.cuda.Stream()
+    busy = torch.empty(1 << 26, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        r = ns.Matrix(ctx)
+        with torch.cuda.stream(side):
+            busy.uniform_()  # keeps the side stream busy ahead of the load
+            ns.matrix_load(ctx, ck, r, stream=side)
+            got = ns.network_stats(ctx, r, stream=side)
+        assert got == oracle.stats(*want)
+        assert_matrix_equal(r, *want)
+        r.free()
+    m.free()
+    ctx.close()
+
+
 def test_malformed_checkpoints_are_rejected(tmp_path):
     ctx = ns.Context(0, path="hash")
     s, d = W.single_window(20000)
