@@ -155,7 +155,7 @@ int radix_sort_pairs64(const u64* keys, const u64* vals, const u64* n_dev,
 // first pass keeps none); returns the index of the buffer holding the result.
 // Keys-only sorts below share this: only the sorted bits are ordered.
 int radix_sort_hi32(const u64* packed, const u64* n_dev, u64* kbuf[2], u64 n, SortScratch& sc, DevStats* st,
-                    cudaStream_t s);
+                    cudaStream_t s, const char* trace_name = nullptr);
 // n_dev (<= n) uint32 keys (four 8-bit digit passes).
 int radix_sort_u32(const u32* keys, const u64* n_dev, u32* kbuf[2], u64 n, SortScratch& sc, DevStats* st,
                    cudaStream_t s);

@@ -1231,12 +1231,12 @@ int radix_sort_lo32(const u64* keys, const u64* n_dev, u64* kbuf[2], u64 n, Sort
 }
 
 int radix_sort_hi32(const u64* packed, const u64* n_dev, u64* kbuf[2], u64 n, SortScratch& sc, DevStats* st,
-                    cudaStream_t s) {
+                    cudaStream_t s, const char* trace_name) {
     SortIn in{};
     in.keys = packed;
     in.n_dev = (const u64*)n_dev;
     in.bulk = ((uintptr_t)packed & 15) == 0;
-    in.trace_name = "k_onesweep<u64 key, by dst>";
+    in.trace_name = trace_name ? trace_name : "k_onesweep<u64 key, by dst>";
     u64* vb[2] = {nullptr, nullptr};
     return radix_sort_t<u64, false, LOAD_KEYS>(in, (u64**)kbuf, vb, n, 32, 4, sc, st, s);
 }

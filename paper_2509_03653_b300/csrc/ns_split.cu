@@ -8,8 +8,13 @@
 // only to be counted by the run kernel.  So, before the sort:
 //
 //   1. sample: 64 evenly spaced blocks of consecutive packets (a quarter of
-//      the window, kSampleMax packets at most) are packed into keys, sorted
-//      and cut into runs with the sort path's own kernels;
+//      the window, kSampleMax packets at most) are packed into keys, each
+//      scrambled by an invertible multiplication, sorted by the upper half of
+//      the scrambled word alone (four digit passes) and cut into runs of
+//      equal words with the sort path's own kernels.  Only the grouping
+//      matters here: two distinct keys interleave only if their scrambled
+//      upper halves coincide, which splits their sample counts and at worst
+//      keeps them out of the hot set;
 //   2. select: the keys seen most often in the sample become the hot set,
 //      in two tiers.  Tier 1: the keys seen at least kMinHotSample times,
 //      the most frequent first, up to kHotMax of them, go into a cuckoo
@@ -36,7 +41,10 @@
 // same list, since a key's count is the sum of its hot and cold occurrences
 // and a hot key has no cold occurrence.  The sample only decides how much
 // work the split saves.  Every hot key occurs in the input (the sample is
-// drawn from it), so every hot count is at least 1.
+// drawn from it), so every hot count is at least 1.  Each hot key holds
+// exactly one slot in one of the two tables, however often it appears among
+// the candidates, and the hot list is read from the tables' slots, so no key
+// is listed twice.
 #include <algorithm>
 #include <cstddef>
 
@@ -62,7 +70,7 @@ constexpr int kBucketBits = kBuckets == 1024 ? 10 : kBuckets == 2048 ? 11 : kBuc
 static_assert(kBucketBits && (1 << kBucketBits) == kBuckets, "kBuckets: 1024, 2048 or 4096");
 constexpr int kHotSlots = kBuckets * kWays;
 constexpr int kHotMax = kHotSlots / 4 * 3;  // hot keys at most: table load <= 3/4
-constexpr int kHotPad = kHotSlots;          // the bitonic sort's power-of-two length (>= kHotMax)
+constexpr int kHotPad = kHotSlots;          // candidates plus room for the left-over ones (>= kHotMax)
 constexpr int kMaxKicks = 500;
 constexpr u64 kEmpty = ~0ull;  // an empty slot (never a hot key)
 constexpr int kSampleBlocks = 64;
@@ -218,14 +226,21 @@ __device__ __forceinline__ int warm_find(const u32* __restrict__ fpw, const u64*
 
 __device__ __forceinline__ u64 pack_key(u32 s, u32 d) { return ((u64)s << 32) | (u64)d; }
 
-// 1. The sample: packets [b * (n / 64), + blen) of each block b, packed.
+// The sample's scramble: multiplication by an odd constant modulo 2^64 (a
+// bijection whose upper half depends on every bit of the key), and its
+// inverse (the constant's multiplicative inverse modulo 2^64).
+constexpr u64 kScramble = 0x9E3779B97F4A7C15ull;
+constexpr u64 kUnscramble = 0xF1DE83E19937733Dull;
+static_assert(kScramble * kUnscramble == 1ull, "inverse modulo 2^64");
+
+// 1. The sample: packets [b * (n / 64), + blen) of each block b, packed and scrambled.
 __global__ void k_sample_gather(const u32* __restrict__ src, const u32* __restrict__ dst, u64 n, u64 blen,
                                 u64* __restrict__ out) {
     const u64 m = blen * kSampleBlocks;
     const u64 stride = n / kSampleBlocks;
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (u64)gridDim.x * blockDim.x) {
         const u64 p = (i / blen) * stride + (i % blen);
-        out[i] = pack_key(__ldg(src + p), __ldg(dst + p));
+        out[i] = pack_key(__ldg(src + p), __ldg(dst + p)) * kScramble;
     }
 }
 
@@ -306,7 +321,7 @@ __global__ void __launch_bounds__(kPickThreads) k_hot_pick(SplitDev* sd) {
 __global__ void k_hot_collect(const u64* __restrict__ heads, const u64* __restrict__ pos, SplitDev* sd) {
     const u64 R = sd->R_sample, t1 = sd->thresh, t2 = sd->thresh2;
     for (u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (u64)gridDim.x * blockDim.x) {
-        const u64 key = heads[r], len = pos[r + 1] - pos[r];
+        const u64 key = heads[r] * kUnscramble, len = pos[r + 1] - pos[r];
         if (key == kEmpty) continue;
         if (len >= t1) {
             const u64 i = atomicAdd(&sd->H1, 1ull);
@@ -318,35 +333,21 @@ __global__ void k_hot_collect(const u64* __restrict__ heads, const u64* __restri
     }
 }
 
-// 2d. One CTA: sorts the hot keys (bitonic, in shared memory), places them
-// in the cuckoo table (one thread, in ascending order), keeps in the hot
-// list only the keys that found a place, and clears the per-slot counts.
+// 2d. One CTA: places the tier-1 candidates in the cuckoo table, writes the
+// keys that found a slot to the head of the hot list (in slot order; the
+// list is sorted once both tiers are placed) and clears the per-slot counts.
+// A candidate list may hold a key more than once (a key whose sample
+// occurrences were not all adjacent); every copy probes the same slots in
+// the same order, so a copy that finds its own key there stops, and each
+// key holds one slot at most.
 constexpr int kTableThreads = 1024;
 __global__ void __launch_bounds__(kTableThreads, 1) k_hot_table(SplitDev* sd) {
     extern __shared__ __align__(16) u64 sh[];
-    u64* keys = sh;              // [kHotPad]
+    u64* keys = sh;              // [kHotPad]: the candidates, then the left-over ones at the end
     u64* table = sh + kHotPad;   // [kHotSlots]
     const u64 H = sd->H1 < (u64)kHotMax ? sd->H1 : (u64)kHotMax;
     for (int i = threadIdx.x; i < kHotPad; i += kTableThreads) keys[i] = (u64)i < H ? sd->hot[i] : kEmpty;
     for (int i = threadIdx.x; i < kHotSlots; i += kTableThreads) table[i] = kEmpty;
-    __syncthreads();
-    // (with tier 2 the hot list is sorted after both tiers are placed)
-    for (int k = 2; kWarmBuckets == 0 && k <= kHotPad; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < kHotPad; i += kTableThreads) {
-                const int p = i ^ j;
-                if (p > i) {
-                    const bool up = (i & k) == 0;
-                    const u64 a = keys[i], b = keys[p];
-                    if ((a > b) == up) {
-                        keys[i] = b;
-                        keys[p] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
     // first, in parallel: every key takes a free slot of its first bucket,
     // else of its second (compare-and-swap on the slot); the few that find
     // both buckets full are left to the evicting insertion below
@@ -356,13 +357,14 @@ __global__ void __launch_bounds__(kTableThreads, 1) k_hot_table(SplitDev* sd) {
     for (int i = threadIdx.x; i < (int)H; i += kTableThreads) {
         const u64 key = keys[i];
         const u32 b1 = bucket1(key), b2 = bucket2(key, b1);
-        bool placed = false;
-        for (int q = 0; q < 2 * kWays && !placed; ++q) {
+        bool done = false;  // placed, or found placed by another copy
+        for (int q = 0; q < 2 * kWays && !done; ++q) {
             const u32 slot = 4 * (q < kWays ? b1 : b2) + (q & (kWays - 1));
-            placed = atomicCAS(reinterpret_cast<unsigned long long*>(&table[slot]), kEmpty, key) == kEmpty;
+            const u64 old = atomicCAS(reinterpret_cast<unsigned long long*>(&table[slot]), kEmpty, key);
+            done = old == kEmpty || old == key;
         }
-        if (!placed) {
-            // the left-over keys go after the sorted ones (index >= H); one
+        if (!done) {
+            // the left-over keys go after the candidates (index >= H); one
             // that finds no room there stays cold
             const u32 j = atomicAdd(&n_left, 1u);
             if ((u64)j < (u64)kHotPad - H) keys[kHotPad - 1 - j] = key;
@@ -373,6 +375,7 @@ __global__ void __launch_bounds__(kTableThreads, 1) k_hot_table(SplitDev* sd) {
         const u32 left = (u64)n_left < (u64)kHotPad - H ? n_left : (u32)((u64)kHotPad - H);
         for (u32 i = 0; i < left; ++i) {
             u64 cur = keys[kHotPad - 1 - i];
+            if (hot_find(table, cur) >= 0) continue;  // another copy is already in
             for (int kick = 0; kick < kMaxKicks && cur != kEmpty; ++kick) {
                 const u32 b1 = bucket1(cur), b2 = bucket2(cur, b1);
                 int free_slot = -1;
@@ -397,21 +400,21 @@ __global__ void __launch_bounds__(kTableThreads, 1) k_hot_table(SplitDev* sd) {
         }
     }
     __syncthreads();
-    // the hot list: the sorted keys that have a slot, in order (a block-wide
-    // ordered compaction, kTableThreads keys per round)
+    // the hot list's head: the table's keys, in slot order (a block-wide
+    // ordered compaction, kTableThreads slots per round)
     __shared__ u32 wcount[kTableThreads / 32];
     __shared__ u32 kept;
     if (threadIdx.x == 0) kept = 0;
     __syncthreads();
-    for (u64 r = 0; r < H; r += kTableThreads) {
-        const u64 i = r + threadIdx.x;
-        const bool keep = i < H && hot_find(table, keys[i]) >= 0;
+    for (int r = 0; r < kHotSlots; r += kTableThreads) {
+        const int i = r + threadIdx.x;
+        const bool keep = table[i] != kEmpty;
         const u32 bal = __ballot_sync(0xFFFFFFFFu, keep);
         if ((threadIdx.x & 31) == 0) wcount[threadIdx.x >> 5] = __popc(bal);
         __syncthreads();
         u32 before = kept;
         for (u32 w = 0; w < (threadIdx.x >> 5); ++w) before += wcount[w];
-        if (keep) sd->list[before + __popc(bal & lanemask_lt())] = keys[i];
+        if (keep) sd->list[before + __popc(bal & lanemask_lt())] = table[i];
         __syncthreads();
         if (threadIdx.x == 0) {
             u32 t = 0;
@@ -433,17 +436,22 @@ __global__ void __launch_bounds__(kTableThreads, 1) k_hot_table(SplitDev* sd) {
 // 2e. Tier 2, many CTAs: each candidate takes a free slot of its first
 // tier-2 bucket, else of its second (compare-and-swap), and is appended to
 // the hot list after the tier-1 keys; one that finds both buckets full
-// stays cold.  The table starts all free and the counts zero.
+// stays cold.  A key already in tier 1, or a copy that finds its own key
+// placed (every copy probes the same slots in the same order), is skipped.
+// The table starts all free and the counts zero.
 __global__ void k_warm_insert(SplitDev* sd) {
     const u64 W = sd->W < (u64)kWarmMax ? sd->W : (u64)kWarmMax, H1 = sd->H1;
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < W; i += (u64)gridDim.x * blockDim.x) {
         const u64 key = sd->warm[i];
+        if (hot_find(sd->table, key) >= 0) continue;
         const u32 x = key_mix(key);
         const u32 b1 = warm_bucket1(x), b2 = warm_bucket2(x, b1);
-        bool placed = false;
-        for (int q = 0; q < 2 * kWays && !placed; ++q) {
+        bool placed = false, done = false;
+        for (int q = 0; q < 2 * kWays && !done; ++q) {
             const u32 slot = 4 * (q < kWays ? b1 : b2) + (q & (kWays - 1));
-            placed = atomicCAS(reinterpret_cast<unsigned long long*>(&sd->table2[slot]), kEmpty, key) == kEmpty;
+            const u64 old = atomicCAS(reinterpret_cast<unsigned long long*>(&sd->table2[slot]), kEmpty, key);
+            placed = old == kEmpty;
+            done = placed || old == key;
         }
         if (placed) sd->list[H1 + atomicAdd(&sd->W2, 1ull)] = key;
     }
@@ -825,7 +833,7 @@ void sort_links_split(const u32* src, const u32* dst, u64 n, u64* kb[2], u64* he
         TraceScope ts(tr, "k_sample_gather", s);
         k_sample_gather<<<sms * 4, 256, 0, s>>>(src, dst, n, blen, kb[1]);
     }
-    const int r = radix_sort_keys64(kb[1], nullptr, kb, m, sc, st, s, "k_onesweep<sample key>");
+    const int r = radix_sort_hi32(kb[1], nullptr, kb, m, sc, st, s, "k_onesweep<sample key>");
     launch_runs(RUN_U64, false, kb[r], nullptr, m, nullptr, heads, pos, nullptr, &sd->R_sample, sc, st, s);
     // 2. the hot set and its table
     {
@@ -854,7 +862,7 @@ void sort_links_split(const u32* src, const u32* dst, u64 n, u64* kb[2], u64* he
         TraceScope ts(tr, "k_warm_fp", s);
         k_warm_fp<<<(kWarmBuckets + 255) / 256, 256, 0, s>>>(sd);
     }
-    if (kWarmBuckets > 0) {
+    {
         // the hot list ascending: both tiers' keys sorted together (kb is
         // free until the split writes the cold keys)
         const int rl = radix_sort_keys64(sd->list, &sd->H, kb, kListMax, sc, st, s, "k_onesweep<hot list>");

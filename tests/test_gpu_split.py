@@ -194,3 +194,30 @@ def test_split_extreme_keys_in_second_tier():
     info = check(ctx, s, d)
     assert info["hot_keys"] > 6144
     ctx.close()
+
+
+def test_split_interleaved_sample_runs_are_harmless():
+    """The sample is grouped by the upper half of each key times an odd
+    constant c (mod 2^64).  For keys k + t c^-1 (t = 0, 1, 2) those products
+    differ by t and share their upper half, so their sample occurrences
+    interleave and each such key can become a candidate more than once, in
+    one tier or in both.  Groups of them at frequencies spanning both tiers
+    and the cold range: A stays exact."""
+    c_inv = 0xF1DE83E19937733D  # the inverse of the sample's multiplier modulo 2^64
+    rng = np.random.default_rng(11)
+    n = 1 << 21
+    keys = []
+    for g in range(40):
+        k = int(rng.integers(1, 1 << 62))
+        f = max(8, int(20000 * 0.82 ** g))
+        for t in range(3):
+            keys += [(k + t * c_inv) % (1 << 64)] * f
+    keys = np.array(keys, dtype=np.uint64)
+    fill = rng.integers(0, 1 << 63, n - keys.size, dtype=np.uint64)
+    allk = np.concatenate([keys, fill])[rng.permutation(n)]
+    s = (allk >> np.uint64(32)).astype(np.uint32)
+    d = (allk & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    ctx = ns.Context(0, path="sort", sort_split="on")
+    info = check(ctx, s, d)
+    assert info["hot_keys"] > 0
+    ctx.close()
