@@ -379,6 +379,14 @@ ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n,
                 (u64*)c->pos.p, (u64*)c->psum.p, runs_out, c->sc, st, s, packed);
     launch_run_stats(RS_ROWS, (const u64*)c->pos.p, (const u64*)c->psum.p, runs_out, n,
                      nullptr, st, c->sms, &c->tracer, s);
+    if (packed_cols && c->last_split) {
+        // columns with the hot-destination split: the heaviest sampled
+        // destinations are counted apart, only the other words are sorted
+        TRY(buf_reserve(c->colsplit, col_split_state_bytes()));
+        col_split_runs(packed, nnz, n, kb, (u64*)c->pos.p, (u64*)c->psum.p, c->colsplit.p, runs_out + 1, c->sc, st,
+                       c->sms, s);
+        return check_launch();
+    }
     if (packed_cols) {
         // columns: the words (dst << 32 | count) sorted by dst, then runs of
         // equal dst (the reverse operations)
@@ -555,7 +563,7 @@ void ns_destroy(ns_ctx* c) {
     cudaDeviceSynchronize();
     Buf* all[] = {&c->ghist, &c->offs, &c->tcount, &c->counters, &c->status, &c->k64[0], &c->k64[1],
                   &c->pos, &c->psum, &c->k32[0], &c->k32[1], &c->v64[0], &c->v64[1], &c->xk, &c->xv,
-                  &c->stage[0], &c->stage[1], &c->split};
+                  &c->stage[0], &c->stage[1], &c->split, &c->colsplit};
     for (Buf* b : all) buf_free_on(*b, c->last_stream);
     if (c->host_stats) cudaFreeHost(c->host_stats);  // used only by blocking reads, all complete
     tracer_destroy(&c->tracer);

@@ -118,6 +118,7 @@ struct ns_ctx {
     cudaStream_t last_stream = nullptr;
     ns::Buf stage[2];  // device copies of host columns (ns_window_build_host)
     ns::Buf split;     // the hot-key split's device state
+    ns::Buf colsplit;  // the hot-destination split's device state
     bool last_split = false;  // the last sort-path build split
     ns::DevStats* host_stats = nullptr;  // pinned
     ns::Tracer tracer;

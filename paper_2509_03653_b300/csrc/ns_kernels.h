@@ -90,6 +90,11 @@ u64 split_state_bytes();
 void sort_links_split(const u32* src, const u32* dst, u64 n, u64* kb[2], u64* heads, u64* pos, void* state,
                       u64* keys_out, u64* counts_out, SortScratch& sc, DevStats* st, int sms, cudaStream_t s);
 cudaError_t split_info(const void* state, u64* hot_keys, u64* cold_packets, cudaStream_t s);
+// the column side's hot-destination split (ns_colsplit.cu)
+u64 col_split_state_bytes();
+void col_split_runs(const u64* words, const u64* nnz, u64 n, u64* kb[2], u64* pos, u64* psum, void* state,
+                    u64* runs_out, SortScratch& sc, DevStats* st, int sms, cudaStream_t s);
+cudaError_t col_split_info(const void* state, u64* hot, u64* cold, cudaStream_t s);
 void launch_diag_wait(int which, u64* status_word, DevStats* st, cudaStream_t s);
 void launch_diag_rand3(u64* a, u64* b, u64* c, u64 mask, u64 threads, u64 seed, cudaStream_t s);
 // a, b, c: tables of mask + 1 16-byte slots (2 (mask + 1) words); mode 0..2

@@ -221,3 +221,34 @@ def test_split_interleaved_sample_runs_are_harmless():
     info = check(ctx, s, d)
     assert info["hot_keys"] > 0
     ctx.close()
+
+
+def test_column_split_heavy_destinations():
+    """The column side's hot-destination split: a few destinations with
+    fan-in in the hundreds of thousands (one of them 0xFFFFFFFF, which marks
+    a free slot of the destination table and is never hot), under a skewed
+    window.  Every column quantity, and A, equal the oracle's."""
+    rng = np.random.default_rng(17)
+    n = 1 << 22
+    s, d = W.zipf_window(n, 1.2, 1 << 18, 29)
+    s, d = s.copy(), d.copy()
+    heavy = np.array([0xFFFFFFFF, 0x0A000001, 0xC0A80001, 0x00000000], np.uint32)
+    for j, h in enumerate(heavy):
+        sl = slice(j, n, 7)  # one packet in seven per heavy destination, from random sources
+        d[sl] = h
+        s[sl] = rng.integers(0, 1 << 32, s[sl].size, dtype=np.uint64).astype(np.uint32)
+    ctx = ns.Context(0, path="sort", sort_split="on")
+    check(ctx, s, d)
+    ctx.close()
+
+
+def test_column_split_single_destination():
+    """Every link into one destination: its column words all go one way, and
+    its fan-in is the number of distinct sources."""
+    rng = np.random.default_rng(19)
+    n = 1 << 21
+    s = rng.integers(0, 1 << 20, n, dtype=np.uint64).astype(np.uint32)
+    d = np.full(n, 0x7F000001, np.uint32)
+    ctx = ns.Context(0, path="sort", sort_split="on")
+    check(ctx, s, d)
+    ctx.close()
