@@ -307,14 +307,22 @@ def sort_path_bytes(N, U, S, D, info):
     16D.  With the split (C cold packets, H hot keys): the split reads the
     packets and writes the cold keys (8N + 8C); the histogram, digit passes
     and link runs see the C cold keys (8C + 128C + 8C + 16 U_C); the merge
-    reads the cold runs and writes the merged list (16 U_C + 16U); the
-    rest as above."""
-    tail = 24 * U + 16 * S + 16 * S + 8 * U + 64 * U + 8 * U + 16 * D + 16 * D
+    reads the cold runs and writes the merged list (16 U_C + 16U).  With the
+    column side's hot-destination split (W cold column words): it reads the
+    U words and writes the cold ones (8U + 8W); the column histogram,
+    passes and runs see the W cold words (8W + 64W + 8W); the cold
+    destinations' runs and statistics are bounded by 32D."""
+    rows = 24 * U + 16 * S + 16 * S
+    if "cold_words" in info:
+        W = info["cold_words"]
+        cols = 8 * U + 8 * W + 8 * W + 64 * W + 8 * W + 32 * D
+    else:
+        cols = 8 * U + 64 * U + 8 * U + 16 * D + 16 * D
     if "cold_packets" not in info:
-        return 144 * N + 32 * U + tail
+        return 144 * N + 32 * U + rows + cols
     C = info["cold_packets"]
     UC = U - info.get("hot_keys", 0)
-    return 8 * N + 8 * C + 144 * C + 16 * UC + 16 * UC + 16 * U + tail
+    return 8 * N + 8 * C + 144 * C + 16 * UC + 16 * UC + 16 * U + rows + cols
 
 
 def c3_run(args, rank, world, local, clocks, N):
@@ -377,6 +385,9 @@ def c3_run(args, rank, world, local, clocks, N):
             si = ns.sort_split_info(ctx)
             if si["used"]:
                 info = {"hot_keys": si["hot_keys"], "cold_packets": si["cold_packets"]}
+            ci = ns.column_split_info(ctx)
+            if ci["used"]:
+                info.update(hot_destinations=ci["hot_destinations"], cold_words=ci["cold_words"])
         U, S, D = st["unique_links"], st["unique_sources"], st["unique_destinations"]
         alg_bytes = 8 * N + 32 * U + 16 * (S + D)
         if path == "sort":

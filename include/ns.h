@@ -307,6 +307,16 @@ ns_status ns_path_tune(ns_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst
 ns_status ns_sort_split_info(ns_ctx* ctx, int* used, uint64_t* hot_keys, uint64_t* cold_packets,
                              ns_stream_t stream);
 
+/* What the context's last sort-path build did with the column side's
+ * hot-destination split (taken with the hot-key split, on windows of fewer
+ * than 2^32 packets): *used = 1 if it split, then *hot_destinations = the
+ * destinations counted apart from the column sort (their column words
+ * never sorted) and *cold_words = the column words that went through the
+ * sort (each pointer may be NULL).  Blocking (reads two counters).  No
+ * counterpart in the paper. */
+ns_status ns_column_split_info(ns_ctx* ctx, int* used, uint64_t* hot_destinations, uint64_t* cold_words,
+                               ns_stream_t stream);
+
 /* The path ns_window_build would take for a window of n packets
  * (NS_PATH_SORT or NS_PATH_HASH). */
 ns_status ns_path_resolve(const ns_ctx* ctx, uint64_t n, int* path);

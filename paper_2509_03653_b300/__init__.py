@@ -25,7 +25,7 @@ __all__ = [
     "matrix_clear", "sync", "PATHS", "SORT_TILES", "path_tune", "path_resolve", "sort_split_info", "matrix_nodes", "NODES", "anonymize", "Slider",
     "slider_push", "window_stats_static", "STATIC_MAX_PACKETS",
     "trace_enable", "trace_read", "Batch", "batch_run", "batch_run_device", "batch_sync", "batch_tune", "matrix_reserve_ex",
-    "owner", "matrix_partition", "matrix_add_entries", "Server", "stream_submit", "stream_poll", "stream_wait", "diag_random_atomics", "diag_random_claims", "matrix_save", "matrix_load",
+    "owner", "matrix_partition", "matrix_add_entries", "Server", "stream_submit", "stream_poll", "stream_wait", "diag_random_atomics", "diag_random_claims", "column_split_info", "matrix_save", "matrix_load",
 ]
 
 STATIC_MAX_PACKETS = 32768  # NS_STATIC_MAX_PACKETS in include/ns.h
@@ -172,6 +172,17 @@ def sort_split_info(ctx: Context, stream=None) -> dict:
     check(ctx._L.ns_sort_split_info(ctx.handle, ctypes.byref(used), ctypes.byref(h), ctypes.byref(cold),
                                     _stream(stream)), "ns_sort_split_info")
     return {"used": bool(used.value), "hot_keys": int(h.value), "cold_packets": int(cold.value)}
+
+
+def column_split_info(ctx: Context, stream=None) -> dict:
+    """What the context's last sort-path build did with the column side's
+    hot-destination split (ns_column_split_info): {"used",
+    "hot_destinations", "cold_words"}."""
+    used = ctypes.c_int(0)
+    h, cold = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    check(ctx._L.ns_column_split_info(ctx.handle, ctypes.byref(used), ctypes.byref(h), ctypes.byref(cold),
+                                      _stream(stream)), "ns_column_split_info")
+    return {"used": bool(used.value), "hot_destinations": int(h.value), "cold_words": int(cold.value)}
 
 
 def path_resolve(ctx: Context, n: int) -> str:

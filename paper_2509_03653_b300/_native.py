@@ -60,6 +60,7 @@ SIGNATURES = {
                           ctypes.POINTER(ctypes.c_float)]),
     "ns_path_resolve": (ST, [P, U64, ctypes.POINTER(ctypes.c_int)]),
     "ns_sort_split_info": (ST, [P, ctypes.POINTER(I32), ctypes.POINTER(U64), ctypes.POINTER(U64), P]),
+    "ns_column_split_info": (ST, [P, ctypes.POINTER(I32), ctypes.POINTER(U64), ctypes.POINTER(U64), P]),
     "ns_matrix_nodes": (ST, [P, P, ctypes.c_int, P, P, P, U64, ctypes.POINTER(U64), P]),
     "ns_anonymize": (ST, [P, P, P, U64, P, U64, P, P, ctypes.POINTER(U64), P]),
     "ns_server_reserve": (ST, [P, U64]),

@@ -379,7 +379,8 @@ ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n,
                 (u64*)c->pos.p, (u64*)c->psum.p, runs_out, c->sc, st, s, packed);
     launch_run_stats(RS_ROWS, (const u64*)c->pos.p, (const u64*)c->psum.p, runs_out, n,
                      nullptr, st, c->sms, &c->tracer, s);
-    if (packed_cols && c->last_split) {
+    c->last_colsplit = packed_cols && c->last_split;
+    if (c->last_colsplit) {
         // columns with the hot-destination split: the heaviest sampled
         // destinations are counted apart, only the other words are sorted
         TRY(buf_reserve(c->colsplit, col_split_state_bytes()));
@@ -845,6 +846,24 @@ ns_status ns_sort_split_info(ns_ctx* c, int* used, uint64_t* hot_keys, uint64_t*
     }
     if (hot_keys) *hot_keys = h;
     if (cold_packets) *cold_packets = cold;
+    return NS_OK;
+}
+
+ns_status ns_column_split_info(ns_ctx* c, int* used, uint64_t* hot_destinations, uint64_t* cold_words,
+                               ns_stream_t stream) {
+    if (!c) return fail(NS_ERR_INVALID, "ns_column_split_info: NULL context");
+    DeviceGuard device_guard(c->device);
+    if (used) *used = c->last_colsplit ? 1 : 0;
+    u64 h = 0, cold = 0;
+    if (c->last_colsplit && c->colsplit.p) {
+        const cudaError_t e = col_split_info(c->colsplit.p, &h, &cold, (cudaStream_t)stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(NS_ERR_CUDA, "ns_column_split_info: %s", cudaGetErrorString(e));
+        }
+    }
+    if (hot_destinations) *hot_destinations = h;
+    if (cold_words) *cold_words = cold;
     return NS_OK;
 }
 

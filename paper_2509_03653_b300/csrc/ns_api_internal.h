@@ -120,6 +120,7 @@ struct ns_ctx {
     ns::Buf split;     // the hot-key split's device state
     ns::Buf colsplit;  // the hot-destination split's device state
     bool last_split = false;  // the last sort-path build split
+    bool last_colsplit = false;  // the last sort-path build split its column side
     ns::DevStats* host_stats = nullptr;  // pinned
     ns::Tracer tracer;
 };

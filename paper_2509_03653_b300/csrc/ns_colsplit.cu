@@ -61,7 +61,7 @@ struct ColDev {
     u32 cand[kCHotMax];     // candidates, any order
     u32 hist[kCBins];       // sampled destinations by run length
     u64 m;                  // sample size
-    u64 H;                  // candidates collected
+    u64 H;                  // candidates collected, then the hot destinations placed
     u64 thresh;             // least sampled fan-in of a hot destination
     u64 cold;               // cold words
     u64 R_sample;           // distinct sampled destinations
@@ -201,12 +201,19 @@ __global__ void __launch_bounds__(kCTableThreads, 1) k_col_table(ColDev* cd) {
             done = old == kDEmpty || old == d;
         }
     }
+    __shared__ u32 placed;
+    if (threadIdx.x == 0) placed = 0;
     __syncthreads();
+    u32 mine = 0;
     for (int i = threadIdx.x; i < kCSlots; i += kCTableThreads) {
         cd->table[i] = table[i];
         cd->links[i] = 0;
         cd->packets[i] = 0;
+        mine += table[i] != kDEmpty ? 1u : 0u;
     }
+    if (mine) atomicAdd(&placed, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) cd->H = placed;  // the hot destinations
 }
 
 // 3. The split.  One CTA of 1024 threads per SM holds the table and its

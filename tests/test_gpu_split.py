@@ -239,6 +239,8 @@ def test_column_split_heavy_destinations():
         s[sl] = rng.integers(0, 1 << 32, s[sl].size, dtype=np.uint64).astype(np.uint32)
     ctx = ns.Context(0, path="sort", sort_split="on")
     check(ctx, s, d)
+    ci = ns.column_split_info(ctx)
+    assert ci["used"] and ci["hot_destinations"] > 0 and ci["cold_words"] > 0
     ctx.close()
 
 
@@ -251,4 +253,14 @@ def test_column_split_single_destination():
     d = np.full(n, 0x7F000001, np.uint32)
     ctx = ns.Context(0, path="sort", sort_split="on")
     check(ctx, s, d)
+    ci = ns.column_split_info(ctx)
+    assert ci["used"] and ci["hot_destinations"] == 1 and ci["cold_words"] == 0
+    ctx.close()
+
+
+def test_column_split_off_without_the_link_split():
+    ctx = ns.Context(0, path="sort", sort_split="off")
+    s, d = W.zipf_window(1 << 20, 1.2, 1 << 16, 3)
+    check(ctx, s, d)
+    assert not ns.column_split_info(ctx)["used"]
     ctx.close()
