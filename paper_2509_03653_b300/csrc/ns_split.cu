@@ -88,7 +88,7 @@ static_assert(kSampleMax / (kHotBins - 1) < (u64)kHotMax, "the top bin alone nev
 // (multiply-high), so the count is set by the shared memory the split
 // kernel has left for tier 2's fingerprint words, not by a power of two.
 #ifndef NS_WARM_BUCKETS
-#define NS_WARM_BUCKETS 23552
+#define NS_WARM_BUCKETS 31232
 #endif
 constexpr int kWarmBuckets = NS_WARM_BUCKETS;  // 0 turns tier 2 off
 static_assert(kWarmBuckets >= 0 && kWarmBuckets % 256 == 0, "kWarmBuckets: a multiple of 256");
@@ -96,9 +96,6 @@ constexpr int kWarmSlots = kWarmBuckets * kWays;
 constexpr int kWarmMax = kWarmSlots / 8 * 5;
 constexpr u32 kMinWarmSample = 2;   // fewest sample occurrences of a tier-2 key
 constexpr int kListMax = kHotMax + kWarmMax;
-// the hot list is sorted in the key buffers, which hold the window's
-// packets, and the split runs from 2^16 packets up
-static_assert(kListMax <= (1 << 16), "the hot list fits the smallest split window");
 constexpr int kArr = kWarmSlots > 0 ? kWarmSlots : 1;  // array extents of an absent tier 2
 constexpr int kWarmArr = kWarmMax > 0 ? kWarmMax : 1;
 constexpr int kIndexStride = 8;     // the merge's shared-memory index holds every 8th hot-list key
@@ -865,8 +862,11 @@ void sort_links_split(const u32* src, const u32* dst, u64 n, u64* kb[2], u64* he
     {
         // the hot list ascending: both tiers' keys sorted together (kb is
         // free until the split writes the cold keys)
-        const int rl = radix_sort_keys64(sd->list, &sd->H, kb, kListMax, sc, st, s, "k_onesweep<hot list>");
-        cudaMemcpyAsync(sd->list, kb[rl], sizeof(sd->list), cudaMemcpyDeviceToDevice, s);
+        // (the list holds at most the sample's distinct keys, a quarter of
+        // the window, so the window's buffers bound its sort)
+        const int rl = radix_sort_keys64(sd->list, &sd->H, kb, std::min<u64>(kListMax, n), sc, st, s,
+                                         "k_onesweep<hot list>");
+        cudaMemcpyAsync(sd->list, kb[rl], sizeof(u64) * std::min<u64>(kListMax, n), cudaMemcpyDeviceToDevice, s);
     }
     // 3. the split: hot keys counted, cold keys into kb[1]
     {
