@@ -384,7 +384,14 @@ ns_status ns_batch_set_params(ns_batch* batch, const ns_batch_params* params);
  * entries, starting at 0 and non-decreasing; d_window_stats is a device array
  * of `windows` ns_stats.  acc must have room reserved for the batch's links
  * if this call is captured into a CUDA graph (growing it needs a blocking
- * read).  Asynchronous; allocates nothing. */
+ * read).  When acc is empty and the batch is in the sort path's range (the
+ * path ns_window_build would take for all its packets at once), acc
+ * receives the batch's matrix from one sort-path build over the packets
+ * d_src/d_dst[0, h_offsets[windows]) -- the same A, as a sorted nonzero
+ * list -- instead of every window's table being added to it; that build
+ * takes the sort path's scratch, sized on first use (capture a graph around
+ * this call only after one uncaptured run of the same size).  Asynchronous;
+ * allocates nothing otherwise. */
 ns_status ns_batch_run(ns_ctx* ctx, ns_batch* batch, const uint32_t* d_src, const uint32_t* d_dst,
                        const uint64_t* h_offsets, uint64_t windows, ns_stats* d_window_stats,
                        ns_matrix* acc, ns_stream_t stream);

@@ -328,7 +328,7 @@ int resolve_tile(const ns_ctx* c, u64 n) {
 // split: -1 = use_split's rule, 0 = no split, 1 = split (from 2^16 packets);
 // tile: -1 = resolve_tile's rule, else the digit passes' tile shape.
 ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n, ns_matrix* out,
-                     cudaStream_t s, int split = -1, int tile = -1) {
+                     cudaStream_t s, int split, int tile) {
     touch(out, s);
     c->sc.tile_shape = tile < 0 ? resolve_tile(c, n) : tile;
     out->fmt = FMT_LIST;

@@ -67,6 +67,13 @@ enum { FMT_EMPTY = 0, FMT_HASH = 1, FMT_LIST = 2 };
 ns_status buf_reserve(Buf& b, size_t bytes);
 ns_status fail_fmt(ns_status s, const char* fmt, ...);
 ns_status to_hash(ns_matrix* m, u64 extra, cudaStream_t s);
+// The path ns_window_build takes for n packets (NS_PATH_SORT or NS_PATH_HASH).
+int resolve_path(const ns_ctx* c, u64 n);
+// The sort-path build of n packets into `out` (its sorted nonzero list and
+// statistics).  split: -1 = the context's rule, 0 = off, 1 = on; tile: -1 =
+// the context's rule, else the digit passes' tile shape.
+ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n, ns_matrix* out, cudaStream_t s,
+                     int split = -1, int tile = -1);
 ns_status check_launch();
 HashView hash_view(const ns_matrix* m);
 void buf_free(Buf& b);

@@ -337,7 +337,14 @@ ns_status ns_batch_run(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uint
     std::vector<Chunk> chunks;
     ns_status st = plan(b, h_offsets, windows, chunks);
     if (st != NS_OK) return st;
-    if (acc) {
+    // An empty aggregate over a batch in the sort path's range is the
+    // matrix of the batch's packets, which lie back to back in the columns:
+    // one sort-path build of them replaces adding every window's table.
+    const bool acc_by_sort = acc && acc->bound == 0 && resolve_path(c, total) == NS_PATH_SORT;
+    if (acc_by_sort) {
+        st = build_sort(c, d_src, d_dst, total, acc, s);
+        if (st != NS_OK) return st;
+    } else if (acc) {
         st = to_hash(acc, total, s);
         if (st != NS_OK) return st;
     }
@@ -375,7 +382,7 @@ ns_status ns_batch_run(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uint
             launch_batch_insert(B, (u32*)b->counter.p + ci, ch.tiles, c->sms, (int)b->params.ctas_per_sm,
                                 b->params.cta_cache != 0, s);
         }
-        if (acc) {
+        if (acc && !acc_by_sort) {
             // every window's link slots, side slots included (a side slot's
             // key field is 0, which is the key it holds)
             TraceScope ts(&c->tracer, "k_insert_slots", s);
@@ -387,7 +394,7 @@ ns_status ns_batch_run(ns_ctx* c, ns_batch* b, const uint32_t* d_src, const uint
         TraceScope ts(&c->tracer, "k_batch_stats_out", s);
         launch_batch_stats_out((const DevStats*)b->wstats.p, windows, (u64*)d_window_stats, c->sms, s);
     }
-    if (acc) acc->bound += total;
+    if (acc && !acc_by_sort) acc->bound += total;  // (the sort-path build set its own)
     return check_launch();
 }
 

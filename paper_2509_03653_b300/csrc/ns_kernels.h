@@ -72,6 +72,17 @@ constexpr int kSortTileShapes = 3;
 
 // Look-back tags are 16 bits; when they wrap, the status words are cleared
 // on the stream so no stale word can carry a live tag.
+//
+// A CUDA graph fixes each launch's tag at capture, so a replay would find
+// the previous replay's words under the very tag it waits for.  While the
+// stream is capturing, the words a launch uses are therefore cleared first,
+// as a node of the graph (outside a capture nothing is cleared).
+inline void clear_status_in_capture(u64* p, u64 words, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (words && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaMemsetAsync(p, 0, words * sizeof(u64), s);
+}
+
 inline u32 next_tag(SortScratch& sc, cudaStream_t s) {
     if (sc.tag >= 0xFFFFu) {
         cudaMemsetAsync(sc.status, 0, sc.status_words * sizeof(u64), s);

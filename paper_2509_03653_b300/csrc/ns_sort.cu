@@ -1138,8 +1138,12 @@ int radix_sort_t(const SortIn& in, K* kbuf[2], u64* vbuf[2], u64 n, int begin_bi
         TraceScope ts(sc.tr, "k_sort_offsets", s);
         k_sort_offsets<<<1, kThreads, 0, s>>>(sc.ghist, passes, sc.offs);
     }
+    // a pass's tiles hold 4096 keys or more, so its status words are within
+    // the first sort_tiles(n) * kRadix
+    const u64 status_used = std::min<u64>(sort_tiles(std::max<u64>(n, 1)) * kRadix, sc.status_words);
     for (int p = 0; p < passes; ++p) {
         const u32 tag = next_tag(sc, s);
+        clear_status_in_capture(sc.status, status_used, s);
         const int shift = begin_bit + 8 * p;
         if (p == 0) {
             // The first pass of a keys-only sort need not be stable: its
@@ -1249,6 +1253,12 @@ void launch_runs(int keymode, bool has_v, const void* keys, const u64* vals, u64
     const u64* nd = (const u64*)n_dev;
     u64* sc_c = sc.status;
     u64* sc_s = sc.status + sc.status_words / 2;
+    {
+        // run tiles hold 1024 keys or more: one count and one sum word each
+        const u64 used = std::min<u64>((n + 1023) / 1024 + 1, sc.status_words / 2);
+        clear_status_in_capture(sc_c, used, s);
+        clear_status_in_capture(sc_s, used, s);
+    }
     u32* tc = sc.tile_counters + 8;
     if (keymode == RUN_U64 && !has_v)
         launch_runs_t<RUN_U64, false>(keys, (const u64*)vals, n, nd, (u64*)head_keys, (u64*)pos,

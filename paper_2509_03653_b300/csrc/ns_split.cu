@@ -705,9 +705,11 @@ __device__ __forceinline__ u64 hot_rank(const u64* idx, u64 NI, const u64* __res
 // below it among the hot keys that fall between the group's first and last
 // keys (span of them: almost always none).
 constexpr int kMergeRounds = 4;
+// cap: the output's capacity (the window's packets); places at or past it
+// are never written (they cannot occur unless a look-back gave up).
 __global__ void __launch_bounds__(kMergeThreads) k_hot_merge(const u64* __restrict__ heads, const u64* __restrict__ pos,
                                                              const SplitDev* sd, u64* __restrict__ keys_out,
-                                                             u64* __restrict__ counts_out, DevStats* st) {
+                                                             u64* __restrict__ counts_out, u64 cap, DevStats* st) {
     extern __shared__ __align__(16) u64 idx[];  // [kIndexMax]
     __shared__ u64 bmax;
     const u32 FULL = 0xFFFFFFFFu, lane = threadIdx.x & 31;
@@ -763,8 +765,10 @@ __global__ void __launch_bounds__(kMergeThreads) k_hot_merge(const u64* __restri
             const u64 i = base + (u64)r * 32 + lane;
             if (i < RC) {
                 const u64 at = i + below[r];
-                keys_out[at] = key[r];
-                counts_out[at] = c[r];
+                if (at < cap) {
+                    keys_out[at] = key[r];
+                    counts_out[at] = c[r];
+                }
                 mx = c[r] > mx ? c[r] : mx;
             } else if (i < total) {
                 const u64 h = i - RC, k = list[h];
@@ -777,8 +781,10 @@ __global__ void __launch_bounds__(kMergeThreads) k_hot_merge(const u64* __restri
                     ch = s2 >= 0 ? sd->count2[s2] : 0;
                 }
                 const u64 at = h + count_below(heads, RC, k);
-                keys_out[at] = k;
-                counts_out[at] = ch;
+                if (at < cap) {
+                    keys_out[at] = k;
+                    counts_out[at] = ch;
+                }
                 mx = ch > mx ? ch : mx;
                 hot_sum += ch;
             }
@@ -886,7 +892,7 @@ void sort_links_split(const u32* src, const u32* dst, u64 n, u64* kb[2], u64* he
         TraceScope ts(tr, "k_hot_merge", s);
         const size_t msmem = sizeof(u64) * kIndexMax;
         const int mgrid = resident_ctas_of((const void*)k_hot_merge, kMergeThreads, msmem);
-        k_hot_merge<<<mgrid, kMergeThreads, msmem, s>>>(heads, pos, sd, keys_out, counts_out, st);
+        k_hot_merge<<<mgrid, kMergeThreads, msmem, s>>>(heads, pos, sd, keys_out, counts_out, n, st);
     }
 }
 

@@ -209,3 +209,63 @@ def test_device_offsets_new_layout_without_recapture():
     b.free()
     acc.free()
     ctx.close()
+
+
+def test_batch_aggregate_by_one_sort_build():
+    """A context on the sort path: an empty aggregate receives the batch's
+    matrix from one sort-path build of all its packets; a second batch into
+    the now non-empty aggregate adds its windows' tables instead.  Per-window
+    quantities and the aggregate equal the oracle both times."""
+    ctx = ns.Context(0, path="sort")
+    src, dst, off = make_batch(SIZES, seed0=90)
+    acc = ns.Matrix(ctx)
+    b, out = run_batch(ctx, src, dst, off, acc)
+    per, want_acc = expected(src, dst, off)
+    assert rows_of(out, len(SIZES)) == per
+    assert ns.network_stats(ctx, acc) == oracle.stats(*want_acc)
+    assert_matrix_equal(acc, *want_acc)
+    src2, dst2, off2 = make_batch([30000, 7, 0, 9999], seed0=95)
+    b2, out2 = run_batch(ctx, src2, dst2, off2, acc)
+    per2, want2 = expected(src2, dst2, off2)
+    assert rows_of(out2, 4) == per2
+    total = oracle.accumulate(want_acc, want2)
+    assert ns.network_stats(ctx, acc) == oracle.stats(*total)
+    assert_matrix_equal(acc, *total)
+    b.free()
+    b2.free()
+
+
+def test_batch_aggregate_by_sort_in_cuda_graph_with_new_packets():
+    """The same, captured in a CUDA graph (aggregate cleared inside it) and
+    replayed on packets with new contents but the same window layout."""
+    ctx = ns.Context(0, path="sort", sort_split="on")
+    sizes = [70000, 0, 5000, 131072, 3]
+    src, dst, off = make_batch(sizes, seed0=101)
+    src2, dst2, _ = make_batch(sizes, seed0=202)
+    Wn, total = len(sizes), int(off[-1])
+    b = ns.Batch(ctx, Wn, total)
+    acc = ns.Matrix(ctx)
+    ds, dd = to_dev(src), to_dev(dst)
+    out = torch.full((Wn * 9,), -1, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ns.matrix_clear(acc)
+        ns.batch_run(ctx, b, ds, dd, off, out, acc)  # outside capture: every buffer reaches its size
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ns.matrix_clear(acc)
+        keep = ns.batch_run(ctx, b, ds, dd, off, out, acc)
+    for a, c in ((src2, dst2), (src, dst), (src2, dst2)):
+        ds.copy_(to_dev(a))
+        dd.copy_(to_dev(c))
+        out.fill_(-1)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        per, want_acc = expected(a, c, off)
+        assert rows_of(out, Wn) == per
+        assert ns.network_stats(ctx, acc) == oracle.stats(*want_acc)
+        assert_matrix_equal(acc, *want_acc)
+    del keep
+    b.free()
