@@ -298,10 +298,11 @@ def headline_config():
             "l2": "inputs larger than L2 (8 GiB of packets)", "parallelism": "single GPU"}
 
 
-def sort_path_bytes(N, U, S, D, info):
+def sort_path_bytes(N, U, S, D, info, passes=8):
     """Minimal bytes of the sort path's passes, kernel by kernel (N < 2^32:
     the column side sorts one u64 word per link).  Without a hot-key split:
-    histogram 8N; eight digit passes 16N each; link runs 8N + 16U; link
+    histogram 8N; `passes` digit passes 16N each (eight with 8-bit digits,
+    seven with the wide plan); link runs 8N + 16U; link
     counts 16U; row runs 24U + 16S; row statistics 16S; column histogram 8U;
     four column passes 16U each; column runs 8U + 16D; column statistics
     16D.  With the split (C cold packets, H hot keys): the split reads the
@@ -318,11 +319,12 @@ def sort_path_bytes(N, U, S, D, info):
         cols = 8 * U + 8 * W + 8 * W + 64 * W + 8 * W + 32 * D
     else:
         cols = 8 * U + 64 * U + 8 * U + 16 * D + 16 * D
+    dp = 16 * passes
     if "cold_packets" not in info:
-        return 144 * N + 32 * U + rows + cols
+        return (16 + dp) * N + 32 * U + rows + cols
     C = info["cold_packets"]
     UC = U - info.get("hot_keys", 0)
-    return 8 * N + 8 * C + 144 * C + 16 * UC + 16 * UC + 16 * U + rows + cols
+    return 8 * N + 8 * C + (16 + dp) * C + 16 * UC + 16 * UC + 16 * U + rows + cols
 
 
 def c3_run(args, rank, world, local, clocks, N):
@@ -344,6 +346,7 @@ def c3_run(args, rank, world, local, clocks, N):
     peak, peak_src = peak_hbm()
     res, stats_by_path = {}, {}
     tuned = None
+    tuned_file = None
     for path in args.paths.split(","):
         tuner_file = None
         if path == "sort" and not args.no_tune:
@@ -358,6 +361,7 @@ def c3_run(args, rank, world, local, clocks, N):
             entries = json.load(open(tuner_file))
             tuned = {"seconds": round(time.time() - tt, 1), **{k.split("|", 1)[1]: json.loads(v) if isinstance(v, str)
                                                                else v for k, v in entries.items()}}
+            tuned_file = tuner_file
         M = ns.Matrix(ctx)
         for _ in range(max(args.warmup, 3)):
             ns.window_build(ctx, d_src, d_dst, M)
@@ -381,10 +385,14 @@ def c3_run(args, rank, world, local, clocks, N):
         tr = ns.trace_read(ctx)
         ns.trace_enable(ctx, False)
         info = {}
+        passes = 8
         if path == "sort":
+            variant = ns.sort_resolve(ctx, N)
+            passes = 7 if variant["digits"] == "wide" else 8
+            info["sort_variant"] = {"tile": variant["tile"], "digits": variant["digits"], "digit_passes": passes}
             si = ns.sort_split_info(ctx)
             if si["used"]:
-                info = {"hot_keys": si["hot_keys"], "cold_packets": si["cold_packets"]}
+                info.update(hot_keys=si["hot_keys"], cold_packets=si["cold_packets"])
             ci = ns.column_split_info(ctx)
             if ci["used"]:
                 info.update(hot_destinations=ci["hot_destinations"], cold_words=ci["cold_words"])
@@ -394,7 +402,7 @@ def c3_run(args, rank, world, local, clocks, N):
             kname = "k_onesweep<u64 key>"
             keys = info.get("cold_packets", N)
             kbytes = 16 * keys  # one digit pass reads and writes every 8-byte key
-            path_bytes = sort_path_bytes(N, U, S, D, info)
+            path_bytes = sort_path_bytes(N, U, S, D, info, passes)
             traffic = profile_traffic("k_onesweep.oneshot_zipf_2p26.md", ["ns_sort.cu", "ns_common.cuh"])
         else:
             kname = "k_insert_packets"
@@ -427,7 +435,9 @@ def c3_run(args, rank, world, local, clocks, N):
     first = args.paths.split(",")[0]
     e2e = None
     if not args.no_e2e:
-        ctx = ns.Context(local, path=first, sort_split=args.sort_split)
+        # the variant the timed builds took (the tuner's record for this size)
+        ctx = ns.Context(local, path=first, sort_split=args.sort_split,
+                         tuner_cache=tuned_file if first == "sort" else None)
         M = ns.Matrix(ctx)
         ns.window_build_host(ctx, h_src, h_dst, M)  # sizes the staging buffers
         steps = max(1, min(args.steps, 5))

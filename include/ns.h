@@ -131,6 +131,16 @@ enum {
     NS_TILE_256X16 = 3  /* 4096-key tiles, four CTAs per SM */
 };
 
+/* The digit plan of the sort path's radix sorts of 64-bit keys (the packed
+ * packets, or the cold keys of the hot-key split; see ns_config.sort_digits).
+ * Exact either way. */
+enum {
+    NS_DIGITS_AUTO = 0, /* ns_path_tune's choice for the size, else NS_DIGITS_8 */
+    NS_DIGITS_8 = 1,    /* eight passes of 8-bit digits (256 buckets) */
+    NS_DIGITS_WIDE = 2  /* seven passes: one of 10-bit digits (1024 buckets, the
+                           unordered first pass), then six of 9-bit digits (512) */
+};
+
 typedef struct {
     int path;                  /* NS_PATH_* used by ns_window_build */
     uint64_t hbm_budget_bytes; /* serving admission and batch arena budget; 0 = 64 GiB */
@@ -143,6 +153,7 @@ typedef struct {
                                   0 = 0.5.  Lower costs memory and shortens probe chains. */
     int sort_split;            /* NS_SPLIT_* for the sort path */
     int sort_tile;             /* NS_TILE_* for the sort path's digit passes */
+    int sort_digits;           /* NS_DIGITS_* for the sort path's digit passes */
 } ns_config;
 
 /* ---- context ----------------------------------------------------------- */
@@ -283,13 +294,15 @@ ns_status ns_window_build_host(ns_ctx* ctx, const uint32_t* h_src, const uint32_
 
 /* Path tuner: builds A from d_src/d_dst (n > 0 packets, device memory)
  * with the sort path in every combination of hot-key split (without, with;
- * no split below 2^16 packets) and digit-pass tile (the three NS_TILE_*
- * shapes) -- only the ones the context's sort_split and sort_tile allow --
+ * no split below 2^16 packets), digit plan (the two NS_DIGITS_* plans) and
+ * digit-pass tile (the three NS_TILE_* shapes) -- only the ones the
+ * context's sort_split, sort_digits and sort_tile allow --
  * and the hash path without and with per-CTA caches (only the one the
  * context's cta_cache forces, if it forces one), three times each, and
  * keeps the fastest of the last two timings of each.  The winner becomes
  * the context's NS_PATH_AUTO / NS_CACHE_AUTO choice, and the fastest sort
- * variant its NS_SPLIT_AUTO / NS_TILE_AUTO choice, for every n' with
+ * variant its NS_SPLIT_AUTO / NS_DIGITS_AUTO / NS_TILE_AUTO choice (see
+ * ns_sort_resolve), for every n' with
  * floor(log2 n') = floor(log2 n); all are stored in the tuner cache file
  * (if the context has one) keyed by GPU name and that power of two, where
  * later contexts on the same GPU find them.  *chosen (NS_PATH_SORT or
@@ -320,6 +333,14 @@ ns_status ns_column_split_info(ns_ctx* ctx, int* used, uint64_t* hot_destination
 /* The path ns_window_build would take for a window of n packets
  * (NS_PATH_SORT or NS_PATH_HASH). */
 ns_status ns_path_resolve(const ns_ctx* ctx, uint64_t n, int* path);
+
+/* The variant a sort-path build of n packets would take, from the context's
+ * settings, else ns_path_tune's choices for the size, else the size rules:
+ * *split = 1 if it takes the hot-key split (else 0), *tile = its NS_TILE_*
+ * digit-pass tile (never NS_TILE_AUTO), *digits = its NS_DIGITS_* digit plan
+ * (never NS_DIGITS_AUTO).  Each pointer may be NULL.  No device work.  No
+ * counterpart in the paper (the tuner's knobs are this library's own). */
+ns_status ns_sort_resolve(const ns_ctx* ctx, uint64_t n, int* split, int* tile, int* digits);
 
 /* acc := acc + add (A = sum_t A_t; equal keys add their counts).  `add` is
  * unchanged and may be rebuilt as soon as the stream work completes.

@@ -22,7 +22,7 @@ from ._native import (FIELDS, NsBatchParams, NsConfig, NsError, NsStats, NsStrea
 __all__ = [
     "FIELDS", "NsError", "Context", "Matrix", "window_build", "window_build_host", "accumulate", "window_ingest",
     "window_ingest_stats", "network_stats", "network_stats_async", "matrix_export", "matrix_nnz", "matrix_reserve",
-    "matrix_clear", "sync", "PATHS", "SORT_TILES", "path_tune", "path_resolve", "sort_split_info", "matrix_nodes", "NODES", "anonymize", "Slider",
+    "matrix_clear", "sync", "PATHS", "SORT_TILES", "SORT_DIGITS", "path_tune", "path_resolve", "sort_resolve", "sort_split_info", "matrix_nodes", "NODES", "anonymize", "Slider",
     "slider_push", "window_stats_static", "STATIC_MAX_PACKETS",
     "trace_enable", "trace_read", "Batch", "batch_run", "batch_run_device", "batch_sync", "batch_tune", "matrix_reserve_ex",
     "owner", "matrix_partition", "matrix_add_entries", "Server", "stream_submit", "stream_poll", "stream_wait", "diag_random_atomics", "diag_random_claims", "column_split_info", "matrix_save", "matrix_load",
@@ -33,6 +33,9 @@ STATIC_MAX_PACKETS = 32768  # NS_STATIC_MAX_PACKETS in include/ns.h
 PATHS = {"auto": 0, "sort": 1, "hash": 2}
 # digit-pass tiles of the sort path (ns_config.sort_tile): threads x keys per thread
 SORT_TILES = {"auto": 0, "512x16": 1, "512x12": 2, "256x16": 3}
+# digit plan of the sort path's 64-bit radix sorts (ns_config.sort_digits):
+# eight 8-bit passes, or "wide": one 10-bit pass, then six 9-bit passes
+SORT_DIGITS = {"auto": 0, "8": 1, "wide": 2}
 
 
 def _stream(stream) -> ctypes.c_void_p:
@@ -59,12 +62,12 @@ class Context:
     def __init__(self, device: int = 0, path: str = "auto", hbm_budget_bytes: int = 0,
                  max_slots: int = 0, tuner_cache: str | None = None, cta_cache: str = "auto",
                  column_sort: str = "auto", hash_load: float = 0.0, sort_split: str = "auto",
-                 sort_tile: str = "auto"):
+                 sort_tile: str = "auto", sort_digits: str = "auto"):
         self._L = load()
         cfg = NsConfig(PATHS[path], hbm_budget_bytes, max_slots,
                        tuner_cache.encode() if tuner_cache else None, {"auto": 0, "on": 1, "off": 2}[cta_cache],
                        {"auto": 0, "pairs": 1}[column_sort], hash_load, {"auto": 0, "on": 1, "off": 2}[sort_split],
-                       SORT_TILES[sort_tile])
+                       SORT_TILES[sort_tile], SORT_DIGITS[sort_digits])
         h = ctypes.c_void_p()
         check(self._L.ns_create(ctypes.byref(h), ctypes.byref(cfg), device), "ns_create")
         self.handle = h
@@ -190,6 +193,17 @@ def path_resolve(ctx: Context, n: int) -> str:
     p = ctypes.c_int(0)
     check(ctx._L.ns_path_resolve(ctx.handle, n, ctypes.byref(p)), "ns_path_resolve")
     return _PATH_NAMES[p.value]
+
+
+def sort_resolve(ctx: Context, n: int) -> dict:
+    """The sort variant a sort-path build of n packets takes (ns_sort_resolve):
+    {"split": bool, "tile": one of SORT_TILES' shapes, "digits": "8" or "wide"}."""
+    sp, tl, dg = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    check(ctx._L.ns_sort_resolve(ctx.handle, n, ctypes.byref(sp), ctypes.byref(tl), ctypes.byref(dg)),
+          "ns_sort_resolve")
+    tiles = {v: k for k, v in SORT_TILES.items()}
+    digits = {v: k for k, v in SORT_DIGITS.items()}
+    return {"split": bool(sp.value), "tile": tiles[tl.value], "digits": digits[dg.value]}
 
 
 def accumulate(ctx: Context, acc: Matrix, add: Matrix, stream=None):

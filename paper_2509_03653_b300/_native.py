@@ -17,7 +17,7 @@ ST = ctypes.c_int  # ns_status
 class NsConfig(ctypes.Structure):
     _fields_ = [("path", I32), ("hbm_budget_bytes", U64), ("max_slots", I32), ("tuner_cache", ctypes.c_char_p),
                 ("cta_cache", I32), ("column_sort", I32), ("hash_load", ctypes.c_double), ("sort_split", I32),
-                ("sort_tile", I32)]
+                ("sort_tile", I32), ("sort_digits", I32)]
 
 
 class NsStats(ctypes.Structure):
@@ -59,6 +59,7 @@ SIGNATURES = {
     "ns_path_tune": (ST, [P, P, P, U64, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                           ctypes.POINTER(ctypes.c_float)]),
     "ns_path_resolve": (ST, [P, U64, ctypes.POINTER(ctypes.c_int)]),
+    "ns_sort_resolve": (ST, [P, U64, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
     "ns_sort_split_info": (ST, [P, ctypes.POINTER(I32), ctypes.POINTER(U64), ctypes.POINTER(U64), P]),
     "ns_column_split_info": (ST, [P, ctypes.POINTER(I32), ctypes.POINTER(U64), ctypes.POINTER(U64), P]),
     "ns_matrix_nodes": (ST, [P, P, ctypes.c_int, P, P, P, U64, ctypes.POINTER(U64), P]),

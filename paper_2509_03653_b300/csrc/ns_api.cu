@@ -291,7 +291,7 @@ ns_status context_pool(ns_ctx* c) {
 
 ns_status sort_scratch(ns_ctx* c, u64 n) {
     const u64 tiles = sort_tiles(std::max<u64>(n, 1));
-    const u64 words = tiles * (u64)sort_radix();
+    const u64 words = tiles * (u64)sort_radix(c->sc.digit_plan);
     if (c->status.bytes < words * sizeof(u64)) {
         TRY(buf_reserve(c->status, words * sizeof(u64)));
         CK(cudaMemsetAsync(c->status.p, 0, words * sizeof(u64), alloc_stream()));
@@ -325,12 +325,30 @@ int resolve_tile(const ns_ctx* c, u64 n) {
     return 0;
 }
 
+// The digit plan of the digit passes over 64-bit keys for n packets: the
+// context's setting, else ns_path_tune's measurement for the size, else
+// eight 8-bit passes.
+int resolve_digits(const ns_ctx* c, u64 n) {
+    if (c->cfg.sort_digits != NS_DIGITS_AUTO) return c->cfg.sort_digits == NS_DIGITS_WIDE ? kDigitsWide : kDigits8;
+    const auto it = c->path_choice.find(n ? 63 - __builtin_clzll(n) : 0);
+    if (it != c->path_choice.end() && it->second.digits >= 0) return it->second.digits;
+    return kDigits8;
+}
+
+void resolve_sort(const ns_ctx* c, u64 n, int* split, int* tile, int* digits) {
+    if (split) *split = use_split(c, n) ? 1 : 0;
+    if (tile) *tile = resolve_tile(c, n);
+    if (digits) *digits = resolve_digits(c, n);
+}
+
 // split: -1 = use_split's rule, 0 = no split, 1 = split (from 2^16 packets);
-// tile: -1 = resolve_tile's rule, else the digit passes' tile shape.
+// tile: -1 = resolve_tile's rule, else the digit passes' tile shape;
+// digits: -1 = resolve_digits's rule, else the digit plan.
 ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n, ns_matrix* out,
-                     cudaStream_t s, int split, int tile) {
+                     cudaStream_t s, int split, int tile, int digits) {
     touch(out, s);
     c->sc.tile_shape = tile < 0 ? resolve_tile(c, n) : tile;
+    c->sc.digit_plan = digits < 0 ? resolve_digits(c, n) : digits;
     out->fmt = FMT_LIST;
     out->bound = n;
     CK(cudaMemsetAsync(out->stats.p, 0, sizeof(DevStats), s));
@@ -441,15 +459,17 @@ void load_path_choices(ns_ctx* c) {
         if (kv.first.compare(0, prefix.size(), prefix) != 0) continue;
         const int lg = atoi(kv.first.c_str() + prefix.size());
         std::string p;
-        double cache = 0, split = -1, tile = -1;
+        double cache = 0, split = -1, tile = -1, digits = -1;
         if (lg < 0 || lg > 40 || !json_string(kv.second, "path", &p)) continue;
         json_number(kv.second, "cta_cache", &cache);
         json_number(kv.second, "sort_split", &split);
         json_number(kv.second, "sort_tile", &tile);
+        json_number(kv.second, "sort_digits", &digits);
         const int sp = split < 0 ? -1 : (split != 0 ? 1 : 0);
         const int tl = (tile >= 0 && tile < kSortTileShapes) ? (int)tile : -1;
-        if (p == "sort") c->path_choice[lg] = {NS_PATH_SORT, false, sp, tl};
-        if (p == "hash") c->path_choice[lg] = {NS_PATH_HASH, cache != 0, sp, tl};
+        const int dg = (digits >= 0 && digits < kDigitPlans) ? (int)digits : -1;
+        if (p == "sort") c->path_choice[lg] = {NS_PATH_SORT, false, sp, tl, dg};
+        if (p == "hash") c->path_choice[lg] = {NS_PATH_HASH, cache != 0, sp, tl, dg};
     }
 }
 
@@ -517,6 +537,8 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
         return fail(NS_ERR_INVALID, "ns_create: unknown sort_split %d", c.sort_split);
     if (c.sort_tile < NS_TILE_AUTO || c.sort_tile > NS_TILE_256X16)
         return fail(NS_ERR_INVALID, "ns_create: unknown sort_tile %d", c.sort_tile);
+    if (c.sort_digits < NS_DIGITS_AUTO || c.sort_digits > NS_DIGITS_WIDE)
+        return fail(NS_ERR_INVALID, "ns_create: unknown sort_digits %d", c.sort_digits);
     if (c.hash_load == 0.0) c.hash_load = 0.5;
     if (!(c.hash_load >= 0.05 && c.hash_load <= 0.9))
         return fail(NS_ERR_INVALID, "ns_create: hash_load %g outside [0.05, 0.9]", c.hash_load);
@@ -533,8 +555,11 @@ ns_status ns_create(ns_ctx** out, const ns_config* cfg, int device) {
     cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, device);
     x->sc.sms = x->sms;
     AllocScope alloc(nullptr, nullptr);
-    ns_status st = buf_reserve(x->ghist, 8 * 256 * sizeof(u64));
-    if (st == NS_OK) st = buf_reserve(x->offs, 9 * 256 * sizeof(u64));  // [8][256] offsets + cursors
+    // digit histograms and bucket starts of either digit plan: eight passes
+    // of 256 digits, or the wide plan's 1024 + 6 x 512; then the first
+    // pass's cursors
+    ns_status st = buf_reserve(x->ghist, 4096 * sizeof(u64));
+    if (st == NS_OK) st = buf_reserve(x->offs, (4096 + 1024) * sizeof(u64));
     if (st == NS_OK) st = buf_reserve(x->tcount, 16 * sizeof(u32));
     if (st == NS_OK) st = buf_reserve(x->counters, 16 * sizeof(u64));
     if (st == NS_OK && cudaMallocHost((void**)&x->host_stats, sizeof(DevStats)) != cudaSuccess)
@@ -755,21 +780,24 @@ ns_status ns_path_tune(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, 
     // packets), then the hash path without and with per-CTA caches (only the
     // forced one if the context fixes cta_cache)
     struct Cand {
-        int path, cache, split, tile;
+        int path, cache, split, tile, digits;
         float ms;
     };
     std::vector<Cand> cand;
     const bool can_split = n >= (1ull << 16);
-    std::vector<int> splits, tiles;
+    std::vector<int> splits, tiles, plans;
     if (c->cfg.sort_split != NS_SPLIT_ON || !can_split) splits.push_back(0);
     if (c->cfg.sort_split != NS_SPLIT_OFF && can_split) splits.push_back(1);
     for (int t = 0; t < kSortTileShapes; ++t)
         if (c->cfg.sort_tile == NS_TILE_AUTO || c->cfg.sort_tile - 1 == t) tiles.push_back(t);
+    if (c->cfg.sort_digits != NS_DIGITS_WIDE) plans.push_back(kDigits8);
+    if (c->cfg.sort_digits != NS_DIGITS_8) plans.push_back(kDigitsWide);
     for (int sp : splits)
-        for (int t : tiles) cand.push_back({NS_PATH_SORT, 0, sp, t, 1e30f});
+        for (int dg : plans)
+            for (int t : tiles) cand.push_back({NS_PATH_SORT, 0, sp, t, dg, 1e30f});
     const size_t n_sort = cand.size();
-    if (c->cfg.cta_cache != NS_CACHE_ON) cand.push_back({NS_PATH_HASH, 0, -1, -1, 1e30f});
-    if (c->cfg.cta_cache != NS_CACHE_OFF) cand.push_back({NS_PATH_HASH, 1, -1, -1, 1e30f});
+    if (c->cfg.cta_cache != NS_CACHE_ON) cand.push_back({NS_PATH_HASH, 0, -1, -1, -1, 1e30f});
+    if (c->cfg.cta_cache != NS_CACHE_OFF) cand.push_back({NS_PATH_HASH, 1, -1, -1, -1, 1e30f});
     ns_matrix* m = nullptr;
     TRY(ns_matrix_create(c, &m));
     cudaEvent_t e0, e1;
@@ -781,7 +809,7 @@ ns_status ns_path_tune(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, 
         // the next two are timed
         for (int rep = 0; rep < 3 && st == NS_OK; ++rep) {
             cudaEventRecord(e0, s);
-            st = k.path == NS_PATH_SORT ? build_sort(c, d_src, d_dst, n, m, s, k.split, k.tile)
+            st = k.path == NS_PATH_SORT ? build_sort(c, d_src, d_dst, n, m, s, k.split, k.tile, k.digits)
                                         : build_hash(c, d_src, d_dst, n, m, s, k.cache);
             cudaEventRecord(e1, s);
             if (st != NS_OK) break;
@@ -802,30 +830,33 @@ ns_status ns_path_tune(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, 
     TRY(st);
     const Cand* best = &cand[0];
     const Cand* best_sort = &cand[0];
-    float best_hash = 1e30f, split_ms = -1, plain_ms = -1;
+    float best_hash = 1e30f, split_ms = -1, plain_ms = -1, d8_ms = -1, wide_ms = -1;
     for (size_t i = 0; i < cand.size(); ++i) {
         const Cand& k = cand[i];
         if (k.ms < best->ms) best = &k;
         if (i < n_sort && k.ms < best_sort->ms) best_sort = &k;
         if (k.path == NS_PATH_HASH) best_hash = std::min(best_hash, k.ms);
         if (k.path == NS_PATH_SORT) {
-            float& r = k.split ? split_ms : plain_ms;  // the best tile of each
+            float& r = k.split ? split_ms : plain_ms;  // the best tile and plan of each
             if (r < 0 || k.ms < r) r = k.ms;
+            float& q = k.digits == kDigitsWide ? wide_ms : d8_ms;  // the best split and tile of each plan
+            if (q < 0 || k.ms < q) q = k.ms;
         }
     }
     const int lg = floor_log2(n);
     // the sort path's choices are kept for the size whichever path wins
-    c->path_choice[lg] = {best->path, best->cache != 0, best_sort->split, best_sort->tile};
+    c->path_choice[lg] = {best->path, best->cache != 0, best_sort->split, best_sort->tile, best_sort->digits};
     if (chosen) *chosen = best->path;
     if (sort_ms) *sort_ms = best_sort->ms;
     if (hash_ms) *hash_ms = best_hash;
     auto cache = tuner_load(c->tuner_cache);
-    char val[256];
+    char val[384];
     snprintf(val, sizeof val,
-             "{\"path\": \"%s\", \"cta_cache\": %d, \"sort_split\": %d, \"sort_tile\": %d, \"sort_ms\": %.4f, "
-             "\"hash_ms\": %.4f, \"sort_split_ms\": %.4f, \"sort_plain_ms\": %.4f}",
+             "{\"path\": \"%s\", \"cta_cache\": %d, \"sort_split\": %d, \"sort_tile\": %d, \"sort_digits\": %d, "
+             "\"sort_ms\": %.4f, \"hash_ms\": %.4f, \"sort_split_ms\": %.4f, \"sort_plain_ms\": %.4f, "
+             "\"sort_digits8_ms\": %.4f, \"sort_wide_ms\": %.4f}",
              best->path == NS_PATH_SORT ? "sort" : "hash", best->cache, best_sort->split, best_sort->tile,
-             best_sort->ms, best_hash, split_ms, plain_ms);
+             best_sort->digits, best_sort->ms, best_hash, split_ms, plain_ms, d8_ms, wide_ms);
     cache[path_key(c->device, lg)] = val;
     tuner_store(c->tuner_cache, cache);
     return NS_OK;
@@ -870,6 +901,16 @@ ns_status ns_column_split_info(ns_ctx* c, int* used, uint64_t* hot_destinations,
 ns_status ns_path_resolve(const ns_ctx* c, uint64_t n, int* path) {
     if (!c || !path) return fail(NS_ERR_INVALID, "ns_path_resolve: NULL argument");
     *path = resolve_path(c, n);
+    return NS_OK;
+}
+
+ns_status ns_sort_resolve(const ns_ctx* c, uint64_t n, int* split, int* tile, int* digits) {
+    if (!c) return fail(NS_ERR_INVALID, "ns_sort_resolve: NULL context");
+    int sp = 0, tl = 0, dg = 0;
+    resolve_sort(c, n, &sp, &tl, &dg);
+    if (split) *split = sp;
+    if (tile) *tile = NS_TILE_512X16 + tl;
+    if (digits) *digits = dg == kDigitsWide ? NS_DIGITS_WIDE : NS_DIGITS_8;
     return NS_OK;
 }
 

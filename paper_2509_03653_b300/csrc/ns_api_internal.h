@@ -71,9 +71,12 @@ ns_status to_hash(ns_matrix* m, u64 extra, cudaStream_t s);
 int resolve_path(const ns_ctx* c, u64 n);
 // The sort-path build of n packets into `out` (its sorted nonzero list and
 // statistics).  split: -1 = the context's rule, 0 = off, 1 = on; tile: -1 =
-// the context's rule, else the digit passes' tile shape.
+// the context's rule, else the digit passes' tile shape; digits: -1 = the
+// context's rule, else the digit plan (kDigits8, kDigitsWide).
 ns_status build_sort(ns_ctx* c, const uint32_t* src, const uint32_t* dst, u64 n, ns_matrix* out, cudaStream_t s,
-                     int split = -1, int tile = -1);
+                     int split = -1, int tile = -1, int digits = -1);
+// The sort variant a build of n packets takes: split (0/1), tile shape, digit plan.
+void resolve_sort(const ns_ctx* c, u64 n, int* split, int* tile, int* digits);
 ns_status check_launch();
 HashView hash_view(const ns_matrix* m);
 void buf_free(Buf& b);
@@ -113,6 +116,7 @@ struct ns_ctx {
         bool cta_cache;
         int split;  // sort path: 1 split, 0 not, -1 the size rule
         int tile;   // sort path: digit-pass tile shape (0..kSortTileShapes-1), -1 the default
+        int digits; // sort path: digit plan (kDigits8, kDigitsWide), -1 the default
     };
     std::map<int, PathChoice> path_choice;
     ns::SortScratch sc{};

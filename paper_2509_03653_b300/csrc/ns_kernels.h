@@ -57,8 +57,9 @@ void tracer_destroy(Tracer* t);
 
 // Per-context scratch of the sort path.
 struct SortScratch {
-    u64* ghist;          // [8][256] digit histograms
+    u64* ghist;          // [8][256] digit histograms (wide plan: 4096 bins)
     u64* offs;           // [8][256] bucket starts, then [256] slot cursors of an unstable first pass
+                         // (wide plan: 4096 bucket starts, then 1024 cursors)
     u64* status;         // look-back status words
     u64 status_words;
     u32* tile_counters;  // [16]
@@ -67,8 +68,11 @@ struct SortScratch {
     Tracer* tr;          // the context's tracer (may be off)
     int tile_shape;      // digit passes over 64-bit keys: 0 = 512 threads x 16 keys,
                          // 1 = 512 x 12, 2 = 256 x 16 (kSortTileShapes)
+    int digit_plan;      // 64-bit keys alone: kDigits8 (eight 8-bit passes) or kDigitsWide
+                         // (a 10-bit unstable pass, then six 9-bit stable passes)
 };
 constexpr int kSortTileShapes = 3;
+constexpr int kDigits8 = 0, kDigitsWide = 1, kDigitPlans = 2;
 
 // Look-back tags are 16 bits; when they wrap, the status words are cleared
 // on the stream so no stale word can carry a live tag.
@@ -111,7 +115,8 @@ void launch_diag_rand3(u64* a, u64* b, u64* c, u64 mask, u64 threads, u64 seed, 
 // a, b, c: tables of mask + 1 16-byte slots (2 (mask + 1) words); mode 0..2
 void launch_diag_claims(u64* a, u64* b, u64* c, u64 mask, u64 threads, u64 seed, int mode, u64* sink,
                         cudaStream_t s);
-int sort_radix();
+// look-back status words per tile of a digit pass under a digit plan
+int sort_radix(int digit_plan);
 
 // Batched windows: per-window tables carved from one arena (ns_batch.cu).
 struct BatchDev {

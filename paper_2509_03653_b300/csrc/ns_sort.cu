@@ -292,6 +292,59 @@ __device__ __forceinline__ void hist_flush(u32* hs, u64* __restrict__ ghist) {
     }
 }
 
+// Loads block [blk, blk + kHistThreads * kHistUnroll) of the keys, kHistUnroll
+// per thread; bit u of the result says whether k[u] is a key.  Each thread
+// loads all of its keys before any is counted, so that enough loads are in
+// flight to cover HBM latency; full blocks of 16-byte-aligned inputs are read
+// with 16-byte loads.
+template <typename K, int LOAD>
+__device__ __forceinline__ u32 hist_load_block(const SortIn& in, u64 blk, u64 n, bool vec, K (&k)[kHistUnroll]) {
+    const u64 per_block = (u64)kHistThreads * kHistUnroll;
+    const u32 t = threadIdx.x;
+    u32 valid = 0;
+    if (vec && n - blk >= per_block) {
+        valid = (1u << kHistUnroll) - 1;
+        if constexpr (LOAD == LOAD_PACK) {
+#pragma unroll
+            for (int h = 0; h < kHistUnroll / 4; ++h) {
+                const u64 i = blk + (u64)h * (4 * kHistThreads) + 4 * t;
+                const uint4 a = __ldg(reinterpret_cast<const uint4*>(in.src + i));
+                const uint4 b = __ldg(reinterpret_cast<const uint4*>(in.dst + i));
+                k[4 * h + 0] = (K)(((u64)a.x << 32) | b.x);
+                k[4 * h + 1] = (K)(((u64)a.y << 32) | b.y);
+                k[4 * h + 2] = (K)(((u64)a.z << 32) | b.z);
+                k[4 * h + 3] = (K)(((u64)a.w << 32) | b.w);
+            }
+        } else if constexpr (sizeof(K) == 8) {
+#pragma unroll
+            for (int h = 0; h < kHistUnroll / 2; ++h) {
+                const u64 i = blk + (u64)h * (2 * kHistThreads) + 2 * t;
+                const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(reinterpret_cast<const u64*>(in.keys) + i));
+                k[2 * h + 0] = (K)a.x;
+                k[2 * h + 1] = (K)a.y;
+            }
+        } else {
+#pragma unroll
+            for (int h = 0; h < kHistUnroll / 4; ++h) {
+                const u64 i = blk + (u64)h * (4 * kHistThreads) + 4 * t;
+                const uint4 a = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const u32*>(in.keys) + i));
+                k[4 * h + 0] = (K)a.x;
+                k[4 * h + 1] = (K)a.y;
+                k[4 * h + 2] = (K)a.z;
+                k[4 * h + 3] = (K)a.w;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < kHistUnroll; ++u) {
+            const u64 i = blk + (u64)u * kHistThreads + t;
+            k[u] = i < n ? load_key<K, LOAD>(in, i) : (K)0;
+            valid |= (i < n ? 1u : 0u) << u;
+        }
+    }
+    return valid;
+}
+
 template <typename K, int LOAD, int PASSES>
 __global__ void __launch_bounds__(kHistThreads, 1) k_sort_hist(SortIn in, u64 n_arg, int begin_bit,
                                                                 u64* __restrict__ ghist) {
@@ -302,57 +355,13 @@ __global__ void __launch_bounds__(kHistThreads, 1) k_sort_hist(SortIn in, u64 n_
     for (int i = threadIdx.x; i < kPairs * kRadix * 32; i += kHistThreads) hs[i] = 0;
     __syncthreads();
     u32* hl = hs + (threadIdx.x & 31);
-    // The CTA takes blocks of kHistThreads * kHistUnroll consecutive keys;
-    // each thread loads its kHistUnroll keys before counting any, so that
-    // enough loads are in flight to cover HBM latency.
+    // The CTA takes blocks of kHistThreads * kHistUnroll consecutive keys.
     const u64 per_block = (u64)kHistThreads * kHistUnroll;
-    // full blocks of 16-byte-aligned inputs are read with 16-byte loads
     const bool vec = in.bulk && LOAD != LOAD_DST_OF;
-    const u32 t = threadIdx.x;
     int rounds = 0;
     for (u64 blk = (u64)blockIdx.x * per_block; blk < n; blk += (u64)gridDim.x * per_block) {
         K k[kHistUnroll];
-        u32 valid = 0;  // bit u: k[u] is a key
-        if (vec && n - blk >= per_block) {
-            valid = (1u << kHistUnroll) - 1;
-            if constexpr (LOAD == LOAD_PACK) {
-#pragma unroll
-                for (int h = 0; h < kHistUnroll / 4; ++h) {
-                    const u64 i = blk + (u64)h * (4 * kHistThreads) + 4 * t;
-                    const uint4 a = __ldg(reinterpret_cast<const uint4*>(in.src + i));
-                    const uint4 b = __ldg(reinterpret_cast<const uint4*>(in.dst + i));
-                    k[4 * h + 0] = (K)(((u64)a.x << 32) | b.x);
-                    k[4 * h + 1] = (K)(((u64)a.y << 32) | b.y);
-                    k[4 * h + 2] = (K)(((u64)a.z << 32) | b.z);
-                    k[4 * h + 3] = (K)(((u64)a.w << 32) | b.w);
-                }
-            } else if constexpr (sizeof(K) == 8) {
-#pragma unroll
-                for (int h = 0; h < kHistUnroll / 2; ++h) {
-                    const u64 i = blk + (u64)h * (2 * kHistThreads) + 2 * t;
-                    const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(reinterpret_cast<const u64*>(in.keys) + i));
-                    k[2 * h + 0] = (K)a.x;
-                    k[2 * h + 1] = (K)a.y;
-                }
-            } else {
-#pragma unroll
-                for (int h = 0; h < kHistUnroll / 4; ++h) {
-                    const u64 i = blk + (u64)h * (4 * kHistThreads) + 4 * t;
-                    const uint4 a = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const u32*>(in.keys) + i));
-                    k[4 * h + 0] = (K)a.x;
-                    k[4 * h + 1] = (K)a.y;
-                    k[4 * h + 2] = (K)a.z;
-                    k[4 * h + 3] = (K)a.w;
-                }
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < kHistUnroll; ++u) {
-                const u64 i = blk + (u64)u * kHistThreads + t;
-                k[u] = i < n ? load_key<K, LOAD>(in, i) : (K)0;
-                valid |= (i < n ? 1u : 0u) << u;
-            }
-        }
+        const u32 valid = hist_load_block<K, LOAD>(in, blk, n, vec, k);
 #pragma unroll
         for (int u = 0; u < kHistUnroll; ++u) {
             if ((valid >> u) & 1u) {
@@ -372,6 +381,148 @@ __global__ void __launch_bounds__(kHistThreads, 1) k_sort_hist(SortIn in, u64 n_
     }
     __syncthreads();
     hist_flush<PASSES>(hs, ghist);
+}
+
+// ---- the wide digit plan for 64-bit keys ----------------------------------------
+//
+// Seven passes instead of eight: a 10-bit first pass (bits 0..9, unstable,
+// 1024 digits) and six stable 9-bit passes (bits 10..63, 512 digits each).
+// Its histograms and bucket starts are laid out [pass 0: 1024][pass 1: 512]
+// ... [pass 6: 512], 4096 entries, followed by pass 0's 1024 slot cursors.
+constexpr int kWidePasses = 7;
+constexpr int kWideBins = 1024 + 6 * 512;
+constexpr int kWideStableRadix = 512;  // look-back status words per tile
+__host__ __device__ constexpr int wide_bits(int p) { return p == 0 ? 10 : 9; }
+__host__ __device__ constexpr int wide_shift(int p) { return p == 0 ? 0 : 10 + 9 * (p - 1); }
+__host__ __device__ constexpr int wide_base(int p) { return p == 0 ? 0 : 1024 + 512 * (p - 1); }
+
+// The wide plan's 4096 bins do not fit lane-private 16-bit columns in one
+// CTA's shared memory (256 KB), so they are counted in two launches of 128
+// KB each, group 0 for passes 0..2 and group 1 for passes 3..6.  As in
+// k_sort_hist, word (slot, lane) holds two 16-bit counts and every lane counts
+// into its own column; the counts are flushed every kHistRounds rounds.
+//   group 0: low half of slot s = digit s of pass 0 (s < 1024); high half =
+//            digit s of pass 1 (s < 512), digit s - 512 of pass 2 (s >= 512)
+//   group 1: low half = digit s of pass 3 / digit s - 512 of pass 4; high
+//            half = digit s of pass 5 / digit s - 512 of pass 6
+constexpr int kWideSlots = 1024;
+static_assert(kWideSlots == kHistThreads, "the flush gives every thread one slot");
+
+__host__ __device__ constexpr int wide_low_pass(int g, u32 slot) { return g == 0 ? 0 : (slot < 512 ? 3 : 4); }
+__host__ __device__ constexpr int wide_high_pass(int g, u32 slot) {
+    return g == 0 ? (slot < 512 ? 1 : 2) : (slot < 512 ? 5 : 6);
+}
+
+template <int G>
+__device__ __forceinline__ void hist_flush_wide(u32* hs, u64* __restrict__ ghist) {
+    const u32 lane = threadIdx.x & 31;
+    const u32 c = threadIdx.x;  // the slot
+    u32* row = hs + c * 32;
+    u64 lo = 0, hi = 0;
+#pragma unroll 8
+    for (int l = 0; l < 32; ++l) {
+        const int j = (l + lane) & 31;  // lanes start in different banks
+        const u32 x = row[j];
+        lo += x & 0xFFFFu;
+        hi += x >> 16;
+        row[j] = 0;
+    }
+    unsigned long long* g = reinterpret_cast<unsigned long long*>(ghist);
+    const u32 lp = wide_low_pass(G, c), hp = wide_high_pass(G, c);
+    const u32 ld = G == 0 ? c : (c & 511u), hd = c & 511u;
+    if (lo) atomicAdd(&g[wide_base(lp) + ld], (unsigned long long)lo);
+    if (hi) atomicAdd(&g[wide_base(hp) + hd], (unsigned long long)hi);
+}
+
+template <typename K, int LOAD, int G>
+__global__ void __launch_bounds__(kHistThreads, 1) k_sort_hist_wide(SortIn in, u64 n_arg, u64* __restrict__ ghist) {
+    static_assert(sizeof(K) == 8, "the wide plan sorts 64-bit keys");
+    extern __shared__ __align__(16) u32 hs[];  // [kWideSlots][32 lanes]
+    const u64 n = in.n_dev ? *in.n_dev : n_arg;
+    for (int i = threadIdx.x; i < kWideSlots * 32; i += kHistThreads) hs[i] = 0;
+    __syncthreads();
+    u32* hl = hs + (threadIdx.x & 31);
+    const u64 per_block = (u64)kHistThreads * kHistUnroll;
+    const bool vec = in.bulk;
+    int rounds = 0;
+    for (u64 blk = (u64)blockIdx.x * per_block; blk < n; blk += (u64)gridDim.x * per_block) {
+        K k[kHistUnroll];
+        const u32 valid = hist_load_block<K, LOAD>(in, blk, n, vec, k);
+#pragma unroll
+        for (int u = 0; u < kHistUnroll; ++u) {
+            if ((valid >> u) & 1u) {
+                const u64 kb = (u64)k[u];
+                if constexpr (G == 0) {
+                    atomicAdd(&hl[((u32)kb & 1023u) * 32], 1u);
+                    atomicAdd(&hl[((u32)(kb >> wide_shift(1)) & 511u) * 32], 0x10000u);
+                    atomicAdd(&hl[(512u + ((u32)(kb >> wide_shift(2)) & 511u)) * 32], 0x10000u);
+                } else {
+                    atomicAdd(&hl[((u32)(kb >> wide_shift(3)) & 511u) * 32], 1u);
+                    atomicAdd(&hl[(512u + ((u32)(kb >> wide_shift(4)) & 511u)) * 32], 1u);
+                    atomicAdd(&hl[((u32)(kb >> wide_shift(5)) & 511u) * 32], 0x10000u);
+                    atomicAdd(&hl[(512u + ((u32)(kb >> wide_shift(6)) & 511u)) * 32], 0x10000u);
+                }
+            }
+        }
+        if (++rounds == kHistRounds) {  // the same count in every thread of the CTA
+            rounds = 0;
+            __syncthreads();
+            hist_flush_wide<G>(hs, ghist);
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    hist_flush_wide<G>(hs, ghist);
+}
+
+template <typename K, int LOAD, int G>
+void launch_hist_wide_group(const SortIn& in, u64 n, u64* ghist, Tracer* tr, cudaStream_t s) {
+    const size_t hsmem = sizeof(u32) * kWideSlots * 32;
+    const int max_grid = resident_ctas((const void*)k_sort_hist_wide<K, LOAD, G>, kHistThreads, hsmem);
+    const u64 blocks = (n + (u64)kHistThreads * kHistUnroll - 1) / ((u64)kHistThreads * kHistUnroll);
+    const int grid = (int)std::max<u64>(1, std::min<u64>(blocks, (u64)max_grid));
+    TraceScope ts(tr, "k_sort_hist", s);
+    k_sort_hist_wide<K, LOAD, G><<<grid, kHistThreads, hsmem, s>>>(in, n, ghist);
+}
+
+template <typename K, int LOAD>
+void launch_hist_wide(const SortIn& in, u64 n, u64* ghist, Tracer* tr, cudaStream_t s) {
+    launch_hist_wide_group<K, LOAD, 0>(in, n, ghist, tr, s);
+    launch_hist_wide_group<K, LOAD, 1>(in, n, ghist, tr, s);
+}
+
+// bucket starts of the wide plan: offs[wide_base(p) + d] = sum of pass p's
+// ghist below d, then pass 0's slot cursors at offs[kWideBins + d]
+__global__ void __launch_bounds__(1024) k_sort_offsets_wide(const u64* __restrict__ ghist, u64* __restrict__ offs) {
+    __shared__ u64 wsum[32];
+    const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int p = 0; p < kWidePasses; ++p) {
+        const int r = 1 << wide_bits(p);
+        const u64 v = (int)threadIdx.x < r ? ghist[wide_base(p) + threadIdx.x] : 0ull;
+        u64 x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u64 y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= (u32)o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            u64 run = 0;
+            for (int i = 0; i < 32; ++i) {
+                const u64 t = wsum[i];
+                wsum[i] = run;
+                run += t;
+            }
+        }
+        __syncthreads();
+        const u64 e = wsum[w] + x - v;
+        if ((int)threadIdx.x < r) {
+            offs[wide_base(p) + threadIdx.x] = e;
+            if (p == 0) offs[kWideBins + threadIdx.x] = e;
+        }
+        __syncthreads();
+    }
 }
 
 template <typename K, int LOAD, int PASSES>
@@ -415,14 +566,16 @@ __global__ void __launch_bounds__(kThreads) k_sort_offsets(const u64* __restrict
 
 typedef unsigned short WCount;  // a per-warp digit count (<= 512)
 
-template <typename K, bool HAS_V, int NT, int IT>
+// RB: digit width in bits (8, 9 or 10); only the arrays a pass uses are sized
+// for its radix (stable passes: per-warp counts; unstable: tile counts)
+template <typename K, bool HAS_V, int NT, int IT, int RB = 8, bool UNSTABLE = false>
 struct ScatterSmem {
-    static constexpr int NW = NT / 32, TILE = NT * IT;
+    static constexpr int NW = NT / 32, TILE = NT * IT, R = 1 << RB;
     K keys[TILE];  // staged tile, then the tile in digit order
     u64 vals[HAS_V ? TILE : 1];
-    WCount whist[NW][kRadix];  // per-warp digit counts (<= 512)
-    u32 tcount[kRadix];  // unstable ranking: the tile's digit counts, then their exclusive scan
-    u64 gdelta[kRadix];  // global position of a digit's first key minus its tile-local start
+    WCount whist[UNSTABLE ? 1 : NW][UNSTABLE ? 1 : R];  // per-warp digit counts (<= 512)
+    u32 tcount[UNSTABLE ? R : 1];  // unstable ranking: the tile's digit counts, then their exclusive scan
+    u64 gdelta[R];  // global position of a digit's first key minus its tile-local start
     u32 wsum[NW];
     u32 total;
     u32 tile;
@@ -434,8 +587,8 @@ struct ScatterSmem {
 // 0 issues bulk copies of the 16-byte-aligned prefix and the threads load the
 // ragged tail (< 4 elements); otherwise all threads load.  Packed mode stages
 // the two uint32 columns side by side in the key buffer's bytes.
-template <typename K, bool HAS_V, int LOAD, int NT, int IT>
-__device__ __forceinline__ bool stage_tile(const SortIn& in, ScatterSmem<K, HAS_V, NT, IT>& sm, u64 base, u32 tile_n,
+template <typename K, bool HAS_V, int LOAD, int NT, int IT, typename SM>
+__device__ __forceinline__ bool stage_tile(const SortIn& in, SM& sm, u64 base, u32 tile_n,
                                            bool bulk, u32 parity, DevStats* st) {
     constexpr int kTile = NT * IT;
     u32* s32 = reinterpret_cast<u32*>(sm.keys);
@@ -501,15 +654,20 @@ __device__ __forceinline__ u32 block_excl_scan_nt(u32 v, u32* wsum, u32* total) 
     return wsum[w] + x - v;
 }
 
-template <typename K, bool HAS_V, int LOAD, int NT, int IT, int RANK>
+template <typename K, bool HAS_V, int LOAD, int NT, int IT, int RANK, int RB>
 __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >= 384) ? 2 : (HAS_V ? 3 : 4))
     k_onesweep(SortIn in, K* __restrict__ kout, u64* __restrict__ vout, u64 n_arg, int shift,
                const u64* __restrict__ offs, u64* __restrict__ status, u32* tile_counter, u32 tag, DevStats* st,
                u32 pf_tiles, u64* __restrict__ cursor) {
     constexpr int kWarps = NT / 32, kTile = NT * IT, kItems = IT;
     constexpr bool UNSTABLE = RANK == RANK_UNSTABLE;
+    // digits of this pass; thread t handles digits [t*DPT, (t+1)*DPT)
+    constexpr int R = 1 << RB, DPT = R > NT ? R / NT : 1;
+    constexpr u32 kMask = (u32)R - 1;
+    static_assert(R <= NT || R % NT == 0, "digits per thread must be whole");
+    using Smem = ScatterSmem<K, HAS_V, NT, IT, RB, UNSTABLE>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ScatterSmem<K, HAS_V, NT, IT>& sm = *reinterpret_cast<ScatterSmem<K, HAS_V, NT, IT>*>(smem_raw);
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const u32 FULL = 0xFFFFFFFFu;
     const u64 n = in.n_dev ? *in.n_dev : n_arg;
@@ -528,9 +686,9 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
     for (;;) {
         if (threadIdx.x == 0) sm.tile = atomicAdd(tile_counter, 1u);
         if constexpr (UNSTABLE) {
-            for (int i = threadIdx.x; i < kRadix; i += NT) sm.tcount[i] = 0;
+            for (int i = threadIdx.x; i < R; i += NT) sm.tcount[i] = 0;
         } else {
-            for (int i = threadIdx.x; i < kWarps * kRadix; i += NT) (&sm.whist[0][0])[i] = 0;
+            for (int i = threadIdx.x; i < kWarps * R; i += NT) (&sm.whist[0][0])[i] = 0;
         }
         __syncthreads();
         const u64 tile = sm.tile;
@@ -595,7 +753,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
 #pragma unroll
             for (int j = 0; j < kItems; ++j) {
                 const u32 li = w0 + j * 32 + lane;
-                if (li < tile_n) rank[j] = atomicAdd(&sm.tcount[(u32)(k[j] >> shift) & 0xFF], 1u);
+                if (li < tile_n) rank[j] = atomicAdd(&sm.tcount[(u32)(k[j] >> shift) & kMask], 1u);
             }
         } else {
         // stable rank within the warp, item by item
@@ -603,14 +761,14 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
         for (int j = 0; j < kItems; ++j) {
             const u32 li = w0 + j * 32 + lane;
             const bool valid = li < tile_n;
-            const u32 d = valid ? ((u32)(k[j] >> shift) & 0xFF) : 0x100u;
+            const u32 d = valid ? ((u32)(k[j] >> shift) & kMask) : (u32)R;
             u32 peers;
             if constexpr (RANK == RANK_BALLOT) {
                 // the lanes agreeing with this one on every bit of d
                 peers = __ballot_sync(FULL, valid);
                 if (!valid) peers = ~peers;
 #pragma unroll
-                for (int b = 0; b < 8; ++b) {
+                for (int b = 0; b < RB; ++b) {
                     const bool bit = (d >> b) & 1u;
                     const u32 bal = __ballot_sync(FULL, bit);
                     peers &= bit ? bal : ~bal;
@@ -630,46 +788,57 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
         }
         __syncthreads();
 
-        // per digit (thread = digit): exclusive over warps, tile count
-        const u32 d = threadIdx.x;
-        u32 run = 0;
-        if (d < (u32)kRadix) {
-            if constexpr (UNSTABLE) {
-                run = sm.tcount[d];
-            } else {
+        // per digit: exclusive over warps, tile count
+        const u32 d0 = threadIdx.x * DPT;
+        u32 run[DPT];
+        u32 trun = 0;  // this thread's digits together
 #pragma unroll
-                for (int ww = 0; ww < kWarps; ++ww) {
-                    const u32 c = sm.whist[ww][d];
-                    sm.whist[ww][d] = (WCount)run;
-                    run += c;
+        for (int q = 0; q < DPT; ++q) {
+            const u32 d = d0 + q;
+            run[q] = 0;
+            if (d < (u32)R) {
+                if constexpr (UNSTABLE) {
+                    run[q] = sm.tcount[d];
+                } else {
+#pragma unroll
+                    for (int ww = 0; ww < kWarps; ++ww) {
+                        const u32 c = sm.whist[ww][d];
+                        sm.whist[ww][d] = (WCount)run[q];
+                        run[q] += c;
+                    }
+                    // publish this tile's count early so successors can proceed
+                    st_volatile(&status[tile * R + d], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, run[q]));
                 }
             }
-            // publish this tile's count early so successors can proceed
-            if constexpr (!UNSTABLE)
-                st_volatile(&status[tile * kRadix + d], pack_status(tag, tile == 0 ? kFlagPrefix : kFlagAgg, run));
+            trun += run[q];
         }
-        const u32 ls = block_excl_scan_nt<NT>(run, sm.wsum, &sm.total);
-        if (d < (u32)kRadix) {
-            if constexpr (UNSTABLE) {
-                sm.tcount[d] = ls;  // the digit's first slot in the tile's digit order
-                // Tiles may take their places in any order: the digit's
-                // global slots come from one atomic on its cursor (which
-                // starts at the digit's bucket start) instead of a look-back.
-                const u64 g = run ? atomicAdd(reinterpret_cast<unsigned long long*>(&cursor[d]),
-                                              (unsigned long long)run)
-                                  : 0ull;
-                sm.gdelta[d] = g - ls;  // modulo 2^64; + i below lands in range
-            } else {
-                // each warp's first slot for digit d in the tile's digit order
+        u32 ls = block_excl_scan_nt<NT>(trun, sm.wsum, &sm.total);
 #pragma unroll
-                for (int ww = 0; ww < kWarps; ++ww) sm.whist[ww][d] = (WCount)(sm.whist[ww][d] + ls);
-                u64 prefix = 0;
-                if (tile > 0) {
-                    prefix = lookback<kLookDigits>(status + d, kRadix, tile, tag, st);
-                    st_volatile(&status[tile * kRadix + d], pack_status(tag, kFlagPrefix, prefix + run));
+        for (int q = 0; q < DPT; ++q) {
+            const u32 d = d0 + q;
+            if (d < (u32)R) {
+                if constexpr (UNSTABLE) {
+                    sm.tcount[d] = ls;  // the digit's first slot in the tile's digit order
+                    // Tiles may take their places in any order: the digit's
+                    // global slots come from one atomic on its cursor (which
+                    // starts at the digit's bucket start) instead of a look-back.
+                    const u64 g = run[q] ? atomicAdd(reinterpret_cast<unsigned long long*>(&cursor[d]),
+                                                     (unsigned long long)run[q])
+                                         : 0ull;
+                    sm.gdelta[d] = g - ls;  // modulo 2^64; + i below lands in range
+                } else {
+                    // each warp's first slot for digit d in the tile's digit order
+#pragma unroll
+                    for (int ww = 0; ww < kWarps; ++ww) sm.whist[ww][d] = (WCount)(sm.whist[ww][d] + ls);
+                    u64 prefix = 0;
+                    if (tile > 0) {
+                        prefix = lookback<kLookDigits>(status + d, R, tile, tag, st);
+                        st_volatile(&status[tile * R + d], pack_status(tag, kFlagPrefix, prefix + run[q]));
+                    }
+                    sm.gdelta[d] = offs[d] + prefix - ls;  // modulo 2^64; + i below lands in range
                 }
-                sm.gdelta[d] = offs[d] + prefix - ls;  // modulo 2^64; + i below lands in range
             }
+            ls += run[q];
         }
         __syncthreads();
 
@@ -678,8 +847,10 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
         for (int j = 0; j < kItems; ++j) {
             const u32 li = w0 + j * 32 + lane;
             if (li < tile_n) {
-                const u32 dj = (u32)(k[j] >> shift) & 0xFF;
-                const u32 pos = (UNSTABLE ? sm.tcount[dj] : (u32)sm.whist[w][dj]) + rank[j];
+                const u32 dj = (u32)(k[j] >> shift) & kMask;
+                u32 pos;
+                if constexpr (UNSTABLE) pos = sm.tcount[dj] + rank[j];
+                else pos = (u32)sm.whist[w][dj] + rank[j];
                 if (pos < (u32)kTile) {
                     sm.keys[pos] = k[j];
                     if constexpr (HAS_V) sm.vals[pos] = v[j];
@@ -692,7 +863,7 @@ __global__ void __launch_bounds__(NT, (NT >= 1024) ? 1 : (NT >= 512) ? 2 : (NT >
         // global positions
         for (u32 i = threadIdx.x; i < tile_n; i += NT) {
             const K key = sm.keys[i];
-            const u32 dk = (u32)(key >> shift) & 0xFF;
+            const u32 dk = (u32)(key >> shift) & kMask;
             const u64 dst = sm.gdelta[dk] + i;
             if (dst < n) {  // always true unless a look-back gave up
                 kout[dst] = key;
@@ -1013,17 +1184,17 @@ constexpr const char* onesweep_name() {
     else return "k_onesweep<u64 key>";
 }
 
-template <typename K, bool HAS_V, int LOAD, int NT, int IT, int RANK>
+template <typename K, bool HAS_V, int LOAD, int NT, int IT, int RANK, int RB>
 void launch_onesweep_nt(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
                         u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s, u64* cursor) {
-    const size_t smem = sizeof(ScatterSmem<K, HAS_V, NT, IT>);
-    const u32 resident = (u32)resident_ctas((const void*)k_onesweep<K, HAS_V, LOAD, NT, IT, RANK>, NT, smem);
+    const size_t smem = sizeof(ScatterSmem<K, HAS_V, NT, IT, RB, RANK == RANK_UNSTABLE>);
+    const u32 resident = (u32)resident_ctas((const void*)k_onesweep<K, HAS_V, LOAD, NT, IT, RANK, RB>, NT, smem);
     constexpr u64 tile = (u64)NT * IT;
     const u64 tiles = (n + tile - 1) / tile;
     if (tiles == 0) return;
     const unsigned grid = (unsigned)std::min<u64>(tiles, resident);
     TraceScope ts(tr, in.trace_name ? in.trace_name : onesweep_name<K, HAS_V>(), s);
-    k_onesweep<K, HAS_V, LOAD, NT, IT, RANK><<<grid, NT, smem, s>>>(
+    k_onesweep<K, HAS_V, LOAD, NT, IT, RANK, RB><<<grid, NT, smem, s>>>(
         in, kout, vout, n, shift, offs, status, tile_counter, tag, st, (u32)NS_ONESWEEP_PF * resident, cursor);
 }
 
@@ -1032,23 +1203,38 @@ void launch_onesweep_nt(const SortIn& in, K* kout, u64* vout, u64 n, int shift, 
 // shared memory would not fit twice).  `rank` picks the ranking (RANK_*;
 // RANK_UNSTABLE for keys only).
 // `cursor` (RANK_UNSTABLE only): per digit, the next free global slot.
+// `bits`: the pass's digit width.  8 for every sort; 64-bit keys without
+// values also take the wide plan's 10-bit first pass (unstable) and 9-bit
+// stable passes (warp match).
 template <typename K, bool HAS_V, int LOAD, int NT, int IT>
 void launch_onesweep_rank(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
                           u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s, int rank,
-                          u64* cursor) {
+                          u64* cursor, int bits) {
+    if constexpr (!HAS_V && sizeof(K) == 8) {
+        if (bits == 10) {
+            launch_onesweep_nt<K, HAS_V, LOAD, NT, IT, RANK_UNSTABLE, 10>(in, kout, vout, n, shift, offs, status,
+                                                                           tile_counter, tag, st, tr, s, cursor);
+            return;
+        }
+        if (bits == 9) {
+            launch_onesweep_nt<K, HAS_V, LOAD, NT, IT, RANK_MATCH, 9>(in, kout, vout, n, shift, offs, status,
+                                                                       tile_counter, tag, st, tr, s, nullptr);
+            return;
+        }
+    }
     if constexpr (!HAS_V) {
         if (rank == RANK_UNSTABLE) {
-            launch_onesweep_nt<K, HAS_V, LOAD, NT, IT, RANK_UNSTABLE>(in, kout, vout, n, shift, offs, status,
-                                                                       tile_counter, tag, st, tr, s, cursor);
+            launch_onesweep_nt<K, HAS_V, LOAD, NT, IT, RANK_UNSTABLE, 8>(in, kout, vout, n, shift, offs, status,
+                                                                          tile_counter, tag, st, tr, s, cursor);
             return;
         }
     }
     if (rank == RANK_BALLOT)
-        launch_onesweep_nt<K, HAS_V, LOAD, NT, IT, RANK_BALLOT>(in, kout, vout, n, shift, offs, status,
-                                                                 tile_counter, tag, st, tr, s, nullptr);
+        launch_onesweep_nt<K, HAS_V, LOAD, NT, IT, RANK_BALLOT, 8>(in, kout, vout, n, shift, offs, status,
+                                                                    tile_counter, tag, st, tr, s, nullptr);
     else
-        launch_onesweep_nt<K, HAS_V, LOAD, NT, IT, RANK_MATCH>(in, kout, vout, n, shift, offs, status, tile_counter,
-                                                                tag, st, tr, s, nullptr);
+        launch_onesweep_nt<K, HAS_V, LOAD, NT, IT, RANK_MATCH, 8>(in, kout, vout, n, shift, offs, status,
+                                                                   tile_counter, tag, st, tr, s, nullptr);
 }
 
 // `shape` (64-bit keys without values): the tile of a digit pass, 512
@@ -1057,23 +1243,23 @@ void launch_onesweep_rank(const SortIn& in, K* kout, u64* vout, u64 n, int shift
 template <typename K, bool HAS_V, int LOAD>
 void launch_onesweep(const SortIn& in, K* kout, u64* vout, u64 n, int shift, const u64* offs, u64* status,
                      u32* tile_counter, u32 tag, DevStats* st, Tracer* tr, cudaStream_t s, int rank,
-                     u64* cursor = nullptr, int shape = 0) {
+                     u64* cursor = nullptr, int shape = 0, int bits = 8) {
     if constexpr (!HAS_V && sizeof(K) == 8) {
         if (shape == 1)
             launch_onesweep_rank<K, HAS_V, LOAD, 512, 12>(in, kout, vout, n, shift, offs, status, tile_counter, tag,
-                                                          st, tr, s, rank, cursor);
+                                                          st, tr, s, rank, cursor, bits);
         else if (shape == 2)
             launch_onesweep_rank<K, HAS_V, LOAD, 256, 16>(in, kout, vout, n, shift, offs, status, tile_counter, tag,
-                                                          st, tr, s, rank, cursor);
+                                                          st, tr, s, rank, cursor, bits);
         else
             launch_onesweep_rank<K, HAS_V, LOAD, NS_ONESWEEP_NT, NS_ONESWEEP_ITEMS>(
-                in, kout, vout, n, shift, offs, status, tile_counter, tag, st, tr, s, rank, cursor);
+                in, kout, vout, n, shift, offs, status, tile_counter, tag, st, tr, s, rank, cursor, bits);
     } else if constexpr (!HAS_V)
         launch_onesweep_rank<K, HAS_V, LOAD, NS_ONESWEEP_NT, NS_ONESWEEP_ITEMS>(
-            in, kout, vout, n, shift, offs, status, tile_counter, tag, st, tr, s, rank, cursor);
+            in, kout, vout, n, shift, offs, status, tile_counter, tag, st, tr, s, rank, cursor, 8);
     else
         launch_onesweep_rank<K, HAS_V, LOAD, 256, kItems>(in, kout, vout, n, shift, offs, status, tile_counter, tag,
-                                                          st, tr, s, rank, cursor);
+                                                          st, tr, s, rank, cursor, 8);
 }
 
 template <int KEYMODE, bool HAS_V>
@@ -1120,30 +1306,63 @@ __global__ void k_diag_mbarrier(DevStats* st) {
 
 u64 sort_tiles(u64 n) { return (n + kTile - 1) / kTile; }
 int resident_ctas_of(const void* fn, int threads, size_t smem) { return resident_ctas(fn, threads, smem); }
-int sort_radix() { return kRadix; }
+int sort_radix(int digit_plan) { return digit_plan == kDigitsWide ? kWideStableRadix : kRadix; }
 
 // Sort n keys by bits [begin_bit, begin_bit + 8*passes).  Pass p reads
 // buffer (p == 0 ? the input : bufs[(p-1)&1]) and writes bufs[p&1].
-// Returns the index (0 or 1) of the buffer holding the result.
+// Returns the index (0 or 1) of the buffer holding the result.  With the
+// wide digit plan (sc.digit_plan), 64-bit keys alone sorted on all 64 bits
+// take seven passes (10 bits, then six of 9) instead of eight.
 template <typename K, bool HAS_V, int LOAD>
 int radix_sort_t(const SortIn& in, K* kbuf[2], u64* vbuf[2], u64 n, int begin_bit, int passes,
                  SortScratch& sc, DevStats* st, cudaStream_t s) {
-    cudaMemsetAsync(sc.ghist, 0, sizeof(u64) * 8 * kRadix, s);
+    // 64-bit keys alone, sorted on every bit, may take the wide digit plan
+    const bool wide = sc.digit_plan == kDigitsWide && !HAS_V && sizeof(K) == 8 && passes == 8 && begin_bit == 0;
+    cudaMemsetAsync(sc.ghist, 0, sizeof(u64) * (wide ? kWideBins : 8 * kRadix), s);
     cudaMemsetAsync(sc.tile_counters, 0, sizeof(u32) * 8, s);
-    if (passes == 8)
-        launch_hist<K, LOAD, 8>(in, n, begin_bit, sc.ghist, sc.tr, s);
-    else  // 4: 32-bit keys, or one half of 64-bit ones
-        launch_hist<K, LOAD, 4>(in, n, begin_bit, sc.ghist, sc.tr, s);
+    if constexpr (!HAS_V && sizeof(K) == 8) {
+        if (wide) launch_hist_wide<K, LOAD>(in, n, sc.ghist, sc.tr, s);
+    }
+    if (!wide) {
+        if (passes == 8)
+            launch_hist<K, LOAD, 8>(in, n, begin_bit, sc.ghist, sc.tr, s);
+        else  // 4: 32-bit keys, or one half of 64-bit ones
+            launch_hist<K, LOAD, 4>(in, n, begin_bit, sc.ghist, sc.tr, s);
+    }
     {
         TraceScope ts(sc.tr, "k_sort_offsets", s);
-        k_sort_offsets<<<1, kThreads, 0, s>>>(sc.ghist, passes, sc.offs);
+        if (wide) k_sort_offsets_wide<<<1, 1024, 0, s>>>(sc.ghist, sc.offs);
+        else k_sort_offsets<<<1, kThreads, 0, s>>>(sc.ghist, passes, sc.offs);
     }
+    if (wide) passes = kWidePasses;
     // a pass's tiles hold 4096 keys or more, so its status words are within
-    // the first sort_tiles(n) * kRadix
-    const u64 status_used = std::min<u64>(sort_tiles(std::max<u64>(n, 1)) * kRadix, sc.status_words);
+    // the first sort_tiles(n) * (its radix)
+    const u64 status_used =
+        std::min<u64>(sort_tiles(std::max<u64>(n, 1)) * (wide ? kWideStableRadix : kRadix), sc.status_words);
     for (int p = 0; p < passes; ++p) {
         const u32 tag = next_tag(sc, s);
         clear_status_in_capture(sc.status, status_used, s);
+        if (wide) {
+            SortIn mid{};
+            if (p > 0) {
+                mid.keys = kbuf[(p - 1) & 1];
+                mid.n_dev = in.n_dev;
+                mid.trace_name = in.trace_name;
+                mid.bulk = ((uintptr_t)kbuf[(p - 1) & 1] & 15) == 0;
+            }
+            if constexpr (!HAS_V && sizeof(K) == 8) {
+                if (p == 0)
+                    launch_onesweep<K, HAS_V, LOAD>(in, kbuf[0], vbuf[0], n, wide_shift(0), sc.offs, sc.status,
+                                                    sc.tile_counters + p, tag, st, sc.tr, s, RANK_UNSTABLE,
+                                                    sc.offs + kWideBins, sc.tile_shape, wide_bits(0));
+                else
+                    launch_onesweep<K, HAS_V, LOAD_KEYS>(mid, kbuf[p & 1], vbuf[p & 1], n, wide_shift(p),
+                                                         sc.offs + wide_base(p), sc.status, sc.tile_counters + p,
+                                                         tag, st, sc.tr, s, RANK_MATCH, nullptr, sc.tile_shape,
+                                                         wide_bits(p));
+            }
+            continue;
+        }
         const int shift = begin_bit + 8 * p;
         if (p == 0) {
             // The first pass of a keys-only sort need not be stable: its

@@ -69,8 +69,8 @@ def test_stream_512_windows_of_2p17():
 
 def test_oneshot_2p30_both_paths():
     """Workload 3: 2^30 packets, in the configuration bench.py times.  Both
-    paths against the oracle: the nine quantities and A's sorted nonzero
-    list, element by element."""
+    paths (the sort path with each digit plan) against the oracle: the nine
+    quantities and A's sorted nonzero list, element by element."""
     N = W.W3_N
     hs, hd, s, d = pinned_pair(N)
     W.large_build(N, src=s, dst=d)
@@ -78,13 +78,13 @@ def test_oneshot_2p30_both_paths():
     want = oracle.stats_parallel(wk, wc)
     assert want["valid_packets"] == N
     ds, dd = hs.cuda(), hd.cuda()
-    for path in ("sort", "hash"):
-        ctx = ns.Context(0, path=path)
+    for path, digits in (("sort", "8"), ("sort", "wide"), ("hash", "auto")):
+        ctx = ns.Context(0, path=path, sort_digits=digits)
         m = ns.Matrix(ctx)
         ns.window_build(ctx, ds, dd, m)
-        assert ns.network_stats(ctx, m) == want, path
+        assert ns.network_stats(ctx, m) == want, (path, digits)
         k, c = export_np(m)
-        assert k.size == wk.size, path
+        assert k.size == wk.size, (path, digits)
         np.testing.assert_array_equal(k, wk)
         np.testing.assert_array_equal(c, wc)
         del k, c

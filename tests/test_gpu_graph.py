@@ -48,11 +48,12 @@ def _replays(ctx, windows, n):
     m.free()
 
 
+@pytest.mark.parametrize("digits", ["8", "wide"])
 @pytest.mark.parametrize("split", ["on", "off"])
-def test_sort_build_graph_replays_new_windows(split):
+def test_sort_build_graph_replays_new_windows(split, digits):
     n = (1 << 21) + 13
     windows = [W.zipf_window(n, 1.2, 1 << 16, 5), W.zipf_window(n, 1.05, 1 << 18, 6),
                gen.uniform_pairs(n, 32, 7)]
-    ctx = ns.Context(0, path="sort", sort_split=split)
+    ctx = ns.Context(0, path="sort", sort_split=split, sort_digits=digits)
     _replays(ctx, windows, n)
     ctx.close()
