@@ -420,6 +420,11 @@ def c3_run(args, rank, world, local, clocks, N):
             "clocks": clocks.summary(t0, t1),
             "path_bytes_frac": path_bytes / (ms / 1e3) / 1e9 / peak,
             "alg_bytes_frac": alg_bytes / (ms / 1e3) / 1e9 / peak,
+            # the minimal passes of the plain sort path (no split, eight
+            # 8-bit digit passes) over this build's time: the bandwidth a
+            # build without the splits would need to match it
+            "plain_sort_bytes_frac": (sort_path_bytes(N, U, S, D, {}) / (ms / 1e3) / 1e9 / peak
+                                      if path == "sort" else None),
             "dominant_kernel": kname, "kernel_ms_avg": kavg, "kernel_launches": kl,
             "kernel_alg_bytes_per_launch": kbytes,
             "kernel_frac": (kbytes / (kavg / 1e3) / 1e9 / peak) if kl else None,
@@ -498,6 +503,7 @@ def run_headline(args, rank, world, local, oneshot_only=False):
             "alg_bytes_per_launch": b["kernel_alg_bytes_per_launch"], "launch_ms_avg": b["kernel_ms_avg"],
             "launches_per_build": b["kernel_launches"], "peak_source": r["peak_src"],
             "path_bytes_frac": b["path_bytes_frac"], "alg_bytes_frac": b["alg_bytes_frac"],
+            "plain_sort_bytes_frac": b.get("plain_sort_bytes_frac"),
         },
         "clocks": b["clocks"],
         "gpu_launches": b["launches_per_build"] * b["steps"],
