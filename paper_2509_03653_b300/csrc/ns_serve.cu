@@ -105,25 +105,72 @@ struct ns_server {
 
 namespace {
 
-ns_status slot_prepare(ns_server* S, Slot& sl, u64 n) {
-    if (!sl.stream) {
-        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.built, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMallocHost((void**)&sl.h_stats, 2 * sizeof(ns_stats)) != cudaSuccess) {
-            cudaGetLastError();
-            return set_fail(NS_ERR_CUDA, "server: slot set-up failed");
-        }
-        ns_status st = ns_matrix_create(S->ctx, &sl.At);
-        if (st != NS_OK) return st;
+// Input buffers grow to the next power of two of the window, so that a slot
+// regrows at most once per doubling and the pool's freed blocks fit other
+// slots' next growth.
+u64 slot_input_bytes(u64 n) {
+    u64 b = 1ull << 16;
+    while (b < n * sizeof(uint32_t)) b <<= 1;
+    return b;
+}
+
+// A slot's stream, events, pinned result buffer, window matrix and device
+// statistics.  ns_server_create sets up every slot, so that none of these
+// (cudaMallocHost in particular, which can wait for the device) runs while
+// windows are being served.
+ns_status slot_setup(ns_server* S, Slot& sl) {
+    if (sl.stream) return NS_OK;
+    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.built, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost((void**)&sl.h_stats, 2 * sizeof(ns_stats)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_fail(NS_ERR_CUDA, "server: slot set-up failed");
     }
+    ns_status st = ns_matrix_create(S->ctx, &sl.At);
+    if (st != NS_OK) return st;
+    AllocScope alloc(S->ctx->pool, sl.stream, true);
+    st = buf_reserve(sl.d_stats, 2 * sizeof(ns_stats));
+    if (st == NS_OK) st = buf_reserve(sl.d_src, slot_input_bytes(0));
+    if (st == NS_OK) st = buf_reserve(sl.d_dst, slot_input_bytes(0));
+    return st;
+}
+
+// Frees every slot's memory, streams and events.  Every window has
+// completed.  A slot's memory comes from the context's pool in stream order
+// on the slot's stream, so it is freed there while that stream still exists;
+// the stream is destroyed afterwards.
+void slots_release(ns_server* S) {
+    for (auto& sl : S->slots) {
+        if (sl.At) {
+            touch(sl.At, sl.stream);
+            ns_matrix_free(sl.At);
+            sl.At = nullptr;
+        }
+        buf_free_on(sl.d_src, sl.stream);
+        buf_free_on(sl.d_dst, sl.stream);
+        buf_free_on(sl.d_stats, sl.stream);
+        if (sl.stream) {
+            cudaStreamSynchronize(sl.stream);
+            cudaStreamDestroy(sl.stream);
+            cudaEventDestroy(sl.built);
+            cudaEventDestroy(sl.done);
+            sl.stream = nullptr;
+        }
+        if (sl.h_stats) cudaFreeHost(sl.h_stats);
+        sl.h_stats = nullptr;
+    }
+}
+
+ns_status slot_prepare(ns_server* S, Slot& sl, u64 n) {
+    ns_status st = slot_setup(S, sl);
+    if (st != NS_OK) return st;
     // The slot's buffers are (re)allocated on its own stream.  A slot is only
     // prepared while idle (its previous window has completed), so freeing the
     // old buffers there is safe, and it stalls no other slot.
     AllocScope alloc(S->ctx->pool, sl.stream, true);
-    ns_status st = buf_reserve(sl.d_stats, 2 * sizeof(ns_stats));
-    if (st == NS_OK) st = buf_reserve(sl.d_src, std::max<u64>(n, 1) * sizeof(uint32_t));
-    if (st == NS_OK) st = buf_reserve(sl.d_dst, std::max<u64>(n, 1) * sizeof(uint32_t));
+    if (sl.d_src.bytes < n * sizeof(uint32_t)) st = buf_reserve(sl.d_src, slot_input_bytes(n));
+    if (st == NS_OK && sl.d_dst.bytes < n * sizeof(uint32_t)) st = buf_reserve(sl.d_dst, slot_input_bytes(n));
     return st;
 }
 
@@ -278,6 +325,16 @@ ns_status ns_server_create(ns_ctx* c, ns_matrix* acc, ns_server** out) {
         delete S;
         return set_fail(NS_ERR_CUDA, "ns_server_create: stream creation failed");
     }
+    // every slot is set up now, not on its first window
+    for (auto& sl : S->slots) {
+        const ns_status st = slot_setup(S, sl);
+        if (st != NS_OK) {
+            slots_release(S);
+            cudaStreamDestroy(S->acc_stream);
+            delete S;
+            return st;
+        }
+    }
     S->sched = std::thread(scheduler_loop, S);
     S->completer = std::thread(completion_loop, S);
     *out = S;
@@ -342,25 +399,7 @@ void ns_server_destroy(ns_server* S) {
     cudaStreamSynchronize(S->acc_stream);
     for (auto& sl : S->slots)
         if (sl.stream) cudaStreamSynchronize(sl.stream);
-    // Every window has completed.  A slot's memory comes from the context's
-    // pool in stream order on the slot's stream, so it is freed there while
-    // that stream still exists; the stream is destroyed afterwards.
-    for (auto& sl : S->slots) {
-        if (sl.At) {
-            touch(sl.At, sl.stream);
-            ns_matrix_free(sl.At);
-            sl.At = nullptr;
-        }
-        buf_free_on(sl.d_src, sl.stream);
-        buf_free_on(sl.d_dst, sl.stream);
-        buf_free_on(sl.d_stats, sl.stream);
-        if (sl.stream) {
-            cudaStreamDestroy(sl.stream);
-            cudaEventDestroy(sl.built);
-            cudaEventDestroy(sl.done);
-        }
-        if (sl.h_stats) cudaFreeHost(sl.h_stats);
-    }
+    slots_release(S);
     cudaStreamDestroy(S->acc_stream);
     delete S;
 }
