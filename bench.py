@@ -161,6 +161,22 @@ def profile_traffic(profile, names):
             "units": float(got["units_per_launch"]) if "units_per_launch" in got else None}
 
 
+def profile_traffic_keyed(profile, names, key):
+    """DRAM bytes per unit for one launch configuration from a committed ncu
+    summary under profiles/ (its `traffic_per_packet[<key>]` line), if the
+    summary was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", profile)
+    if not os.path.exists(path):
+        return None
+    sha, val = None, None
+    for line in open(path):
+        if line.startswith("source_sha256:"):
+            sha = line.split(":", 1)[1].strip()
+        if line.startswith(f"traffic_per_packet[{key}]:"):
+            val = float(line.split(":", 1)[1])
+    return val if sha == sources_sha(names) else None
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons while running."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -745,6 +761,12 @@ def c4_record(args, local, clocks, steps=None):
     kbytes = 8 * total + 16 * sumU + 16 * (sumS + sumD)
     peak, peak_src = peak_hbm()
     frac = (kbytes / (ktot / kl / 1e3) / 1e9 / peak) if kl else None
+    # DRAM traffic per launch: the committed ncu summary's bytes per packet for
+    # the configuration the tuner picked, times the packets of one launch
+    tpp = profile_traffic_keyed("k_batch_insert.batched_1024_windows.md", ["ns_hash.cu", "ns_batch.cu", "ns_common.cuh"],
+                                f"{params['tile_packets']},{params['ctas_per_sm']},{params['max_load']:g},"
+                                f"{params['cta_cache']}")
+    traffic = tpp * total / kl if (tpp and kl) else None
     b, p_ = res["batched"], res["plain"]
     batch.free()
     At.free()
@@ -759,7 +781,7 @@ def c4_record(args, local, clocks, steps=None):
                   "launches_per_step": 3 * Wn},
         "results_agree": agree, "batch_params": params, "tune_s": round(tune_s, 1), "generator_s": round(gen_s, 1),
         "roofline": {"bound": "hbm", "kernel": "k_batch_insert", "alg_bytes_per_launch": kbytes / max(kl, 1),
-                     "achieved": frac * peak if frac else None, "peak": peak, "frac": frac, "traffic": None,
+                     "achieved": frac * peak if frac else None, "peak": peak, "frac": frac, "traffic": traffic,
                      "peak_source": peak_src},
         "kernels_ms": kernels_ms(tr),
         "aggregate": b["aggregate"],
