@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--paths", default="sort,hash", help="oneshot: aggregation paths to run (first = value)")
     ap.add_argument("--sort-split", default="auto", choices=["auto", "on", "off"],
                     help="headline/oneshot: the sort path's hot-key split")
+    ap.add_argument("--sort-digits", default="auto", choices=["auto", "8", "wide"],
+                    help="oneshot/headline: the sort path's digit plan (auto: the path tuner's choice)")
     ap.add_argument("--no-tune", action="store_true",
                     help="headline/oneshot: skip ns_path_tune before timing the sort path")
     ap.add_argument("--windows", type=int, default=WINDOWS, help="stream: windows (512 = the full workload)")
@@ -368,7 +370,8 @@ def c3_run(args, rank, world, local, clocks, N):
         if path == "sort" and not args.no_tune:
             import tempfile
             tuner_file = os.path.join(tempfile.mkdtemp(prefix="ns_tune_"), "tuner.json")
-        ctx = ns.Context(local, path=path, sort_split=args.sort_split, tuner_cache=tuner_file)
+        ctx = ns.Context(local, path=path, sort_split=args.sort_split, tuner_cache=tuner_file,
+                         sort_digits=args.sort_digits)
         if tuner_file:
             # the path tuner on this input: the timed builds below take its
             # split and tile choices for this size
@@ -458,7 +461,7 @@ def c3_run(args, rank, world, local, clocks, N):
     if not args.no_e2e:
         # the variant the timed builds took (the tuner's record for this size)
         ctx = ns.Context(local, path=first, sort_split=args.sort_split,
-                         tuner_cache=tuned_file if first == "sort" else None)
+                         tuner_cache=tuned_file if first == "sort" else None, sort_digits=args.sort_digits)
         M = ns.Matrix(ctx)
         ns.window_build_host(ctx, h_src, h_dst, M)  # sizes the staging buffers
         steps = max(1, min(args.steps, 5))
