@@ -440,7 +440,7 @@ def c3_run(args, rank, world, local, clocks, N):
             "path_bytes_frac": path_bytes / (ms / 1e3) / 1e9 / peak,
             "alg_bytes_frac": alg_bytes / (ms / 1e3) / 1e9 / peak,
             # the minimal passes of the plain sort path (no split, eight
-            # 8-bit digit passes) over this build's time: the bandwidth a
+            # 8-bit digit passes) over the measured build time: the bandwidth a
             # build without the splits would need to match it
             "plain_sort_bytes_frac": (sort_path_bytes(N, U, S, D, {}) / (ms / 1e3) / 1e9 / peak
                                       if path == "sort" else None),

@@ -1,6 +1,6 @@
 """The sharded multi-GPU form of the traffic-matrix path, simulated over CPU
-ranks (two gloo processes, no GPU; every box of this build has one GPU, so
-the library itself runs replicas only).
+ranks (two gloo processes, no GPU; the multi-GPU benchmark runs independent
+replicas, and this checks the sharded decomposition's arithmetic).
 
 Each rank takes a disjoint share of the packets and aggregates it locally;
 the oracle stands in for the rank's GPU.  Then:
