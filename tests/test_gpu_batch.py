@@ -235,10 +235,12 @@ def test_batch_aggregate_by_one_sort_build():
     b2.free()
 
 
-def test_batch_aggregate_by_sort_in_cuda_graph_with_new_packets():
+@pytest.mark.parametrize("digits", ["8", "wide"])
+def test_batch_aggregate_by_sort_in_cuda_graph_with_new_packets(digits):
     """The same, captured in a CUDA graph (aggregate cleared inside it) and
-    replayed on packets with new contents but the same window layout."""
-    ctx = ns.Context(0, path="sort", sort_split="on")
+    replayed on packets with new contents but the same window layout, with
+    either digit plan."""
+    ctx = ns.Context(0, path="sort", sort_split="on", sort_digits=digits)
     sizes = [70000, 0, 5000, 131072, 3]
     src, dst, off = make_batch(sizes, seed0=101)
     src2, dst2, _ = make_batch(sizes, seed0=202)
