@@ -88,6 +88,9 @@ __global__ void k_labels(const u64* __restrict__ order, u64 n, u32* __restrict__
 // spread over all 32 bits, so a range holds a few entries even with tens of
 // millions of distinct addresses, and the 32 MiB table stays in L2.
 constexpr int kBucketBits = 22;
+// the set tables up to which the gather goes through the set (2^25 slots:
+// the first table of any window of more than 2^23 packets)
+constexpr u64 kSetLabelMaxSlots = 1ull << 25;
 
 __global__ void k_buckets(const u64* __restrict__ u, u64 N, u64* __restrict__ bucket) {
     const u64 nb = 1ull << kBucketBits;
@@ -212,6 +215,46 @@ __global__ void k_set_compact(const u32* __restrict__ T, u64 cap, SetCounters* s
         if (lane == 0) base = atomicAdd((unsigned long long*)&sc->out, (unsigned long long)__popc(has));
         base = __shfl_sync(FULL, base, 0);
         if (v != 0u) out[base + __popc(has & ((1u << lane) - 1u))] = v - 1u;
+    }
+}
+
+// The gather through the address set itself, when its table is the first,
+// L2-sized one: TL[h] = label << 32 | (address + 1) for every occupied slot h
+// of the set (its label found once, by the search below), 0 elsewhere.  A
+// packet's address then finds its label by the same probe sequence that
+// inserted it: usually one line of TL, instead of the prefix table and a
+// binary search.
+__global__ void k_set_labels(const u32* __restrict__ T, u64 cap, const u64* __restrict__ w,
+                             const u64* __restrict__ bucket, u64 N, u64* __restrict__ TL) {
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 h = (u64)blockIdx.x * blockDim.x + threadIdx.x; h < cap; h += stride) {
+        const u32 v = T[h];
+        TL[h] = v ? ((u64)find_label(w, bucket, N, v - 1u) << 32) | v : 0ull;
+    }
+}
+
+__device__ __forceinline__ u32 set_label(const u64* __restrict__ TL, u64 mask, u32 x, const u64* __restrict__ w,
+                                         const u64* __restrict__ bucket, u64 N) {
+    if (x != 0xFFFFFFFFu) {  // (that address has no slot: it sets a flag word)
+        const u32 v = x + 1u;
+        u64 h = mix32(x) & mask;
+        for (u32 p = 0; p < kMaxProbes; ++p) {
+            const u64 t = TL[h];
+            if ((u32)t == v) return (u32)(t >> 32);
+            h = (h + 1) & mask;
+        }
+    }
+    return find_label(w, bucket, N, x);  // every address of the columns has a slot, so only 0xFFFFFFFF gets here
+}
+
+__global__ void k_relabel_set(const u32* src, const u32* dst, u64 n, const u64* __restrict__ TL, u64 mask,
+                              const u64* __restrict__ w, const u64* __restrict__ bucket, u64 N, u32* out_src,
+                              u32* out_dst) {
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const u32 a = src[k], b = dst[k];
+        out_src[k] = set_label(TL, mask, a, w, bucket, N);
+        out_dst[k] = set_label(TL, mask, b, w, bucket, N);
     }
 }
 
@@ -454,7 +497,19 @@ ns_status ns_anonymize(ns_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, 
         TraceScope t(&c->tracer, "k_attach_labels", s);
         k_attach_labels<<<grid_of(N, c->sms), 256, 0, s>>>(uniq, label, N);
     }
-    {
+    if (cap <= kSetLabelMaxSlots) {
+        // the set's own table, widened to carry the labels (256 MiB at most)
+        st = buf_reserve(x.b[4], cap * sizeof(u64));
+        if (st != NS_OK) return st;
+        u64* TL = (u64*)x.b[4].p;
+        {
+            TraceScope t(&c->tracer, "k_set_labels", s);
+            k_set_labels<<<grid_of(cap, c->sms), 256, 0, s>>>((const u32*)x.b[0].p, cap, uniq, bucket, N, TL);
+        }
+        TraceScope t(&c->tracer, "k_relabel", s);
+        k_relabel_set<<<grid_of(n, c->sms), 256, 0, s>>>(d_src, d_dst, n, TL, cap - 1, uniq, bucket, N, d_out_src,
+                                                         d_out_dst);
+    } else {
         TraceScope t(&c->tracer, "k_relabel", s);
         k_relabel<<<grid_of(n, c->sms), 256, 0, s>>>(d_src, d_dst, n, uniq, bucket, N, d_out_src, d_out_dst);
     }
