@@ -1,6 +1,7 @@
 // ns_sort.cu -- sort-path kernels.
 //
-//  * LSD radix sort, 8-bit digits, "onesweep" structure: one histogram pass
+//  * LSD radix sort, 8-bit digits (64-bit keys alone may take the wide plan
+//    below: one 10-bit and six 9-bit passes), "onesweep" structure: one histogram pass
 //    computes every digit's global bucket offsets up front, then each digit
 //    pass is a single kernel in which a CTA takes the next tile from an atomic
 //    counter, ranks its keys stably in shared memory, obtains its global
